@@ -1,0 +1,352 @@
+"""FP64 CPU oracle for the D2-clustering assignment step (arXiv 1302.0435).
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py may import this package.  It shares no code
+with paper_1302_0435_gb300/ and never imports it; inputs come from the
+seeded generators, which hold none of the method's arithmetic.
+
+Contents (each function cites the passage it follows):
+  mallows            Eq. (D2opt) with z fixed: exact transportation LP (C).
+  mallows_pairs      the same over a list of (object, centroid) pairs (C).
+  assign             Alg. 2 Step 2, nearest centroid, ties to smallest j (C).
+  update_locations   Eq. (WeightedUpdate) / Eq. (UpdateZ), numpy.
+  update_label, update_global_label, propagate_weights
+                     Eq. (UpdateLabel), Eq. (UpdateGlobalLabel) and the
+                     weight rule of the weighted D2-clustering section.
+  cluster_level      Alg. 3 levels with the segment-wise Alg. 2 loop.
+
+Bags are passed as any object with attributes ``loc`` ([T, d] array),
+``w`` ([T]) and ``off`` ([N+1] int64, bag b = rows off[b]:off[b+1]).
+Every function converts to float64 first.
+
+Parity pins for every function live in tests/test_oracle_pins.py and
+tests/test_oracle_update_level.py; no function here is "parity unpinned".
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+OK = 0
+EINVAL = -1
+ENOMEM = -2
+ENOTCONVERGED = -3
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.d2o_normalise.argtypes = [dp, ctypes.c_int64, dp]
+        lib.d2o_cost.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int64, ctypes.c_int32, dp]
+        lib.d2o_cost.restype = None
+        lib.d2o_transport.argtypes = [dp, dp, ctypes.c_int64, dp, ctypes.c_int64, dp, dp, dp, dp, ip]
+        lib.d2o_mallows.argtypes = [dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int64, ctypes.c_int32,
+                                    dp, dp, dp, dp, ip]
+        lib.d2o_mallows_pairs.argtypes = [dp, dp, ip, dp, dp, ip, ctypes.c_int32, ip, ip,
+                                          ctypes.c_int64, ctypes.c_int32, dp, i32p]
+        lib.d2o_assign.argtypes = [dp, dp, ip, ctypes.c_int64, dp, dp, ip, ctypes.c_int64,
+                                   ctypes.c_int32, ctypes.c_int32, i32p, dp, dp]
+        _LIB = lib
+    return _LIB
+
+
+def _p(a, ctype=ctypes.c_double):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(st, what):
+    if st != OK:
+        raise OracleError("%s failed with status %d" % (what, st))
+
+
+def normalise(w):
+    """Equal-mass rule of Eq. (D2opt): divide a bag's weights by their sum."""
+    w = _f64(w)
+    out = np.empty_like(w)
+    _check(_lib().d2o_normalise(_p(w), w.size, _p(out)), "normalise")
+    return out
+
+
+def cost(x, y):
+    """Ground cost of Eq. (D2opt): c[a, r] = ||x_a - y_r||^2 by explicit differences."""
+    x = _f64(x)
+    y = _f64(y)
+    if x.ndim == 1:
+        x = x[:, None]
+    if y.ndim == 1:
+        y = y[:, None]
+    m, d = x.shape
+    n = y.shape[0]
+    C = np.empty((m, n))
+    _lib().d2o_cost(_p(x), m, _p(y), n, d, _p(C))
+    return C
+
+
+def transport(C, p, q):
+    """Exact transportation LP of Eq. (D2opt) with z fixed, for given cost and
+    marginals (already normalised).  Returns (value, flow, u, v, pivots)."""
+    C = _f64(C)
+    p = _f64(p)
+    q = _f64(q)
+    m, n = C.shape
+    w = np.empty((m, n))
+    u = np.empty(m)
+    v = np.empty(n)
+    obj = np.empty(1)
+    piv = np.zeros(1, dtype=np.int64)
+    st = _lib().d2o_transport(_p(C), _p(p), m, _p(q), n, _p(w), _p(u), _p(v), _p(obj),
+                              _p(piv, ctypes.c_int64))
+    _check(st, "transport")
+    return float(obj[0]), w, u, v, int(piv[0])
+
+
+def mallows(x, wx, y, wy):
+    """Mallows distance D^2 between bags (x, wx) and (y, wy): Eq. (D2opt) with
+    z fixed.  Weights are normalised first.  Returns (D2, flow, u, v, pivots)."""
+    x = _f64(x)
+    y = _f64(y)
+    if x.ndim == 1:
+        x = x[:, None]
+    if y.ndim == 1:
+        y = y[:, None]
+    wx = _f64(wx)
+    wy = _f64(wy)
+    m, d = x.shape
+    n = y.shape[0]
+    if y.shape[1] != d:
+        raise ValueError("dimension mismatch")
+    w = np.empty((m, n))
+    u = np.empty(m)
+    v = np.empty(n)
+    d2 = np.empty(1)
+    piv = np.zeros(1, dtype=np.int64)
+    st = _lib().d2o_mallows(_p(x), _p(wx), m, _p(y), _p(wy), n, d, _p(d2), _p(w), _p(u), _p(v),
+                            _p(piv, ctypes.c_int64))
+    _check(st, "mallows")
+    return float(d2[0]), w, u, v, int(piv[0])
+
+
+def _bag_arrays(b):
+    loc = _f64(b.loc)
+    if loc.ndim == 1:
+        loc = loc[:, None]
+    return loc, _f64(b.w), _i64(b.off)
+
+
+def bag(b, i):
+    """Rows of bag i as (loc [m, d], w [m]) in float64."""
+    lo, hi = int(b.off[i]), int(b.off[i + 1])
+    loc = np.asarray(b.loc[lo:hi], dtype=np.float64)
+    if loc.ndim == 1:
+        loc = loc[:, None]
+    return loc, np.asarray(b.w[lo:hi], dtype=np.float64)
+
+
+def mallows_pairs(objs, cents, pair_obj, pair_cen, nthreads=1):
+    """D^2 of Eq. (D2opt) for each listed (object, centroid) pair."""
+    xl, xw, xo = _bag_arrays(objs)
+    yl, yw, yo = _bag_arrays(cents)
+    pi = _i64(pair_obj)
+    pj = _i64(pair_cen)
+    out = np.empty(pi.size)
+    st = np.zeros(pi.size, dtype=np.int32)
+    rc = _lib().d2o_mallows_pairs(_p(xl), _p(xw), _p(xo, ctypes.c_int64), _p(yl), _p(yw),
+                                  _p(yo, ctypes.c_int64), xl.shape[1], _p(pi, ctypes.c_int64),
+                                  _p(pj, ctypes.c_int64), pi.size, nthreads, _p(out),
+                                  _p(st, ctypes.c_int32))
+    _check(rc, "mallows_pairs")
+    return out
+
+
+def assign(objs, cents, nthreads=1, return_all=False):
+    """Alg. 2 Step 2: C(i) = argmin_j D(v_i, z_j), ties to the smallest j.
+    Returns (labels int32 [N], dist2 [N]) and, if asked, the [N, K] D^2 matrix."""
+    xl, xw, xo = _bag_arrays(objs)
+    yl, yw, yo = _bag_arrays(cents)
+    N = xo.size - 1
+    K = yo.size - 1
+    labels = np.empty(N, dtype=np.int32)
+    dist2 = np.empty(N)
+    allm = np.empty((N, K)) if return_all else None
+    rc = _lib().d2o_assign(_p(xl), _p(xw), _p(xo, ctypes.c_int64), N, _p(yl), _p(yw),
+                           _p(yo, ctypes.c_int64), K, xl.shape[1], nthreads,
+                           _p(labels, ctypes.c_int32), _p(dist2), _p(allm) if allm is not None else None)
+    _check(rc, "assign")
+    if return_all:
+        return labels, dist2, allm
+    return labels, dist2
+
+
+def assigned_flows(objs, cents, labels):
+    """Optimal flows of each assigned pair (i, C(i)) as COO arrays
+    (obj, alpha, r, w), from the oracle's own LP solutions (Eq. (D2opt))."""
+    co, ca, cr, cw = [], [], [], []
+    N = len(objs.off) - 1
+    for i in range(N):
+        x, wx = bag(objs, i)
+        y, wy = bag(cents, int(labels[i]))
+        _, w, _, _, _ = mallows(x, wx, y, wy)
+        a, r = np.nonzero(w)
+        co.append(np.full(a.size, i, dtype=np.int64))
+        ca.append(a.astype(np.int64))
+        cr.append(r.astype(np.int64))
+        cw.append(w[a, r])
+    if N == 0:
+        z = np.zeros(0, dtype=np.int64)
+        return z, z, z, np.zeros(0)
+    return np.concatenate(co), np.concatenate(ca), np.concatenate(cr), np.concatenate(cw)
+
+
+def update_locations(objs, omega, labels, flow_obj, flow_alpha, flow_r, flow_w, cents):
+    """Eq. (WeightedUpdate) (Eq. (UpdateZ) when omega = 1), centroid weights
+    held fixed (the constrained form of Alg. 2 Step 3*):
+
+        z_j^(r) = sum_{i: C(i)=j} omega_i sum_a w_ra^(i) v_i^(a)
+                  / sum_{i: C(i)=j} omega_i sum_a w_ra^(i)
+
+    with the flows given as COO entries (object i, support a, centroid
+    support r, flow w), summed in entry order.  Where the denominator is
+    zero (empty cluster, or a support that receives no mass) the previous
+    location is kept.  Returns the new [sum n_j, d] float64 locations."""
+    xl, _, xo = _bag_arrays(objs)
+    yl, _, yo = _bag_arrays(cents)
+    N = xo.size - 1
+    om = np.ones(N) if omega is None else _f64(omega)
+    lab = np.asarray(labels, dtype=np.int64)
+    fo = _i64(flow_obj)
+    fa = _i64(flow_alpha)
+    fr = _i64(flow_r)
+    fw = _f64(flow_w)
+    rows = yo[lab[fo]] + fr
+    src = xo[fo] + fa
+    coef = om[fo] * fw
+    num = np.zeros_like(yl)
+    den = np.zeros(yl.shape[0])
+    np.add.at(num, rows, coef[:, None] * xl[src])
+    np.add.at(den, rows, coef)
+    new = yl.copy()
+    ok = den > 0
+    new[ok] = num[ok] / den[ok][:, None]
+    return new
+
+
+def update_label(seg_labels, seg_sizes_centroids):
+    """Eq. (UpdateLabel): labels of segment mu are offset by the number of
+    centroids merged before it, |Z^(mu-1)|.  seg_labels is a list of label
+    arrays (one per segment, in segment order) and seg_sizes_centroids the
+    number of centroids each segment produced.  Returns the offset labels."""
+    out = []
+    offset = 0
+    for lab, k in zip(seg_labels, seg_sizes_centroids):
+        out.append(np.asarray(lab, dtype=np.int64) + offset)
+        offset += int(k)
+    return out
+
+
+def update_global_label(C, C_tilde):
+    """Eq. (UpdateGlobalLabel): C(i) = C~(C(i)) for every original object."""
+    return np.asarray(C_tilde, dtype=np.int64)[np.asarray(C, dtype=np.int64)]
+
+
+def propagate_weights(C_tilde, omega, k_prime):
+    """Weight of a parent point = sum of its children's weights (weighted
+    D2-clustering section; Alg. 3 Step 3): omega_i = sum_{a: C~(a)=i} omega'_a."""
+    out = np.zeros(int(k_prime))
+    np.add.at(out, np.asarray(C_tilde, dtype=np.int64), _f64(omega))
+    return out
+
+
+class _Bags:
+    def __init__(self, loc, w, off):
+        self.loc = loc
+        self.w = w
+        self.off = off
+
+
+def _slice_bags(b, lo, hi):
+    o = np.asarray(b.off, dtype=np.int64)
+    s, e = int(o[lo]), int(o[hi])
+    return _Bags(np.asarray(b.loc[s:e]), np.asarray(b.w[s:e]), o[lo:hi + 1] - s)
+
+
+def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, nthreads=1):
+    """Alg. 3 level loop with the segment-wise weighted D2-clustering of
+    Alg. 2 (constrained update, Step 3*) inside each segment.
+
+    Level loop: split the current data into contiguous segments of at most
+    seg_size (tau) objects; in each segment start from init_cents and run
+    `iters` rounds of (Alg. 2 Step 2 assign, Eq. (WeightedUpdate) update);
+    merge labels with Eq. (UpdateLabel) and Eq. (UpdateGlobalLabel); give
+    each centroid the summed weight of its members; if more than one segment
+    was used, the merged centroids become the next level's weighted data.
+    Stops after the level that fits in one segment.  After each update the
+    locations are rounded to loc_round (e.g. np.float32) when given, so that
+    every level's data keep the input location precision.
+
+    Returns (centroid locations [K*n, d] float64, centroid weights [K],
+    labels [N] int64)."""
+    K = int(K)
+    if seg_size <= K:
+        raise ValueError("segment size must exceed K for the hierarchy to shrink")
+    data = _Bags(np.asarray(objs.loc), np.asarray(objs.w), np.asarray(objs.off, dtype=np.int64))
+    N0 = len(data.off) - 1
+    om = np.ones(N0) if omega is None else _f64(omega)
+    C = np.arange(N0, dtype=np.int64)
+    while True:
+        n_l = len(data.off) - 1
+        M = 1 if n_l <= seg_size else int(math.ceil(n_l / seg_size))
+        seg_labels, seg_cents = [], []
+        for mu in range(M):
+            lo, hi = mu * seg_size, min((mu + 1) * seg_size, n_l)
+            seg = _slice_bags(data, lo, hi)
+            om_seg = om[lo:hi]
+            cents = _Bags(_f64(init_cents.loc).copy(), _f64(init_cents.w).copy(),
+                          _i64(init_cents.off).copy())
+            lab = None
+            for _ in range(int(iters)):
+                lab, _ = assign(seg, cents, nthreads=nthreads)
+                fo, fa, fr, fw = assigned_flows(seg, cents, lab)
+                newloc = update_locations(seg, om_seg, lab, fo, fa, fr, fw, cents)
+                if loc_round is not None:
+                    newloc = newloc.astype(loc_round).astype(np.float64)
+                cents = _Bags(newloc, cents.w, cents.off)
+            if lab is None:
+                lab, _ = assign(seg, cents, nthreads=nthreads)
+            seg_labels.append(lab)
+            seg_cents.append(cents)
+        C_tilde = np.concatenate(update_label(seg_labels, [K] * M))
+        C = update_global_label(C, C_tilde)
+        w_new = propagate_weights(C_tilde, om, M * K)
+        if M == 1:
+            c0 = seg_cents[0]
+            return _f64(c0.loc), w_new, C
+        locs = np.concatenate([c.loc for c in seg_cents])
+        ws = np.concatenate([c.w for c in seg_cents])
+        n_per = [np.diff(c.off) for c in seg_cents]
+        offs = np.concatenate([[0], np.cumsum(np.concatenate(n_per))]).astype(np.int64)
+        data = _Bags(locs, ws, offs)
+        om = w_new

@@ -1,0 +1,221 @@
+/*
+ * d2.h -- C-ABI of the GB300 (sm_103a) assignment step of parallel
+ * D2-clustering (Zhang, Wang & Li, "Parallel D2-Clustering: Large-Scale
+ * Clustering of Discrete Distributions", arXiv 1302.0435).
+ *
+ * Objects and centroids are discrete distributions ("bags of weighted
+ * vectors", Sec. 2, the notation above Eq. (D2opt)):
+ *     v = {(v^(a), p^(a)) : a = 1..t},   v^(a) in R^d,  p^(a) >= 0.
+ * The distance between a bag and a centroid is the Mallows distance: the
+ * optimum of the transportation LP of Eq. (D2opt) with the centroid fixed,
+ *     D^2(z, v) = min_w sum_{r,a} w_{r,a} ||z^(r) - v^(a)||^2
+ *     s.t. sum_a w_{r,a} = p_z^(r),  sum_r w_{r,a} = p_v^(a),  w >= 0.
+ * Every call returns D^2 (the squared distance); D itself is its root.
+ *
+ * Conventions common to every call
+ *  - Status: every call returns an int, D2_OK (0) or a negative D2_E* code;
+ *    d2_strerror() names it.  Nothing crosses this boundary as an exception
+ *    or abort.  A call that fails leaves its outputs unspecified.
+ *  - Weights: each bag's weights are divided by their sum in FP64 before use
+ *    (the total-mass-one constraint of Eq. (D2opt)).  A bag with a negative,
+ *    NaN or infinite weight, a zero total, or no support is rejected with
+ *    D2_EINVAL.  Zero-weight supports are allowed.
+ *  - Memory: the caller owns every buffer it passes.  Pointers may address
+ *    device memory (cudaMalloc, torch CUDA tensors) or host memory (pageable
+ *    or pinned); the library tells them apart with cudaPointerGetAttributes.
+ *    Host inputs are copied to device scratch owned by the context and host
+ *    outputs are copied back before the call returns.  The library never
+ *    frees caller memory.
+ *  - Streams: work is enqueued on the context's stream (d2_set_stream).  A
+ *    call whose outputs are all device pointers returns without waiting;
+ *    outputs are valid after d2_sync() or an event recorded on that stream.
+ *    A call with any host output synchronises before it returns.
+ *  - Threads: one context per host thread; a context is not re-entrant.
+ *  - Precision: see d2_config.precision.  D^2 outputs are FP64.
+ */
+#ifndef D2_H
+#define D2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define D2_OK 0
+#define D2_EINVAL (-1)          /* bad argument, offsets, sizes or weights */
+#define D2_ENOMEM (-2)          /* device or host allocation failed */
+#define D2_ENOTCONVERGED (-3)   /* a pair hit its pivot budget (see per-pair status) */
+#define D2_ETIMEOUT (-4)        /* a device wait gave up (serving loop) */
+#define D2_ECUDA (-5)           /* a CUDA runtime call failed */
+#define D2_EUNSUPPORTED (-6)    /* size or dtype outside what the kernels support */
+#define D2_ENOCENTROIDS (-7)    /* no resident centroid set */
+
+/* element types */
+#define D2_F64 0
+#define D2_F32 1
+#define D2_BF16 2
+
+/* precision modes (d2_config.precision) */
+#define D2_PREC_AUTO 0   /* FP64 for FP64 inputs, otherwise D2_PREC_FP32 */
+#define D2_PREC_FP64 1   /* costs, duals, pricing and objective in FP64 */
+#define D2_PREC_FP32 2   /* FP32 cost tile and FP32 pivots reach a basis; the
+                            same tree and exact integer flows then continue on
+                            an FP64 tile with FP64 potentials until no FP64
+                            reduced cost is negative, and the objective is
+                            summed in FP64.  d2_assign screens all centroids
+                            with the FP32 solve alone and certifies in FP64
+                            every centroid the FP32 error bound cannot rule
+                            out, so labels and dist2 are FP64-exact. */
+
+/* Limits of the current kernels. */
+#define D2_MAX_SUPPORT 64   /* supports per bag (objects and centroids) */
+#define D2_MAX_DIM 256      /* vector dimension d */
+
+/*
+ * A ragged batch of bags in CSR form.  Bag b owns supports
+ * [off[b], off[b+1]) of loc (row-major, dim values per support, element type
+ * loc_dtype) and w (element type w_dtype, D2_F64 or D2_F32).  off has
+ * count+1 entries, off[0] = 0, nondecreasing.  All three pointers must be in
+ * the same memory space (all device or all host).
+ */
+typedef struct {
+    const void* loc;
+    const void* w;
+    const int64_t* off;
+    int64_t count;
+    int32_t dim;
+    int32_t loc_dtype;
+    int32_t w_dtype;
+    int32_t reserved;
+} d2_bags;
+
+/* Context configuration; zero-initialise and set what you need. */
+typedef struct {
+    int32_t precision;          /* D2_PREC_* ; 0 = AUTO */
+    int32_t pivot_budget;       /* pivots per pair = pivot_budget*(m+n); 0 = 64 */
+    int32_t group_lanes;        /* lanes per pair: 0 = autotune, or 1/2/4/8/16/32 */
+    int32_t reserved[5];
+} d2_config;
+
+/*
+ * Optimal flows of solved pairs, one record of `stride` entries per pair:
+ * entry e of pair t is (cell[t*stride+e], w[t*stride+e]) with
+ * cell = (a << 16) | r (a: object support, r: centroid support) and w the
+ * flow (mass moved from v^(a) to z^(r), total 1 per pair).  A pair uses
+ * m+n-1 entries (its basis; some flows may be zero); unused entries have
+ * cell = -1 and w = 0.  stride must be >= 2*D2_MAX_SUPPORT-1 or >= the
+ * largest m+n-1 of the call.  Both arrays are caller-owned, device or host.
+ */
+typedef struct {
+    int32_t* cell;
+    double* w;
+    int64_t stride;
+} d2_flows;
+
+typedef struct d2_ctx d2_ctx;
+
+/* Create a context on CUDA device `device`.  cfg may be NULL (defaults).
+ * Creates its own non-blocking stream.  Returns D2_ECUDA if the device
+ * cannot be used (no GPU, or the library was not built for it). */
+int d2_ctx_create(d2_ctx** out, int32_t device, const d2_config* cfg);
+/* Destroy a context and free everything it owns (not caller buffers). */
+int d2_ctx_destroy(d2_ctx* ctx);
+/* Use the caller's cudaStream_t (NULL: back to the context's own stream). */
+int d2_set_stream(d2_ctx* ctx, void* cuda_stream);
+/* Wait for all work enqueued by this context. */
+int d2_sync(d2_ctx* ctx);
+/* Static description of a status code. */
+const char* d2_strerror(int32_t status);
+/* Version string of the library build. */
+const char* d2_version(void);
+
+/*
+ * Set the resident centroid set z_1..z_K (Alg. 2 Step 1 hands in the
+ * initial centroids; the paper draws them at random).  The bags are copied
+ * into context-owned device memory and stay resident across calls; their
+ * weights are normalised once.  loc_dtype decides the storage precision of
+ * the centroid locations: d2_update_locations rounds its FP64 result to it.
+ */
+int d2_set_centroids(d2_ctx* ctx, const d2_bags* cents);
+/* Read back the resident centroids: loc_out [sum n_j][dim] FP64, w_out
+ * [sum n_j] FP64 (normalised), off_out [K+1] int64; any may be NULL.
+ * Pointers may be host or device.  K and total supports via k_out/t_out. */
+int d2_get_centroids(d2_ctx* ctx, double* loc_out, double* w_out, int64_t* off_out,
+                     int64_t* k_out, int64_t* t_out);
+
+/*
+ * Ground-cost matrix of one pair (the objective coefficients of
+ * Eq. (D2opt)): C[a*n_j + r] = ||v_i^(a) - z_j^(r)||^2 for object i of
+ * `objs` and resident centroid j, as the kernels compute it in `precision`
+ * (D2_PREC_FP64: FP64 explicit differences; D2_PREC_FP32: the FP32 tile the
+ * FP32 solver prices with, widened to FP64).  C: m_i*n_j doubles.
+ */
+int d2_cost_matrix(d2_ctx* ctx, const d2_bags* objs, int64_t i, int64_t j, int32_t precision,
+                   double* C);
+
+/*
+ * Mallows distance D^2 (Eq. (D2opt) with z fixed) for npairs listed pairs
+ * (object pair_obj[t] of `objs`, resident centroid pair_cen[t]).
+ * dist2[t]: FP64 result.  flows (may be NULL): optimal basis flows per pair.
+ * status (may be NULL): per-pair D2_OK / D2_ENOTCONVERGED / D2_EINVAL.
+ * Returns D2_ENOTCONVERGED if any pair hit its pivot budget (its dist2 is
+ * then the cost of the last feasible plan, an upper bound).
+ */
+int d2_mallows_batch(d2_ctx* ctx, const d2_bags* objs, const int64_t* pair_obj,
+                     const int64_t* pair_cen, int64_t npairs, double* dist2, d2_flows* flows,
+                     int32_t* status);
+
+/*
+ * Alg. 2 Step 2: labels[i] = argmin_j D(v_i, z_j) over the resident
+ * centroids (ties: smallest j), dist2[i] = D^2(v_i, z_labels[i]) in FP64.
+ * omega (may be NULL = all ones): object weights omega_i of Eq. (WeightedD2).
+ * eps_total (may be NULL): sum_i omega_i dist2[i], the objective of
+ * Eq. (WeightedD2) at the current centroids (Alg. 1 Step 3 / Alg. 2 Step 4).
+ * flows (may be NULL): optimal flows of each assigned pair (i, labels[i]),
+ * which d2_update_locations can consume.
+ */
+int d2_assign(d2_ctx* ctx, const d2_bags* objs, const double* omega, int32_t* labels,
+              double* dist2, double* eps_total, d2_flows* flows);
+
+/*
+ * Centroid location update, Eq. (WeightedUpdate) (Eq. (UpdateZ) when omega
+ * is NULL), with the centroid weights held fixed as in Alg. 2 Step 3*:
+ *     z_j^(r) <- sum_{i:C(i)=j} omega_i sum_a w^(i)_{r,a} v_i^(a)
+ *               / sum_{i:C(i)=j} omega_i sum_a w^(i)_{r,a}
+ * where w^(i) is the optimal flow of pair (i, labels[i]).  flows: the flows
+ * d2_assign returned for these labels, or NULL to re-solve the N assigned
+ * pairs.  Updates the resident centroids in place; a support whose
+ * denominator is zero (empty cluster, no mass) keeps its location.
+ * Summation order is fixed (objects in index order), so results are
+ * deterministic run to run.
+ */
+int d2_update_locations(d2_ctx* ctx, const d2_bags* objs, const double* omega,
+                        const int32_t* labels, const d2_flows* flows);
+
+/*
+ * One hierarchical clustering job in the manner of Alg. 3 on one GPU:
+ * the current data are split into contiguous segments of at most seg_size
+ * (tau) objects; every segment starts from the resident centroid set (which
+ * must hold K centroids) and runs `iters` rounds of (d2_assign,
+ * d2_update_locations) -- all segments in one batched launch per step; the
+ * labels are merged with Eq. (UpdateLabel) and Eq. (UpdateGlobalLabel); each
+ * centroid's weight is the summed omega of its members; if more than one
+ * segment was used the merged centroids become the next level's weighted
+ * data, until a level fits in one segment.  seg_size must exceed K.
+ * Outputs (caller-allocated, host or device):
+ *   out_loc  [K*n][dim] FP64 final centroid locations (n = resident n),
+ *   out_cent_weight [K] FP64 summed member weights,
+ *   labels   [N] int32 final cluster of every object.
+ * The resident centroid set is left unchanged.
+ */
+int d2_cluster_level(d2_ctx* ctx, const d2_bags* objs, const double* omega, int32_t K,
+                     int64_t seg_size, int32_t iters, double* out_loc, double* out_cent_weight,
+                     int32_t* labels);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* D2_H */

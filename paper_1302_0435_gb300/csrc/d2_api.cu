@@ -1,0 +1,720 @@
+// d2_api.cu -- implementation of the C-ABI declared in include/d2.h:
+// context, host/device pointer staging, and the five calls of the
+// assignment step (cost matrix, Mallows batch, assign, location update,
+// hierarchical level driver).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/d2.h"
+#include "d2_internal.h"
+
+using d2k::CentView;
+using d2k::FlowOut;
+using d2k::ObjView;
+using d2k::SolveCfg;
+
+namespace {
+
+enum Slot {
+  kObjOff, kObjLoc, kObjW, kOmega, kPairObj, kPairCen, kOutD2, kOutLab, kOutStatus, kFlowCell,
+  kFlowW, kEpsTerms, kEpsOut, kUpd, kLabelsIn, kCentIn0, kCentIn1, kCentIn2,
+  // level driver
+  kLvDataLoc, kLvDataW, kLvDataOff, kLvOmega, kLvOmegaNew, kLvC, kLvCT, kLvLab, kLvD2,
+  kLvCLoc32, kLvCLoc64, kLvCQ, kLvCW, kLvCOff, kLvTmp,
+  kSlots
+};
+
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace
+
+struct d2_ctx {
+  int device = 0;
+  int sms = 1;
+  cudaStream_t own = nullptr;
+  cudaStream_t stream = nullptr;
+  d2_config cfg{};
+  // resident centroids
+  long long K = 0, Tc = 0;
+  int d = 0, nmax = 0, cent_ldt = D2_F32;
+  float* c_loc32 = nullptr;
+  double* c_loc64 = nullptr;
+  long long* c_Q = nullptr;
+  double* c_w64 = nullptr;
+  long long* c_off = nullptr;
+  std::vector<long long> h_coff;
+  // scratch
+  Buf slot[kSlots];
+  int* d_err = nullptr;
+  int* d_info = nullptr;
+  int* h_pin = nullptr;  // pinned host ints
+};
+
+namespace {
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) {                    \
+      return e_ == cudaErrorMemoryAllocation ? D2_ENOMEM : D2_ECUDA; \
+    }                                           \
+  } while (0)
+
+void* grow(d2_ctx* c, int s, size_t bytes, int* rc) {
+  Buf& b = c->slot[s];
+  if (bytes == 0) bytes = 16;
+  if (b.n >= bytes) return b.p;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.n = 0;
+  size_t want = bytes + bytes / 4;
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    *rc = D2_ENOMEM;
+    return nullptr;
+  }
+  b.n = want;
+  return b.p;
+}
+
+// 1 = device-accessible allocation, 0 = host memory, -1 = null
+int where(const void* p) {
+  if (!p) return -1;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+
+size_t esize(int dt) { return dt == D2_F64 ? 8 : (dt == D2_F32 ? 4 : 2); }
+
+bool bags_ok(const d2_bags* b) {
+  if (!b || !b->loc || !b->w || !b->off || b->count < 0 || b->dim < 1 || b->dim > D2_MAX_DIM)
+    return false;
+  if (b->loc_dtype < D2_F64 || b->loc_dtype > D2_BF16) return false;
+  if (b->w_dtype != D2_F64 && b->w_dtype != D2_F32) return false;
+  const int w0 = where(b->off), w1 = where(b->loc), w2 = where(b->w);
+  return w0 == w1 && w1 == w2;
+}
+
+// Stage a bag batch on the device.  Host batches are copied into slots.
+int stage_bags(d2_ctx* c, const d2_bags* b, int s_off, int s_loc, int s_w, ObjView* v) {
+  v->count = b->count;
+  v->d = b->dim;
+  v->ldt = b->loc_dtype;
+  v->wdt = b->w_dtype;
+  if (where(b->off) == 1) {
+    v->loc = b->loc;
+    v->w = b->w;
+    v->off = reinterpret_cast<const long long*>(b->off);
+    return D2_OK;
+  }
+  const long long T = b->count > 0 ? b->off[b->count] : 0;
+  if (b->off[0] != 0 || T < 0) return D2_EINVAL;
+  int rc = D2_OK;
+  void* doff = grow(c, s_off, (size_t)(b->count + 1) * 8, &rc);
+  void* dloc = grow(c, s_loc, (size_t)T * b->dim * esize(b->loc_dtype), &rc);
+  void* dw = grow(c, s_w, (size_t)T * esize(b->w_dtype), &rc);
+  if (rc != D2_OK) return rc;
+  CK(cudaMemcpyAsync(doff, b->off, (size_t)(b->count + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+  if (T > 0) {
+    CK(cudaMemcpyAsync(dloc, b->loc, (size_t)T * b->dim * esize(b->loc_dtype),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(dw, b->w, (size_t)T * esize(b->w_dtype), cudaMemcpyHostToDevice, c->stream));
+  }
+  v->loc = dloc;
+  v->w = dw;
+  v->off = static_cast<const long long*>(doff);
+  return D2_OK;
+}
+
+// Device copy of a caller array (host arrays are staged into slot s).
+template <typename T>
+int stage_in(d2_ctx* c, const T* p, size_t n, int s, const T** out) {
+  if (!p) { *out = nullptr; return D2_OK; }
+  if (where(p) == 1) { *out = p; return D2_OK; }
+  int rc = D2_OK;
+  void* d = grow(c, s, n * sizeof(T), &rc);
+  if (rc != D2_OK) return rc;
+  if (n) CK(cudaMemcpyAsync(d, p, n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  *out = static_cast<const T*>(d);
+  return D2_OK;
+}
+
+// Device destination for a caller output (host outputs get a slot).
+template <typename T>
+int stage_out(d2_ctx* c, T* p, size_t n, int s, T** out, bool* host) {
+  *host = false;
+  if (!p) { *out = nullptr; return D2_OK; }
+  if (where(p) == 1) { *out = p; return D2_OK; }
+  int rc = D2_OK;
+  void* d = grow(c, s, n * sizeof(T), &rc);
+  if (rc != D2_OK) return rc;
+  *out = static_cast<T*>(d);
+  *host = true;
+  return D2_OK;
+}
+
+// max support and offset validity of a bag batch (device offsets)
+int scan(d2_ctx* c, const ObjView& v, int* mmax) {
+  CK(d2k::scan_bags(v.off, v.count, c->d_info, c->stream));
+  CK(cudaMemcpyAsync(c->h_pin, c->d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->h_pin[1]) return D2_EINVAL;
+  *mmax = c->h_pin[0];
+  if (v.count > 0 && (*mmax < 1 || *mmax > D2_MAX_SUPPORT)) return D2_EUNSUPPORTED;
+  return D2_OK;
+}
+
+int mode_for(const d2_ctx* c, int obj_ldt) {
+  if (c->cfg.precision == D2_PREC_FP64) return 0;
+  if (obj_ldt == D2_F64 || c->cent_ldt == D2_F64) return 0;
+  return 1;
+}
+
+SolveCfg solve_cfg(const d2_ctx* c, int mode, int mmax) {
+  SolveCfg s;
+  s.mode = mode;
+  s.group = c->cfg.group_lanes > 0 ? c->cfg.group_lanes : 32;
+  if (s.group != 8 && s.group != 16 && s.group != 32) s.group = 32;
+  s.mmax = std::max(mmax, 1);
+  s.nmax = std::max(c->nmax, 1);
+  s.budget = c->cfg.pivot_budget > 0 ? c->cfg.pivot_budget : 64;
+  s.sms = c->sms;
+  return s;
+}
+
+CentView resident_view(const d2_ctx* c) {
+  CentView v;
+  v.loc32 = c->c_loc32;
+  v.loc64 = c->c_loc64;
+  v.Qpre = c->c_Q;
+  v.off = c->c_off;
+  v.K = c->K;
+  v.d = c->d;
+  return v;
+}
+
+int read_err(d2_ctx* c, int* bits) {
+  CK(cudaMemcpyAsync(c->h_pin + 2, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *bits = c->h_pin[2];
+  return D2_OK;
+}
+
+void free_centroids(d2_ctx* c) {
+  cudaFree(c->c_loc32); cudaFree(c->c_loc64); cudaFree(c->c_Q); cudaFree(c->c_w64); cudaFree(c->c_off);
+  c->c_loc32 = nullptr; c->c_loc64 = nullptr; c->c_Q = nullptr; c->c_w64 = nullptr; c->c_off = nullptr;
+  c->K = c->Tc = 0;
+  c->h_coff.clear();
+}
+
+__global__ void k_pairs_from_labels(const int* labels, long long N, long long* pobj, long long* pcen) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    pobj[i] = i;
+    pcen[i] = labels[i];
+  }
+}
+
+// replicate the resident set M times (level centroid sets)
+__global__ void k_replicate(const float* l32, const double* l64, const long long* Q, const double* w,
+                            const long long* off, long long K, long long Tc, int d, long long M,
+                            float* o32, double* o64, long long* oQ, double* ow, long long* ooff) {
+  const long long tot = M * Tc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long src = t % Tc;
+    oQ[t] = Q[src];
+    ow[t] = w[src];
+    for (int k = 0; k < d; ++k) {
+      o32[t * d + k] = l32[src * d + k];
+      o64[t * d + k] = l64[src * d + k];
+    }
+  }
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j <= M * K;
+       j += (long long)gridDim.x * blockDim.x) {
+    const long long mu = j / K, jj = j % K;
+    ooff[j] = (j == M * K) ? M * Tc : mu * Tc + off[jj];
+  }
+}
+
+// C~ = label + segment*K (Eq. (UpdateLabel)); C = C~[C] (Eq. (UpdateGlobalLabel))
+__global__ void k_merge_labels(const int* lab, long long n_l, long long seg, int K, int* ct) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_l;
+       i += (long long)gridDim.x * blockDim.x)
+    ct[i] = lab[i] < 0 ? -1 : (int)((i / seg) * K + lab[i]);
+}
+__global__ void k_compose(int* C, long long N, const int* ct) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    C[i] = C[i] < 0 ? -1 : ct[C[i]];
+}
+
+unsigned blocks_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (unsigned)std::max<long long>(1, std::min<long long>(b, 8192));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* d2_strerror(int32_t s) {
+  switch (s) {
+    case D2_OK: return "ok";
+    case D2_EINVAL: return "invalid argument, offsets, sizes or weights";
+    case D2_ENOMEM: return "out of memory";
+    case D2_ENOTCONVERGED: return "a pair hit its pivot budget";
+    case D2_ETIMEOUT: return "device wait timed out";
+    case D2_ECUDA: return "CUDA runtime error";
+    case D2_EUNSUPPORTED: return "size or type not supported by the kernels";
+    case D2_ENOCENTROIDS: return "no resident centroid set";
+    default: return "unknown status";
+  }
+}
+
+const char* d2_version(void) { return "d2-gb300 0.1 (sm_103a)"; }
+
+int d2_ctx_create(d2_ctx** out, int32_t device, const d2_config* cfg) {
+  if (!out) return D2_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return D2_ECUDA;
+  }
+  d2_ctx* c = new (std::nothrow) d2_ctx();
+  if (!c) return D2_ENOMEM;
+  c->device = device;
+  if (cfg) c->cfg = *cfg;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&c->d_err, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->d_info, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->h_pin, 8 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    d2_ctx_destroy(c);
+    return D2_ECUDA;
+  }
+  c->stream = c->own;
+  c->sms = d2k::device_sms(device);
+  *out = c;
+  return D2_OK;
+}
+
+int d2_ctx_destroy(d2_ctx* c) {
+  if (!c) return D2_EINVAL;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_centroids(c);
+  for (auto& b : c->slot) if (b.p) cudaFree(b.p);
+  if (c->d_err) cudaFree(c->d_err);
+  if (c->d_info) cudaFree(c->d_info);
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+  return D2_OK;
+}
+
+int d2_set_stream(d2_ctx* c, void* s) {
+  if (!c) return D2_EINVAL;
+  c->stream = s ? static_cast<cudaStream_t>(s) : c->own;
+  return D2_OK;
+}
+
+int d2_sync(d2_ctx* c) {
+  if (!c) return D2_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  return D2_OK;
+}
+
+int d2_set_centroids(d2_ctx* c, const d2_bags* b) {
+  if (!c || !bags_ok(b) || b->count < 1) return D2_EINVAL;
+  cudaSetDevice(c->device);
+  ObjView v;
+  int rc = stage_bags(c, b, kCentIn0, kCentIn1, kCentIn2, &v);
+  if (rc != D2_OK) return rc;
+  std::vector<long long> h(b->count + 1);
+  CK(cudaMemcpyAsync(h.data(), v.off, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (h[0] != 0) return D2_EINVAL;
+  int nmax = 0;
+  for (long long j = 0; j < b->count; ++j) {
+    const long long n = h[j + 1] - h[j];
+    if (n < 1) return D2_EINVAL;
+    if (n > D2_MAX_SUPPORT) return D2_EUNSUPPORTED;
+    nmax = std::max<int>(nmax, (int)n);
+  }
+  free_centroids(c);
+  const long long Tc = h[b->count];
+  const int d = b->dim;
+  if (cudaMalloc(&c->c_loc32, (size_t)Tc * d * 4) != cudaSuccess ||
+      cudaMalloc(&c->c_loc64, (size_t)Tc * d * 8) != cudaSuccess ||
+      cudaMalloc(&c->c_Q, (size_t)Tc * 8) != cudaSuccess ||
+      cudaMalloc(&c->c_w64, (size_t)Tc * 8) != cudaSuccess ||
+      cudaMalloc(&c->c_off, (size_t)(b->count + 1) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    free_centroids(c);
+    return D2_ENOMEM;
+  }
+  CK(cudaMemcpyAsync(c->c_off, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CK(d2k::prep_centroids(v.loc, v.ldt, v.w, v.wdt, c->c_off, b->count, d, c->c_loc32, c->c_loc64,
+                         c->c_Q, c->c_w64, c->d_err, c->stream));
+  int bits = 0;
+  rc = read_err(c, &bits);
+  if (rc != D2_OK) return rc;
+  if (bits) {
+    free_centroids(c);
+    return D2_EINVAL;
+  }
+  c->K = b->count;
+  c->Tc = Tc;
+  c->d = d;
+  c->nmax = nmax;
+  c->cent_ldt = b->loc_dtype;
+  c->h_coff = h;
+  return D2_OK;
+}
+
+int d2_get_centroids(d2_ctx* c, double* loc_out, double* w_out, int64_t* off_out, int64_t* k_out,
+                     int64_t* t_out) {
+  if (!c) return D2_EINVAL;
+  if (c->K == 0) return D2_ENOCENTROIDS;
+  cudaSetDevice(c->device);
+  if (k_out) *k_out = c->K;
+  if (t_out) *t_out = c->Tc;
+  if (loc_out) CK(cudaMemcpyAsync(loc_out, c->c_loc64, (size_t)c->Tc * c->d * 8, cudaMemcpyDefault, c->stream));
+  if (w_out) CK(cudaMemcpyAsync(w_out, c->c_w64, (size_t)c->Tc * 8, cudaMemcpyDefault, c->stream));
+  if (off_out) CK(cudaMemcpyAsync(off_out, c->c_off, (size_t)(c->K + 1) * 8, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return D2_OK;
+}
+
+int d2_cost_matrix(d2_ctx* c, const d2_bags* objs, int64_t i, int64_t j, int32_t precision,
+                   double* C) {
+  if (!c || !C || !bags_ok(objs)) return D2_EINVAL;
+  if (c->K == 0) return D2_ENOCENTROIDS;
+  if (i < 0 || i >= objs->count || j < 0 || j >= c->K || objs->dim != c->d) return D2_EINVAL;
+  cudaSetDevice(c->device);
+  ObjView v;
+  int rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v);
+  if (rc != D2_OK) return rc;
+  long long oo[2];
+  CK(cudaMemcpyAsync(oo, v.off + i, 16, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const long long m = oo[1] - oo[0];
+  const long long n = c->h_coff[j + 1] - c->h_coff[j];
+  if (m < 1) return D2_EINVAL;
+  if (m > D2_MAX_SUPPORT) return D2_EUNSUPPORTED;
+  double* dC;
+  bool host;
+  rc = stage_out(c, C, (size_t)(m * n), kOutD2, &dC, &host);
+  if (rc != D2_OK) return rc;
+  const int mode = precision == D2_PREC_FP32 ? 1 : 0;
+  CK(d2k::cost_matrix(v, resident_view(c), i, j, mode, dC, c->stream));
+  if (host) CK(cudaMemcpyAsync(C, dC, (size_t)(m * n) * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return D2_OK;
+}
+
+int d2_mallows_batch(d2_ctx* c, const d2_bags* objs, const int64_t* pair_obj, const int64_t* pair_cen,
+                     int64_t npairs, double* dist2, d2_flows* flows, int32_t* status) {
+  if (!c || !bags_ok(objs) || npairs < 0 || (npairs > 0 && (!pair_obj || !pair_cen || !dist2)))
+    return D2_EINVAL;
+  if (c->K == 0) return D2_ENOCENTROIDS;
+  if (objs->dim != c->d) return D2_EINVAL;
+  if (npairs == 0) return D2_OK;
+  cudaSetDevice(c->device);
+  ObjView v;
+  int rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v);
+  if (rc != D2_OK) return rc;
+  int mmax = 0;
+  rc = scan(c, v, &mmax);
+  if (rc != D2_OK) return rc;
+  if (flows && flows->stride < (long long)mmax + c->nmax - 1) return D2_EINVAL;
+  const long long* po;
+  const long long* pc;
+  if ((rc = stage_in(c, reinterpret_cast<const long long*>(pair_obj), (size_t)npairs, kPairObj, &po)) ||
+      (rc = stage_in(c, reinterpret_cast<const long long*>(pair_cen), (size_t)npairs, kPairCen, &pc)))
+    return rc;
+  double* dd;
+  int* ds = nullptr;
+  bool h1 = false, h2 = false, h3 = false, h4 = false;
+  if ((rc = stage_out(c, dist2, (size_t)npairs, kOutD2, &dd, &h1))) return rc;
+  if ((rc = stage_out(c, status, (size_t)npairs, kOutStatus, &ds, &h2))) return rc;
+  FlowOut fo{nullptr, nullptr, 0};
+  if (flows) {
+    fo.stride = flows->stride;
+    if ((rc = stage_out(c, flows->cell, (size_t)(npairs * flows->stride), kFlowCell, &fo.cell, &h3)) ||
+        (rc = stage_out(c, flows->w, (size_t)(npairs * flows->stride), kFlowW, &fo.w, &h4)))
+      return rc;
+  }
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  const SolveCfg cfg = solve_cfg(c, mode_for(c, objs->loc_dtype), mmax);
+  CK(d2k::mallows_pairs(v, resident_view(c), po, pc, npairs, cfg, dd, fo, ds, c->d_err, c->stream));
+  if (h1) CK(cudaMemcpyAsync(dist2, dd, (size_t)npairs * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (h2) CK(cudaMemcpyAsync(status, ds, (size_t)npairs * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (h3) CK(cudaMemcpyAsync(flows->cell, fo.cell, (size_t)(npairs * fo.stride) * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (h4) CK(cudaMemcpyAsync(flows->w, fo.w, (size_t)(npairs * fo.stride) * 8, cudaMemcpyDeviceToHost, c->stream));
+  int bits = 0;
+  if ((rc = read_err(c, &bits))) return rc;
+  if (bits & d2k::kErrInvalid) return D2_EINVAL;
+  if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
+  return D2_OK;
+}
+
+int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labels, double* dist2,
+              double* eps_total, d2_flows* flows) {
+  if (!c || !bags_ok(objs) || !labels || !dist2) return D2_EINVAL;
+  if (c->K == 0) return D2_ENOCENTROIDS;
+  if (objs->dim != c->d) return D2_EINVAL;
+  if (objs->count == 0) {
+    if (eps_total) {
+      const double z = 0.0;
+      CK(cudaMemcpy(eps_total, &z, 8, cudaMemcpyDefault));
+    }
+    return D2_OK;
+  }
+  cudaSetDevice(c->device);
+  const long long N = objs->count;
+  ObjView v;
+  int rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v);
+  if (rc != D2_OK) return rc;
+  int mmax = 0;
+  if ((rc = scan(c, v, &mmax))) return rc;
+  if (flows && flows->stride < (long long)mmax + c->nmax - 1) return D2_EINVAL;
+  const double* om;
+  if ((rc = stage_in(c, omega, (size_t)N, kOmega, &om))) return rc;
+  int* dl;
+  double* dd;
+  bool h1, h2, h3 = false, h4 = false;
+  if ((rc = stage_out(c, labels, (size_t)N, kOutLab, &dl, &h1))) return rc;
+  if ((rc = stage_out(c, dist2, (size_t)N, kOutD2, &dd, &h2))) return rc;
+  FlowOut fo{nullptr, nullptr, 0};
+  if (flows) {
+    fo.stride = flows->stride;
+    if ((rc = stage_out(c, flows->cell, (size_t)(N * flows->stride), kFlowCell, &fo.cell, &h3)) ||
+        (rc = stage_out(c, flows->w, (size_t)(N * flows->stride), kFlowW, &fo.w, &h4)))
+      return rc;
+  }
+  double* terms = nullptr;
+  if (eps_total) {
+    terms = static_cast<double*>(grow(c, kEpsTerms, (size_t)N * 8, &rc));
+    if (rc != D2_OK) return rc;
+  }
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  const SolveCfg cfg = solve_cfg(c, mode_for(c, objs->loc_dtype), mmax);
+  CK(d2k::assign(v, resident_view(c), N, (int)c->K, cfg, om, dl, dd, terms, fo, c->d_err, c->stream));
+  if (eps_total) {
+    double* de = static_cast<double*>(grow(c, kEpsOut, 8, &rc));
+    if (rc != D2_OK) return rc;
+    CK(d2k::sum_fixed_order(terms, N, de, c->stream));
+    CK(cudaMemcpyAsync(eps_total, de, 8, cudaMemcpyDefault, c->stream));
+  }
+  if (h1) CK(cudaMemcpyAsync(labels, dl, (size_t)N * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (h2) CK(cudaMemcpyAsync(dist2, dd, (size_t)N * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (h3) CK(cudaMemcpyAsync(flows->cell, fo.cell, (size_t)(N * fo.stride) * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (h4) CK(cudaMemcpyAsync(flows->w, fo.w, (size_t)(N * fo.stride) * 8, cudaMemcpyDeviceToHost, c->stream));
+  int bits = 0;
+  if ((rc = read_err(c, &bits))) return rc;
+  if (bits & d2k::kErrInvalid) return D2_EINVAL;
+  if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
+  return D2_OK;
+}
+
+namespace {
+
+// flows for pairs (i, labels[i]) re-solved in FP64 into slots
+int resolve_assigned(d2_ctx* c, const ObjView& v, const int* dl, int mmax, const CentView& cv,
+                     FlowOut* fo) {
+  const long long N = v.count;
+  int rc = D2_OK;
+  long long* po = static_cast<long long*>(grow(c, kPairObj, (size_t)N * 8, &rc));
+  long long* pc = static_cast<long long*>(grow(c, kPairCen, (size_t)N * 8, &rc));
+  double* dd = static_cast<double*>(grow(c, kOutD2, (size_t)N * 8, &rc));
+  fo->stride = (long long)mmax + c->nmax - 1;
+  fo->cell = static_cast<int*>(grow(c, kFlowCell, (size_t)(N * fo->stride) * 4, &rc));
+  fo->w = static_cast<double*>(grow(c, kFlowW, (size_t)(N * fo->stride) * 8, &rc));
+  if (rc != D2_OK) return rc;
+  k_pairs_from_labels<<<blocks_for(N), 256, 0, c->stream>>>(dl, N, po, pc);
+  SolveCfg cfg = solve_cfg(c, 0, mmax);
+  CK(d2k::mallows_pairs(v, cv, po, pc, N, cfg, dd, *fo, nullptr, c->d_err, c->stream));
+  return D2_OK;
+}
+
+}  // namespace
+
+int d2_update_locations(d2_ctx* c, const d2_bags* objs, const double* omega, const int32_t* labels,
+                        const d2_flows* flows) {
+  if (!c || !bags_ok(objs) || !labels) return D2_EINVAL;
+  if (c->K == 0) return D2_ENOCENTROIDS;
+  if (objs->dim != c->d) return D2_EINVAL;
+  const long long N = objs->count;
+  if (N == 0) return D2_OK;
+  cudaSetDevice(c->device);
+  ObjView v;
+  int rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v);
+  if (rc != D2_OK) return rc;
+  int mmax = 0;
+  if ((rc = scan(c, v, &mmax))) return rc;
+  const double* om;
+  const int* dl;
+  if ((rc = stage_in(c, omega, (size_t)N, kOmega, &om))) return rc;
+  if ((rc = stage_in(c, labels, (size_t)N, kLabelsIn, &dl))) return rc;
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  FlowOut fo{nullptr, nullptr, 0};
+  if (flows) {
+    if (!flows->cell || !flows->w || flows->stride < 1) return D2_EINVAL;
+    fo.stride = flows->stride;
+    const int* fc;
+    const double* fw;
+    if ((rc = stage_in(c, flows->cell, (size_t)(N * flows->stride), kFlowCell, &fc)) ||
+        (rc = stage_in(c, flows->w, (size_t)(N * flows->stride), kFlowW, &fw)))
+      return rc;
+    fo.cell = const_cast<int*>(fc);
+    fo.w = const_cast<double*>(fw);
+  } else {
+    if ((rc = resolve_assigned(c, v, dl, mmax, resident_view(c), &fo))) return rc;
+  }
+  void* scr = grow(c, kUpd, d2k::update_scratch_bytes(N, c->K), &rc);
+  if (rc != D2_OK) return rc;
+  CK(d2k::update_locations(v, om, dl, N, (int)c->K, fo, c->K, c->c_off, c->d, c->cent_ldt,
+                           c->c_loc32, c->c_loc64, scr, c->stream));
+  int bits = 0;
+  if ((rc = read_err(c, &bits))) return rc;
+  if (bits & d2k::kErrInvalid) return D2_EINVAL;
+  if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
+  return D2_OK;
+}
+
+int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t K, int64_t seg_size,
+                     int32_t iters, double* out_loc, double* out_cent_weight, int32_t* labels) {
+  if (!c || !bags_ok(objs) || K < 1 || iters < 0 || !out_loc || !out_cent_weight || !labels)
+    return D2_EINVAL;
+  if (c->K == 0) return D2_ENOCENTROIDS;
+  if (c->K != K || objs->dim != c->d || seg_size <= K) return D2_EINVAL;
+  const long long N0 = objs->count;
+  if (N0 < 1) return D2_EINVAL;
+  cudaSetDevice(c->device);
+  int rc = D2_OK;
+  ObjView v;
+  if ((rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v))) return rc;
+  int mmax = 0;
+  if ((rc = scan(c, v, &mmax))) return rc;
+  const double* om0;
+  if ((rc = stage_in(c, omega, (size_t)N0, kOmega, &om0))) return rc;
+  const int d = c->d;
+  const long long Tc = c->Tc;
+  // global labels C (identity), current omega
+  int* C = static_cast<int*>(grow(c, kLvC, (size_t)N0 * 4, &rc));
+  double* om = static_cast<double*>(grow(c, kLvOmega, (size_t)N0 * 8, &rc));
+  if (rc != D2_OK) return rc;
+  {
+    std::vector<int> id(N0);
+    for (long long i = 0; i < N0; ++i) id[i] = (int)i;
+    CK(cudaMemcpyAsync(C, id.data(), (size_t)N0 * 4, cudaMemcpyHostToDevice, c->stream));
+    if (om0) CK(cudaMemcpyAsync(om, om0, (size_t)N0 * 8, cudaMemcpyDeviceToDevice, c->stream));
+    else {
+      std::vector<double> ones(N0, 1.0);
+      CK(cudaMemcpyAsync(om, ones.data(), (size_t)N0 * 8, cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  ObjView cur = v;
+  int cur_mmax = mmax;
+  for (int level = 0;; ++level) {
+    const long long n_l = cur.count;
+    const long long M = n_l <= seg_size ? 1 : (n_l + seg_size - 1) / seg_size;
+    const long long seg = M == 1 ? n_l : seg_size;
+    const long long KT = M * K;
+    // centroid sets of this level: M copies of the resident set
+    float* l32 = static_cast<float*>(grow(c, kLvCLoc32, (size_t)(M * Tc) * d * 4, &rc));
+    double* l64 = static_cast<double*>(grow(c, kLvCLoc64, (size_t)(M * Tc) * d * 8, &rc));
+    long long* lQ = static_cast<long long*>(grow(c, kLvCQ, (size_t)(M * Tc) * 8, &rc));
+    double* lw = static_cast<double*>(grow(c, kLvCW, (size_t)(M * Tc) * 8, &rc));
+    long long* loff = static_cast<long long*>(grow(c, kLvCOff, (size_t)(KT + 1) * 8, &rc));
+    int* lab = static_cast<int*>(grow(c, kLvLab, (size_t)n_l * 4, &rc));
+    double* ld2 = static_cast<double*>(grow(c, kLvD2, (size_t)n_l * 8, &rc));
+    int* ct = static_cast<int*>(grow(c, kLvCT, (size_t)n_l * 4, &rc));
+    double* wnew = static_cast<double*>(grow(c, kLvOmegaNew, (size_t)KT * 8, &rc));
+    const long long stride = (long long)cur_mmax + c->nmax - 1;
+    FlowOut fo;
+    fo.stride = stride;
+    fo.cell = static_cast<int*>(grow(c, kFlowCell, (size_t)(n_l * stride) * 4, &rc));
+    fo.w = static_cast<double*>(grow(c, kFlowW, (size_t)(n_l * stride) * 8, &rc));
+    void* scr = grow(c, kUpd, d2k::update_scratch_bytes(n_l, KT), &rc);
+    if (rc != D2_OK) return rc;
+    k_replicate<<<blocks_for(M * Tc), 256, 0, c->stream>>>(c->c_loc32, c->c_loc64, c->c_Q, c->c_w64,
+                                                           c->c_off, K, Tc, d, M, l32, l64, lQ, lw,
+                                                           loff);
+    CK(cudaGetLastError());
+    CentView cv{l32, l64, lQ, loff, KT, d};
+    const SolveCfg cfg = solve_cfg(c, mode_for(c, cur.ldt), cur_mmax);
+    for (int it = 0; it < std::max(iters, 1); ++it) {
+      CK(d2k::assign(cur, cv, seg, K, cfg, om, lab, ld2, nullptr, fo, c->d_err, c->stream));
+      if (it < iters)
+        CK(d2k::update_locations(cur, om, lab, seg, K, fo, KT, loff, d, c->cent_ldt, l32, l64, scr,
+                                 c->stream));
+    }
+    // merge (Eq. (UpdateLabel), Eq. (UpdateGlobalLabel)) and member weights
+    FlowOut sort_only{nullptr, nullptr, 0};
+    CK(d2k::update_locations(cur, om, lab, seg, K, sort_only, KT, loff, d, c->cent_ldt, l32, l64,
+                             scr, c->stream));
+    CK(d2k::group_weight_sum(om, n_l, KT, scr, wnew, c->stream));
+    k_merge_labels<<<blocks_for(n_l), 256, 0, c->stream>>>(lab, n_l, seg, K, ct);
+    k_compose<<<blocks_for(N0), 256, 0, c->stream>>>(C, N0, ct);
+    CK(cudaGetLastError());
+    if (M == 1) {
+      CK(cudaMemcpyAsync(out_loc, l64, (size_t)Tc * d * 8, cudaMemcpyDefault, c->stream));
+      CK(cudaMemcpyAsync(out_cent_weight, wnew, (size_t)K * 8, cudaMemcpyDefault, c->stream));
+      CK(cudaMemcpyAsync(labels, C, (size_t)N0 * 4, cudaMemcpyDefault, c->stream));
+      break;
+    }
+    // the merged centroids become the next level's weighted data
+    const bool f64 = c->cent_ldt == D2_F64;
+    void* dloc = grow(c, kLvDataLoc, (size_t)(M * Tc) * d * (f64 ? 8 : 4), &rc);
+    double* dw = static_cast<double*>(grow(c, kLvDataW, (size_t)(M * Tc) * 8, &rc));
+    long long* doff = static_cast<long long*>(grow(c, kLvDataOff, (size_t)(KT + 1) * 8, &rc));
+    double* om2 = static_cast<double*>(grow(c, kLvTmp, (size_t)KT * 8, &rc));
+    if (rc != D2_OK) return rc;
+    CK(cudaMemcpyAsync(dloc, f64 ? (const void*)l64 : (const void*)l32, (size_t)(M * Tc) * d * (f64 ? 8 : 4),
+                       cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(dw, lw, (size_t)(M * Tc) * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(doff, loff, (size_t)(KT + 1) * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(om2, wnew, (size_t)KT * 8, cudaMemcpyDeviceToDevice, c->stream));
+    // omega for the next level lives in kLvOmega (grown to KT)
+    double* omn = static_cast<double*>(grow(c, kLvOmega, std::max<size_t>((size_t)KT * 8, (size_t)N0 * 8), &rc));
+    if (rc != D2_OK) return rc;
+    CK(cudaMemcpyAsync(omn, om2, (size_t)KT * 8, cudaMemcpyDeviceToDevice, c->stream));
+    om = omn;
+    cur.loc = dloc;
+    cur.w = dw;
+    cur.off = doff;
+    cur.count = KT;
+    cur.ldt = f64 ? D2_F64 : D2_F32;
+    cur.wdt = D2_F64;
+    cur_mmax = c->nmax;
+    if (level > 64) return D2_EINVAL;
+  }
+  int bits = 0;
+  if ((rc = read_err(c, &bits))) return rc;
+  if (bits & d2k::kErrInvalid) return D2_EINVAL;
+  if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
+  return D2_OK;
+}
+
+}  // extern "C"

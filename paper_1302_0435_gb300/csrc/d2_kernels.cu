@@ -1,0 +1,487 @@
+// d2_kernels.cu -- CUDA kernels of the assignment step for sm_103a:
+// bag validation, centroid preparation, per-pair Mallows distance
+// (Eq. (D2opt) with z fixed), nearest-centroid assignment (Alg. 2 Step 2)
+// and single-pair cost matrices.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <climits>
+#include <cmath>
+
+#include "d2_internal.h"
+#include "d2_solver.cuh"
+
+namespace d2k {
+
+// ---------------------------------------------------------------- loads --
+
+template <typename T>
+__device__ __forceinline__ T ldx(const void* p, int dt, long long idx) {
+  if (dt == 0) return (T)(static_cast<const double*>(p)[idx]);
+  if (dt == 1) return (T)(static_cast<const float*>(p)[idx]);
+  return (T)__bfloat162float(static_cast<const __nv_bfloat16*>(p)[idx]);
+}
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+
+// Ground-cost tile of Eq. (D2opt): C[a*n+r] = sum_k (x_ak - y_rk)^2, by
+// explicit differences accumulated with FMA in coordinate order.  Returns
+// the tile maximum (group-uniform).
+template <typename T, int G>
+__device__ T build_cost(const Grp<G>& g, T* C, int m, int n, const void* xl, int xdt,
+                        long long xrow0, const T* yl, int d) {
+  const int mn = m * n;
+  const int q = G / n, rem = G - (G / n) * n;
+  int a = g.lane / n, r = g.lane - (g.lane / n) * n;
+  T cmax = T(0);
+  for (int t = g.lane; t < mn; t += G) {
+    const T* yr = yl + (long long)r * d;
+    const long long xi = (xrow0 + a) * (long long)d;
+    T acc = T(0);
+    for (int k = 0; k < d; ++k) {
+      const T df = ldx<T>(xl, xdt, xi + k) - yr[k];
+      acc = fmaT(df, df, acc);
+    }
+    C[t] = acc;
+    cmax = acc > cmax ? acc : cmax;
+    r += rem; a += q;
+    if (r >= n) { r -= n; ++a; }
+  }
+  cmax = gmax<G>(g, cmax);
+  g.sync();
+  return cmax;
+}
+
+// Objective sum_{tree edges} w * c, FP32 (screening estimate).
+template <int G>
+__device__ float objective32(const Simplex<float, G>& S) {
+  float acc = 0.f;
+  for (int y = S.g.lane + 1; y < S.N; y += G) {
+    const int p = S.s.par[y];
+    acc = fmaf((float)((double)S.s.flow[y] * kInvMass), S.s.cost[S.edge_cell(y, p)], acc);
+  }
+  return gsum<G>(S.g, acc);
+}
+
+// Objective in FP64 with the tile's own costs.
+template <int G>
+__device__ double objective64(const Simplex<double, G>& S) {
+  double acc = 0.0;
+  for (int y = S.g.lane + 1; y < S.N; y += G) {
+    const int p = S.s.par[y];
+    acc = fma((double)S.s.flow[y] * kInvMass, S.s.cost[S.edge_cell(y, p)], acc);
+  }
+  return gsum<G>(S.g, acc);
+}
+
+template <typename T, int G>
+__device__ void write_flows(const Simplex<T, G>& S, int* cell, double* w, long long stride) {
+  for (int y = S.g.lane + 1; y < S.N; y += G) {
+    const int p = S.s.par[y];
+    const int row = y < S.m ? y : p;
+    const int col = y < S.m ? p - S.m : y - S.m;
+    cell[y - 1] = (row << 16) | col;
+    w[y - 1] = (double)S.s.flow[y] * kInvMass;
+  }
+  for (long long e = S.N - 1 + S.g.lane; e < stride; e += G) {
+    cell[e] = -1;
+    w[e] = 0.0;
+  }
+}
+
+template <int G>
+__device__ bool load_obj_prefix(const Grp<G>& g, const ObjView& ob, long long o0, int m,
+                                long long* P) {
+  if (ob.wdt == 0) return load_prefix<G>(g, static_cast<const double*>(ob.w) + o0, m, P);
+  return load_prefix<G>(g, static_cast<const float*>(ob.w) + o0, m, P);
+}
+
+template <int G>
+__device__ void load_cent_prefix(const Grp<G>& g, const CentView& cv, long long c0, int n,
+                                 long long* Q) {
+  for (int r = g.lane; r < n; r += G) Q[r] = cv.Qpre[c0 + r];
+  g.sync();
+}
+
+// Tolerances on the most negative reduced cost accepted as optimal.
+__device__ __forceinline__ double tol64(double cmax) { return cmax * 0x1p-43; }
+__device__ __forceinline__ float tol32(float cmax) { return cmax * 0x1p-20f; }
+
+// Exact solve of pair (object at o0/m, centroid at c0/n).  With
+// fp32_start the basis is first driven to FP32 optimality on the FP32 tile
+// (cheap pivots); the same tree and integer flows then continue on the FP64
+// tile with FP64 potentials until no FP64 reduced cost is below -tol64, so
+// the result is FP64-optimal either way.  *obj: FP64 objective.
+template <int G>
+__device__ int solve_exact(const Grp<G>& g, PairMem<double>& s, const ObjView& ob, long long o0,
+                           int m, const CentView& cv, long long c0, int n, int budget,
+                           bool fp32_start, double* obj) {
+  load_cent_prefix<G>(g, cv, c0, n, s.Q);
+  const int cap = budget * (m + n);
+  int piv = 0;
+  if (fp32_start) {
+    PairMem<float> s32 = recast<float>(s);
+    const float c32 = build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
+                                           cv.loc32 + c0 * cv.d, cv.d);
+    Simplex<float, G> S32{s32, m, n, m + n, g};
+    S32.solve(cap, tol32(c32), &piv);
+    g.sync();
+  }
+  const double cmax = build_cost<double, G>(g, s.cost, m, n, ob.loc, ob.ldt, o0,
+                                            cv.loc64 + c0 * cv.d, cv.d);
+  Simplex<double, G> S{s, m, n, m + n, g};
+  if (!fp32_start) S.init_northwest();
+  const int st = S.run(cap, tol64(cmax), &piv);
+  *obj = objective64<G>(S);
+  return st;
+}
+
+// -------------------------------------------------------------- kernels --
+
+__global__ void k_scan_bags(const long long* off, long long count, int* info) {
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < count;
+       b += (long long)gridDim.x * blockDim.x) {
+    const long long m = off[b + 1] - off[b];
+    if (m < 1 || (b == 0 && off[0] != 0)) atomicOr(&info[1], 1);
+    atomicMax(&info[0], (int)(m > INT_MAX ? INT_MAX : (m < 0 ? 0 : m)));
+  }
+}
+
+template <int G>
+__global__ void k_prep_centroids(const void* loc, int ldt, const void* w, int wdt,
+                                 const long long* off, long long K, int d, float* loc32,
+                                 double* loc64, long long* Qpre, double* w64, int* err) {
+  Grp<G> g;
+  const int gpb = blockDim.x / G;
+  for (long long j = (long long)blockIdx.x * gpb + threadIdx.x / G; j < K;
+       j += (long long)gridDim.x * gpb) {
+    const long long c0 = off[j];
+    const long long n = off[j + 1] - c0;
+    if (n < 1 || n > 64) {
+      if (g.lane == 0) atomicOr(err, kErrInvalid);
+      continue;
+    }
+    bool ok = wdt == 0 ? load_prefix<G>(g, static_cast<const double*>(w) + c0, (int)n, Qpre + c0)
+                       : load_prefix<G>(g, static_cast<const float*>(w) + c0, (int)n, Qpre + c0);
+    if (!ok && g.lane == 0) atomicOr(err, kErrInvalid);
+    // normalised FP64 weights as seen by the solver
+    for (int r = g.lane; r < n; r += G) {
+      const long long prev = r > 0 ? Qpre[c0 + r - 1] : 0LL;
+      w64[c0 + r] = ok ? (double)(Qpre[c0 + r] - prev) * kInvMass : 0.0;
+    }
+    for (long long e = g.lane; e < n * d; e += G) {
+      const double v = ldx<double>(loc, ldt, c0 * d + e);
+      loc64[c0 * d + e] = v;
+      loc32[c0 * d + e] = (float)v;
+    }
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
+                                                       const long long* pobj, const long long* pcen,
+                                                       long long npairs, SolveCfg cfg, size_t slice,
+                                                       double* dist2, FlowOut fo, int* status, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Grp<G> g;
+  const int gpb = blockDim.x / G;
+  unsigned char* base = smem + (threadIdx.x / G) * slice;
+  for (long long t = (long long)blockIdx.x * gpb + threadIdx.x / G; t < npairs;
+       t += (long long)gridDim.x * gpb) {
+    const long long i = pobj[t], j = pcen[t];
+    int st = kStInvalid;
+    double res = nan("");
+    if (i >= 0 && i < ob.count && j >= 0 && j < cv.K) {
+      const long long o0 = ob.off[i];
+      const int m = (int)(ob.off[i + 1] - o0);
+      const long long c0 = cv.off[j];
+      const int n = (int)(cv.off[j + 1] - c0);
+      if (m >= 1 && m <= cfg.mmax && n >= 1 && n <= cfg.nmax) {
+        PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax);
+        if (load_obj_prefix<G>(g, ob, o0, m, s64.P)) {
+          st = solve_exact<G>(g, s64, ob, o0, m, cv, c0, n, cfg.budget, cfg.mode == 1, &res);
+          if (fo.cell)
+            write_flows<double, G>(Simplex<double, G>{s64, m, n, m + n, g}, fo.cell + t * fo.stride,
+                                   fo.w + t * fo.stride, fo.stride);
+        }
+      }
+    }
+    if (g.lane == 0) {
+      dist2[t] = res;
+      if (status) status[t] = st == kStOk ? 0 : (st == kStNotConverged ? -3 : -1);
+      if (st == kStInvalid) atomicOr(err, kErrInvalid);
+      if (st == kStNotConverged) atomicOr(err, kErrNotConverged);
+    }
+    g.sync();
+  }
+}
+
+// Nearest centroid, Alg. 2 Step 2.  Object i uses centroids
+// [(i/seg_size)*K, (i/seg_size)*K + K) of the set (one segment = all).
+// mode 1: every centroid is solved with an FP32 tile and FP32 pivots; the
+// FP32 objective D32_j has a bound err_j on its distance to the FP64
+// optimum, and every centroid whose interval [D32_j-err_j, D32_j+err_j]
+// reaches below the smallest upper end is re-solved in FP64.  The label is
+// the smallest-index minimum of those FP64 values, so it agrees with an
+// all-FP64 argmin.  mode 0: every centroid in FP64.
+template <int G>
+__global__ void __launch_bounds__(128) k_assign(ObjView ob, CentView cv, long long seg_size, int K,
+                                                SolveCfg cfg, size_t slice, const double* omega,
+                                                int* labels, double* dist2, double* eps_terms,
+                                                FlowOut fo, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Grp<G> g;
+  const int gpb = blockDim.x / G;
+  unsigned char* base = smem + (threadIdx.x / G) * slice;
+  PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax);
+  PairMem<float> s32 = recast<float>(s64);
+  int* cand = s64.sc;                                  // [8]
+  float* clo = reinterpret_cast<float*>(s64.sc + 8);   // [8]
+  for (long long i = (long long)blockIdx.x * gpb + threadIdx.x / G; i < ob.count;
+       i += (long long)gridDim.x * gpb) {
+    const long long o0 = ob.off[i];
+    const int m = (int)(ob.off[i + 1] - o0);
+    const long long cb = (i / seg_size) * (long long)K;
+    int best_j = -1;
+    double best = nan("");
+    int st = kStOk;
+    const bool okm = m >= 1 && m <= cfg.mmax && cb + K <= cv.K;
+    if (!okm || !load_obj_prefix<G>(g, ob, o0, m, s64.P)) {
+      st = kStInvalid;
+    } else {
+      int ncand = 0;
+      bool all = cfg.mode == 0;
+      if (cfg.mode == 1) {
+        float best_hi = FLT_MAX;
+        const float rel = (float)(cv.d + 3) * 0x1p-24f + 0x1p-17f;
+        for (int j = 0; j < K; ++j) {
+          const long long c0 = cv.off[cb + j];
+          const int n = (int)(cv.off[cb + j + 1] - c0);
+          if (n < 1 || n > cfg.nmax) { st = kStInvalid; break; }
+          load_cent_prefix<G>(g, cv, c0, n, s32.Q);
+          const float cmax = build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
+                                                  cv.loc32 + c0 * cv.d, cv.d);
+          Simplex<float, G> S{s32, m, n, m + n, g};
+          if (S.solve(cfg.budget * (m + n), tol32(cmax), nullptr) != kStOk) all = true;
+          const float D = objective32<G>(S);
+          const float e = D * rel + cmax * 0x1p-16f;
+          const float lo = D - e, hi = D + e;
+          if (lo <= best_hi) {
+            if (ncand < 8) {
+              if (g.lane == 0) { cand[ncand] = j; clo[ncand] = lo; }
+              ++ncand;
+            } else {
+              all = true;
+            }
+          }
+          g.sync();
+          if (hi < best_hi) {
+            best_hi = hi;
+            int k2 = 0;
+            for (int c = 0; c < ncand; ++c) {
+              const int cj = cand[c];
+              const float cl = clo[c];
+              g.sync();
+              if (cl <= best_hi) {
+                if (g.lane == 0) { cand[k2] = cj; clo[k2] = cl; }
+                ++k2;
+              }
+              g.sync();
+            }
+            ncand = k2;
+          }
+        }
+      }
+      if (st == kStOk) {
+        const int count = all ? K : ncand;
+        for (int c = 0; c < count; ++c) {
+          const int j = all ? c : cand[c];
+          g.sync();
+          const long long c0 = cv.off[cb + j];
+          const int n = (int)(cv.off[cb + j + 1] - c0);
+          if (n < 1 || n > cfg.nmax) { st = kStInvalid; break; }
+          double D;
+          const int s2 = solve_exact<G>(g, s64, ob, o0, m, cv, c0, n, cfg.budget, cfg.mode == 1, &D);
+          if (s2 != kStOk) st = s2;
+          if (best_j < 0 || D < best) {
+            best = D;
+            best_j = j;
+            if (fo.cell)
+              write_flows<double, G>(Simplex<double, G>{s64, m, n, m + n, g}, fo.cell + i * fo.stride,
+                                     fo.w + i * fo.stride, fo.stride);
+          }
+        }
+      }
+    }
+    if (g.lane == 0) {
+      labels[i] = st == kStInvalid ? -1 : best_j;
+      dist2[i] = st == kStInvalid ? nan("") : best;
+      if (eps_terms) eps_terms[i] = (omega ? omega[i] : 1.0) * dist2[i];
+      if (st == kStInvalid) atomicOr(err, kErrInvalid);
+      if (st == kStNotConverged) atomicOr(err, kErrNotConverged);
+    }
+    g.sync();
+  }
+}
+
+__global__ void k_cost_matrix(ObjView ob, CentView cv, long long i, long long j, int mode,
+                              double* C) {
+  const long long o0 = ob.off[i];
+  const int m = (int)(ob.off[i + 1] - o0);
+  const long long c0 = cv.off[j];
+  const int n = (int)(cv.off[j + 1] - c0);
+  for (int t = threadIdx.x; t < m * n; t += blockDim.x) {
+    const int a = t / n, r = t % n;
+    if (mode == 0) {
+      double acc = 0.0;
+      for (int k = 0; k < cv.d; ++k) {
+        const double df = ldx<double>(ob.loc, ob.ldt, (o0 + a) * cv.d + k) - cv.loc64[(c0 + r) * cv.d + k];
+        acc = fma(df, df, acc);
+      }
+      C[t] = acc;
+    } else {
+      float acc = 0.f;
+      for (int k = 0; k < cv.d; ++k) {
+        const float df = ldx<float>(ob.loc, ob.ldt, (o0 + a) * cv.d + k) - cv.loc32[(c0 + r) * cv.d + k];
+        acc = fmaf(df, df, acc);
+      }
+      C[t] = (double)acc;
+    }
+  }
+}
+
+// Fixed-order sum (one block, strided partials then a tree): deterministic.
+__global__ void k_sum_fixed(const double* v, long long n, double* out) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) acc += v[t];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// ------------------------------------------------------------ launchers --
+
+int device_sms(int dev) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  return v > 0 ? v : 1;
+}
+
+cudaError_t scan_bags(const long long* off, long long count, int* d_info, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(d_info, 0, 2 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  if (count <= 0) return cudaSuccess;
+  const long long blocks = (count + 255) / 256;
+  k_scan_bags<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(off, count, d_info);
+  return cudaGetLastError();
+}
+
+cudaError_t prep_centroids(const void* loc, int ldt, const void* w, int wdt, const long long* off,
+                           long long K, int d, float* loc32, double* loc64, long long* Qpre,
+                           double* w64, int* d_err, cudaStream_t st) {
+  const long long blocks = (K + 3) / 4;
+  k_prep_centroids<32><<<(unsigned)(blocks < 65535 ? blocks : 65535), 128, 0, st>>>(
+      loc, ldt, w, wdt, off, K, d, loc32, loc64, Qpre, w64, d_err);
+  return cudaGetLastError();
+}
+
+// Groups per block: up to 128 threads, whole warps only, within the
+// 227 KB shared-memory limit of a block.  0 if one warp does not fit.
+static int groups_per_block(int G, size_t slice) {
+  const size_t limit = 227 * 1024;
+  const int per_warp = 32 / G;
+  int gpb = 128 / G;
+  while (gpb >= per_warp && (size_t)gpb * slice > limit) gpb -= per_warp;
+  return gpb >= per_warp ? gpb : 0;
+}
+
+template <typename KernelT>
+static cudaError_t launch_cfg(KernelT kern, size_t smem, int threads, int sms, long long work,
+                              int gpb, unsigned* grid) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long need = (work + gpb - 1) / gpb;
+  long long cap = (long long)per_sm * sms;
+  long long gsz = need < cap ? need : cap;
+  *grid = (unsigned)(gsz > 0 ? gsz : 1);
+  return cudaSuccess;
+}
+
+template <int G>
+static cudaError_t mallows_pairs_g(const ObjView& ob, const CentView& cv, const long long* pobj,
+                                   const long long* pcen, long long npairs, const SolveCfg& cfg,
+                                   double* dist2, FlowOut fo, int* status, int* d_err,
+                                   cudaStream_t st) {
+  const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax);
+  const int gpb = groups_per_block(G, slice);
+  if (gpb == 0) return cudaErrorInvalidConfiguration;
+  const size_t smem = slice * gpb;
+  unsigned grid = 1;
+  cudaError_t e = launch_cfg(k_mallows_pairs<G>, smem, gpb * G, cfg.sms, npairs, gpb, &grid);
+  if (e != cudaSuccess) return e;
+  k_mallows_pairs<G><<<grid, gpb * G, smem, st>>>(ob, cv, pobj, pcen, npairs, cfg, slice, dist2, fo,
+                                               status, d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t mallows_pairs(const ObjView& ob, const CentView& cv, const long long* pobj,
+                          const long long* pcen, long long npairs, const SolveCfg& cfg,
+                          double* dist2, FlowOut fo, int* status, int* d_err, cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  switch (cfg.group) {
+    case 8: return mallows_pairs_g<8>(ob, cv, pobj, pcen, npairs, cfg, dist2, fo, status, d_err, st);
+    case 16: return mallows_pairs_g<16>(ob, cv, pobj, pcen, npairs, cfg, dist2, fo, status, d_err, st);
+    default: return mallows_pairs_g<32>(ob, cv, pobj, pcen, npairs, cfg, dist2, fo, status, d_err, st);
+  }
+}
+
+template <int G>
+static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg_size, int K,
+                            const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
+                            double* eps_terms, FlowOut fo, int* d_err, cudaStream_t st) {
+  const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax);
+  const int gpb = groups_per_block(G, slice);
+  if (gpb == 0) return cudaErrorInvalidConfiguration;
+  const size_t smem = slice * gpb;
+  unsigned grid = 1;
+  cudaError_t e = launch_cfg(k_assign<G>, smem, gpb * G, cfg.sms, ob.count, gpb, &grid);
+  if (e != cudaSuccess) return e;
+  k_assign<G><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, cfg, slice, omega, labels, dist2,
+                                        eps_terms, fo, d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, int K,
+                   const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
+                   double* eps_terms, FlowOut fo, int* d_err, cudaStream_t st) {
+  if (ob.count <= 0) return cudaSuccess;
+  switch (cfg.group) {
+    case 8: return assign_g<8>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, d_err, st);
+    case 16: return assign_g<16>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, d_err, st);
+    default: return assign_g<32>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, d_err, st);
+  }
+}
+
+cudaError_t cost_matrix(const ObjView& ob, const CentView& cv, long long i, long long j, int mode,
+                        double* C, cudaStream_t st) {
+  k_cost_matrix<<<1, 256, 0, st>>>(ob, cv, i, j, mode, C);
+  return cudaGetLastError();
+}
+
+cudaError_t sum_fixed_order(const double* v, long long n, double* out, cudaStream_t st) {
+  k_sum_fixed<<<1, 256, 0, st>>>(v, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace d2k

@@ -1,0 +1,245 @@
+"""Thin Python binding of libd2.so (include/d2.h), same call names.
+
+Argument marshalling only: every step of the assignment step runs in the
+CUDA library.  Tensors are torch tensors (device or host) or numpy arrays
+(host); pointers and sizes are passed straight through the C ABI.  If the
+library cannot be loaded this module raises -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libd2.so")
+
+D2_OK, D2_EINVAL, D2_ENOMEM, D2_ENOTCONVERGED = 0, -1, -2, -3
+D2_ETIMEOUT, D2_ECUDA, D2_EUNSUPPORTED, D2_ENOCENTROIDS = -4, -5, -6, -7
+D2_F64, D2_F32, D2_BF16 = 0, 1, 2
+D2_PREC_AUTO, D2_PREC_FP64, D2_PREC_FP32 = 0, 1, 2
+MAX_SUPPORT = 64
+
+EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_strerror",
+           "d2_version", "d2_set_centroids", "d2_get_centroids", "d2_cost_matrix",
+           "d2_mallows_batch", "d2_assign", "d2_update_locations", "d2_cluster_level"]
+
+
+class D2Bags(ctypes.Structure):
+    _fields_ = [("loc", ctypes.c_void_p), ("w", ctypes.c_void_p), ("off", ctypes.c_void_p),
+                ("count", ctypes.c_int64), ("dim", ctypes.c_int32), ("loc_dtype", ctypes.c_int32),
+                ("w_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class D2Config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("pivot_budget", ctypes.c_int32),
+                ("group_lanes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class D2Flows(ctypes.Structure):
+    _fields_ = [("cell", ctypes.c_void_p), ("w", ctypes.c_void_p), ("stride", ctypes.c_int64)]
+
+
+class D2Error(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (%d)" % (what, strerror(code), code))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load libd2.so; raises OSError if it is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError("libd2.so not built: %s (run `python -m paper_1302_0435_gb300.build`)" % p)
+    lib = ctypes.CDLL(p)
+    vp = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    i32 = ctypes.c_int32
+    lib.d2_ctx_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(D2Config)]
+    lib.d2_ctx_destroy.argtypes = [vp]
+    lib.d2_set_stream.argtypes = [vp, vp]
+    lib.d2_sync.argtypes = [vp]
+    lib.d2_strerror.argtypes = [i32]
+    lib.d2_strerror.restype = ctypes.c_char_p
+    lib.d2_version.restype = ctypes.c_char_p
+    lib.d2_set_centroids.argtypes = [vp, ctypes.POINTER(D2Bags)]
+    lib.d2_get_centroids.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.d2_cost_matrix.argtypes = [vp, ctypes.POINTER(D2Bags), i64, i64, i32, vp]
+    lib.d2_mallows_batch.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, i64, vp,
+                                     ctypes.POINTER(D2Flows), vp]
+    lib.d2_assign.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, vp, vp, ctypes.POINTER(D2Flows)]
+    lib.d2_update_locations.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, ctypes.POINTER(D2Flows)]
+    lib.d2_cluster_level.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i32, i64, i32, vp, vp, vp]
+    _lib = lib
+    return lib
+
+
+def strerror(code):
+    return load().d2_strerror(int(code)).decode()
+
+
+def _ptr(x):
+    """Raw address of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return x.ctypes.data
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr()
+
+
+def _check(rc, what):
+    if rc != D2_OK:
+        raise D2Error(rc, what)
+
+
+_DT = {"f64": D2_F64, "f32": D2_F32, "bf16": D2_BF16}
+
+
+class BagsRef:
+    """A bag batch as the C ABI sees it, holding references to its arrays."""
+
+    def __init__(self, loc, w, off, count, dim, loc_dtype, w_dtype):
+        self.loc, self.w, self.off = loc, w, off
+        self.s = D2Bags(_ptr(loc), _ptr(w), _ptr(off), int(count), int(dim), int(loc_dtype),
+                        int(w_dtype), 0)
+
+    @property
+    def count(self):
+        return self.s.count
+
+
+def bags_from_synth(b, device=None, pinned=False):
+    """Marshal a synth.Bags into host numpy arrays (device=None), pinned host
+    tensors (pinned=True) or device tensors (device='cuda:0')."""
+    if b.loc_dtype == "bf16":
+        loc_np = np.ascontiguousarray(b.loc_bits.view(np.int16))
+    else:
+        loc_np = np.ascontiguousarray(b.loc)
+    w_np = np.ascontiguousarray(b.w)
+    off_np = np.ascontiguousarray(b.off.astype(np.int64))
+    if device is None and not pinned:
+        return BagsRef(loc_np, w_np, off_np, b.count, b.dim, _DT[b.loc_dtype], _DT[b.w_dtype])
+    import torch
+    tl = torch.from_numpy(loc_np)
+    if b.loc_dtype == "bf16":
+        tl = tl.view(torch.bfloat16)
+    tw, to = torch.from_numpy(w_np), torch.from_numpy(off_np)
+    if pinned:
+        tl, tw, to = tl.pin_memory(), tw.pin_memory(), to.pin_memory()
+    else:
+        tl, tw, to = tl.to(device), tw.to(device), to.to(device)
+    return BagsRef(tl, tw, to, b.count, b.dim, _DT[b.loc_dtype], _DT[b.w_dtype])
+
+
+class Context:
+    """d2_ctx_create / d2_ctx_destroy."""
+
+    def __init__(self, device=0, precision=D2_PREC_AUTO, pivot_budget=0, group_lanes=0):
+        lib = load()
+        self.h = ctypes.c_void_p()
+        cfg = D2Config(precision, pivot_budget, group_lanes)
+        _check(lib.d2_ctx_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)), "d2_ctx_create")
+        self._cents = None
+
+    def close(self):
+        if self.h:
+            load().d2_ctx_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def d2_set_stream(ctx, stream):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    h = getattr(stream, "cuda_stream", stream)
+    _check(load().d2_set_stream(ctx.h, h), "d2_set_stream")
+
+
+def d2_sync(ctx):
+    _check(load().d2_sync(ctx.h), "d2_sync")
+
+
+def d2_set_centroids(ctx, cents):
+    ref = cents if isinstance(cents, BagsRef) else bags_from_synth(cents)
+    _check(load().d2_set_centroids(ctx.h, ctypes.byref(ref.s)), "d2_set_centroids")
+
+
+def d2_get_centroids(ctx, dim):
+    """Resident centroids as numpy (loc [T, dim] f64, w [T] f64, off [K+1])."""
+    lib = load()
+    k = ctypes.c_int64()
+    t = ctypes.c_int64()
+    _check(lib.d2_get_centroids(ctx.h, None, None, None, ctypes.byref(k), ctypes.byref(t)),
+           "d2_get_centroids")
+    loc = np.empty((t.value, dim))
+    w = np.empty(t.value)
+    off = np.empty(k.value + 1, dtype=np.int64)
+    _check(lib.d2_get_centroids(ctx.h, _ptr(loc), _ptr(w), _ptr(off), None, None), "d2_get_centroids")
+    return loc, w, off
+
+
+def d2_cost_matrix(ctx, objs, i, j, precision, m, n):
+    C = np.empty((m, n))
+    _check(load().d2_cost_matrix(ctx.h, ctypes.byref(objs.s), int(i), int(j), int(precision), _ptr(C)),
+           "d2_cost_matrix")
+    return C
+
+
+def _flows(flows):
+    if flows is None:
+        return None
+    cell, w = flows
+    stride = cell.shape[-1]
+    return D2Flows(_ptr(cell), _ptr(w), stride)
+
+
+def d2_mallows_batch(ctx, objs, pair_obj, pair_cen, dist2, flows=None, status=None):
+    """dist2/status/flows are caller buffers (torch or numpy); flows = (cell, w)
+    with shape [npairs, stride].  Returns the status code (raises on errors
+    other than D2_ENOTCONVERGED)."""
+    f = _flows(flows)
+    rc = load().d2_mallows_batch(ctx.h, ctypes.byref(objs.s), _ptr(pair_obj), _ptr(pair_cen),
+                                 int(len(pair_obj)), _ptr(dist2), ctypes.byref(f) if f else None,
+                                 _ptr(status))
+    if rc not in (D2_OK, D2_ENOTCONVERGED):
+        _check(rc, "d2_mallows_batch")
+    return rc
+
+
+def d2_assign(ctx, objs, labels, dist2, omega=None, eps=None, flows=None):
+    f = _flows(flows)
+    rc = load().d2_assign(ctx.h, ctypes.byref(objs.s), _ptr(omega), _ptr(labels), _ptr(dist2),
+                          _ptr(eps), ctypes.byref(f) if f else None)
+    if rc not in (D2_OK, D2_ENOTCONVERGED):
+        _check(rc, "d2_assign")
+    return rc
+
+
+def d2_update_locations(ctx, objs, labels, omega=None, flows=None):
+    f = _flows(flows)
+    rc = load().d2_update_locations(ctx.h, ctypes.byref(objs.s), _ptr(omega), _ptr(labels),
+                                    ctypes.byref(f) if f else None)
+    if rc not in (D2_OK, D2_ENOTCONVERGED):
+        _check(rc, "d2_update_locations")
+    return rc
+
+
+def d2_cluster_level(ctx, objs, K, seg_size, iters, out_loc, out_cent_weight, labels, omega=None):
+    rc = load().d2_cluster_level(ctx.h, ctypes.byref(objs.s), _ptr(omega), int(K), int(seg_size),
+                                 int(iters), _ptr(out_loc), _ptr(out_cent_weight), _ptr(labels))
+    if rc not in (D2_OK, D2_ENOTCONVERGED):
+        _check(rc, "d2_cluster_level")
+    return rc

@@ -1,0 +1,420 @@
+"""Benchmark of the D2-clustering assignment step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one hierarchical clustering job of the image-like workload
+(N=200,000 bags of 8-16 supports in d=6, Dirichlet(0.5) weights, FP32;
+K=64 centroids of 16 supports per segment; segments of 5,000 bags; 10
+rounds of (assign, location update) per segment; then the 2,560 segment
+centroids are clustered to 64 with 10 more rounds).  Every assign solves
+the exact Mallows LP for each (bag, centroid) pair of its segment, so the
+unit is one pair LP: 200000*64*10 + 2560*64*10 pair LPs per step.
+
+Prints one JSON line (rank 0).  `value` is device-timed pairs/s with the
+inputs resident in HBM; `e2e` is the same through the C-ABI with pinned
+host buffers (inputs copied in and labels/centroids copied out inside the
+timed region).  `roofline` reports the dominant kernel (k_assign) against
+the FP32/INT issue peak; `cpu_baseline` times the FP64 CPU oracle on a
+bounded sample on this host's cores.
+
+--impl reference times that oracle itself as the comparison arm.
+Multi-GPU (torchrun): every rank clusters its own copy of the workload
+(independent problems, no data-path collective) -> weak scaling.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="image_like", N=200_000, K=64, seg=5000, iters=10, n=16, d=6)
+METRIC = "exact Mallows pairs/s at rel err<=1e-6 vs FP64 oracle"
+UNIT = "pairs/s"
+L2_BYTES = 129 * 1024 * 1024
+ALU_LANES_PER_SM = 128
+
+
+def pairs_per_step(N, K, seg, iters):
+    """Pair LPs solved by the assign steps of one clustering job."""
+    total = 0
+    n_l = N
+    while True:
+        M = 1 if n_l <= seg else -(-n_l // seg)
+        total += n_l * K * max(iters, 1)
+        if M == 1:
+            return total
+        n_l = M * K
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        hi = max(sm)
+        loaded = [s for s in sm if s >= 0.5 * hi] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1302_0435_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(cs, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per k_assign launch from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "k_assign_image_like.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        prof = json.load(f)
+    if prof.get("source_hash") != kernel_source_hash():
+        return None
+    return prof.get("dram_bytes_per_launch_full")
+
+
+# ---------------------------------------------------------------- oracle --
+
+def cpu_sample(objs, cents, target_s, seed=7):
+    """Time the FP64 oracle on a random sample of (object, centroid) pairs
+    sized to take about target_s seconds on all host cores."""
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    K = cents.count
+    # calibrate on a small sample
+    pi = rng.integers(0, objs.count, size=64 * cores)
+    pj = rng.integers(0, K, size=pi.size)
+    t0 = time.perf_counter()
+    oracle.mallows_pairs(objs, cents, pi, pj, nthreads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    npairs = int(max(pi.size, min(2_000_000, pi.size * target_s / dt)))
+    pi = rng.integers(0, objs.count, size=npairs)
+    pj = rng.integers(0, K, size=npairs)
+    t0 = time.perf_counter()
+    _, piv = oracle.mallows_pairs(objs, cents, pi, pj, nthreads=cores, return_pivots=True)
+    dt = time.perf_counter() - t0
+    sizes = np.diff(objs.off)[pi]
+    ncent = np.diff(cents.off)[pj]
+    d = objs.dim
+    ops = 2.0 * sizes * ncent * d + piv * (sizes * ncent + 4.0 * (sizes + ncent))
+    return dict(value=npairs / dt, unit=UNIT, cores=cores, kind="oracle",
+                sample="%d random (bag, centroid) pairs of the workload's first segment set "
+                       "(FP64 transportation simplex, %d threads)" % (npairs, cores),
+                seconds=dt, mean_pivots=float(piv.mean()), ops_per_pair=float(ops.mean()))
+
+
+def run_reference(args):
+    """The comparison arm: the FP64 oracle itself, on host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1302_0435_gb300 import synth
+    objs, cents = synth.image_like(N=WORKLOAD["N"], K=WORKLOAD["K"])
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(11)
+    # size one step to about 4 s of oracle work on this host
+    cal = 256 * cores
+    t0 = time.perf_counter()
+    oracle.mallows_pairs(objs, cents, rng.integers(0, objs.count, size=cal),
+                         rng.integers(0, cents.count, size=cal), nthreads=cores)
+    step_pairs = int(max(cal, 4.0 * cal / max(time.perf_counter() - t0, 1e-3)))
+
+    def step():
+        pi = rng.integers(0, objs.count, size=step_pairs)
+        pj = rng.integers(0, cents.count, size=step_pairs)
+        oracle.mallows_pairs(objs, cents, pi, pj, nthreads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    v = step_pairs * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d random pairs per step of the image_like workload" % step_pairs},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config():
+    w = WORKLOAD
+    return {"workload": "image_like: N=%d bags, 8-16 supports, d=%d, Dirichlet(0.5), FP32; K=%d "
+                        "centroids of %d supports per segment; segments of %d; %d rounds per level; "
+                        "top-level merge" % (w["N"], w["d"], w["K"], w["n"], w["seg"], w["iters"]),
+            "N": w["N"], "K": w["K"], "seg_size": w["seg"], "iters": w["iters"],
+            "pairs_per_step": pairs_per_step(w["N"], w["K"], w["seg"], w["iters"]),
+            "l2": "flushed between steps (256 MiB write), not timed"}
+
+
+# ------------------------------------------------------------------ ours --
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1302_0435_gb300 import build, d2, synth
+    build.build()
+    d2.load()
+    w = WORKLOAD
+    objs, cents = synth.image_like(N=w["N"], K=w["K"], seed=1002 + rank)
+    ctx = d2.Context(dev.index)
+    stream = torch.cuda.current_stream(dev)
+    d2.d2_set_stream(ctx, stream)
+    d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device=dev))
+    ob = d2.bags_from_synth(objs, device=dev)
+    T = cents.loc.shape[0]
+    out_loc = torch.empty((T, w["d"]), dtype=torch.float64, device=dev)
+    out_w = torch.empty(w["K"], dtype=torch.float64, device=dev)
+    labels = torch.empty(w["N"], dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    ppstep = pairs_per_step(w["N"], w["K"], w["seg"], w["iters"])
+
+    def step():
+        d2.d2_cluster_level(ctx, ob, w["K"], w["seg"], w["iters"], out_loc, out_w, labels)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    launches0 = d2.d2_get_stats()["kernel_launches"]
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1) / 1e3)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    launches = d2.d2_get_stats()["kernel_launches"] - launches0
+    clk = clocks.stop()
+    t_total = reduce_max(sum(times), ws)
+    value = ppstep * args.steps * ws / t_total
+
+    # dominant kernel: k_assign over the full bag set against one segment's K centroids
+    lab1 = torch.empty(w["N"], dtype=torch.int32, device=dev)
+    dd1 = torch.empty(w["N"], dtype=torch.float64, device=dev)
+    d2.d2_assign(ctx, ob, lab1, dd1)
+    torch.cuda.synchronize(dev)
+    kt = []
+    for _ in range(3):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d2.d2_assign(ctx, ob, lab1, dd1)
+        e1.record(stream)
+        e1.synchronize()
+        kt.append(e0.elapsed_time(e1) / 1e3)
+    k_sec = statistics.median(kt)
+    k_pairs = w["N"] * w["K"]
+
+    # end to end through the C-ABI with pinned host buffers
+    hb = d2.bags_from_synth(objs, pinned=True)
+    h_loc = torch.empty((T, w["d"]), dtype=torch.float64).pin_memory()
+    h_w = torch.empty(w["K"], dtype=torch.float64).pin_memory()
+    h_lab = torch.empty(w["N"], dtype=torch.int32).pin_memory()
+    bi = hb.loc.numel() * hb.loc.element_size() + hb.w.numel() * hb.w.element_size() + \
+        hb.off.numel() * 8
+    bo = h_loc.numel() * 8 + h_w.numel() * 8 + h_lab.numel() * 4
+    e2e_steps = max(1, min(args.steps, 2))
+    d2.d2_cluster_level(ctx, hb, w["K"], w["seg"], w["iters"], h_loc, h_w, h_lab)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        d2.d2_cluster_level(ctx, hb, w["K"], w["seg"], w["iters"], h_loc, h_w, h_lab)
+    torch.cuda.synchronize(dev)
+    e2e_t = reduce_max(time.perf_counter() - t0, ws)
+    e2e_v = ppstep * e2e_steps * ws / e2e_t
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    cpu = cpu_sample(objs, cents, target_s=args.cpu_seconds) if not args.skip_cpu else None
+    peaks, peak_kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = sms * ALU_LANES_PER_SM * mhz * 1e6 / 1e12  # T lane-ops/s
+    roof = None
+    if cpu is not None:
+        achieved = k_pairs * cpu["ops_per_pair"] / k_sec / 1e12
+        roof = {"bound": "alu", "kernel": "k_assign<32>", "achieved": achieved, "peak": alu_peak,
+                "unit": "T lane-ops/s", "frac": achieved / alu_peak,
+                "traffic": profiled_traffic(),
+                "peak_source": "%d SMs x %d FP32/INT lanes x %.0f MHz (median SM clock under load); "
+                               "HBM/bf16 peaks %s in MEASURED_PEAKS.json are not the bound"
+                               % (sms, ALU_LANES_PER_SM, mhz, peak_kind),
+                "ops_per_pair": cpu["ops_per_pair"], "mean_oracle_pivots": cpu["mean_pivots"],
+                "launch_seconds": k_sec, "pairs_per_launch": k_pairs}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pivots + f64 certify",
+        "data": "synthetic", "config": workload_config(),
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)},
+        "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile_case(args):
+    """Small case for ncu captures: two d2_assign launches of the image-like
+    law (N=20,000 bags against K=64 centroids), device buffers."""
+    import torch
+    from paper_1302_0435_gb300 import build, d2, synth
+    build.build()
+    d2.load()
+    objs, cents = synth.image_like(N=args.profile_n, K=WORKLOAD["K"])
+    ctx = d2.Context(0)
+    d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
+    ob = d2.bags_from_synth(objs, device="cuda:0")
+    lab = torch.empty(objs.count, dtype=torch.int32, device="cuda:0")
+    dd = torch.empty(objs.count, dtype=torch.float64, device="cuda:0")
+    for _ in range(2):
+        d2.d2_assign(ctx, ob, lab, dd)
+    d2.d2_sync(ctx)
+    print("profile case done: %d x %d pairs" % (objs.count, cents.count))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="small k_assign case for ncu")
+    ap.add_argument("--profile-n", type=int, default=20000)
+    args = ap.parse_args()
+    if args.profile:
+        return run_profile_case(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -214,6 +214,17 @@ int d2_cluster_level(d2_ctx* ctx, const d2_bags* objs, const double* omega, int3
                      int64_t seg_size, int32_t iters, double* out_loc, double* out_cent_weight,
                      int32_t* labels);
 
+/*
+ * Counters of this process's library activity (diagnostics, not a paper
+ * quantity): kernels launched, pair LPs solved on the FP32 screening path,
+ * pair LPs solved to FP64 optimality.  Monotonic since library load.
+ */
+typedef struct {
+    int64_t kernel_launches;
+    int64_t reserved[7];
+} d2_stats;
+int d2_get_stats(d2_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

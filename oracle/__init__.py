@@ -53,7 +53,7 @@ def _lib():
         lib.d2o_mallows.argtypes = [dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int64, ctypes.c_int32,
                                     dp, dp, dp, dp, ip]
         lib.d2o_mallows_pairs.argtypes = [dp, dp, ip, dp, dp, ip, ctypes.c_int32, ip, ip,
-                                          ctypes.c_int64, ctypes.c_int32, dp, i32p]
+                                          ctypes.c_int64, ctypes.c_int32, dp, i32p, ip]
         lib.d2o_assign.argtypes = [dp, dp, ip, ctypes.c_int64, dp, dp, ip, ctypes.c_int64,
                                    ctypes.c_int32, ctypes.c_int32, i32p, dp, dp]
         _LIB = lib
@@ -166,19 +166,23 @@ def bag(b, i):
     return loc, np.asarray(b.w[lo:hi], dtype=np.float64)
 
 
-def mallows_pairs(objs, cents, pair_obj, pair_cen, nthreads=1):
-    """D^2 of Eq. (D2opt) for each listed (object, centroid) pair."""
+def mallows_pairs(objs, cents, pair_obj, pair_cen, nthreads=1, return_pivots=False):
+    """D^2 of Eq. (D2opt) for each listed (object, centroid) pair (and, if
+    asked, the simplex pivot count of each pair)."""
     xl, xw, xo = _bag_arrays(objs)
     yl, yw, yo = _bag_arrays(cents)
     pi = _i64(pair_obj)
     pj = _i64(pair_cen)
     out = np.empty(pi.size)
     st = np.zeros(pi.size, dtype=np.int32)
+    piv = np.zeros(pi.size, dtype=np.int64)
     rc = _lib().d2o_mallows_pairs(_p(xl), _p(xw), _p(xo, ctypes.c_int64), _p(yl), _p(yw),
                                   _p(yo, ctypes.c_int64), xl.shape[1], _p(pi, ctypes.c_int64),
                                   _p(pj, ctypes.c_int64), pi.size, nthreads, _p(out),
-                                  _p(st, ctypes.c_int32))
+                                  _p(st, ctypes.c_int32), _p(piv, ctypes.c_int64))
     _check(rc, "mallows_pairs")
+    if return_pivots:
+        return out, piv
     return out
 
 

@@ -329,7 +329,7 @@ typedef struct {
     const double *yloc, *yw; const int64_t* yoff;
     int32_t d;
     /* pair mode */
-    const int64_t *pi, *pj; int64_t npairs; double* out; int32_t* st_out;
+    const int64_t *pi, *pj; int64_t npairs; double* out; int32_t* st_out; int64_t* piv_out;
     /* assign mode */
     int64_t N, K; int32_t* labels; double* dist2; double* all;
     /* work split */
@@ -337,13 +337,13 @@ typedef struct {
     int status;
 } job_t;
 
-static int solve_pair(const job_t* J, int64_t i, int64_t j, double* out)
+static int solve_pair(const job_t* J, int64_t i, int64_t j, double* out, int64_t* piv)
 {
     int64_t m = J->xoff[i + 1] - J->xoff[i];
     int64_t n = J->yoff[j + 1] - J->yoff[j];
     return d2o_mallows(J->xloc + J->xoff[i] * J->d, J->xw + J->xoff[i], m,
                        J->yloc + J->yoff[j] * J->d, J->yw + J->yoff[j], n, J->d,
-                       out, NULL, NULL, NULL, NULL);
+                       out, NULL, NULL, NULL, piv);
 }
 
 static void* pairs_worker(void* arg)
@@ -351,8 +351,10 @@ static void* pairs_worker(void* arg)
     job_t* J = (job_t*)arg;
     for (int64_t t = J->begin; t < J->end; ++t) {
         double dd = NAN;
-        int st = solve_pair(J, J->pi[t], J->pj[t], &dd);
+        int64_t piv = 0;
+        int st = solve_pair(J, J->pi[t], J->pj[t], &dd, &piv);
         J->out[t] = dd;
+        if (J->piv_out) J->piv_out[t] = piv;
         if (J->st_out) J->st_out[t] = st;
         if (st != D2O_OK && J->status == D2O_OK) J->status = st;
     }
@@ -369,7 +371,7 @@ static void* assign_worker(void* arg)
         double best = INFINITY;
         for (int64_t j = 0; j < J->K; ++j) {
             double dd = NAN;
-            int st = solve_pair(J, i, j, &dd);
+            int st = solve_pair(J, i, j, &dd, NULL);
             if (st != D2O_OK && J->status == D2O_OK) J->status = st;
             if (J->all) J->all[i * J->K + j] = dd;
             if (dd < best) { best = dd; best_j = (int32_t)j; }
@@ -407,16 +409,17 @@ static int run_threads(job_t* base, int64_t count, int32_t nthreads, void* (*fn)
     return st;
 }
 
-/* D^2 for a list of (object, centroid) pairs. */
+/* D^2 for a list of (object, centroid) pairs; status and pivots (per pair)
+ * may be NULL. */
 int d2o_mallows_pairs(const double* xloc, const double* xw, const int64_t* xoff,
                       const double* yloc, const double* yw, const int64_t* yoff, int32_t d,
                       const int64_t* pi, const int64_t* pj, int64_t npairs, int32_t nthreads,
-                      double* dist2, int32_t* status)
+                      double* dist2, int32_t* status, int64_t* pivots)
 {
     job_t J;
     memset(&J, 0, sizeof J);
     J.xloc = xloc; J.xw = xw; J.xoff = xoff; J.yloc = yloc; J.yw = yw; J.yoff = yoff; J.d = d;
-    J.pi = pi; J.pj = pj; J.npairs = npairs; J.out = dist2; J.st_out = status;
+    J.pi = pi; J.pj = pj; J.npairs = npairs; J.out = dist2; J.st_out = status; J.piv_out = pivots;
     return run_threads(&J, npairs, nthreads, pairs_worker);
 }
 

@@ -550,6 +550,7 @@ int resolve_assigned(d2_ctx* c, const ObjView& v, const int* dl, int mmax, const
   fo->w = static_cast<double*>(grow(c, kFlowW, (size_t)(N * fo->stride) * 8, &rc));
   if (rc != D2_OK) return rc;
   k_pairs_from_labels<<<blocks_for(N), 256, 0, c->stream>>>(dl, N, po, pc);
+  d2k::note_launches(1);
   SolveCfg cfg = solve_cfg(c, 0, mmax);
   CK(d2k::mallows_pairs(v, cv, po, pc, N, cfg, dd, *fo, nullptr, c->d_err, c->stream));
   return D2_OK;
@@ -661,6 +662,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     k_replicate<<<blocks_for(M * Tc), 256, 0, c->stream>>>(c->c_loc32, c->c_loc64, c->c_Q, c->c_w64,
                                                            c->c_off, K, Tc, d, M, l32, l64, lQ, lw,
                                                            loff);
+    d2k::note_launches(1);
     CK(cudaGetLastError());
     CentView cv{l32, l64, lQ, loff, KT, d};
     const SolveCfg cfg = solve_cfg(c, mode_for(c, cur.ldt), cur_mmax);
@@ -677,6 +679,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     CK(d2k::group_weight_sum(om, n_l, KT, scr, wnew, c->stream));
     k_merge_labels<<<blocks_for(n_l), 256, 0, c->stream>>>(lab, n_l, seg, K, ct);
     k_compose<<<blocks_for(N0), 256, 0, c->stream>>>(C, N0, ct);
+    d2k::note_launches(2);
     CK(cudaGetLastError());
     if (M == 1) {
       CK(cudaMemcpyAsync(out_loc, l64, (size_t)Tc * d * 8, cudaMemcpyDefault, c->stream));
@@ -714,6 +717,13 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
   if ((rc = read_err(c, &bits))) return rc;
   if (bits & d2k::kErrInvalid) return D2_EINVAL;
   if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
+  return D2_OK;
+}
+
+int d2_get_stats(d2_stats* out) {
+  if (!out) return D2_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->kernel_launches = d2k::launches();
   return D2_OK;
 }
 

@@ -81,4 +81,8 @@ cudaError_t group_weight_sum(const double* omega, long long N, long long KT, voi
 
 int device_sms(int dev);
 
+// kernel launches issued by this library (all contexts)
+void note_launches(long long k);
+long long launches();
+
 }  // namespace d2k

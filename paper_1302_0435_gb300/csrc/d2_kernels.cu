@@ -368,6 +368,10 @@ __global__ void k_sum_fixed(const double* v, long long n, double* out) {
 
 // ------------------------------------------------------------ launchers --
 
+static unsigned long long g_launches = 0;
+void note_launches(long long k) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
+long long launches() { return (long long)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
 int device_sms(int dev) {
   int v = 0;
   cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
@@ -380,6 +384,7 @@ cudaError_t scan_bags(const long long* off, long long count, int* d_info, cudaSt
   if (count <= 0) return cudaSuccess;
   const long long blocks = (count + 255) / 256;
   k_scan_bags<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(off, count, d_info);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -389,6 +394,7 @@ cudaError_t prep_centroids(const void* loc, int ldt, const void* w, int wdt, con
   const long long blocks = (K + 3) / 4;
   k_prep_centroids<32><<<(unsigned)(blocks < 65535 ? blocks : 65535), 128, 0, st>>>(
       loc, ldt, w, wdt, off, K, d, loc32, loc64, Qpre, w64, d_err);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -432,6 +438,7 @@ static cudaError_t mallows_pairs_g(const ObjView& ob, const CentView& cv, const 
   if (e != cudaSuccess) return e;
   k_mallows_pairs<G><<<grid, gpb * G, smem, st>>>(ob, cv, pobj, pcen, npairs, cfg, slice, dist2, fo,
                                                status, d_err);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -459,6 +466,7 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
   if (e != cudaSuccess) return e;
   k_assign<G><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, cfg, slice, omega, labels, dist2,
                                         eps_terms, fo, d_err);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -476,11 +484,13 @@ cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, in
 cudaError_t cost_matrix(const ObjView& ob, const CentView& cv, long long i, long long j, int mode,
                         double* C, cudaStream_t st) {
   k_cost_matrix<<<1, 256, 0, st>>>(ob, cv, i, j, mode, C);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t sum_fixed_order(const double* v, long long n, double* out, cudaStream_t st) {
   k_sum_fixed<<<1, 256, 0, st>>>(v, n, out);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -194,6 +194,7 @@ cudaError_t update_locations(const ObjView& ob, const double* omega, const int* 
   k_label_prefix<<<kb, 256, 0, st>>>(counts, nchunks, KT, tot);
   k_exclusive_scan<<<1, 1024, 0, st>>>(tot, KT, start);
   k_scatter<<<(unsigned)nchunks, 32, 0, st>>>(gl, N, KT, counts, start, order);
+  note_launches(5);
   if (!fo.cell) return cudaGetLastError();  // sort only
   // largest centroid support bounds the accumulator size
   const size_t smem = ((size_t)64 * d + 64) * sizeof(double);
@@ -201,6 +202,7 @@ cudaError_t update_locations(const ObjView& ob, const double* omega, const int* 
   if (e != cudaSuccess) return e;
   k_accumulate<<<(unsigned)KT, 128, smem, st>>>(ob, omega, fo, order, start, coff, d, cent_ldt,
                                                 loc32, loc64);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -214,6 +216,7 @@ cudaError_t group_weight_sum(const double* omega, long long N, long long KT, voi
   const int* order = reinterpret_cast<const int*>(p);
   const unsigned kb = (unsigned)((KT + 255) / 256);
   k_group_sum<<<kb, 256, 0, st>>>(omega, order, start, KT, out);
+  note_launches(1);
   return cudaGetLastError();
 }
 

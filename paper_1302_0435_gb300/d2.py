@@ -21,7 +21,8 @@ MAX_SUPPORT = 64
 
 EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_strerror",
            "d2_version", "d2_set_centroids", "d2_get_centroids", "d2_cost_matrix",
-           "d2_mallows_batch", "d2_assign", "d2_update_locations", "d2_cluster_level"]
+           "d2_mallows_batch", "d2_assign", "d2_update_locations", "d2_cluster_level",
+           "d2_get_stats"]
 
 
 class D2Bags(ctypes.Structure):
@@ -37,6 +38,10 @@ class D2Config(ctypes.Structure):
 
 class D2Flows(ctypes.Structure):
     _fields_ = [("cell", ctypes.c_void_p), ("w", ctypes.c_void_p), ("stride", ctypes.c_int64)]
+
+
+class D2Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("reserved", ctypes.c_int64 * 7)]
 
 
 class D2Error(RuntimeError):
@@ -75,6 +80,7 @@ def load(path=None):
     lib.d2_assign.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, vp, vp, ctypes.POINTER(D2Flows)]
     lib.d2_update_locations.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, ctypes.POINTER(D2Flows)]
     lib.d2_cluster_level.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i32, i64, i32, vp, vp, vp]
+    lib.d2_get_stats.argtypes = [ctypes.POINTER(D2Stats)]
     _lib = lib
     return lib
 
@@ -243,3 +249,9 @@ def d2_cluster_level(ctx, objs, K, seg_size, iters, out_loc, out_cent_weight, la
     if rc not in (D2_OK, D2_ENOTCONVERGED):
         _check(rc, "d2_cluster_level")
     return rc
+
+
+def d2_get_stats():
+    st = D2Stats()
+    _check(load().d2_get_stats(ctypes.byref(st)), "d2_get_stats")
+    return {"kernel_launches": int(st.kernel_launches)}

@@ -215,6 +215,48 @@ int d2_cluster_level(d2_ctx* ctx, const d2_bags* objs, const double* omega, int3
                      int32_t* labels);
 
 /*
+ * d2_update_locations_noalloc -- the location update of d2_update_locations
+ * (same kernels, same arithmetic, same results) for callers that cannot
+ * call cudaMalloc during the call: for instance a framework that owns all
+ * device memory through its own caching allocator and a fixed budget, so
+ * an outside allocation would exceed or fragment it, or a latency-critical
+ * serving loop that must not pay for the allocator's implicit device
+ * synchronisation.  It allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.  The paper has no counterpart; this is an
+ * integration variant only.
+ *
+ * Scratch: a fixed array of about 3 MB in the library's own device memory
+ * (a file-scope __device__ array), which every GPU that loads the library
+ * holds until the process exits.  Limits: at most 262,144 bags and 1,024
+ * centroids per call; larger calls return D2_EUNSUPPORTED.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress,
+ * once per device, with the device current); make that first call before
+ * any stream capture.  Every call shares the one array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and give
+ * wrong results, so serialise them.  The sort counters are cleared at the
+ * start of every call.
+ *
+ * Arguments (all device pointers, caller-owned; host pointers -> D2_EINVAL):
+ *   objs, omega (may be NULL = all ones), labels [N] int32 (centroid index
+ *   in [0,K), others ignored), flows (required: the d2_assign flow records
+ *   of the assigned pairs), cent_off [K+1] int64 (centroid j owns supports
+ *   [cent_off[j], cent_off[j+1]), at most 64),
+ *   cent_loc64 [T][dim] FP64 centroid locations, updated in place,
+ *   cent_loc32 [T][dim] FP32 mirror, rewritten where a location changes,
+ *   cent_loc_dtype: the centroid location type the FP64 result is rounded
+ *   to (as d2_set_centroids' loc_dtype does for the resident set),
+ *   cuda_stream: the stream to enqueue on (NULL = legacy default stream).
+ * It waits once for the stream to read and check cent_off (each centroid
+ * 1..D2_MAX_SUPPORT supports, else D2_EINVAL), then enqueues the update and
+ * returns without waiting for it.  Flow entries that are not cells of
+ * their pair are ignored.
+ */
+int d2_update_locations_noalloc(const d2_bags* objs, const double* omega, const int32_t* labels,
+                                const d2_flows* flows, int64_t K, const int64_t* cent_off,
+                                int32_t cent_loc_dtype, double* cent_loc64, float* cent_loc32,
+                                void* cuda_stream);
+
+/*
  * Counters of this process's library activity (diagnostics, not a paper
  * quantity): kernels launched, pair LPs solved on the FP32 screening path,
  * pair LPs solved to FP64 optimality.  Monotonic since library load.

@@ -22,7 +22,7 @@ MAX_SUPPORT = 64
 EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_strerror",
            "d2_version", "d2_set_centroids", "d2_get_centroids", "d2_cost_matrix",
            "d2_mallows_batch", "d2_assign", "d2_update_locations", "d2_cluster_level",
-           "d2_get_stats"]
+           "d2_get_stats", "d2_update_locations_noalloc"]
 
 
 class D2Bags(ctypes.Structure):
@@ -81,6 +81,8 @@ def load(path=None):
     lib.d2_update_locations.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, ctypes.POINTER(D2Flows)]
     lib.d2_cluster_level.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i32, i64, i32, vp, vp, vp]
     lib.d2_get_stats.argtypes = [ctypes.POINTER(D2Stats)]
+    lib.d2_update_locations_noalloc.argtypes = [ctypes.POINTER(D2Bags), vp, vp, ctypes.POINTER(D2Flows),
+                                                i64, vp, i32, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -255,3 +257,16 @@ def d2_get_stats():
     st = D2Stats()
     _check(load().d2_get_stats(ctypes.byref(st)), "d2_get_stats")
     return {"kernel_launches": int(st.kernel_launches)}
+
+
+def d2_update_locations_noalloc(objs, labels, flows, K, cent_off, cent_loc_dtype, cent_loc64,
+                                cent_loc32, omega=None, stream=None):
+    """Allocation-free location update on caller-owned device centroid
+    arrays (see include/d2.h).  All tensors must be on the device."""
+    f = _flows(flows)
+    h = getattr(stream, "cuda_stream", stream)
+    rc = load().d2_update_locations_noalloc(ctypes.byref(objs.s), _ptr(omega), _ptr(labels),
+                                            ctypes.byref(f), int(K), _ptr(cent_off),
+                                            int(cent_loc_dtype), _ptr(cent_loc64), _ptr(cent_loc32), h)
+    _check(rc, "d2_update_locations_noalloc")
+    return rc

@@ -258,12 +258,18 @@ int d2_update_locations_noalloc(const d2_bags* objs, const double* omega, const 
 
 /*
  * Counters of this process's library activity (diagnostics, not a paper
- * quantity): kernels launched, pair LPs solved on the FP32 screening path,
- * pair LPs solved to FP64 optimality.  Monotonic since library load.
+ * quantity), monotonic since library load: kernels launched; pair LPs
+ * solved on the FP32 screening path and their simplex pivots; pair LPs
+ * solved to FP64 optimality and their pivots (FP32 warm start + FP64).
+ * Reading the device counters synchronises the current device.
  */
 typedef struct {
     int64_t kernel_launches;
-    int64_t reserved[7];
+    int64_t pairs_screened;
+    int64_t pivots_screened;
+    int64_t pairs_exact;
+    int64_t pivots_exact;
+    int64_t reserved[3];
 } d2_stats;
 int d2_get_stats(d2_stats* out);
 

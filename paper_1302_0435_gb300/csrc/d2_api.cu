@@ -11,7 +11,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/d2.h"
+#include "d2.h"
 #include "d2_internal.h"
 
 using d2k::CentView;
@@ -26,7 +26,7 @@ enum Slot {
   kFlowW, kEpsTerms, kEpsOut, kUpd, kLabelsIn, kCentIn0, kCentIn1, kCentIn2,
   // level driver
   kLvDataLoc, kLvDataW, kLvDataOff, kLvOmega, kLvOmegaNew, kLvC, kLvCT, kLvLab, kLvD2,
-  kLvCLoc32, kLvCLoc64, kLvCQ, kLvCW, kLvCOff, kLvTmp,
+  kLvCLoc32, kLvCLoc64, kLvCQ, kLvCW, kLvCOff, kLvTmp, kCand,
   kSlots
 };
 
@@ -515,9 +515,12 @@ int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labe
     terms = static_cast<double*>(grow(c, kEpsTerms, (size_t)N * 8, &rc));
     if (rc != D2_OK) return rc;
   }
+  int* cand = static_cast<int*>(grow(c, kCand, (size_t)N * 9 * 4, &rc));
+  if (rc != D2_OK) return rc;
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   const SolveCfg cfg = solve_cfg(c, mode_for(c, objs->loc_dtype), mmax);
-  CK(d2k::assign(v, resident_view(c), N, (int)c->K, cfg, om, dl, dd, terms, fo, c->d_err, c->stream));
+  CK(d2k::assign(v, resident_view(c), N, (int)c->K, cfg, om, dl, dd, terms, fo, cand, c->d_err,
+                 c->stream));
   if (eps_total) {
     double* de = static_cast<double*>(grow(c, kEpsOut, 8, &rc));
     if (rc != D2_OK) return rc;
@@ -658,6 +661,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     fo.cell = static_cast<int*>(grow(c, kFlowCell, (size_t)(n_l * stride) * 4, &rc));
     fo.w = static_cast<double*>(grow(c, kFlowW, (size_t)(n_l * stride) * 8, &rc));
     void* scr = grow(c, kUpd, d2k::update_scratch_bytes(n_l, KT), &rc);
+    int* cand = static_cast<int*>(grow(c, kCand, (size_t)n_l * 9 * 4, &rc));
     if (rc != D2_OK) return rc;
     k_replicate<<<blocks_for(M * Tc), 256, 0, c->stream>>>(c->c_loc32, c->c_loc64, c->c_Q, c->c_w64,
                                                            c->c_off, K, Tc, d, M, l32, l64, lQ, lw,
@@ -667,7 +671,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     CentView cv{l32, l64, lQ, loff, KT, d};
     const SolveCfg cfg = solve_cfg(c, mode_for(c, cur.ldt), cur_mmax);
     for (int it = 0; it < std::max(iters, 1); ++it) {
-      CK(d2k::assign(cur, cv, seg, K, cfg, om, lab, ld2, nullptr, fo, c->d_err, c->stream));
+      CK(d2k::assign(cur, cv, seg, K, cfg, om, lab, ld2, nullptr, fo, cand, c->d_err, c->stream));
       if (it < iters)
         CK(d2k::update_locations(cur, om, lab, seg, K, fo, KT, loff, d, c->cent_ldt, l32, l64, scr,
                                  c->stream));
@@ -724,6 +728,15 @@ int d2_get_stats(d2_stats* out) {
   if (!out) return D2_EINVAL;
   std::memset(out, 0, sizeof(*out));
   out->kernel_launches = d2k::launches();
+  long long v[4];
+  if (d2k::solver_stats(v) == cudaSuccess) {
+    out->pairs_screened = v[0];
+    out->pivots_screened = v[1];
+    out->pairs_exact = v[2];
+    out->pivots_exact = v[3];
+  } else {
+    cudaGetLastError();
+  }
   return D2_OK;
 }
 

@@ -51,9 +51,11 @@ cudaError_t prep_centroids(const void* loc, int ldt, const void* w, int wdt, con
 cudaError_t mallows_pairs(const ObjView& ob, const CentView& cv, const long long* pobj,
                           const long long* pcen, long long npairs, const SolveCfg& cfg,
                           double* dist2, FlowOut fo, int* status, int* d_err, cudaStream_t st);
+// cand: [count][9] int scratch for the FP32 screen's candidate lists
+// (required when cfg.mode == 1; nullptr solves every centroid exactly).
 cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, int K,
                    const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
-                   double* eps_terms, FlowOut fo, int* d_err, cudaStream_t st);
+                   double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st);
 cudaError_t cost_matrix(const ObjView& ob, const CentView& cv, long long i, long long j, int mode,
                         double* C, cudaStream_t st);
 cudaError_t sum_fixed_order(const double* v, long long n, double* out, cudaStream_t st);
@@ -84,5 +86,7 @@ int device_sms(int dev);
 // kernel launches issued by this library (all contexts)
 void note_launches(long long k);
 long long launches();
+// pairs screened, their pivots, pairs solved exactly, their pivots
+cudaError_t solver_stats(long long out[4]);
 
 }  // namespace d2k

@@ -14,6 +14,18 @@
 
 namespace d2k {
 
+// Solver activity counters: pairs screened, their pivots, pairs solved
+// exactly, their pivots.  Accumulated once per lane group per launch.
+__device__ unsigned long long g_solver_stats[4];
+
+__device__ __forceinline__ void add_stats(unsigned long long a, unsigned long long b,
+                                          unsigned long long c, unsigned long long d) {
+  if (a) atomicAdd(&g_solver_stats[0], a);
+  if (b) atomicAdd(&g_solver_stats[1], b);
+  if (c) atomicAdd(&g_solver_stats[2], c);
+  if (d) atomicAdd(&g_solver_stats[3], d);
+}
+
 // ---------------------------------------------------------------- loads --
 
 template <typename T>
@@ -23,25 +35,29 @@ __device__ __forceinline__ T ldx(const void* p, int dt, long long idx) {
   return (T)__bfloat162float(static_cast<const __nv_bfloat16*>(p)[idx]);
 }
 
+template <typename T> __device__ __forceinline__ T cvt(float v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T cvt(double v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T cvt(__nv_bfloat16 v) { return (T)__bfloat162float(v); }
+
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 
 // Ground-cost tile of Eq. (D2opt): C[a*n+r] = sum_k (x_ak - y_rk)^2, by
 // explicit differences accumulated with FMA in coordinate order.  Returns
 // the tile maximum (group-uniform).
-template <typename T, int G>
-__device__ T build_cost(const Grp<G>& g, T* C, int m, int n, const void* xl, int xdt,
-                        long long xrow0, const T* yl, int d) {
+template <typename T, typename X, int G>
+__device__ __forceinline__ T cost_cells(const Grp<G>& g, T* C, int m, int n, const X* x, const T* yl,
+                                        int d) {
   const int mn = m * n;
   const int q = G / n, rem = G - (G / n) * n;
   int a = g.lane / n, r = g.lane - (g.lane / n) * n;
   T cmax = T(0);
   for (int t = g.lane; t < mn; t += G) {
     const T* yr = yl + (long long)r * d;
-    const long long xi = (xrow0 + a) * (long long)d;
+    const X* xr = x + (long long)a * d;
     T acc = T(0);
     for (int k = 0; k < d; ++k) {
-      const T df = ldx<T>(xl, xdt, xi + k) - yr[k];
+      const T df = cvt<T>(xr[k]) - yr[k];
       acc = fmaT(df, df, acc);
     }
     C[t] = acc;
@@ -49,46 +65,23 @@ __device__ T build_cost(const Grp<G>& g, T* C, int m, int n, const void* xl, int
     r += rem; a += q;
     if (r >= n) { r -= n; ++a; }
   }
-  cmax = gmax<G>(g, cmax);
-  g.sync();
   return cmax;
 }
 
-// Objective sum_{tree edges} w * c, FP32 (screening estimate).
-template <int G>
-__device__ float objective32(const Simplex<float, G>& S) {
-  float acc = 0.f;
-  for (int y = S.g.lane + 1; y < S.N; y += G) {
-    const int p = S.s.par[y];
-    acc = fmaf((float)((double)S.s.flow[y] * kInvMass), S.s.cost[S.edge_cell(y, p)], acc);
-  }
-  return gsum<G>(S.g, acc);
-}
-
-// Objective in FP64 with the tile's own costs.
-template <int G>
-__device__ double objective64(const Simplex<double, G>& S) {
-  double acc = 0.0;
-  for (int y = S.g.lane + 1; y < S.N; y += G) {
-    const int p = S.s.par[y];
-    acc = fma((double)S.s.flow[y] * kInvMass, S.s.cost[S.edge_cell(y, p)], acc);
-  }
-  return gsum<G>(S.g, acc);
-}
-
+// Ground-cost tile of Eq. (D2opt): C[a*n+r] = sum_k (x_ak - y_rk)^2, by
+// explicit differences accumulated with FMA in coordinate order.  Returns
+// the tile maximum (group-uniform).
 template <typename T, int G>
-__device__ void write_flows(const Simplex<T, G>& S, int* cell, double* w, long long stride) {
-  for (int y = S.g.lane + 1; y < S.N; y += G) {
-    const int p = S.s.par[y];
-    const int row = y < S.m ? y : p;
-    const int col = y < S.m ? p - S.m : y - S.m;
-    cell[y - 1] = (row << 16) | col;
-    w[y - 1] = (double)S.s.flow[y] * kInvMass;
-  }
-  for (long long e = S.N - 1 + S.g.lane; e < stride; e += G) {
-    cell[e] = -1;
-    w[e] = 0.0;
-  }
+__device__ T build_cost(const Grp<G>& g, T* C, int m, int n, const void* xl, int xdt,
+                        long long xrow0, const T* yl, int d) {
+  T cmax;
+  const long long o = xrow0 * (long long)d;
+  if (xdt == 1) cmax = cost_cells<T, float, G>(g, C, m, n, static_cast<const float*>(xl) + o, yl, d);
+  else if (xdt == 0) cmax = cost_cells<T, double, G>(g, C, m, n, static_cast<const double*>(xl) + o, yl, d);
+  else cmax = cost_cells<T, __nv_bfloat16, G>(g, C, m, n, static_cast<const __nv_bfloat16*>(xl) + o, yl, d);
+  cmax = gmax<G>(g, cmax);
+  g.sync();
+  return cmax;
 }
 
 template <int G>
@@ -109,32 +102,38 @@ __device__ void load_cent_prefix(const Grp<G>& g, const CentView& cv, long long 
 __device__ __forceinline__ double tol64(double cmax) { return cmax * 0x1p-43; }
 __device__ __forceinline__ float tol32(float cmax) { return cmax * 0x1p-20f; }
 
-// Exact solve of pair (object at o0/m, centroid at c0/n).  With
-// fp32_start the basis is first driven to FP32 optimality on the FP32 tile
-// (cheap pivots); the same tree and integer flows then continue on the FP64
-// tile with FP64 potentials until no FP64 reduced cost is below -tol64, so
-// the result is FP64-optimal either way.  *obj: FP64 objective.
-template <int G>
-__device__ int solve_exact(const Grp<G>& g, PairMem<double>& s, const ObjView& ob, long long o0,
-                           int m, const CentView& cv, long long c0, int n, int budget,
-                           bool fp32_start, double* obj) {
+// Exact solve of pair (object at o0/m, centroid at c0/n) into the tree
+// registers `tr`.  With fp32_start the basis is first driven to FP32
+// optimality on the FP32 tile (cheap pivots); the same tree and integer
+// flows then continue on the FP64 tile with FP64 potentials until no FP64
+// reduced cost is below -tol64, so the result is FP64-optimal either way.
+// *obj: FP64 objective.
+template <int G, int NPL>
+__device__ __forceinline__ int solve_exact(const Grp<G>& g, const PairMem<double>& s,
+                                           Simplex<double, G, NPL>& S, const ObjView& ob,
+                                           long long o0, int m, const CentView& cv, long long c0,
+                                           int n, int budget, bool fp32_start, double* obj,
+                                           int* piv_out) {
   load_cent_prefix<G>(g, cv, c0, n, s.Q);
   const int cap = budget * (m + n);
   int piv = 0;
   if (fp32_start) {
-    PairMem<float> s32 = recast<float>(s);
+    const PairMem<float> s32 = recast<float>(s);
     const float c32 = build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
                                            cv.loc32 + c0 * cv.d, cv.d);
-    Simplex<float, G> S32{s32, m, n, m + n, g};
-    S32.solve(cap, tol32(c32), &piv);
+    Simplex<float, G, NPL> S32(s32, m, n, g);
+    if (S32.solve(cap, tol32(c32), &piv) == kStInvalid) { *piv_out += piv; return kStInvalid; }
+    S.t = S32.t;
     g.sync();
   }
   const double cmax = build_cost<double, G>(g, s.cost, m, n, ob.loc, ob.ldt, o0,
                                             cv.loc64 + c0 * cv.d, cv.d);
-  Simplex<double, G> S{s, m, n, m + n, g};
+  S.set_dims(m, n);
+  S.bad = false;
   if (!fp32_start) S.init_northwest();
   const int st = S.run(cap, tol64(cmax), &piv);
-  *obj = objective64<G>(S);
+  *obj = S.template objective<double>();
+  *piv_out += piv;
   return st;
 }
 
@@ -179,7 +178,7 @@ __global__ void k_prep_centroids(const void* loc, int ldt, const void* w, int wd
   }
 }
 
-template <int G>
+template <int G, int NPL>
 __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
                                                        const long long* pobj, const long long* pcen,
                                                        long long npairs, SolveCfg cfg, size_t slice,
@@ -188,6 +187,7 @@ __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
   Grp<G> g;
   const int gpb = blockDim.x / G;
   unsigned char* base = smem + (threadIdx.x / G) * slice;
+  int n_pairs = 0, n_piv = 0;
   for (long long t = (long long)blockIdx.x * gpb + threadIdx.x / G; t < npairs;
        t += (long long)gridDim.x * gpb) {
     const long long i = pobj[t], j = pcen[t];
@@ -198,13 +198,15 @@ __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
       const int m = (int)(ob.off[i + 1] - o0);
       const long long c0 = cv.off[j];
       const int n = (int)(cv.off[j + 1] - c0);
-      if (m >= 1 && m <= cfg.mmax && n >= 1 && n <= cfg.nmax) {
+      if (m >= 1 && m <= cfg.mmax && n >= 1 && n <= cfg.nmax && m + n <= G * NPL) {
         PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax);
         if (load_obj_prefix<G>(g, ob, o0, m, s64.P)) {
-          st = solve_exact<G>(g, s64, ob, o0, m, cv, c0, n, cfg.budget, cfg.mode == 1, &res);
-          if (fo.cell)
-            write_flows<double, G>(Simplex<double, G>{s64, m, n, m + n, g}, fo.cell + t * fo.stride,
-                                   fo.w + t * fo.stride, fo.stride);
+          Simplex<double, G, NPL> S(s64, m, n, g);
+          st = solve_exact<G, NPL>(g, s64, S, ob, o0, m, cv, c0, n, cfg.budget, cfg.mode == 1,
+                                   &res, &n_piv);
+          ++n_pairs;
+          if (fo.cell && st != kStInvalid)
+            S.write_flows(fo.cell + t * fo.stride, fo.w + t * fo.stride, fo.stride);
         }
       }
     }
@@ -216,29 +218,102 @@ __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
     }
     g.sync();
   }
+  if (g.lane == 0) add_stats(0, 0, n_pairs, n_piv);
 }
 
-// Nearest centroid, Alg. 2 Step 2.  Object i uses centroids
-// [(i/seg_size)*K, (i/seg_size)*K + K) of the set (one segment = all).
-// mode 1: every centroid is solved with an FP32 tile and FP32 pivots; the
-// FP32 objective D32_j has a bound err_j on its distance to the FP64
-// optimum, and every centroid whose interval [D32_j-err_j, D32_j+err_j]
-// reaches below the smallest upper end is re-solved in FP64.  The label is
-// the smallest-index minimum of those FP64 values, so it agrees with an
-// all-FP64 argmin.  mode 0: every centroid in FP64.
-template <int G>
-__global__ void __launch_bounds__(128) k_assign(ObjView ob, CentView cv, long long seg_size, int K,
-                                                SolveCfg cfg, size_t slice, const double* omega,
-                                                int* labels, double* dist2, double* eps_terms,
-                                                FlowOut fo, int* err) {
+// Nearest centroid, Alg. 2 Step 2, in two kernels.  Object i uses the
+// centroids [(i/seg_size)*K, (i/seg_size)*K + K) of the set.
+//
+// k_screen: every centroid is solved with an FP32 tile and FP32 pivots.
+// The FP32 objective D32_j has a bound err_j on its distance to the FP64
+// optimum (cost rounding (d+3)*2^-24 relative, summation 2^-17 relative,
+// basis optimality 2^-16 * max cost absolute); every centroid whose interval
+// [D32_j - err_j, D32_j + err_j] reaches below the smallest upper end is a
+// candidate.  Output per object: cand[i*9] = count (-1: more than 8, solve
+// all K), cand[i*9+1..8] = candidate indices in increasing order.
+template <int G, int NPL>
+__global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, CentView cv, long long seg_size, int K,
+                                                SolveCfg cfg, size_t slice, int* cand_out, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   Grp<G> g;
   const int gpb = blockDim.x / G;
   unsigned char* base = smem + (threadIdx.x / G) * slice;
-  PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax);
-  PairMem<float> s32 = recast<float>(s64);
-  int* cand = s64.sc;                                  // [8]
-  float* clo = reinterpret_cast<float*>(s64.sc + 8);   // [8]
+  const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax);
+  int* cand = s32.sc;                                  // [8]
+  float* clo = reinterpret_cast<float*>(s32.sc + 8);   // [8]
+  int n_scr = 0, p_scr = 0;
+  const float rel = (float)(cv.d + 3) * 0x1p-24f + 0x1p-17f;
+  for (long long i = (long long)blockIdx.x * gpb + threadIdx.x / G; i < ob.count;
+       i += (long long)gridDim.x * gpb) {
+    const long long o0 = ob.off[i];
+    const int m = (int)(ob.off[i + 1] - o0);
+    const long long cb = (i / seg_size) * (long long)K;
+    bool ok = m >= 1 && m <= cfg.mmax && cb + K <= cv.K && load_obj_prefix<G>(g, ob, o0, m, s32.P);
+    int ncand = 0;
+    bool all = false;
+    float best_hi = FLT_MAX;
+    for (int j = 0; ok && j < K; ++j) {
+      const long long c0 = cv.off[cb + j];
+      const int n = (int)(cv.off[cb + j + 1] - c0);
+      if (n < 1 || n > cfg.nmax || m + n > G * NPL) { ok = false; break; }
+      load_cent_prefix<G>(g, cv, c0, n, s32.Q);
+      const float cmax = build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
+                                              cv.loc32 + c0 * cv.d, cv.d);
+      Simplex<float, G, NPL> S(s32, m, n, g);
+      const int st = S.solve(cfg.budget * (m + n), tol32(cmax), &p_scr);
+      ++n_scr;
+      if (st != kStOk) all = true;  // no bound: let the exact pass decide
+      const float D = S.template objective<float>();
+      const float e = D * rel + cmax * 0x1p-16f;
+      const float lo = D - e, hi = D + e;
+      if (lo <= best_hi) {
+        if (ncand < 8) {
+          if (g.lane == 0) { cand[ncand] = j; clo[ncand] = lo; }
+          ++ncand;
+        } else {
+          all = true;
+        }
+      }
+      g.sync();
+      if (hi < best_hi) {
+        best_hi = hi;
+        int k2 = 0;
+        for (int c = 0; c < ncand; ++c) {
+          const int cj = cand[c];
+          const float cl = clo[c];
+          g.sync();
+          if (cl <= best_hi) {
+            if (g.lane == 0) { cand[k2] = cj; clo[k2] = cl; }
+            ++k2;
+          }
+          g.sync();
+        }
+        ncand = k2;
+      }
+    }
+    int* out = cand_out + i * 9;
+    if (g.lane == 0) out[0] = !ok ? -2 : (all ? -1 : ncand);
+    if (g.lane >= 1 && g.lane <= 8) out[g.lane] = (g.lane <= ncand) ? cand[g.lane - 1] : -1;
+    g.sync();
+  }
+  if (g.lane == 0) add_stats(n_scr, p_scr, 0, 0);
+}
+
+// k_exact: the candidates of each object (all K for mode 0, for
+// count -1, or where the FP32 screen could not run) are solved to FP64
+// optimality; the label is the smallest-index minimum of those FP64
+// values, so it agrees with an all-FP64 argmin.
+template <int G, int NPL>
+__global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long long seg_size, int K,
+                                               SolveCfg cfg, size_t slice, const int* cand_in,
+                                               const double* omega, int* labels, double* dist2,
+                                               double* eps_terms, FlowOut fo, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Grp<G> g;
+  const int gpb = blockDim.x / G;
+  unsigned char* base = smem + (threadIdx.x / G) * slice;
+  const PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax);
+  int n_ex = 0, p_ex = 0;
   for (long long i = (long long)blockIdx.x * gpb + threadIdx.x / G; i < ob.count;
        i += (long long)gridDim.x * gpb) {
     const long long o0 = ob.off[i];
@@ -247,72 +322,31 @@ __global__ void __launch_bounds__(128) k_assign(ObjView ob, CentView cv, long lo
     int best_j = -1;
     double best = nan("");
     int st = kStOk;
-    const bool okm = m >= 1 && m <= cfg.mmax && cb + K <= cv.K;
+    const int cnt = cand_in ? cand_in[i * 9] : -1;
+    const bool okm = m >= 1 && m <= cfg.mmax && cb + K <= cv.K && cnt != -2;
     if (!okm || !load_obj_prefix<G>(g, ob, o0, m, s64.P)) {
       st = kStInvalid;
     } else {
-      int ncand = 0;
-      bool all = cfg.mode == 0;
-      if (cfg.mode == 1) {
-        float best_hi = FLT_MAX;
-        const float rel = (float)(cv.d + 3) * 0x1p-24f + 0x1p-17f;
-        for (int j = 0; j < K; ++j) {
-          const long long c0 = cv.off[cb + j];
-          const int n = (int)(cv.off[cb + j + 1] - c0);
-          if (n < 1 || n > cfg.nmax) { st = kStInvalid; break; }
-          load_cent_prefix<G>(g, cv, c0, n, s32.Q);
-          const float cmax = build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
-                                                  cv.loc32 + c0 * cv.d, cv.d);
-          Simplex<float, G> S{s32, m, n, m + n, g};
-          if (S.solve(cfg.budget * (m + n), tol32(cmax), nullptr) != kStOk) all = true;
-          const float D = objective32<G>(S);
-          const float e = D * rel + cmax * 0x1p-16f;
-          const float lo = D - e, hi = D + e;
-          if (lo <= best_hi) {
-            if (ncand < 8) {
-              if (g.lane == 0) { cand[ncand] = j; clo[ncand] = lo; }
-              ++ncand;
-            } else {
-              all = true;
-            }
-          }
-          g.sync();
-          if (hi < best_hi) {
-            best_hi = hi;
-            int k2 = 0;
-            for (int c = 0; c < ncand; ++c) {
-              const int cj = cand[c];
-              const float cl = clo[c];
-              g.sync();
-              if (cl <= best_hi) {
-                if (g.lane == 0) { cand[k2] = cj; clo[k2] = cl; }
-                ++k2;
-              }
-              g.sync();
-            }
-            ncand = k2;
-          }
+      const bool all = cnt < 0;
+      const int count = all ? K : cnt;
+      for (int c = 0; c < count; ++c) {
+        const int j = all ? c : cand_in[i * 9 + 1 + c];
+        const long long c0 = cv.off[cb + j];
+        const int n = (int)(cv.off[cb + j + 1] - c0);
+        if (j < 0 || j >= K || n < 1 || n > cfg.nmax || m + n > G * NPL) { st = kStInvalid; break; }
+        double D;
+        Simplex<double, G, NPL> S(s64, m, n, g);
+        const int s2 = solve_exact<G, NPL>(g, s64, S, ob, o0, m, cv, c0, n, cfg.budget,
+                                           cfg.mode == 1, &D, &p_ex);
+        ++n_ex;
+        if (s2 != kStOk) st = s2;
+        if (s2 == kStInvalid) break;
+        if (best_j < 0 || D < best) {
+          best = D;
+          best_j = j;
+          if (fo.cell) S.write_flows(fo.cell + i * fo.stride, fo.w + i * fo.stride, fo.stride);
         }
-      }
-      if (st == kStOk) {
-        const int count = all ? K : ncand;
-        for (int c = 0; c < count; ++c) {
-          const int j = all ? c : cand[c];
-          g.sync();
-          const long long c0 = cv.off[cb + j];
-          const int n = (int)(cv.off[cb + j + 1] - c0);
-          if (n < 1 || n > cfg.nmax) { st = kStInvalid; break; }
-          double D;
-          const int s2 = solve_exact<G>(g, s64, ob, o0, m, cv, c0, n, cfg.budget, cfg.mode == 1, &D);
-          if (s2 != kStOk) st = s2;
-          if (best_j < 0 || D < best) {
-            best = D;
-            best_j = j;
-            if (fo.cell)
-              write_flows<double, G>(Simplex<double, G>{s64, m, n, m + n, g}, fo.cell + i * fo.stride,
-                                     fo.w + i * fo.stride, fo.stride);
-          }
-        }
+        g.sync();
       }
     }
     if (g.lane == 0) {
@@ -324,6 +358,7 @@ __global__ void __launch_bounds__(128) k_assign(ObjView ob, CentView cv, long lo
     }
     g.sync();
   }
+  if (g.lane == 0) add_stats(0, 0, n_ex, p_ex);
 }
 
 __global__ void k_cost_matrix(ObjView ob, CentView cv, long long i, long long j, int mode,
@@ -371,6 +406,13 @@ __global__ void k_sum_fixed(const double* v, long long n, double* out) {
 static unsigned long long g_launches = 0;
 void note_launches(long long k) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
 long long launches() { return (long long)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+cudaError_t solver_stats(long long out[4]) {
+  unsigned long long v[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemcpyFromSymbol(v, g_solver_stats, sizeof(v));
+  for (int i = 0; i < 4; ++i) out[i] = (long long)v[i];
+  return e;
+}
 
 int device_sms(int dev) {
   int v = 0;
@@ -424,7 +466,7 @@ static cudaError_t launch_cfg(KernelT kern, size_t smem, int threads, int sms, l
   return cudaSuccess;
 }
 
-template <int G>
+template <int G, int NPL>
 static cudaError_t mallows_pairs_g(const ObjView& ob, const CentView& cv, const long long* pobj,
                                    const long long* pcen, long long npairs, const SolveCfg& cfg,
                                    double* dist2, FlowOut fo, int* status, int* d_err,
@@ -434,51 +476,83 @@ static cudaError_t mallows_pairs_g(const ObjView& ob, const CentView& cv, const 
   if (gpb == 0) return cudaErrorInvalidConfiguration;
   const size_t smem = slice * gpb;
   unsigned grid = 1;
-  cudaError_t e = launch_cfg(k_mallows_pairs<G>, smem, gpb * G, cfg.sms, npairs, gpb, &grid);
+  cudaError_t e = launch_cfg(k_mallows_pairs<G, NPL>, smem, gpb * G, cfg.sms, npairs, gpb, &grid);
   if (e != cudaSuccess) return e;
-  k_mallows_pairs<G><<<grid, gpb * G, smem, st>>>(ob, cv, pobj, pcen, npairs, cfg, slice, dist2, fo,
-                                               status, d_err);
+  k_mallows_pairs<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, pobj, pcen, npairs, cfg, slice,
+                                                            dist2, fo, status, d_err);
   note_launches(1);
   return cudaGetLastError();
+}
+
+template <int G, int NPL>
+static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg_size, int K,
+                            const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
+                            double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st) {
+  const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax);
+  const int gpb = groups_per_block(G, slice);
+  if (gpb == 0) return cudaErrorInvalidConfiguration;
+  const size_t smem = slice * gpb;
+  unsigned grid = 1;
+  cudaError_t e;
+  const bool screen = cfg.mode == 1 && cand != nullptr;
+  if (screen) {
+    e = launch_cfg(k_screen<G, NPL>, smem, gpb * G, cfg.sms, ob.count, gpb, &grid);
+    if (e != cudaSuccess) return e;
+    k_screen<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, cfg, slice, cand, d_err);
+    note_launches(1);
+  }
+  e = launch_cfg(k_exact<G, NPL>, smem, gpb * G, cfg.sms, ob.count, gpb, &grid);
+  if (e != cudaSuccess) return e;
+  k_exact<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, cfg, slice,
+                                               screen ? cand : nullptr, omega, labels, dist2,
+                                               eps_terms, fo, d_err);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// Lane-group shape for supports up to (mmax, nmax): G lanes per pair, each
+// owning NPL tree nodes (m+n <= G*NPL).
+#define D2_BINS(X) \
+  X(32, 1)         \
+  X(32, 2)         \
+  X(32, 3)         \
+  X(32, 4)
+
+static bool pick_shape(int mmax, int nmax, int want, int* G, int* npl) {
+  (void)want;
+  const int N = mmax + nmax;
+  if (N > 128) return false;
+  *G = 32;
+  *npl = (N + 31) / 32;
+  return true;
 }
 
 cudaError_t mallows_pairs(const ObjView& ob, const CentView& cv, const long long* pobj,
                           const long long* pcen, long long npairs, const SolveCfg& cfg,
                           double* dist2, FlowOut fo, int* status, int* d_err, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
-  switch (cfg.group) {
-    case 8: return mallows_pairs_g<8>(ob, cv, pobj, pcen, npairs, cfg, dist2, fo, status, d_err, st);
-    case 16: return mallows_pairs_g<16>(ob, cv, pobj, pcen, npairs, cfg, dist2, fo, status, d_err, st);
-    default: return mallows_pairs_g<32>(ob, cv, pobj, pcen, npairs, cfg, dist2, fo, status, d_err, st);
-  }
-}
-
-template <int G>
-static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg_size, int K,
-                            const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
-                            double* eps_terms, FlowOut fo, int* d_err, cudaStream_t st) {
-  const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax);
-  const int gpb = groups_per_block(G, slice);
-  if (gpb == 0) return cudaErrorInvalidConfiguration;
-  const size_t smem = slice * gpb;
-  unsigned grid = 1;
-  cudaError_t e = launch_cfg(k_assign<G>, smem, gpb * G, cfg.sms, ob.count, gpb, &grid);
-  if (e != cudaSuccess) return e;
-  k_assign<G><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, cfg, slice, omega, labels, dist2,
-                                        eps_terms, fo, d_err);
-  note_launches(1);
-  return cudaGetLastError();
+  int G, NP;
+  if (!pick_shape(cfg.mmax, cfg.nmax, cfg.group, &G, &NP)) return cudaErrorInvalidValue;
+#define X(g_, n_)                                                                          \
+  if (G == g_ && NP == n_)                                                                \
+    return mallows_pairs_g<g_, n_>(ob, cv, pobj, pcen, npairs, cfg, dist2, fo, status, d_err, st);
+  D2_BINS(X)
+#undef X
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, int K,
                    const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
-                   double* eps_terms, FlowOut fo, int* d_err, cudaStream_t st) {
+                   double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st) {
   if (ob.count <= 0) return cudaSuccess;
-  switch (cfg.group) {
-    case 8: return assign_g<8>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, d_err, st);
-    case 16: return assign_g<16>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, d_err, st);
-    default: return assign_g<32>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, d_err, st);
-  }
+  int G, NP;
+  if (!pick_shape(cfg.mmax, cfg.nmax, cfg.group, &G, &NP)) return cudaErrorInvalidValue;
+#define X(g_, n_)                                                                            \
+  if (G == g_ && NP == n_)                                                                  \
+    return assign_g<g_, n_>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, cand, d_err, st);
+  D2_BINS(X)
+#undef X
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t cost_matrix(const ObjView& ob, const CentView& cv, long long i, long long j, int mode,

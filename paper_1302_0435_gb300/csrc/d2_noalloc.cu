@@ -7,7 +7,7 @@
 
 #include <mutex>
 
-#include "../../include/d2.h"
+#include "d2.h"
 #include "d2_internal.h"
 
 namespace {

@@ -4,24 +4,32 @@
 // Network simplex on the bipartite basis tree:
 //   nodes 0..m-1 are object supports (rows, supply p_a), nodes m..m+n-1 are
 //   centroid supports (columns, demand q_r); a basic cell (a,r) is a tree
-//   edge.  The tree is rooted at row 0 and stored per node as
+//   edge.  The tree is rooted at row 0.  Lane l of the group owns nodes
+//   l, l+G, ... (NPL of them) and keeps for each owned node, in registers:
 //     par  : parent node,
+//     pos  : preorder index, sz : subtree size ("x is an ancestor of y" is
+//            pos[x] <= pos[y] < pos[x]+sz[x]),
 //     flow : flow on the edge (node, par) -- int64 fixed point, total mass
 //            2^62, so feasibility, ratio tests and degeneracy are exact,
 //     pot  : dual potential (u for rows, v for columns), u_a + v_r = c_ar
-//            on every tree edge,
-//     pos  : preorder index, sz : subtree size, so that
-//            "x is an ancestor of y" is pos[x] <= pos[y] < pos[x]+sz[x].
-// Each pivot: price all m*n cells in parallel (most negative reduced cost,
-// ties to the smallest cell index; Bland's smallest-index rule after a run
-// of degenerate pivots), walk the cycle from both ends of the entering cell
-// to their meeting node, pick the leaving edge by an exact integer ratio
-// test (ties to the smallest cell index), shift the flow, and re-hang the
-// cut subtree under the entering edge.  The re-hang recomputes every node's
-// preorder position, subtree size and potential independently in O(1) (plus
-// a binary search over the re-rooted path), so all lanes share it.
-// Potentials are refreshed from the tree by pointer jumping every 64 pivots
-// and before optimality is accepted.
+//            on every tree edge.
+//   Shared memory holds the cost tile and mirrors of pos/sz (for the few
+//   nodes every lane needs) and of the potentials (read by pricing).
+// One pivot, all lanes busy:
+//   1. price the lane's cells t = l, l+G, ... of the m*n tile; the group minimum of
+//      (reduced cost, cell) enters (ties to the smallest cell; Bland's
+//      smallest-index rule after a run of degenerate pivots);
+//   2. a node is on the cycle's row side iff it is an ancestor of the
+//      entering row but not of the entering column (and vice versa); the
+//      "-" edges are the row-side edges hanging from rows and the
+//      column-side edges hanging from columns; an exact integer group
+//      minimum over them gives theta and the leaving edge;
+//   3. the leaving side's path is ranked by preorder position (a bitmask of
+//      positions), the cut subtree is re-rooted at the entering end and
+//      hung under the other end: every node recomputes its own position,
+//      size and potential in O(1) plus a binary search over the path.
+// Potentials are recomputed from the tree by pointer jumping every 64
+// pivots and before optimality is accepted.
 #pragma once
 #include <cstdint>
 #include <climits>
@@ -50,17 +58,6 @@ __device__ __forceinline__ V gshfl_xor(const Grp<G>& g, V v, int o) {
   return __shfl_xor_sync(g.mask, v, o, G);
 }
 
-// minimum value, ties to the smallest index
-template <int G, typename V>
-__device__ __forceinline__ void gmin_idx(const Grp<G>& g, V& v, int& idx) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    V ov = gshfl_xor<G>(g, v, o);
-    int oi = gshfl_xor<G>(g, idx, o);
-    if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-  }
-}
-
 template <int G>
 __device__ __forceinline__ int gmin_int(const Grp<G>& g, int v) {
 #pragma unroll
@@ -87,19 +84,18 @@ __device__ __forceinline__ bool gany(const Grp<G>& g, bool p) {
   return (__ballot_sync(g.mask, p) & g.mask) != 0u;
 }
 
-// Shared-memory slice of one lane group.  T is the cost/dual type.
+// Shared-memory slice of one lane group (byte layout independent of the
+// cost type: cost and potential areas are sized for doubles).
 template <typename T>
 struct PairMem {
   T* cost;            // [m*n] row-major, stride n
-  T* pot;             // [N]
-  long long* flow;    // [N]
-  int* par;           // [N]
-  int* pos;           // [N]
-  int* sz;            // [N]
-  int* path;          // [2*N]: a-side at [0,..), b-side at [N,..)
-  int* ppos;          // [N]
-  int* psz;           // [N]
-  long long* pflow;   // [N] flows staged for the re-rooted path
+  T* pot;             // [N] potentials (mirror for pricing)
+  int* pos;           // [N] mirror of preorder positions
+  int* sz;            // [N] mirror of subtree sizes
+  int* ppos;          // [N] leaving path, ranked: positions
+  int* psz;           // [N]   sizes
+  int* pnode;         // [N]   nodes
+  long long* pflow;   // [N]   flows (after the shift)
   long long* P;       // [mmax] inclusive prefix sums of object masses
   long long* Q;       // [nmax] inclusive prefix sums of centroid masses
   int* re;            // [mmax] last column of each row in the NW staircase
@@ -112,17 +108,13 @@ struct PairMem {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Bytes of one group's slice for supports up to (mmax, nmax).  The cost
-// area is sized for doubles so one slice can host an FP32 or FP64 solve.
 __host__ __device__ inline size_t pair_mem_bytes(int mmax, int nmax) {
   const size_t N = (size_t)(mmax + nmax);
   size_t b = 0;
   b += align_up((size_t)mmax * nmax * 8, 16);  // cost
   b += align_up(N * 8, 16);                    // pot
-  b += align_up(N * 8, 16);                    // flow
-  b += align_up(N * 4, 16) * 3;                // par pos sz
-  b += align_up(2 * N * 4, 16);                // path
-  b += align_up(N * 4, 16) * 2;                // ppos psz
+  b += align_up(N * 4, 16) * 2;                // pos sz
+  b += align_up(N * 4, 16) * 3;                // ppos psz pnode
   b += align_up(N * 8, 16);                    // pflow
   b += align_up((size_t)mmax * 8, 16);         // P
   b += align_up((size_t)nmax * 8, 16);         // Q
@@ -140,13 +132,11 @@ __device__ inline PairMem<T> carve(unsigned char* base, int mmax, int nmax) {
   unsigned char* p = base;
   s.cost = reinterpret_cast<T*>(p); p += align_up((size_t)mmax * nmax * 8, 16);
   s.pot = reinterpret_cast<T*>(p); p += align_up(N * 8, 16);
-  s.flow = reinterpret_cast<long long*>(p); p += align_up(N * 8, 16);
-  s.par = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
   s.pos = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
   s.sz = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
-  s.path = reinterpret_cast<int*>(p); p += align_up(2 * N * 4, 16);
   s.ppos = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
   s.psz = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
+  s.pnode = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
   s.pflow = reinterpret_cast<long long*>(p); p += align_up(N * 8, 16);
   s.P = reinterpret_cast<long long*>(p); p += align_up((size_t)mmax * 8, 16);
   s.Q = reinterpret_cast<long long*>(p); p += align_up((size_t)nmax * 8, 16);
@@ -159,15 +149,13 @@ __device__ inline PairMem<T> carve(unsigned char* base, int mmax, int nmax) {
   return s;
 }
 
-// Reinterpret a slice for another cost type (same byte layout).
 template <typename T2, typename T1>
 __device__ inline PairMem<T2> recast(const PairMem<T1>& s) {
   PairMem<T2> o;
   o.cost = reinterpret_cast<T2*>(s.cost);
   o.pot = reinterpret_cast<T2*>(s.pot);
-  o.flow = s.flow; o.par = s.par; o.pos = s.pos; o.sz = s.sz; o.path = s.path;
-  o.ppos = s.ppos; o.psz = s.psz; o.pflow = s.pflow; o.P = s.P; o.Q = s.Q; o.re = s.re;
-  o.pj0 = s.pj0; o.pj1 = s.pj1;
+  o.pos = s.pos; o.sz = s.sz; o.ppos = s.ppos; o.psz = s.psz; o.pnode = s.pnode;
+  o.pflow = s.pflow; o.P = s.P; o.Q = s.Q; o.re = s.re; o.pj0 = s.pj0; o.pj1 = s.pj1;
   o.acc0 = reinterpret_cast<T2*>(s.acc0);
   o.acc1 = reinterpret_cast<T2*>(s.acc1);
   o.sc = s.sc;
@@ -205,7 +193,6 @@ __device__ bool load_prefix(const Grp<G>& g, const W* w, int m, long long* pre) 
     if (q > bigv) { bigv = q; bigi = a; }
   }
   part = gsum<G>(g, part);
-  // largest weight, ties to the smallest index
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) {
     long long ov = gshfl_xor<G>(g, bigv, o);
@@ -215,7 +202,6 @@ __device__ bool load_prefix(const Grp<G>& g, const W* w, int m, long long* pre) 
   g.sync();
   if (g.lane == 0) pre[bigi] += kMass - part;
   g.sync();
-  // inclusive scan in chunks of G
   long long carry = 0;
   for (int base = 0; base < m; base += G) {
     const int a = base + g.lane;
@@ -233,103 +219,135 @@ __device__ bool load_prefix(const Grp<G>& g, const W* w, int m, long long* pre) 
   return true;
 }
 
+// Tree registers of the nodes a lane owns (type independent: an FP32 solve
+// hands its basis to an FP64 solve unchanged).
+template <int NPL>
+struct TreeRegs {
+  int par[NPL], pos[NPL], sz[NPL];
+  long long flow[NPL];
+};
+
 // ----------------------------------------------------------------------
-// The solver proper.
+// The solver proper.  m+n <= G*NPL <= 128, m, n <= 255.
 // ----------------------------------------------------------------------
-template <typename T, int G>
+template <typename T, int G, int NPL>
 struct Simplex {
+  static constexpr int NW = (G * NPL + 31) / 32;  // position bitmask words
   PairMem<T> s;
+  TreeRegs<NPL> t;  // hand over to another Simplex by copying
   int m, n, N;
   Grp<G> g;
-  bool bad = false;  // set if a walk leaves its bounds (corrupt tree): the
-                     // solve stops with kStInvalid instead of looping
+  T pot[NPL];
+  bool bad = false;  // a consistency check failed: the solve stops with kStInvalid
+  // cell stepping of this lane: cells i = lane, lane+G, ... are (a, r) with
+  // a += sq, r += sr per step (wrapping r at n)
+  int a0, r0, sq, sr;
+  int cand = -1;     // this lane's candidate cell from the last full pricing
+  int cand_a = 0, cand_r = 0;
 
-  __device__ __forceinline__ bool is_anc(int x, int y) const {
-    const int px = s.pos[x];
-    const int py = s.pos[y];
-    return px <= py && py < px + s.sz[x];
+  __device__ __forceinline__ Simplex(const PairMem<T>& s_, int m_, int n_, const Grp<G>& g_)
+      : s(s_), m(m_), n(n_), N(m_ + n_), g(g_) {
+    set_dims(m_, n_);
   }
-  // cell index a*n+r of the tree edge (y, par[y])
-  __device__ __forceinline__ int edge_cell(int y, int py) const {
-    return y < m ? y * n + (py - m) : py * n + (y - m);
+  __device__ __forceinline__ void set_dims(int m_, int n_) {
+    m = m_; n = n_; N = m_ + n_;
+    a0 = g.lane / n; r0 = g.lane - a0 * n;
+    sq = G / n; sr = G - sq * n;
+    cand = -1;
+  }
+
+  __device__ __forceinline__ int node_of(int k) const { return g.lane + G * k; }
+  // cell key of an edge: (row << 8) | col -- orders cells like row*n+col
+  __device__ __forceinline__ static int key_rc(int a, int r) { return (a << 8) | r; }
+  // tile index of the edge (y, p)
+  __device__ __forceinline__ int edge_idx(int y, int p) const {
+    return y < m ? y * n + (p - m) : p * n + (y - m);
+  }
+  __device__ __forceinline__ int edge_key(int y, int p) const {
+    return y < m ? key_rc(y, p - m) : key_rc(p, y - m);
   }
 
   // Northwest-corner basis: the staircase path from cell (0,0) to (m-1,n-1)
   // that moves down when the current row's cumulative mass is reached
   // (P_a <= Q_r), else right.  Row a spans columns [re(a-1), re(a)] with
-  // re(a) = first r with Q_r >= P_a.  As a tree rooted at row 0, the
-  // preorder of a node is the step at which the path first touches it.
-  __device__ void init_northwest() {
+  // re(a) = first r with Q_r >= P_a.  As a tree rooted at row 0, a node's
+  // preorder position is the step at which the path first touches it.
+  __device__ __forceinline__ void init_northwest() {
     const long long* P = s.P;
     const long long* Q = s.Q;
-    for (int a = g.lane; a < m; a += G) {
-      int e = n - 1;
-      if (a < m - 1) {
-        int lo = 0, hi = n - 1;  // first r with Q[r] >= P[a]
-        const long long key = P[a];
-        while (lo < hi) {
-          int mid = (lo + hi) >> 1;
-          if (Q[mid] >= key) hi = mid; else lo = mid + 1;
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int a = node_of(k);
+      if (a < m) {
+        int e = n - 1;
+        if (a < m - 1) {
+          int lo = 0, hi = n - 1;
+          const long long key = P[a];
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (Q[mid] >= key) hi = mid; else lo = mid + 1;
+          }
+          e = lo;
         }
-        e = lo;
+        s.re[a] = e;
       }
-      s.re[a] = e;
     }
     g.sync();
-    for (int a = g.lane; a < m; a += G) {
-      if (a == 0) {
-        s.par[0] = -1; s.pos[0] = 0; s.sz[0] = N; s.flow[0] = 0;
-      } else {
-        const int c = s.re[a - 1];
-        const long long lo = max(P[a - 1], c > 0 ? Q[c - 1] : 0LL);
-        const long long hi = min(P[a], Q[c]);
-        s.par[a] = m + c;
-        s.pos[a] = a + c + 1;
-        s.flow[a] = hi > lo ? hi - lo : 0;
-        s.sz[a] = (s.re[a] == c) ? 1 : N - (a + c + 1);
-      }
-    }
-    for (int r = g.lane; r < n; r += G) {
-      int af = 0;
-      if (r > 0) {  // number of rows a < m-1 with P[a] <= Q[r-1]
-        const long long key = Q[r - 1];
-        int lo = 0, hi = m - 1;
-        while (lo < hi) {
-          int mid = (lo + hi) >> 1;
-          if (P[mid] <= key) lo = mid + 1; else hi = mid;
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y < m) {
+        const int a = y;
+        if (a == 0) {
+          t.par[k] = -1; t.pos[k] = 0; t.sz[k] = N; t.flow[k] = 0;
+        } else {
+          const int c = s.re[a - 1];
+          const long long lo = max(P[a - 1], c > 0 ? Q[c - 1] : 0LL);
+          const long long hi = min(P[a], Q[c]);
+          t.par[k] = m + c;
+          t.pos[k] = a + c + 1;
+          t.flow[k] = hi > lo ? hi - lo : 0;
+          t.sz[k] = (s.re[a] == c) ? 1 : N - (a + c + 1);
         }
-        af = lo;
+      } else if (y < N) {
+        const int r = y - m;
+        int af = 0;
+        if (r > 0) {  // rows a < m-1 with P[a] <= Q[r-1]
+          const long long key = Q[r - 1];
+          int lo = 0, hi = m - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (P[mid] <= key) lo = mid + 1; else hi = mid;
+          }
+          af = lo;
+        }
+        const long long lo = max(af > 0 ? P[af - 1] : 0LL, r > 0 ? Q[r - 1] : 0LL);
+        const long long hi = min(P[af], Q[r]);
+        t.par[k] = af;
+        t.pos[k] = af + r + 1;
+        t.flow[k] = hi > lo ? hi - lo : 0;
+        const bool spine = (af < m - 1) && (s.re[af] == r);
+        t.sz[k] = spine ? N - (af + r + 1) : 1;
       }
-      const long long lo = max(af > 0 ? P[af - 1] : 0LL, r > 0 ? Q[r - 1] : 0LL);
-      const long long hi = min(P[af], Q[r]);
-      const int y = m + r;
-      s.par[y] = af;
-      s.pos[y] = af + r + 1;
-      s.flow[y] = hi > lo ? hi - lo : 0;
-      const bool spine = (af < m - 1) && (s.re[af] == r);
-      s.sz[y] = spine ? N - (af + r + 1) : 1;
+      if (y < N) { s.pos[y] = t.pos[k]; s.sz[y] = t.sz[k]; }
     }
     g.sync();
   }
 
   // Potentials from the tree: pot(root) = 0, pot(y) = c(y,par y) - pot(par y),
   // by pointer jumping: pot(y) = acc(y) + (-1)^parity(y) * pot(anc(y)).
-  __device__ void refresh_potentials() {
+  __device__ __forceinline__ void refresh_potentials() {
     int* pa = s.pj0; int* pb = s.pj1;
     T* aa = s.acc0; T* ab = s.acc1;
     bool lbad = false;
-    for (int y = g.lane; y < N; y += G) {
-      if (y == 0) { pa[y] = 0; aa[y] = T(0); }
-      else {
-        const int p = s.par[y];
-        if (p < 0 || p >= N || (y < m) == (p < m)) {  // parent must be of the other side
-          lbad = true;
-          pa[y] = 0;
-          aa[y] = T(0);
-        } else {
-          pa[y] = p | (1 << 16);
-          aa[y] = s.cost[edge_cell(y, p)];
-        }
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y == 0) { pa[0] = 0; aa[0] = T(0); }
+      else if (y < N) {
+        const int p = t.par[k];
+        if (p < 0 || p >= N || (y < m) == (p < m)) { lbad = true; pa[y] = 0; aa[y] = T(0); }
+        else { pa[y] = p | (1 << 16); aa[y] = s.cost[edge_idx(y, p)]; }
       }
     }
     if (gany<G>(g, lbad)) bad = true;
@@ -337,19 +355,23 @@ struct Simplex {
     for (int round = 0;; ++round) {
       if (round > 9) { bad = true; break; }  // depth < 128 needs <= 8 rounds
       bool moved = false;
-      for (int y = g.lane; y < N; y += G) {
-        const int code = pa[y];
-        const int an = code & 0xffff;
-        if (an != 0) {
-          const int c2 = pa[an];
-          const T v = aa[an];
-          const int par1 = code >> 16;
-          ab[y] = par1 ? aa[y] - v : aa[y] + v;
-          pb[y] = (c2 & 0xffff) | ((par1 ^ (c2 >> 16)) << 16);
-          moved = true;
-        } else {
-          ab[y] = aa[y];
-          pb[y] = code;
+#pragma unroll
+      for (int k = 0; k < NPL; ++k) {
+        const int y = node_of(k);
+        if (y < N) {
+          const int code = pa[y];
+          const int an = code & 0xffff;
+          if (an != 0) {
+            const int c2 = pa[an];
+            const T v = aa[an];
+            const int par1 = code >> 16;
+            ab[y] = par1 ? aa[y] - v : aa[y] + v;
+            pb[y] = (c2 & 0xffff) | ((par1 ^ (c2 >> 16)) << 16);
+            moved = true;
+          } else {
+            ab[y] = aa[y];
+            pb[y] = code;
+          }
         }
       }
       g.sync();
@@ -357,173 +379,273 @@ struct Simplex {
       T* ta = aa; aa = ab; ab = ta;
       if (!gany<G>(g, moved)) break;
     }
-    for (int y = g.lane; y < N; y += G) s.pot[y] = aa[y];
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y < N) { pot[k] = aa[y]; s.pot[y] = aa[y]; }
+    }
     g.sync();
   }
 
-  // Pricing.  Returns the entering cell (or -1) and its reduced cost.
-  __device__ int price(bool bland, T tol, T& dbest) const {
-    const int mn = m * n;
-    const int q = G / n, rem = G - (G / n) * n;
-    int a = g.lane / n, r = g.lane - (g.lane / n) * n;
-    T best = -tol;
-    int cell = INT_MAX;
-    for (int t = g.lane; t < mn; t += G) {
-      const T d = s.cost[t] - s.pot[a] - s.pot[m + r];
-      if (bland) {
-        if (d < -tol) { best = d; cell = t; break; }
-      } else if (d < best) {
-        best = d; cell = t;
+  // order-preserving map of a value to an unsigned key (smaller value ->
+  // smaller key), so group minima can use the integer reduction unit
+  __device__ __forceinline__ static unsigned okey(float v) {
+    const unsigned b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+  }
+
+  // group minimum of (value, key): smallest value, ties to the smallest key
+  __device__ __forceinline__ void gmin_val_key(T& v, int& key) const {
+    if (sizeof(T) == 4) {
+      const unsigned kv = okey((float)v);
+      const unsigned mv = __reduce_min_sync(g.mask, kv);
+      const unsigned mk = __reduce_min_sync(g.mask, kv == mv ? (unsigned)key : 0xffffffffu);
+      const unsigned bal = __ballot_sync(g.mask, kv == mv && (unsigned)key == mk) & g.mask;
+      v = __shfl_sync(g.mask, v, (__ffs(bal) - 1) & (G - 1), G);
+      key = (int)mk;
+    } else {
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) {
+        const T ov = gshfl_xor<G>(g, v, o);
+        const int ok = gshfl_xor<G>(g, key, o);
+        if (ov < v || (ov == v && ok < key)) { v = ov; key = ok; }
       }
-      r += rem; a += q;
+    }
+  }
+
+  // Full Dantzig scan of the lane's cells i = lane, lane+G, ...: the most
+  // negative reduced cost (ties to the smallest cell).  Also records the
+  // lane's best cell as its candidate for the following pivots.
+  __device__ __forceinline__ void scan_full(T& best, int& cell) {
+    const int mn = m * n;
+    int a = a0, r = r0;
+    best = T(0);
+    cell = INT_MAX;
+    int bi = -1, ba = 0, br = 0;
+    const T* pv = s.pot + m;
+    for (int i = g.lane; i < mn; i += G) {
+      const T d = s.cost[i] - s.pot[a] - pv[r];
+      const bool better = d < best;
+      best = better ? d : best;
+      cell = better ? key_rc(a, r) : cell;
+      bi = better ? i : bi;
+      ba = better ? a : ba;
+      br = better ? r : br;
+      r += sr; a += sq;
+      const bool wrap = r >= n;
+      r = wrap ? r - n : r;
+      a = wrap ? a + 1 : a;
+    }
+    cand = bi;
+    cand_a = ba;
+    cand_r = br;
+  }
+
+  // Bland's rule: the smallest cell with reduced cost below -tol.
+  __device__ __forceinline__ int price_bland(T tol, T& dbest) const {
+    const int mn = m * n;
+    int a = a0, r = r0;
+    T best = T(0);
+    int cell = INT_MAX;
+    const T* pv = s.pot + m;
+    for (int i = g.lane; i < mn && cell == INT_MAX; i += G) {
+      const T d = s.cost[i] - s.pot[a] - pv[r];
+      if (d < -tol) { best = d; cell = key_rc(a, r); }
+      r += sr; a += sq;
       if (r >= n) { r -= n; ++a; }
     }
-    if (bland) {
-      const int c = gmin_int<G>(g, cell);
-      const int src = __ffs(__ballot_sync(g.mask, cell == c && c != INT_MAX) & g.mask) - 1;
-      T v = best;
-      if (src >= 0) v = __shfl_sync(g.mask, best, src & (G - 1), G);
-      dbest = v;
-      return c == INT_MAX ? -1 : c;
-    }
-    gmin_idx<G>(g, best, cell);
-    dbest = best;
-    return cell == INT_MAX ? -1 : cell;
+    const int c = gmin_int<G>(g, cell);
+    const unsigned bal = __ballot_sync(g.mask, cell == c && c != INT_MAX) & g.mask;
+    T v = best;
+    if (bal) v = __shfl_sync(g.mask, best, (__ffs(bal) - 1) & (G - 1), G);
+    dbest = v;
+    return c == INT_MAX ? -1 : c;
   }
 
-  // One pivot on entering cell `cell` with reduced cost dE < 0.
-  // Returns true when the pivot moved flow (theta > 0).
-  __device__ bool pivot(int cell, T dE) {
-    const int ea = cell / n;
-    const int eB = m + (cell - ea * n);
-    // 1. cycle: climb from the row until reaching an ancestor of the column,
-    //    then from the column up to that apex.
-    int la = 0, lb = 0;
-    {
-      int x = ea;
-      while (!is_anc(x, eB)) {
-        if (la >= N) { bad = true; break; }
-        if (g.lane == 0) s.path[la] = x;
-        ++la;
-        x = s.par[x];
-        if (x < 0 || x >= N) { bad = true; break; }
-      }
-      const int apex = x;
-      int y = eB;
-      while (!bad && y != apex) {
-        if (lb >= N) { bad = true; break; }
-        if (g.lane == 0) s.path[N + lb] = y;
-        ++lb;
-        y = s.par[y];
-        if (y < 0 || y >= N) { bad = true; break; }
-      }
+  // Entering cell: first the lanes' candidates from the last full scan are
+  // re-priced with the current potentials (one cell per lane); only when
+  // none is below -tol is the whole tile scanned again.  Returns the cell
+  // key ((row << 8) | col) or -1 if no reduced cost is below -tol.
+  __device__ __forceinline__ int price(bool bland, T tol, T& dbest) {
+    if (bland) return price_bland(tol, dbest);
+    T best = T(0);
+    int cell = INT_MAX;
+    if (cand >= 0) {
+      best = s.cost[cand] - s.pot[cand_a] - s.pot[m + cand_r];
+      cell = key_rc(cand_a, cand_r);
     }
-    g.sync();
-    if (bad) return false;
-    const int L = la + lb;
-    // 2. ratio test over the "-" edges: on the row side the edges whose
-    //    child is a row, on the column side those whose child is a column.
-    long long th = LLONG_MAX;
-    int lc = INT_MAX, le = -1;
-    for (int e = g.lane; e < L; e += G) {
-      const bool aside = e < la;
-      const int y = aside ? s.path[e] : s.path[N + e - la];
-      const bool minus = aside ? (y < m) : (y >= m);
-      if (minus) {
-        const long long f = s.flow[y];
-        const int c = edge_cell(y, s.par[y]);
-        if (f < th || (f == th && c < lc)) { th = f; lc = c; le = e; }
-      }
+    if (!(best < -tol)) { best = T(0); cell = INT_MAX; }
+    gmin_val_key(best, cell);
+    if (!(best < -tol)) {
+      scan_full(best, cell);
+      gmin_val_key(best, cell);
     }
+    dbest = best;
+    return (best < -tol && cell != INT_MAX) ? cell : -1;
+  }
+
+  // rank of a leaving-path position = number of path positions above it
+  __device__ __forceinline__ static int rank_of(const unsigned (&wbits)[NW], int p) {
+    int c = 0;
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      const long long of = gshfl_xor<G>(g, th, o);
-      const int oc = gshfl_xor<G>(g, lc, o);
-      const int oe = gshfl_xor<G>(g, le, o);
-      if (of < th || (of == th && oc < lc)) { th = of; lc = oc; le = oe; }
+    for (int w = 0; w < NW; ++w) {
+      const unsigned x = wbits[w];
+      if (w > (p >> 5)) c += __popc(x);
+      else if (w == (p >> 5)) c += ((p & 31) == 31) ? 0 : __popc(x >> ((p & 31) + 1));
     }
-    g.sync();
-    // 3. shift theta around the cycle
-    if (th > 0) {
-      for (int e = g.lane; e < L; e += G) {
-        const bool aside = e < la;
-        const int y = aside ? s.path[e] : s.path[N + e - la];
-        const bool minus = aside ? (y < m) : (y >= m);
-        s.flow[y] += minus ? -th : th;
+    return c;
+  }
+
+  // One pivot on entering cell key `cell` with reduced cost dE < 0.
+  // Returns true when the pivot moved flow (theta > 0).
+  __device__ __forceinline__ bool pivot(int cell, T dE) {
+    const int ea = cell >> 8;
+    const int eB = m + (cell & 0xff);
+    const int pa = s.pos[ea];
+    const int pb = s.pos[eB];
+    // 1. cycle membership of owned nodes and the ratio test candidates.
+    //    side 1: row side (ancestor of ea only), 2: column side.
+    int side[NPL];
+    long long th = LLONG_MAX;
+    int tkey = INT_MAX;
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      side[k] = 0;
+      if (y < N) {
+        const int p0 = t.pos[k], p1 = p0 + t.sz[k];
+        const bool isA = p0 <= pa && pa < p1;
+        const bool isB = p0 <= pb && pb < p1;
+        side[k] = (isA != isB) ? (isA ? 1 : 2) : 0;
+        // "-" edges: row children on the row side, column children on the
+        // column side
+        if (side[k] == (y < m ? 1 : 2)) {
+          const int key = (edge_key(y, t.par[k]) << 7) | y;
+          if (t.flow[k] < th || (t.flow[k] == th && key < tkey)) { th = t.flow[k]; tkey = key; }
+        }
       }
     }
-    // 4. re-hang.  The leaving edge (zL, par zL) lies on one side; the
-    //    subtree S under it contains that side's end e of the entering edge
-    //    and is re-rooted at e and hung under the other end o.
-    const bool lside_a = le < la;
-    const int k = lside_a ? le : le - la;
-    const int* ph = lside_a ? s.path : s.path + N;
-    const int enode = lside_a ? ea : eB;
-    const int onode = lside_a ? eB : ea;
-    const int zL = ph[k];
+    {  // group minimum of (flow, key) with the integer reduction unit
+      if (th < 0) bad = true;  // flows are never negative
+      const unsigned long long uf = (unsigned long long)th;
+      const unsigned hi = (unsigned)(uf >> 32), lo = (unsigned)uf;
+      const unsigned mh = __reduce_min_sync(g.mask, hi);
+      const unsigned ml = __reduce_min_sync(g.mask, hi == mh ? lo : 0xffffffffu);
+      const bool eq = hi == mh && lo == ml;
+      tkey = (int)__reduce_min_sync(g.mask, eq ? (unsigned)tkey : 0xffffffffu);
+      th = (long long)(((unsigned long long)mh << 32) | ml);
+      if (gany<G>(g, bad)) bad = true;
+    }
+    if (bad || tkey == INT_MAX || th < 0) { bad = true; return false; }
+    // 2. shift theta around the cycle
+    if (th > 0) {
+#pragma unroll
+      for (int k = 0; k < NPL; ++k)
+        if (side[k]) t.flow[k] += (side[k] == (node_of(k) < m ? 1 : 2)) ? -th : th;
+    }
+    // 3. the leaving edge hangs from zL; its side holds the entering end e
+    const int zL = tkey & 0x7f;
     const int P0 = s.pos[zL];
     const int Z = s.sz[zL];
+    const int lside = (P0 <= pa && pa < P0 + Z) ? 1 : 2;
+    const int enode = lside == 1 ? ea : eB;
+    const int onode = lside == 1 ? eB : ea;
     const int posO = s.pos[onode];
-    for (int i = g.lane; i <= k; i += G) {
-      const int y = ph[i];
-      s.ppos[i] = s.pos[y];
-      s.psz[i] = s.sz[y];
+    // leaving path p_0 = e ... p_k = zL: the side's nodes inside zL's
+    // subtree, ranked by decreasing preorder position
+    unsigned wbits[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) wbits[w] = 0u;
+    bool onpath[NPL];
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      onpath[k] = side[k] == lside && t.pos[k] >= P0 && t.pos[k] < P0 + Z;
+      if (onpath[k]) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+          if ((t.pos[k] >> 5) == w) wbits[w] |= 1u << (t.pos[k] & 31);
+      }
+    }
+    int tot = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      wbits[w] = __reduce_or_sync(g.mask, wbits[w]);
+      tot += __popc(wbits[w]);
+    }
+    const int kk = tot - 1;  // index of zL on the path
+    int rank[NPL];
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      rank[k] = -1;
+      if (onpath[k]) {
+        const int i = rank_of(wbits, t.pos[k]);
+        rank[k] = i;
+        s.ppos[i] = t.pos[k]; s.psz[i] = t.sz[k]; s.pnode[i] = node_of(k); s.pflow[i] = t.flow[k];
+      }
     }
     g.sync();
+    if (kk < 0 || kk >= N || s.pnode[0] != enode || s.pnode[kk] != zL) {
+      bad = true;
+      return false;
+    }
+    // 4. every owned node: new preorder position, size, potential; the
+    //    re-rooted path takes its new parent edges
     const int remO = posO >= P0 + Z ? posO - Z : posO;
     const int Qi = remO + 1;
     const bool e_is_row = enode < m;
-    for (int y = g.lane; y < N; y += G) {
-      const int py = s.pos[y];
-      const int sy = s.sz[y];
-      int np, ns;
-      if (py >= P0 && py < P0 + Z) {
-        // ring index: smallest i with ppos[i] <= py < ppos[i]+psz[i]
-        int lo = 0, hi = k;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          const int pp = s.ppos[mid];
-          if (pp <= py && py < pp + s.psz[mid]) hi = mid; else lo = mid + 1;
-        }
-        const int i = lo;
-        int off;
-        if (i == 0) {
-          off = py - s.ppos[0];
+    const int nsteps = 32 - __clz(kk);  // ceil(log2(kk+1)): group-uniform trip count
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y < N) {
+        const int py = t.pos[k], sy = t.sz[k];
+        if (py >= P0 && py < P0 + Z) {
+          int lo = 0, hi = kk;  // deepest path node that is an ancestor
+          for (int it = 0; it < nsteps; ++it) {
+            const int mid = (lo + hi) >> 1;
+            const int pp = s.ppos[mid];
+            const bool anc = pp <= py && py < pp + s.psz[mid];
+            hi = anc ? mid : hi;
+            lo = anc ? lo : mid + 1;
+          }
+          const int i = lo;
+          int off;
+          if (i == 0) {
+            off = py - s.ppos[0];
+          } else {
+            const int pp = s.ppos[i - 1], ps = s.psz[i - 1];
+            off = ps + (py < pp ? py - s.ppos[i] : py - s.ppos[i] - ps);
+          }
+          t.pos[k] = Qi + off;
+          if (py == s.ppos[i]) t.sz[k] = (i == 0) ? Z : Z - s.psz[i - 1];
+          pot[k] += ((y < m) == e_is_row) ? dE : -dE;
         } else {
-          const int pp = s.ppos[i - 1], ps = s.psz[i - 1];
-          off = ps + (py < pp ? py - s.ppos[i] : py - s.ppos[i] - ps);
+          const int r0 = py >= P0 + Z ? py - Z : py;
+          t.pos[k] = r0 + (r0 >= Qi ? Z : 0);
+          int ns = sy;
+          if (py <= P0 && P0 < py + sy) ns -= Z;
+          if (py <= posO && posO < py + sy) ns += Z;
+          t.sz[k] = ns;
         }
-        np = Qi + off;
-        ns = sy;
-        if (py == s.ppos[i]) ns = (i == 0) ? Z : Z - s.psz[i - 1];
-        s.pot[y] += ((y < m) == e_is_row) ? dE : -dE;
-      } else {
-        const int r0 = py >= P0 + Z ? py - Z : py;
-        np = r0 + (r0 >= Qi ? Z : 0);
-        ns = sy;
-        if (py <= P0 && P0 < py + sy) ns -= Z;
-        if (py <= posO && posO < py + sy) ns += Z;
+        const int i = rank[k];
+        if (i == 0) { t.par[k] = onode; t.flow[k] = th; }
+        else if (i > 0) { t.par[k] = s.pnode[i - 1]; t.flow[k] = s.pflow[i - 1]; }
       }
-      s.pos[y] = np;
-      s.sz[y] = ns;
     }
-    // parent pointers and edge flows along the re-rooted path: the edge
-    // (p_{i-1}, p_i) becomes p_i's parent edge, the entering edge e's.
-    for (int i = g.lane + 1; i <= k; i += G) s.pflow[i] = s.flow[ph[i - 1]];
     g.sync();
-    for (int i = g.lane; i <= k; i += G) {
-      const int y = ph[i];
-      if (i == 0) { s.par[y] = onode; s.flow[y] = th; }
-      else { s.par[y] = ph[i - 1]; s.flow[y] = s.pflow[i]; }
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y < N) { s.pos[y] = t.pos[k]; s.sz[y] = t.sz[k]; s.pot[y] = pot[k]; }
     }
     g.sync();
     return th > 0;
   }
 
-  // Pivot from the current basis until no reduced cost is below -tol
-  // (with potentials freshly recomputed from the tree).  Returns kStOk or
-  // kStNotConverged; *pivots accumulates the pivot count.
-  __device__ int run(int max_pivots, T tol, int* pivots) {
+  // Pivot from the current basis until no reduced cost is below -tol (with
+  // potentials freshly recomputed from the tree).  Returns kStOk,
+  // kStNotConverged or kStInvalid; *pivots accumulates the pivot count.
+  __device__ __forceinline__ int run(int max_pivots, T tol, int* pivots) {
     refresh_potentials();
     if (bad) return kStInvalid;
     int done = 0, degen = 0, since = 0;
@@ -556,10 +678,41 @@ struct Simplex {
     return st;
   }
 
-  // Full solve from the northwest corner.
-  __device__ int solve(int max_pivots, T tol, int* pivots) {
+  __device__ __forceinline__ int solve(int max_pivots, T tol, int* pivots) {
     init_northwest();
     return run(max_pivots, tol, pivots);
+  }
+
+  // sum over tree edges of flow * cost, in the accumulator type A
+  template <typename A>
+  __device__ __forceinline__ A objective() const {
+    A acc = A(0);
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y > 0 && y < N)
+        acc += (A)((double)t.flow[k] * kInvMass) * (A)s.cost[edge_idx(y, t.par[k])];
+    }
+    return gsum<G>(g, acc);
+  }
+
+  // Basis flows as (cell, w) records: entry y-1 for node y != root.
+  __device__ __forceinline__ void write_flows(int* cell, double* w, long long stride) const {
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y > 0 && y < N) {
+        const int p = t.par[k];
+        const int row = y < m ? y : p;
+        const int col = y < m ? p - m : y - m;
+        cell[y - 1] = (row << 16) | col;
+        w[y - 1] = (double)t.flow[k] * kInvMass;
+      }
+    }
+    for (long long e = N - 1 + g.lane; e < stride; e += G) {
+      cell[e] = -1;
+      w[e] = 0.0;
+    }
   }
 };
 

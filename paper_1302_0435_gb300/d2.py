@@ -41,7 +41,9 @@ class D2Flows(ctypes.Structure):
 
 
 class D2Stats(ctypes.Structure):
-    _fields_ = [("kernel_launches", ctypes.c_int64), ("reserved", ctypes.c_int64 * 7)]
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("pairs_screened", ctypes.c_int64),
+                ("pivots_screened", ctypes.c_int64), ("pairs_exact", ctypes.c_int64),
+                ("pivots_exact", ctypes.c_int64), ("reserved", ctypes.c_int64 * 3)]
 
 
 class D2Error(RuntimeError):
@@ -256,7 +258,8 @@ def d2_cluster_level(ctx, objs, K, seg_size, iters, out_loc, out_cent_weight, la
 def d2_get_stats():
     st = D2Stats()
     _check(load().d2_get_stats(ctypes.byref(st)), "d2_get_stats")
-    return {"kernel_launches": int(st.kernel_launches)}
+    return {k: int(getattr(st, k)) for k in ("kernel_launches", "pairs_screened", "pivots_screened",
+                                              "pairs_exact", "pivots_exact")}
 
 
 def d2_update_locations_noalloc(objs, labels, flows, K, cent_off, cent_loc_dtype, cent_loc64,

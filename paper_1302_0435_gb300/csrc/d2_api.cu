@@ -26,7 +26,7 @@ enum Slot {
   kFlowW, kEpsTerms, kEpsOut, kUpd, kLabelsIn, kCentIn0, kCentIn1, kCentIn2,
   // level driver
   kLvDataLoc, kLvDataW, kLvDataOff, kLvOmega, kLvOmegaNew, kLvC, kLvCT, kLvLab, kLvD2,
-  kLvCLoc32, kLvCLoc64, kLvCQ, kLvCW, kLvCOff, kLvTmp, kCand,
+  kLvCLoc32, kLvCLoc64, kLvCQ, kLvCW, kLvCOff, kLvTmp, kCand, kWarmMeta, kWarmFlow,
   kSlots
 };
 
@@ -261,6 +261,9 @@ __global__ void k_compose(int* C, long long N, const int* ct) {
        i += (long long)gridDim.x * blockDim.x)
     C[i] = C[i] < 0 ? -1 : ct[C[i]];
 }
+
+// Device memory the level driver may use for saved bases (warm starts).
+constexpr size_t kWarmBudgetBytes = (size_t)32 << 30;
 
 unsigned blocks_for(long long n) {
   long long b = (n + 255) / 256;
@@ -670,8 +673,24 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     CK(cudaGetLastError());
     CentView cv{l32, l64, lQ, loff, KT, d};
     const SolveCfg cfg = solve_cfg(c, mode_for(c, cur.ldt), cur_mmax);
+    // Saved bases of all (object, centroid) pairs of this level: the rounds
+    // re-solve the same pairs with the same marginals and moved centroid
+    // locations, so each solve starts from its previous optimal basis.
+    d2k::WarmStore ws{nullptr, nullptr, nullptr, nullptr, 0, 0};
+    const long long npairs = n_l * (long long)K;
+    const int ns = cur_mmax + c->nmax;
+    const size_t meta_bytes = (size_t)npairs * ns * 3;
+    const size_t flow_bytes = (size_t)npairs * ns * 8;
+    if (cfg.mode == 1 && iters > 1 && meta_bytes + flow_bytes <= kWarmBudgetBytes) {
+      unsigned char* meta = static_cast<unsigned char*>(grow(c, kWarmMeta, meta_bytes, &rc));
+      long long* wf = static_cast<long long*>(grow(c, kWarmFlow, flow_bytes, &rc));
+      if (rc != D2_OK) return rc;
+      ws = d2k::WarmStore{meta, meta + (size_t)npairs * ns, meta + (size_t)npairs * ns * 2, wf, ns, 0};
+    }
     for (int it = 0; it < std::max(iters, 1); ++it) {
-      CK(d2k::assign(cur, cv, seg, K, cfg, om, lab, ld2, nullptr, fo, cand, c->d_err, c->stream));
+      ws.warm = it > 0;
+      CK(d2k::assign(cur, cv, seg, K, cfg, om, lab, ld2, nullptr, fo, cand, c->d_err, c->stream,
+                     ws.par8 ? &ws : nullptr));
       if (it < iters)
         CK(d2k::update_locations(cur, om, lab, seg, K, fo, KT, loff, d, c->cent_ldt, l32, l64, scr,
                                  c->stream));

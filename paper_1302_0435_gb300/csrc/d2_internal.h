@@ -32,6 +32,19 @@ struct FlowOut {
   long long stride;
 };
 
+// Saved optimal bases of every (object, centroid) pair of an assign call,
+// pair t = i*K + j, node y at [t*ns + y]: parent / position / size bytes and
+// int64 flow.  `warm`: the arrays hold bases saved by a previous call on the
+// same pairs (same marginals), so solves start from them.
+struct WarmStore {
+  unsigned char* par8;
+  unsigned char* pos8;
+  unsigned char* sz8;
+  long long* flow;
+  int ns;
+  int warm;
+};
+
 // Launch-wide solver settings.
 struct SolveCfg {
   int mode;        // 0: FP64 throughout; 1: FP32 screen/pivots + FP64 certify
@@ -53,9 +66,11 @@ cudaError_t mallows_pairs(const ObjView& ob, const CentView& cv, const long long
                           double* dist2, FlowOut fo, int* status, int* d_err, cudaStream_t st);
 // cand: [count][9] int scratch for the FP32 screen's candidate lists
 // (required when cfg.mode == 1; nullptr solves every centroid exactly).
+// ws (may be null): saved bases, see WarmStore.
 cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, int K,
                    const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
-                   double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st);
+                   double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st,
+                   const WarmStore* ws = nullptr);
 cudaError_t cost_matrix(const ObjView& ob, const CentView& cv, long long i, long long j, int mode,
                         double* C, cudaStream_t st);
 cudaError_t sum_fixed_order(const double* v, long long n, double* out, cudaStream_t st);

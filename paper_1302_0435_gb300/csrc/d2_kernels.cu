@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
 // all K), cand[i*9+1..8] = candidate indices in increasing order.
 template <int G, int NPL>
 __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, CentView cv, long long seg_size, int K,
-                                                SolveCfg cfg, size_t slice, int* cand_out, int* err) {
+                                                SolveCfg cfg, size_t slice, int* cand_out, WarmStore ws,
+                                                int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   Grp<G> g;
   const int gpb = blockDim.x / G;
@@ -260,7 +261,19 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       const float cmax = build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
                                               cv.loc32 + c0 * cv.d, cv.d);
       Simplex<float, G, NPL> S(s32, m, n, g);
-      const int st = S.solve(cfg.budget * (m + n), tol32(cmax), &p_scr);
+      const long long wt = (i * (long long)K + j) * ws.ns;
+      int st;
+      if (ws.par8 && ws.warm) {
+        S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+        st = S.run(cfg.budget * (m + n), tol32(cmax), &p_scr);
+      } else {
+        st = S.solve(cfg.budget * (m + n), tol32(cmax), &p_scr);
+      }
+      if (ws.par8) {
+        // always leave a valid basis for the next round
+        if (st == kStInvalid) S.init_northwest();
+        S.store_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+      }
       ++n_scr;
       if (st != kStOk) all = true;  // no bound: let the exact pass decide
       const float D = S.template objective<float>();
@@ -307,7 +320,8 @@ template <int G, int NPL>
 __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long long seg_size, int K,
                                                SolveCfg cfg, size_t slice, const int* cand_in,
                                                const double* omega, int* labels, double* dist2,
-                                               double* eps_terms, FlowOut fo, int* err) {
+                                               double* eps_terms, FlowOut fo, WarmStore ws,
+                                               int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   Grp<G> g;
   const int gpb = blockDim.x / G;
@@ -336,8 +350,20 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
         if (j < 0 || j >= K || n < 1 || n > cfg.nmax || m + n > G * NPL) { st = kStInvalid; break; }
         double D;
         Simplex<double, G, NPL> S(s64, m, n, g);
-        const int s2 = solve_exact<G, NPL>(g, s64, S, ob, o0, m, cv, c0, n, cfg.budget,
-                                           cfg.mode == 1, &D, &p_ex);
+        int s2;
+        if (ws.par8 && cand_in && !all) {
+          // the screen just saved this pair's FP32-optimal basis: continue in FP64
+          const long long wt = (i * (long long)K + j) * ws.ns;
+          load_cent_prefix<G>(g, cv, c0, n, s64.Q);
+          const double cmax = build_cost<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
+                                                    cv.loc64 + c0 * cv.d, cv.d);
+          S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+          s2 = S.run(cfg.budget * (m + n), tol64(cmax), &p_ex);
+          D = S.template objective<double>();
+        } else {
+          s2 = solve_exact<G, NPL>(g, s64, S, ob, o0, m, cv, c0, n, cfg.budget, cfg.mode == 1, &D,
+                                   &p_ex);
+        }
         ++n_ex;
         if (s2 != kStOk) st = s2;
         if (s2 == kStInvalid) break;
@@ -487,7 +513,10 @@ static cudaError_t mallows_pairs_g(const ObjView& ob, const CentView& cv, const 
 template <int G, int NPL>
 static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg_size, int K,
                             const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
-                            double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st) {
+                            double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st,
+                            const WarmStore* wsp) {
+  WarmStore ws{nullptr, nullptr, nullptr, nullptr, 0, 0};
+  if (wsp) ws = *wsp;
   const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax);
   const int gpb = groups_per_block(G, slice);
   if (gpb == 0) return cudaErrorInvalidConfiguration;
@@ -498,14 +527,16 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
   if (screen) {
     e = launch_cfg(k_screen<G, NPL>, smem, gpb * G, cfg.sms, ob.count, gpb, &grid);
     if (e != cudaSuccess) return e;
-    k_screen<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, cfg, slice, cand, d_err);
+    k_screen<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, cfg, slice, cand, ws, d_err);
     note_launches(1);
   }
   e = launch_cfg(k_exact<G, NPL>, smem, gpb * G, cfg.sms, ob.count, gpb, &grid);
   if (e != cudaSuccess) return e;
+  WarmStore wx = ws;
+  if (!screen) wx.par8 = nullptr;
   k_exact<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, cfg, slice,
                                                screen ? cand : nullptr, omega, labels, dist2,
-                                               eps_terms, fo, d_err);
+                                               eps_terms, fo, wx, d_err);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -543,13 +574,14 @@ cudaError_t mallows_pairs(const ObjView& ob, const CentView& cv, const long long
 
 cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, int K,
                    const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
-                   double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st) {
+                   double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st,
+                   const WarmStore* ws) {
   if (ob.count <= 0) return cudaSuccess;
   int G, NP;
   if (!pick_shape(cfg.mmax, cfg.nmax, cfg.group, &G, &NP)) return cudaErrorInvalidValue;
 #define X(g_, n_)                                                                            \
   if (G == g_ && NP == n_)                                                                  \
-    return assign_g<g_, n_>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, cand, d_err, st);
+    return assign_g<g_, n_>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, cand, d_err, st, ws);
   D2_BINS(X)
 #undef X
   return cudaErrorInvalidValue;

@@ -683,6 +683,40 @@ struct Simplex {
     return run(max_pivots, tol, pivots);
   }
 
+  // Saved basis of one pair: per node parent, preorder position, subtree
+  // size (bytes) and edge flow, at [y] of arrays with room for N nodes.
+  __device__ __forceinline__ void store_tree(unsigned char* par8, unsigned char* pos8,
+                                             unsigned char* sz8, long long* flow) const {
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y < N) {
+        par8[y] = (unsigned char)(t.par[k] & 0xff);
+        pos8[y] = (unsigned char)t.pos[k];
+        sz8[y] = (unsigned char)t.sz[k];
+        flow[y] = t.flow[k];
+      }
+    }
+  }
+  // Restore a saved basis (the marginals must be those it was saved with,
+  // so its flows are still the basic solution).
+  __device__ __forceinline__ void load_tree(const unsigned char* par8, const unsigned char* pos8,
+                                            const unsigned char* sz8, const long long* flow) {
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y < N) {
+        t.par[k] = y == 0 ? -1 : (int)par8[y];
+        t.pos[k] = pos8[y];
+        t.sz[k] = sz8[y];
+        t.flow[k] = flow[y];
+        s.pos[y] = t.pos[k];
+        s.sz[y] = t.sz[k];
+      }
+    }
+    g.sync();
+  }
+
   // sum over tree edges of flow * cost, in the accumulator type A
   template <typename A>
   __device__ __forceinline__ A objective() const {

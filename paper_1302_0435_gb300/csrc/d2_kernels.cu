@@ -227,7 +227,9 @@ __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
 // k_screen: every centroid is solved with an FP32 tile and FP32 pivots.
 // The FP32 objective D32_j has a bound err_j on its distance to the FP64
 // optimum (cost rounding (d+3)*2^-24 relative, summation 2^-17 relative,
-// basis optimality 2^-16 * max cost absolute); every centroid whose interval
+// basis optimality 2^-14 * max cost absolute, which covers the stopping
+// tolerance 2^-20 * max cost and the drift of the incrementally updated
+// FP32 potentials, refreshed every 64 pivots); every centroid whose interval
 // [D32_j - err_j, D32_j + err_j] reaches below the smallest upper end is a
 // candidate.  Output per object: cand[i*9] = count (-1: more than 8, solve
 // all K), cand[i*9+1..8] = candidate indices in increasing order.
@@ -265,9 +267,9 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       int st;
       if (ws.par8 && ws.warm) {
         S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
-        st = S.run(cfg.budget * (m + n), tol32(cmax), &p_scr);
+        st = S.run(cfg.budget * (m + n), tol32(cmax), &p_scr, false);
       } else {
-        st = S.solve(cfg.budget * (m + n), tol32(cmax), &p_scr);
+        st = S.solve(cfg.budget * (m + n), tol32(cmax), &p_scr, false);
       }
       if (ws.par8) {
         // always leave a valid basis for the next round
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       ++n_scr;
       if (st != kStOk) all = true;  // no bound: let the exact pass decide
       const float D = S.template objective<float>();
-      const float e = D * rel + cmax * 0x1p-16f;
+      const float e = D * rel + cmax * 0x1p-14f;
       const float lo = D - e, hi = D + e;
       if (lo <= best_hi) {
         if (ncand < 8) {

@@ -642,10 +642,13 @@ struct Simplex {
     return th > 0;
   }
 
-  // Pivot from the current basis until no reduced cost is below -tol (with
-  // potentials freshly recomputed from the tree).  Returns kStOk,
-  // kStNotConverged or kStInvalid; *pivots accumulates the pivot count.
-  __device__ __forceinline__ int run(int max_pivots, T tol, int* pivots) {
+  // Pivot from the current basis until no reduced cost is below -tol.
+  // With fresh_stop, optimality is only accepted on potentials freshly
+  // recomputed from the tree (an FP32 screen whose error bound already
+  // covers the drift of incrementally updated potentials passes false).
+  // Returns kStOk, kStNotConverged or kStInvalid; *pivots accumulates the
+  // pivot count.
+  __device__ __forceinline__ int run(int max_pivots, T tol, int* pivots, bool fresh_stop = true) {
     refresh_potentials();
     if (bad) return kStInvalid;
     int done = 0, degen = 0, since = 0;
@@ -655,7 +658,7 @@ struct Simplex {
       T dE;
       const int cell = price(bland, tol, dE);
       if (cell < 0) {
-        if (since == 0) break;
+        if (since == 0 || !fresh_stop) break;
         refresh_potentials();
         if (bad) { st = kStInvalid; break; }
         since = 0;
@@ -678,9 +681,9 @@ struct Simplex {
     return st;
   }
 
-  __device__ __forceinline__ int solve(int max_pivots, T tol, int* pivots) {
+  __device__ __forceinline__ int solve(int max_pivots, T tol, int* pivots, bool fresh_stop = true) {
     init_northwest();
-    return run(max_pivots, tol, pivots);
+    return run(max_pivots, tol, pivots, fresh_stop);
   }
 
   // Saved basis of one pair: per node parent, preorder position, subtree

@@ -351,6 +351,9 @@ def run_ours(args):
         return 0
 
     cpu = cpu_sample(objs, cents, target_s=args.cpu_seconds) if not args.skip_cpu else None
+    serve = None
+    if not args.skip_serve:
+        serve = serve_measure(dev)
     peaks, peak_kind = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
@@ -374,12 +377,102 @@ def run_ours(args):
         "data": "synthetic", "config": workload_config(),
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)},
         "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+        "serve": serve,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def serve_measure(dev, n_requests=60, lam_fracs=(0.8,), n_sat=24, seed=1005):
+    """Serving workload: Poisson arrivals of assignment requests (log-uniform
+    1-4096 bags of 4-64 supports, d=32) against K=1024 resident centroids of
+    32 supports, through the continuous-batching server.  Saturated
+    throughput comes from a burst of n_sat requests; then requests arrive at
+    lam_frac of the saturated request rate and each one's submit-to-done
+    latency is recorded.  The plain one-pair-per-launch GPU form
+    (d2_mallows_batch with one pair per call) is timed beside it."""
+    import threading
+    import torch
+    from paper_1302_0435_gb300 import d2, synth
+    cents, means = synth.serving_centroids(K=1024, seed=seed)
+    ctx = d2.Context(dev.index)
+    d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device=dev))
+    rng = np.random.default_rng(seed + 1)
+    K = cents.count
+    srv = d2.Server(ctx, slots=8)
+    # warm the slots' buffers
+    warm = [d2.bags_from_synth(synth.serving_request(rng, means, size=4096)) for _ in range(2)]
+    for t in [srv.submit(b) for b in warm]:
+        srv.poll(t)
+    burst = [d2.bags_from_synth(synth.serving_request(rng, means)) for _ in range(n_sat)]
+    t0 = time.perf_counter()
+    ts = [srv.submit(b) for b in burst]
+    for t in ts:
+        srv.poll(t)
+    sat_dt = time.perf_counter() - t0
+    sat_pairs = sum(b.count for b in burst) * K / sat_dt
+    sat_rps = n_sat / sat_dt
+    out = {"workload": "serving: K=1024 resident centroids (n=32, d=32), requests log-uniform "
+                       "1-4096 bags of 4-64 supports", "slots": 8,
+           "saturated_pairs_per_s": sat_pairs, "saturated_requests_per_s": sat_rps, "levels": []}
+    for frac in lam_fracs:
+        lam = frac * sat_rps
+        reqs = [d2.bags_from_synth(synth.serving_request(rng, means)) for _ in range(n_requests)]
+        gaps = rng.exponential(1.0 / lam, size=n_requests)
+        lat = []
+        tickets = []
+        done = threading.Event()
+
+        def poller():
+            i = 0
+            while i < n_requests:
+                while len(tickets) <= i:
+                    time.sleep(0.0002)
+                rc, _, _, ms = srv.poll(tickets[i])
+                lat.append(ms)
+                i += 1
+            done.set()
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        t_start = time.perf_counter()
+        nxt = t_start
+        for b, gap in zip(reqs, gaps):
+            nxt += gap
+            wait = nxt - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(srv.submit(b))
+        done.wait()
+        wall = time.perf_counter() - t_start
+        lat = np.array(lat)
+        out["levels"].append({"lambda_frac": frac, "requests": n_requests,
+                              "p50_ms": float(np.percentile(lat, 50)),
+                              "p99_ms": float(np.percentile(lat, 99)),
+                              "pairs_per_s": sum(b.count for b in reqs) * K / wall})
+    srv.close()
+    # plain form: one pair per launch
+    one = synth.serving_request(rng, means, size=64)
+    ob = d2.bags_from_synth(one, device=dev)
+    po = torch.zeros(1, dtype=torch.int64, device=dev)
+    pc = torch.zeros(1, dtype=torch.int64, device=dev)
+    dd = torch.empty(1, dtype=torch.float64, device=dev)
+    calls = 300
+    d2.d2_mallows_batch(ctx, ob, po, pc, dd)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for c in range(calls):
+        po.fill_(c % one.count)
+        pc.fill_(c % K)
+        d2.d2_mallows_batch(ctx, ob, po, pc, dd)
+    d2.d2_sync(ctx)
+    plain_dt = time.perf_counter() - t0
+    out["plain_one_pair_per_launch"] = {"pairs_per_s": calls / plain_dt,
+                                        "ms_per_pair": 1e3 * plain_dt / calls}
+    ctx.close()
+    return out
 
 
 def run_profile_case(args):
@@ -410,11 +503,22 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serving sweep at 0.5/0.8/0.95 of saturation (own JSON line)")
     ap.add_argument("--profile", action="store_true", help="small k_assign case for ncu")
     ap.add_argument("--profile-n", type=int, default=20000)
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args)
+    if args.serve_full:
+        import torch
+        from paper_1302_0435_gb300 import build, d2
+        build.build()
+        d2.load()
+        res = serve_measure(torch.device("cuda", 0), n_requests=200, lam_fracs=(0.5, 0.8, 0.95))
+        print(json.dumps({"metric": "serve p50/p99 ms", "serve": res}), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

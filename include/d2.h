@@ -215,6 +215,33 @@ int d2_cluster_level(d2_ctx* ctx, const d2_bags* objs, const double* omega, int3
                      int32_t* labels);
 
 /*
+ * Serving: continuous batching of assignment requests (Alg. 2 Step 2)
+ * against the context's resident centroid set.  A worker thread admits
+ * queued requests into `slots` concurrent slots (one CUDA stream each) as
+ * slots free up and as long as the device bytes of the requests in flight
+ * stay within mem_budget_bytes (0 = 8 GiB; a request larger than the budget
+ * is admitted alone).  Requests that arrive while others are on the GPU are
+ * admitted at once and their kernels overlap on the device.  Every request
+ * is solved by the same deterministic per-pair solver as d2_assign, so its
+ * labels and distances are identical alone and in any mix.  The resident
+ * centroid set must not change while a server exists.
+ *
+ * d2_server_submit copies a host request (objs: host pointers) and returns a
+ * ticket at once.  d2_server_poll waits up to timeout_ms (<0: forever) for
+ * a ticket, copies its labels [N] and dist2 [N] (host pointers, may be NULL)
+ * and the submit-to-completion latency in ms, and forgets the ticket;
+ * returns D2_ETIMEOUT if not done yet (the ticket stays valid).
+ */
+typedef struct d2_server d2_server;
+int d2_server_create(d2_server** out, d2_ctx* ctx, int32_t slots, int64_t mem_budget_bytes);
+int d2_server_submit(d2_server* srv, const d2_bags* objs, int64_t* ticket);
+int d2_server_poll(d2_server* srv, int64_t ticket, int32_t* labels, double* dist2,
+                   double* latency_ms, int32_t timeout_ms);
+int d2_server_stats(d2_server* srv, int64_t* admitted, int64_t* completed, int64_t* peak_inflight,
+                    int64_t* queued);
+int d2_server_destroy(d2_server* srv);
+
+/*
  * d2_update_locations_noalloc -- the location update of d2_update_locations
  * (same kernels, same arithmetic, same results) for callers that cannot
  * call cudaMalloc during the call: for instance a framework that owns all

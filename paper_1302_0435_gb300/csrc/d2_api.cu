@@ -272,6 +272,20 @@ unsigned blocks_for(long long n) {
 
 }  // namespace
 
+namespace d2k {
+CentView ctx_centroids(const d2_ctx* c, int* nmax, int* d, int* device, int* mode, int* budget,
+                       int* sms, long long* K) {
+  *nmax = c->nmax;
+  *d = c->d;
+  *device = c->device;
+  *mode = (c->cfg.precision == D2_PREC_FP64 || c->cent_ldt == D2_F64) ? 0 : 1;
+  *budget = c->cfg.pivot_budget > 0 ? c->cfg.pivot_budget : 64;
+  *sms = c->sms;
+  *K = c->K;
+  return resident_view(c);
+}
+}  // namespace d2k
+
 extern "C" {
 
 const char* d2_strerror(int32_t s) {

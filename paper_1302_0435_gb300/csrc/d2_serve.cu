@@ -1,0 +1,381 @@
+// d2_serve.cu -- continuous-batching server for assignment requests
+// (Alg. 2 Step 2 against a resident centroid set).  A worker thread admits
+// queued requests into slots as slots and device memory free up; each slot
+// owns a CUDA stream and grow-only device/pinned buffers, so requests that
+// arrive while others are on the GPU start at once and their kernels
+// overlap with the running ones.  Each request's labels and distances are
+// computed by the same deterministic per-pair solver as d2_assign, so a
+// result does not depend on what else is in flight.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "d2.h"
+#include "d2_internal.h"
+
+namespace {
+
+struct Request {
+  long long ticket = 0;
+  long long count = 0;
+  int dim = 0, ldt = 0, wdt = 0, mmax = 0;
+  std::vector<unsigned char> loc, w;
+  std::vector<long long> off;
+  // results
+  std::vector<int> labels;
+  std::vector<double> dist2;
+  int status = D2_OK;
+  bool done = false;
+  std::chrono::steady_clock::time_point t_submit, t_start, t_done;
+  size_t bytes = 0;  // device bytes while in flight
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::shared_ptr<Request> req;
+  bool staging = false;
+  // device
+  void* d_loc = nullptr; size_t n_loc = 0;
+  void* d_w = nullptr; size_t n_w = 0;
+  long long* d_off = nullptr; size_t n_off = 0;
+  int* d_lab = nullptr; size_t n_lab = 0;
+  double* d_d2 = nullptr; size_t n_d2 = 0;
+  int* d_cand = nullptr; size_t n_cand = 0;
+  int* d_err = nullptr;
+  // pinned host
+  unsigned char* h_in = nullptr; size_t n_in = 0;
+  unsigned char* h_out = nullptr; size_t n_out = 0;
+  int* h_err = nullptr;
+};
+
+template <typename T>
+bool grow_dev(T** p, size_t* cap, size_t bytes) {
+  if (*cap >= bytes && *p) return true;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(reinterpret_cast<void**>(p), bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  *cap = bytes;
+  return true;
+}
+
+bool grow_host(unsigned char** p, size_t* cap, size_t bytes) {
+  if (*cap >= bytes && *p) return true;
+  if (*p) cudaFreeHost(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMallocHost(reinterpret_cast<void**>(p), bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  *cap = bytes;
+  return true;
+}
+
+size_t esz(int dt) { return dt == D2_F64 ? 8 : (dt == D2_F32 ? 4 : 2); }
+
+}  // namespace
+
+struct d2_server {
+  d2_ctx* ctx = nullptr;
+  int device = 0;
+  d2k::CentView cv{};
+  int nmax = 0, d = 0, mode = 1, budget_pivots = 64, sms = 1;
+  long long K = 0;
+  size_t mem_budget = 0, mem_inflight = 0;
+  std::vector<Slot> slots;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::unordered_map<long long, std::shared_ptr<Request>> table;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::thread worker;
+  std::atomic<bool> stop{false};
+  long long next_ticket = 1;
+  long long admitted = 0, completed = 0, peak_inflight = 0;
+
+  bool launch(Slot& s, const std::shared_ptr<Request>& r);
+  void run();
+};
+
+// Stage a request into a slot and enqueue its copies and kernels.
+bool d2_server::launch(Slot& s, const std::shared_ptr<Request>& r) {
+  const long long N = r->count;
+  const long long T = r->off.empty() ? 0 : r->off.back();
+  const size_t b_loc = (size_t)T * r->dim * esz(r->ldt);
+  const size_t b_w = (size_t)T * esz(r->wdt);
+  const size_t b_off = (size_t)(N + 1) * 8;
+  const size_t b_in = b_loc + b_w + b_off;
+  const size_t b_out = (size_t)N * 4 + (size_t)N * 8 + 16;
+  if (!grow_dev(reinterpret_cast<unsigned char**>(&s.d_loc), &s.n_loc, std::max<size_t>(b_loc, 16)) ||
+      !grow_dev(reinterpret_cast<unsigned char**>(&s.d_w), &s.n_w, std::max<size_t>(b_w, 16)) ||
+      !grow_dev(&s.d_off, &s.n_off, b_off) || !grow_dev(&s.d_lab, &s.n_lab, (size_t)N * 4 + 16) ||
+      !grow_dev(&s.d_d2, &s.n_d2, (size_t)N * 8 + 16) ||
+      !grow_dev(&s.d_cand, &s.n_cand, (size_t)N * 9 * 4 + 16) || !grow_host(&s.h_in, &s.n_in, b_in) ||
+      !grow_host(&s.h_out, &s.n_out, b_out))
+    return false;
+  std::memcpy(s.h_in, r->loc.data(), b_loc);
+  std::memcpy(s.h_in + b_loc, r->w.data(), b_w);
+  std::memcpy(s.h_in + b_loc + b_w, r->off.data(), b_off);
+  cudaMemsetAsync(s.d_err, 0, sizeof(int), s.stream);
+  cudaMemcpyAsync(s.d_loc, s.h_in, b_loc, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.d_w, s.h_in + b_loc, b_w, cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.d_off, s.h_in + b_loc + b_w, b_off, cudaMemcpyHostToDevice, s.stream);
+  d2k::ObjView ob;
+  ob.loc = s.d_loc;
+  ob.w = s.d_w;
+  ob.off = s.d_off;
+  ob.count = N;
+  ob.d = r->dim;
+  ob.ldt = r->ldt;
+  ob.wdt = r->wdt;
+  d2k::SolveCfg cfg;
+  cfg.mode = (r->ldt == D2_F64) ? 0 : mode;
+  cfg.group = 32;
+  cfg.mmax = r->mmax;
+  cfg.nmax = nmax;
+  cfg.budget = budget_pivots;
+  cfg.sms = sms;
+  d2k::FlowOut fo{nullptr, nullptr, 0};
+  cudaError_t e = d2k::assign(ob, cv, N, (int)K, cfg, nullptr, s.d_lab, s.d_d2, nullptr, fo,
+                              s.d_cand, s.d_err, s.stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaMemcpyAsync(s.h_out, s.d_lab, (size_t)N * 4, cudaMemcpyDeviceToHost, s.stream);
+  cudaMemcpyAsync(s.h_out + (size_t)N * 4, s.d_d2, (size_t)N * 8, cudaMemcpyDeviceToHost, s.stream);
+  cudaMemcpyAsync(s.h_err, s.d_err, sizeof(int), cudaMemcpyDeviceToHost, s.stream);
+  cudaEventRecord(s.ev, s.stream);
+  return cudaGetLastError() == cudaSuccess;
+}
+
+void d2_server::run() {
+  cudaSetDevice(device);
+  std::unique_lock<std::mutex> lk(mu);
+  while (!stop.load()) {
+    bool progressed = false;
+    // completions
+    for (Slot& s : slots) {
+      if (!s.req) continue;
+      const cudaError_t q = cudaEventQuery(s.ev);
+      if (q == cudaErrorNotReady) continue;
+      std::shared_ptr<Request> r = s.req;
+      const long long N = r->count;
+      if (q != cudaSuccess) {
+        cudaGetLastError();
+        r->status = D2_ECUDA;
+      } else {
+        r->labels.resize(N);
+        r->dist2.resize(N);
+        std::memcpy(r->labels.data(), s.h_out, (size_t)N * 4);
+        std::memcpy(r->dist2.data(), s.h_out + (size_t)N * 4, (size_t)N * 8);
+        const int bits = *s.h_err;
+        r->status = (bits & d2k::kErrInvalid) ? D2_EINVAL
+                  : (bits & d2k::kErrNotConverged) ? D2_ENOTCONVERGED : D2_OK;
+      }
+      r->t_done = std::chrono::steady_clock::now();
+      r->done = true;
+      mem_inflight -= r->bytes;
+      s.req.reset();
+      ++completed;
+      progressed = true;
+      cv_done.notify_all();
+    }
+    // admissions: free slot and memory budget (staging runs unlocked)
+    while (!queue.empty()) {
+      std::shared_ptr<Request> r = queue.front();
+      Slot* free_slot = nullptr;
+      for (Slot& s : slots)
+        if (!s.req && !s.staging) { free_slot = &s; break; }
+      if (!free_slot) break;
+      if (mem_inflight > 0 && mem_inflight + r->bytes > mem_budget) break;
+      queue.pop_front();
+      free_slot->staging = true;
+      mem_inflight += r->bytes;
+      lk.unlock();
+      r->t_start = std::chrono::steady_clock::now();
+      const bool ok = launch(*free_slot, r);
+      lk.lock();
+      free_slot->staging = false;
+      if (!ok) {
+        mem_inflight -= r->bytes;
+        r->status = D2_ENOMEM;
+        r->done = true;
+        r->t_done = std::chrono::steady_clock::now();
+        cv_done.notify_all();
+        continue;
+      }
+      free_slot->req = r;
+      ++admitted;
+      long long inflight = 0;
+      for (Slot& s : slots) inflight += s.req ? 1 : 0;
+      peak_inflight = std::max(peak_inflight, inflight);
+      progressed = true;
+    }
+    if (!progressed) {
+      bool busy = false;
+      for (Slot& s : slots) busy |= (bool)s.req;
+      // in flight: poll the events every 50 us; idle: sleep until work arrives
+      if (busy) cv_work.wait_for(lk, std::chrono::microseconds(50));
+      else cv_work.wait_for(lk, std::chrono::milliseconds(20));
+    }
+  }
+}
+
+// The context's resident centroid set (read-only while a server runs).
+namespace d2k {
+CentView ctx_centroids(const d2_ctx* c, int* nmax, int* d, int* device, int* mode, int* budget,
+                       int* sms, long long* K);
+}
+
+extern "C" int d2_server_create(d2_server** out, d2_ctx* ctx, int32_t nslots, int64_t mem_budget) {
+  if (!out || !ctx || nslots < 1 || nslots > 64 || mem_budget < 0) return D2_EINVAL;
+  *out = nullptr;
+  d2_server* sv = new (std::nothrow) d2_server();
+  if (!sv) return D2_ENOMEM;
+  sv->ctx = ctx;
+  int mode = 1;
+  sv->cv = d2k::ctx_centroids(ctx, &sv->nmax, &sv->d, &sv->device, &mode, &sv->budget_pivots, &sv->sms,
+                              &sv->K);
+  sv->mode = mode;
+  if (sv->K == 0) {
+    delete sv;
+    return D2_ENOCENTROIDS;
+  }
+  sv->mem_budget = mem_budget > 0 ? (size_t)mem_budget : ((size_t)8 << 30);
+  cudaSetDevice(sv->device);
+  sv->slots.resize(nslots);
+  for (Slot& s : sv->slots) {
+    if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&s.d_err, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&s.h_err), sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      sv->stop = true;
+      for (Slot& t : sv->slots) {
+        if (t.stream) cudaStreamDestroy(t.stream);
+        if (t.ev) cudaEventDestroy(t.ev);
+        if (t.d_err) cudaFree(t.d_err);
+        if (t.h_err) cudaFreeHost(t.h_err);
+      }
+      delete sv;
+      return D2_ECUDA;
+    }
+  }
+  sv->worker = std::thread([sv] { sv->run(); });
+  *out = sv;
+  return D2_OK;
+}
+
+extern "C" int d2_server_submit(d2_server* sv, const d2_bags* objs, int64_t* ticket) {
+  if (!sv || !objs || !ticket || !objs->loc || !objs->w || !objs->off || objs->count < 1 ||
+      objs->dim != sv->d || objs->loc_dtype < D2_F64 || objs->loc_dtype > D2_BF16 ||
+      (objs->w_dtype != D2_F64 && objs->w_dtype != D2_F32))
+    return D2_EINVAL;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, objs->off) == cudaSuccess &&
+      (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged))
+    return D2_EINVAL;  // requests are host data
+  cudaGetLastError();
+  auto r = std::make_shared<Request>();
+  const long long N = objs->count;
+  const long long T = objs->off[N];
+  if (objs->off[0] != 0 || T < N) return D2_EINVAL;
+  int mmax = 0;
+  for (long long i = 0; i < N; ++i) {
+    const long long m = objs->off[i + 1] - objs->off[i];
+    if (m < 1) return D2_EINVAL;
+    if (m > D2_MAX_SUPPORT) return D2_EUNSUPPORTED;
+    mmax = std::max<int>(mmax, (int)m);
+  }
+  if (mmax + sv->nmax > 128) return D2_EUNSUPPORTED;
+  r->count = N;
+  r->dim = objs->dim;
+  r->ldt = objs->loc_dtype;
+  r->wdt = objs->w_dtype;
+  r->mmax = mmax;
+  const size_t b_loc = (size_t)T * objs->dim * esz(objs->loc_dtype);
+  const size_t b_w = (size_t)T * esz(objs->w_dtype);
+  r->loc.assign(static_cast<const unsigned char*>(objs->loc), static_cast<const unsigned char*>(objs->loc) + b_loc);
+  r->w.assign(static_cast<const unsigned char*>(objs->w), static_cast<const unsigned char*>(objs->w) + b_w);
+  r->off.assign(objs->off, objs->off + N + 1);
+  r->bytes = b_loc + b_w + (size_t)(N + 1) * 8 + (size_t)N * (4 + 8 + 36);
+  r->t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r->ticket = sv->next_ticket++;
+    sv->table[r->ticket] = r;
+    sv->queue.push_back(r);
+  }
+  sv->cv_work.notify_one();
+  *ticket = r->ticket;
+  return D2_OK;
+}
+
+extern "C" int d2_server_poll(d2_server* sv, int64_t ticket, int32_t* labels, double* dist2,
+                              double* latency_ms, int32_t timeout_ms) {
+  if (!sv) return D2_EINVAL;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->table.find(ticket);
+  if (it == sv->table.end()) return D2_EINVAL;
+  std::shared_ptr<Request> r = it->second;
+  const auto pred = [&] { return r->done; };
+  if (timeout_ms < 0) sv->cv_done.wait(lk, pred);
+  else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) return D2_ETIMEOUT;
+  if (labels) std::memcpy(labels, r->labels.data(), r->labels.size() * 4);
+  if (dist2) std::memcpy(dist2, r->dist2.data(), r->dist2.size() * 8);
+  if (latency_ms)
+    *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  const int st = r->status;
+  sv->table.erase(it);
+  return st;
+}
+
+extern "C" int d2_server_stats(d2_server* sv, int64_t* admitted, int64_t* completed,
+                               int64_t* peak_inflight, int64_t* queued) {
+  if (!sv) return D2_EINVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (admitted) *admitted = sv->admitted;
+  if (completed) *completed = sv->completed;
+  if (peak_inflight) *peak_inflight = sv->peak_inflight;
+  if (queued) *queued = (int64_t)sv->queue.size();
+  return D2_OK;
+}
+
+extern "C" int d2_server_destroy(d2_server* sv) {
+  if (!sv) return D2_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv_work.notify_all();
+  if (sv->worker.joinable()) sv->worker.join();
+  cudaSetDevice(sv->device);
+  for (Slot& s : sv->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.ev) cudaEventDestroy(s.ev);
+    cudaFree(s.d_loc); cudaFree(s.d_w); cudaFree(s.d_off); cudaFree(s.d_lab); cudaFree(s.d_d2);
+    cudaFree(s.d_cand); cudaFree(s.d_err);
+    if (s.h_in) cudaFreeHost(s.h_in);
+    if (s.h_out) cudaFreeHost(s.h_out);
+    if (s.h_err) cudaFreeHost(s.h_err);
+  }
+  delete sv;
+  return D2_OK;
+}

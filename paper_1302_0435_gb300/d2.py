@@ -22,7 +22,8 @@ MAX_SUPPORT = 64
 EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_strerror",
            "d2_version", "d2_set_centroids", "d2_get_centroids", "d2_cost_matrix",
            "d2_mallows_batch", "d2_assign", "d2_update_locations", "d2_cluster_level",
-           "d2_get_stats", "d2_update_locations_noalloc"]
+           "d2_get_stats", "d2_update_locations_noalloc", "d2_server_create", "d2_server_submit",
+           "d2_server_poll", "d2_server_stats", "d2_server_destroy"]
 
 
 class D2Bags(ctypes.Structure):
@@ -83,6 +84,11 @@ def load(path=None):
     lib.d2_update_locations.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, ctypes.POINTER(D2Flows)]
     lib.d2_cluster_level.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i32, i64, i32, vp, vp, vp]
     lib.d2_get_stats.argtypes = [ctypes.POINTER(D2Stats)]
+    lib.d2_server_create.argtypes = [ctypes.POINTER(vp), vp, i32, i64]
+    lib.d2_server_submit.argtypes = [vp, ctypes.POINTER(D2Bags), ctypes.POINTER(i64)]
+    lib.d2_server_poll.argtypes = [vp, i64, vp, vp, ctypes.POINTER(ctypes.c_double), i32]
+    lib.d2_server_stats.argtypes = [vp, vp, vp, vp, vp]
+    lib.d2_server_destroy.argtypes = [vp]
     lib.d2_update_locations_noalloc.argtypes = [ctypes.POINTER(D2Bags), vp, vp, ctypes.POINTER(D2Flows),
                                                 i64, vp, i32, vp, vp, vp]
     _lib = lib
@@ -273,3 +279,52 @@ def d2_update_locations_noalloc(objs, labels, flows, K, cent_off, cent_loc_dtype
                                             int(cent_loc_dtype), _ptr(cent_loc64), _ptr(cent_loc32), h)
     _check(rc, "d2_update_locations_noalloc")
     return rc
+
+
+class Server:
+    """d2_server_*: continuous batching of assignment requests against the
+    context's resident centroids."""
+
+    def __init__(self, ctx, slots=8, mem_budget=0):
+        self.h = ctypes.c_void_p()
+        _check(load().d2_server_create(ctypes.byref(self.h), ctx.h, int(slots), int(mem_budget)),
+               "d2_server_create")
+        self.ctx = ctx
+        self._keep = {}
+
+    def submit(self, bags):
+        """bags: host BagsRef (numpy arrays); returns a ticket."""
+        t = ctypes.c_int64()
+        _check(load().d2_server_submit(self.h, ctypes.byref(bags.s), ctypes.byref(t)), "d2_server_submit")
+        self._keep[t.value] = bags.count
+        return t.value
+
+    def poll(self, ticket, timeout_ms=-1):
+        """Returns (status, labels, dist2, latency_ms); status D2_ETIMEOUT
+        means not done yet."""
+        n = self._keep[ticket]
+        lab = np.empty(n, dtype=np.int32)
+        d2v = np.empty(n)
+        lat = ctypes.c_double()
+        rc = load().d2_server_poll(self.h, int(ticket), _ptr(lab), _ptr(d2v), ctypes.byref(lat),
+                                   int(timeout_ms))
+        if rc == D2_ETIMEOUT:
+            return rc, None, None, None
+        del self._keep[ticket]
+        return rc, lab, d2v, lat.value
+
+    def stats(self):
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(load().d2_server_stats(self.h, *[ctypes.byref(x) for x in v]), "d2_server_stats")
+        return dict(zip(["admitted", "completed", "peak_inflight", "queued"], [x.value for x in v]))
+
+    def close(self):
+        if self.h:
+            load().d2_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

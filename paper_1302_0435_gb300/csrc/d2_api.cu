@@ -532,7 +532,7 @@ int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labe
     terms = static_cast<double*>(grow(c, kEpsTerms, (size_t)N * 8, &rc));
     if (rc != D2_OK) return rc;
   }
-  int* cand = static_cast<int*>(grow(c, kCand, (size_t)N * 9 * 4, &rc));
+  int* cand = static_cast<int*>(grow(c, kCand, (size_t)d2k::assign_scratch_ints(N, c->K, c->sms) * 4, &rc));
   if (rc != D2_OK) return rc;
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   const SolveCfg cfg = solve_cfg(c, mode_for(c, objs->loc_dtype), mmax);
@@ -678,7 +678,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     fo.cell = static_cast<int*>(grow(c, kFlowCell, (size_t)(n_l * stride) * 4, &rc));
     fo.w = static_cast<double*>(grow(c, kFlowW, (size_t)(n_l * stride) * 8, &rc));
     void* scr = grow(c, kUpd, d2k::update_scratch_bytes(n_l, KT), &rc);
-    int* cand = static_cast<int*>(grow(c, kCand, (size_t)n_l * 9 * 4, &rc));
+    int* cand = static_cast<int*>(grow(c, kCand, (size_t)d2k::assign_scratch_ints(n_l, K, c->sms) * 4, &rc));
     if (rc != D2_OK) return rc;
     k_replicate<<<blocks_for(M * Tc), 256, 0, c->stream>>>(c->c_loc32, c->c_loc64, c->c_Q, c->c_w64,
                                                            c->c_off, K, Tc, d, M, l32, l64, lQ, lw,

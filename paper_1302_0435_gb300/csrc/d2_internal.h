@@ -1,6 +1,7 @@
 // d2_internal.h -- host-side launchers shared by the C-ABI implementation.
 // Device views are plain structs of pointers (all device memory).
 #pragma once
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -64,13 +65,21 @@ cudaError_t prep_centroids(const void* loc, int ldt, const void* w, int wdt, con
 cudaError_t mallows_pairs(const ObjView& ob, const CentView& cv, const long long* pobj,
                           const long long* pcen, long long npairs, const SolveCfg& cfg,
                           double* dist2, FlowOut fo, int* status, int* d_err, cudaStream_t st);
-// cand: [count][9] int scratch for the FP32 screen's candidate lists
-// (required when cfg.mode == 1; nullptr solves every centroid exactly).
+// cand: int scratch of assign_scratch_ints(count, K) for the FP32 screen's
+// candidate lists (required when cfg.mode == 1; nullptr solves every
+// centroid exactly).
 // ws (may be null): saved bases, see WarmStore.
 cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, int K,
                    const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
                    double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st,
                    const WarmStore* ws = nullptr);
+// ints of assign scratch for `count` objects and K centroids per object
+inline long long assign_scratch_ints(long long count, long long K, int sms = 160) {
+  const long long want = (long long)sms * 96;
+  long long NB = std::max<long long>(1, (want + count - 1) / (count > 0 ? count : 1));
+  NB = std::min<long long>(NB, std::max<long long>(1, K / 8));
+  return 4 + ((count * 9 + 3) & ~3LL) + count * NB * 18 + 4;
+}
 cudaError_t cost_matrix(const ObjView& ob, const CentView& cv, long long i, long long j, int mode,
                         double* C, cudaStream_t st);
 cudaError_t sum_fixed_order(const double* v, long long n, double* out, cudaStream_t st);

@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cmath>
@@ -231,23 +232,37 @@ __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
 // tolerance 2^-20 * max cost and the drift of the incrementally updated
 // FP32 potentials, refreshed every 64 pivots); every centroid whose interval
 // [D32_j - err_j, D32_j + err_j] reaches below the smallest upper end is a
-// candidate.  Output per object: cand[i*9] = count (-1: more than 8, solve
-// all K), cand[i*9+1..8] = candidate indices in increasing order.
+// candidate.
+// Work items are (object i, centroid block jb) with blocks of KB centroids,
+// so small batches still fill the GPU; lane groups take items from an
+// atomic counter (persistent kernel).  Output per item (18 ints at
+// item*18): count (-1: more than 8, -2: invalid object), 8 candidate
+// indices in increasing order, their 8 lower ends (float bits), and the
+// block's smallest upper end (float bits).
+constexpr int kItemInts = 18;
+
 template <int G, int NPL>
 __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, CentView cv, long long seg_size, int K,
-                                                SolveCfg cfg, size_t slice, int* cand_out, WarmStore ws,
-                                                int* err) {
+                                                int KB, int NB, SolveCfg cfg, size_t slice,
+                                                int* items_out, unsigned long long* queue,
+                                                WarmStore ws, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   Grp<G> g;
-  const int gpb = blockDim.x / G;
   unsigned char* base = smem + (threadIdx.x / G) * slice;
   const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax);
   int* cand = s32.sc;                                  // [8]
   float* clo = reinterpret_cast<float*>(s32.sc + 8);   // [8]
   int n_scr = 0, p_scr = 0;
   const float rel = (float)(cv.d + 3) * 0x1p-24f + 0x1p-17f;
-  for (long long i = (long long)blockIdx.x * gpb + threadIdx.x / G; i < ob.count;
-       i += (long long)gridDim.x * gpb) {
+  const unsigned long long total = (unsigned long long)ob.count * NB;
+  for (;;) {
+    unsigned long long item = 0;
+    if (g.lane == 0) item = atomicAdd(queue, 1ull);
+    item = __shfl_sync(g.mask, item, 0, G);
+    if (item >= total) break;
+    const long long i = (long long)(item / NB);
+    const int jb = (int)(item - (unsigned long long)i * NB);
+    const int j0 = jb * KB, j1 = min(K, j0 + KB);
     const long long o0 = ob.off[i];
     const int m = (int)(ob.off[i + 1] - o0);
     const long long cb = (i / seg_size) * (long long)K;
@@ -255,7 +270,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
     int ncand = 0;
     bool all = false;
     float best_hi = FLT_MAX;
-    for (int j = 0; ok && j < K; ++j) {
+    for (int j = j0; ok && j < j1; ++j) {
       const long long c0 = cv.off[cb + j];
       const int n = (int)(cv.off[cb + j + 1] - c0);
       if (n < 1 || n > cfg.nmax || m + n > G * NPL) { ok = false; break; }
@@ -306,12 +321,51 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
         ncand = k2;
       }
     }
-    int* out = cand_out + i * 9;
-    if (g.lane == 0) out[0] = !ok ? -2 : (all ? -1 : ncand);
-    if (g.lane >= 1 && g.lane <= 8) out[g.lane] = (g.lane <= ncand) ? cand[g.lane - 1] : -1;
+    int* out = items_out + item * kItemInts;
+    if (g.lane == 0) {
+      out[0] = !ok ? -2 : (all ? -1 : ncand);
+      out[17] = __float_as_int(best_hi);
+    }
+    if (g.lane >= 1 && g.lane <= 8) {
+      out[g.lane] = (g.lane <= ncand) ? cand[g.lane - 1] : -1;
+      out[8 + g.lane] = __float_as_int((g.lane <= ncand) ? clo[g.lane - 1] : FLT_MAX);
+    }
     g.sync();
   }
   if (g.lane == 0) add_stats(n_scr, p_scr, 0, 0);
+}
+
+// Per object: merge its NB block lists into one candidate list (count, 8
+// indices increasing) at cand[i*9]: keep the block candidates whose lower
+// end reaches the smallest upper end over all blocks.
+__global__ void k_merge(const int* items, long long N, int NB, int* cand) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int* it = items + i * NB * kItemInts;
+    float best_hi = FLT_MAX;
+    int state = 0;  // 0 ok, -1 all, -2 invalid
+    for (int b = 0; b < NB; ++b) {
+      const int c = it[b * kItemInts];
+      if (c == -2) state = -2;
+      else if (c == -1 && state == 0) state = -1;
+      best_hi = fminf(best_hi, __int_as_float(it[b * kItemInts + 17]));
+    }
+    int cnt = 0;
+    int* out = cand + i * 9;
+    if (state == 0) {
+      for (int b = 0; b < NB && state == 0; ++b) {
+        const int* blk = it + b * kItemInts;
+        for (int c = 0; c < blk[0]; ++c) {
+          if (__int_as_float(blk[9 + c]) <= best_hi) {
+            if (cnt < 8) out[1 + cnt] = blk[1 + c];
+            ++cnt;
+          }
+        }
+      }
+      if (cnt > 8) state = -1;
+    }
+    out[0] = state == 0 ? cnt : state;
+  }
 }
 
 // k_exact: the candidates of each object (all K for mode 0, for
@@ -527,17 +581,32 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
   cudaError_t e;
   const bool screen = cfg.mode == 1 && cand != nullptr;
   if (screen) {
-    e = launch_cfg(k_screen<G, NPL>, smem, gpb * G, cfg.sms, ob.count, gpb, &grid);
+    // centroid blocks: enough (object, block) items to fill the GPU
+    const long long want = (long long)cfg.sms * 96;
+    int NB = (int)std::min<long long>(std::max<long long>(1, (want + ob.count - 1) / ob.count),
+                                      std::max(1, K / 8));
+    const int KB = (K + NB - 1) / NB;
+    NB = (K + KB - 1) / KB;
+    // scratch layout: [queue counter: 4 ints][merged lists: count*9][items]
+    unsigned long long* queue = reinterpret_cast<unsigned long long*>(cand);
+    int* merged = cand + 4;
+    int* items = merged + ((ob.count * 9 + 3) & ~3LL);
+    e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_screen<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, cfg, slice, cand, ws, d_err);
-    note_launches(1);
+    e = launch_cfg(k_screen<G, NPL>, smem, gpb * G, cfg.sms, ob.count * (long long)NB, gpb, &grid);
+    if (e != cudaSuccess) return e;
+    k_screen<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, KB, NB, cfg, slice, items,
+                                                  queue, ws, d_err);
+    const unsigned mb = (unsigned)std::min<long long>((ob.count + 255) / 256, 4096);
+    k_merge<<<mb, 256, 0, st>>>(items, ob.count, NB, merged);
+    note_launches(2);
   }
   e = launch_cfg(k_exact<G, NPL>, smem, gpb * G, cfg.sms, ob.count, gpb, &grid);
   if (e != cudaSuccess) return e;
   WarmStore wx = ws;
   if (!screen) wx.par8 = nullptr;
   k_exact<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, cfg, slice,
-                                               screen ? cand : nullptr, omega, labels, dist2,
+                                               screen ? cand + 4 : nullptr, omega, labels, dist2,
                                                eps_terms, fo, wx, d_err);
   note_launches(1);
   return cudaGetLastError();

@@ -125,7 +125,8 @@ bool d2_server::launch(Slot& s, const std::shared_ptr<Request>& r) {
       !grow_dev(reinterpret_cast<unsigned char**>(&s.d_w), &s.n_w, std::max<size_t>(b_w, 16)) ||
       !grow_dev(&s.d_off, &s.n_off, b_off) || !grow_dev(&s.d_lab, &s.n_lab, (size_t)N * 4 + 16) ||
       !grow_dev(&s.d_d2, &s.n_d2, (size_t)N * 8 + 16) ||
-      !grow_dev(&s.d_cand, &s.n_cand, (size_t)N * 9 * 4 + 16) || !grow_host(&s.h_in, &s.n_in, b_in) ||
+      !grow_dev(&s.d_cand, &s.n_cand, (size_t)d2k::assign_scratch_ints(N, K, sms) * 4 + 16) ||
+      !grow_host(&s.h_in, &s.n_in, b_in) ||
       !grow_host(&s.h_out, &s.n_out, b_out))
     return false;
   std::memcpy(s.h_in, r->loc.data(), b_loc);
@@ -314,7 +315,8 @@ extern "C" int d2_server_submit(d2_server* sv, const d2_bags* objs, int64_t* tic
   r->loc.assign(static_cast<const unsigned char*>(objs->loc), static_cast<const unsigned char*>(objs->loc) + b_loc);
   r->w.assign(static_cast<const unsigned char*>(objs->w), static_cast<const unsigned char*>(objs->w) + b_w);
   r->off.assign(objs->off, objs->off + N + 1);
-  r->bytes = b_loc + b_w + (size_t)(N + 1) * 8 + (size_t)N * (4 + 8 + 36);
+  r->bytes = b_loc + b_w + (size_t)(N + 1) * 8 + (size_t)N * (4 + 8) +
+             (size_t)d2k::assign_scratch_ints(N, sv->K, sv->sms) * 4;
   r->t_submit = std::chrono::steady_clock::now();
   {
     std::lock_guard<std::mutex> lk(sv->mu);

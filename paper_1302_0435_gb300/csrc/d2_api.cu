@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "d2.h"
@@ -26,7 +28,8 @@ enum Slot {
   kFlowW, kEpsTerms, kEpsOut, kUpd, kLabelsIn, kCentIn0, kCentIn1, kCentIn2,
   // level driver
   kLvDataLoc, kLvDataW, kLvDataOff, kLvOmega, kLvOmegaNew, kLvC, kLvCT, kLvLab, kLvD2,
-  kLvCLoc32, kLvCLoc64, kLvCQ, kLvCW, kLvCOff, kLvTmp, kCand, kWarmMeta, kWarmFlow,
+  kLvCLoc32, kLvCLoc64, kLvCQ, kLvCW, kLvCOff, kLvTmp, kCand, kWarmMeta, kWarmFlow, kBins,
+  kBinSort, kTuneLab, kTuneD2,
   kSlots
 };
 
@@ -57,6 +60,10 @@ struct d2_ctx {
   int* d_err = nullptr;
   int* d_info = nullptr;
   int* h_pin = nullptr;  // pinned host ints
+  // autotuned launch shape per (nodes-per-lane bin, K, m bound, n bound, d,
+  // mode): threads per block and screening items per SM
+  std::map<std::tuple<int, long long, int, int, int, int>, std::pair<int, int>> tuned;
+  int tuning_runs = 0;
 };
 
 namespace {
@@ -268,6 +275,114 @@ constexpr size_t kWarmBudgetBytes = (size_t)32 << 30;
 unsigned blocks_for(long long n) {
   long long b = (n + 255) / 256;
   return (unsigned)std::max<long long>(1, std::min<long long>(b, 8192));
+}
+
+}  // namespace
+
+namespace {
+
+// Object bins by the nodes per lane their trees need (see d2k::bin_objects),
+// as a stable partition: order[start[b] .. start[b+1]) are bin b's objects
+// in increasing index.  Host copy of start in hstart[0..4].
+struct Bins {
+  int* order = nullptr;
+  long long hstart[5] = {0, 0, 0, 0, 0};
+  bool binned = false;
+};
+
+int make_bins(d2_ctx* c, const ObjView& v, int nmax, Bins* b) {
+  int rc = D2_OK;
+  const long long N = v.count;
+  int* bins = static_cast<int*>(grow(c, kBins, (size_t)N * 4, &rc));
+  void* scr = grow(c, kBinSort, d2k::update_scratch_bytes(N, 4), &rc);
+  if (rc != D2_OK) return rc;
+  CK(d2k::bin_objects(v, nmax, bins, c->stream));
+  d2k::FlowOut none{nullptr, nullptr, 0};
+  CK(d2k::update_locations(v, nullptr, bins, N, 4, none, 4, nullptr, v.d, 0, nullptr, nullptr, scr,
+                           c->stream));
+  // scratch layout of the sort: counts | tot | start | order | ...
+  const long long nchunks = (N + 1023) / 1024;
+  unsigned char* p = static_cast<unsigned char*>(scr);
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  p += al((size_t)nchunks * 4 * 4);
+  p += al((size_t)5 * 8);
+  const long long* start = reinterpret_cast<const long long*>(p);
+  p += al((size_t)5 * 8);
+  b->order = reinterpret_cast<int*>(p);
+  CK(cudaMemcpyAsync(b->hstart, start, 5 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  b->binned = true;
+  return D2_OK;
+}
+
+// One assign over a batch, bin by bin (largest trees first), each bin with
+// its autotuned launch shape.  ws may be null.
+int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, int K, int mode,
+               int mmax, const double* om, int* lab, double* d2o, double* terms, FlowOut fo,
+               int* cand, const d2k::WarmStore* ws, const Bins& bins) {
+  const int nmax = std::max(c->nmax, 1);
+  SolveCfg base = solve_cfg(c, mode, mmax);
+  if (!bins.binned) {
+    CK(d2k::assign(v, cv, seg, K, base, om, lab, d2o, terms, fo, cand, c->d_err, c->stream, ws));
+    return D2_OK;
+  }
+  for (int b = 3; b >= 0; --b) {
+    const long long cnt = bins.hstart[b + 1] - bins.hstart[b];
+    if (cnt <= 0) continue;
+    SolveCfg cfg = base;
+    cfg.mmax = std::max(1, std::min(mmax, 32 * (b + 1) - nmax));
+    cfg.oidx = bins.order + bins.hstart[b];
+    cfg.nobj = cnt;
+    const auto key = std::make_tuple(b, (long long)K, cfg.mmax, nmax, v.d, mode);
+    auto it = c->tuned.find(key);
+    if (it == c->tuned.end() && c->cfg.group_lanes == 0 && mode == 1 && cnt >= 8192) {
+      // autotune on a sample of this bin: threads per block x screening items per SM
+      SolveCfg t = cfg;
+      t.nobj = 2048;
+      int rc = D2_OK;
+      int* tl = static_cast<int*>(grow(c, kTuneLab, (size_t)v.count * 4, &rc));
+      double* td = static_cast<double*>(grow(c, kTuneD2, (size_t)v.count * 8, &rc));
+      if (rc != D2_OK) return rc;
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      float best = 1e30f;
+      std::pair<int, int> pick(128, 96);
+      const int tpbs[2] = {64, 128};
+      const int ipsms[3] = {48, 96, 192};
+      for (int tp : tpbs)
+        for (int ip : ipsms) {
+          t.tpb = tp;
+          t.ipsm = ip;
+          CK(cudaEventRecord(e0, c->stream));
+          CK(d2k::assign(v, cv, seg, K, t, om, tl, td, nullptr, FlowOut{nullptr, nullptr, 0}, cand,
+                         c->d_err, c->stream, nullptr));
+          CK(cudaEventRecord(e1, c->stream));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best) { best = ms; pick = std::make_pair(tp, ip); }
+        }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      ++c->tuning_runs;
+      it = c->tuned.emplace(key, pick).first;
+    }
+    if (it != c->tuned.end()) {
+      cfg.tpb = it->second.first;
+      cfg.ipsm = it->second.second;
+    }
+    CK(d2k::assign(v, cv, seg, K, cfg, om, lab, d2o, terms, fo, cand, c->d_err, c->stream, ws));
+  }
+  return D2_OK;
+}
+
+// Bin only when the batch is large and its trees span more than one bin.
+bool want_bins(const d2_ctx* c, long long count, int mmax) {
+  const int nmax = std::max(c->nmax, 1);
+  const int lo_bin = (1 + nmax + 31) / 32 - 1;
+  const int hi_bin = (mmax + nmax + 31) / 32 - 1;
+  return count >= 4096 && hi_bin > lo_bin;
 }
 
 }  // namespace
@@ -535,9 +650,11 @@ int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labe
   int* cand = static_cast<int*>(grow(c, kCand, (size_t)d2k::assign_scratch_ints(N, c->K, c->sms) * 4, &rc));
   if (rc != D2_OK) return rc;
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-  const SolveCfg cfg = solve_cfg(c, mode_for(c, objs->loc_dtype), mmax);
-  CK(d2k::assign(v, resident_view(c), N, (int)c->K, cfg, om, dl, dd, terms, fo, cand, c->d_err,
-                 c->stream));
+  Bins bins;
+  if (want_bins(c, N, mmax) && (rc = make_bins(c, v, c->nmax, &bins))) return rc;
+  if ((rc = run_assign(c, v, resident_view(c), N, (int)c->K, mode_for(c, objs->loc_dtype), mmax, om,
+                       dl, dd, terms, fo, cand, nullptr, bins)))
+    return rc;
   if (eps_total) {
     double* de = static_cast<double*>(grow(c, kEpsOut, 8, &rc));
     if (rc != D2_OK) return rc;
@@ -701,14 +818,62 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
       if (rc != D2_OK) return rc;
       ws = d2k::WarmStore{meta, meta + (size_t)npairs * ns, meta + (size_t)npairs * ns * 2, wf, ns, 0};
     }
+    Bins bins;
+    if (want_bins(c, n_l, cur_mmax) && (rc = make_bins(c, cur, c->nmax, &bins))) return rc;
+    // Rounds 2.. repeat the same launches (same pairs, warm bases): round 1
+    // is captured into a CUDA graph once and replayed.
+    cudaGraphExec_t gexec = nullptr;
+    long long glaunches = 0;
+    const bool graphs = iters > 2 && c->stream != nullptr && c->stream != cudaStreamLegacy &&
+                        c->stream != cudaStreamPerThread;
     for (int it = 0; it < std::max(iters, 1); ++it) {
       ws.warm = it > 0;
-      CK(d2k::assign(cur, cv, seg, K, cfg, om, lab, ld2, nullptr, fo, cand, c->d_err, c->stream,
-                     ws.par8 ? &ws : nullptr));
-      if (it < iters)
-        CK(d2k::update_locations(cur, om, lab, seg, K, fo, KT, loff, d, c->cent_ldt, l32, l64, scr,
-                                 c->stream));
+      if (gexec && it >= 2) {
+        CK(cudaGraphLaunch(gexec, c->stream));
+        d2k::note_launches(glaunches);
+        continue;
+      }
+      const bool capture = graphs && it == 1;
+      const long long l0 = d2k::launches();
+      if (capture && cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+      }
+      cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+      cudaStreamIsCapturing(c->stream, &cst);
+      const bool capturing = cst == cudaStreamCaptureStatusActive;
+      int rc2 = run_assign(c, cur, cv, seg, K, cfg.mode, cur_mmax, om, lab, ld2, nullptr, fo, cand,
+                           ws.par8 ? &ws : nullptr, bins);
+      cudaError_t ue = cudaSuccess;
+      if (rc2 == D2_OK && it < iters)
+        ue = d2k::update_locations(cur, om, lab, seg, K, fo, KT, loff, d, c->cent_ldt, l32, l64, scr,
+                                   c->stream);
+      if (capturing) {
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+        bool ok = ce == cudaSuccess && rc2 == D2_OK && ue == cudaSuccess && graph &&
+                  cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        glaunches = d2k::launches() - l0;
+        if (!ok) {
+          cudaGetLastError();
+          if (gexec) cudaGraphExecDestroy(gexec);
+          gexec = nullptr;
+          // run the round directly instead
+          if ((rc = run_assign(c, cur, cv, seg, K, cfg.mode, cur_mmax, om, lab, ld2, nullptr, fo,
+                               cand, ws.par8 ? &ws : nullptr, bins)))
+            return rc;
+          if (it < iters)
+            CK(d2k::update_locations(cur, om, lab, seg, K, fo, KT, loff, d, c->cent_ldt, l32, l64,
+                                     scr, c->stream));
+        } else {
+          CK(cudaGraphLaunch(gexec, c->stream));
+        }
+        continue;
+      }
+      if (rc2 != D2_OK) return rc2;
+      CK(ue);
     }
+    if (gexec) cudaGraphExecDestroy(gexec);
     // merge (Eq. (UpdateLabel), Eq. (UpdateGlobalLabel)) and member weights
     FlowOut sort_only{nullptr, nullptr, 0};
     CK(d2k::update_locations(cur, om, lab, seg, K, sort_only, KT, loff, d, c->cent_ldt, l32, l64,

@@ -53,6 +53,10 @@ struct SolveCfg {
   int mmax, nmax;  // support bounds of the launch
   int budget;      // pivots per pair = budget*(m+n)
   int sms;         // SM count
+  int tpb = 128;   // threads per block of the solver kernels (64 or 128)
+  int ipsm = 96;   // screening work items per SM the centroid blocks aim for
+  const int* oidx = nullptr;  // objects of this launch (nullptr: 0..count-1)
+  long long nobj = -1;        // entries of oidx (-1: all ob.count objects)
 };
 
 // Error bits raised by kernels into a device int.
@@ -73,12 +77,13 @@ cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, in
                    const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
                    double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st,
                    const WarmStore* ws = nullptr);
-// ints of assign scratch for `count` objects and K centroids per object
+// ints of assign scratch for `count` objects and K centroids per object:
+// queue counter, merged lists [count*9], and per-(object, centroid block)
+// items; a launch over nobj <= count objects makes at most
+// nobj*ceil(want/nobj) <= want + count items, want <= sms*256.
 inline long long assign_scratch_ints(long long count, long long K, int sms = 160) {
-  const long long want = (long long)sms * 96;
-  long long NB = std::max<long long>(1, (want + count - 1) / (count > 0 ? count : 1));
-  NB = std::min<long long>(NB, std::max<long long>(1, K / 8));
-  return 4 + ((count * 9 + 3) & ~3LL) + count * NB * 18 + 4;
+  (void)K;
+  return 4 + ((count * 9 + 3) & ~3LL) + (count + (long long)sms * 256) * 18 + 4;
 }
 cudaError_t cost_matrix(const ObjView& ob, const CentView& cv, long long i, long long j, int mode,
                         double* C, cudaStream_t st);
@@ -104,6 +109,11 @@ cudaError_t update_locations(const ObjView& ob, const double* omega, const int* 
 // only sorts): per centroid sum of omega over its members, object order.
 cudaError_t group_weight_sum(const double* omega, long long N, long long KT, void* scratch,
                              double* out, cudaStream_t st);
+
+// Bin of each object by the lanes' node count its tree needs with centroid
+// supports up to nmax: bin b holds m + nmax <= 32*(b+1); -1 if m is out of
+// range.  labels_out: [count] ints.
+cudaError_t bin_objects(const ObjView& ob, int nmax, int* bins_out, cudaStream_t st);
 
 int device_sms(int dev);
 

@@ -254,14 +254,16 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
   float* clo = reinterpret_cast<float*>(s32.sc + 8);   // [8]
   int n_scr = 0, p_scr = 0;
   const float rel = (float)(cv.d + 3) * 0x1p-24f + 0x1p-17f;
-  const unsigned long long total = (unsigned long long)ob.count * NB;
+  const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
+  const unsigned long long total = (unsigned long long)nobj * NB;
   for (;;) {
     unsigned long long item = 0;
     if (g.lane == 0) item = atomicAdd(queue, 1ull);
     item = __shfl_sync(g.mask, item, 0, G);
     if (item >= total) break;
-    const long long i = (long long)(item / NB);
-    const int jb = (int)(item - (unsigned long long)i * NB);
+    const long long tt = (long long)(item / NB);
+    const long long i = cfg.oidx ? (long long)cfg.oidx[tt] : tt;
+    const int jb = (int)(item - (unsigned long long)tt * NB);
     const int j0 = jb * KB, j1 = min(K, j0 + KB);
     const long long o0 = ob.off[i];
     const int m = (int)(ob.off[i + 1] - o0);
@@ -338,10 +340,11 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
 // Per object: merge its NB block lists into one candidate list (count, 8
 // indices increasing) at cand[i*9]: keep the block candidates whose lower
 // end reaches the smallest upper end over all blocks.
-__global__ void k_merge(const int* items, long long N, int NB, int* cand) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int* it = items + i * NB * kItemInts;
+__global__ void k_merge(const int* items, long long N, int NB, const int* oidx, int* cand) {
+  for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < N;
+       tt += (long long)gridDim.x * blockDim.x) {
+    const long long i = oidx ? (long long)oidx[tt] : tt;
+    const int* it = items + tt * NB * kItemInts;
     float best_hi = FLT_MAX;
     int state = 0;  // 0 ok, -1 all, -2 invalid
     for (int b = 0; b < NB; ++b) {
@@ -384,8 +387,10 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
   unsigned char* base = smem + (threadIdx.x / G) * slice;
   const PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax);
   int n_ex = 0, p_ex = 0;
-  for (long long i = (long long)blockIdx.x * gpb + threadIdx.x / G; i < ob.count;
-       i += (long long)gridDim.x * gpb) {
+  const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
+  for (long long tt = (long long)blockIdx.x * gpb + threadIdx.x / G; tt < nobj;
+       tt += (long long)gridDim.x * gpb) {
+    const long long i = cfg.oidx ? (long long)cfg.oidx[tt] : tt;
     const long long o0 = ob.off[i];
     const int m = (int)(ob.off[i + 1] - o0);
     const long long cb = (i / seg_size) * (long long)K;
@@ -441,6 +446,15 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
     g.sync();
   }
   if (g.lane == 0) add_stats(0, 0, n_ex, p_ex);
+}
+
+__global__ void k_bin_of(const long long* off, long long count, int nmax, int* bins) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long m = off[i + 1] - off[i];
+    const long long nn = m + nmax;
+    bins[i] = (m < 1 || nn > 128) ? -1 : (int)((nn + 31) / 32 - 1);
+  }
 }
 
 __global__ void k_cost_matrix(ObjView ob, CentView cv, long long i, long long j, int mode,
@@ -524,10 +538,10 @@ cudaError_t prep_centroids(const void* loc, int ldt, const void* w, int wdt, con
 
 // Groups per block: up to 128 threads, whole warps only, within the
 // 227 KB shared-memory limit of a block.  0 if one warp does not fit.
-static int groups_per_block(int G, size_t slice) {
+static int groups_per_block(int G, size_t slice, int tpb = 128) {
   const size_t limit = 227 * 1024;
   const int per_warp = 32 / G;
-  int gpb = 128 / G;
+  int gpb = (tpb >= 32 && tpb <= 128 ? tpb : 128) / G;
   while (gpb >= per_warp && (size_t)gpb * slice > limit) gpb -= per_warp;
   return gpb >= per_warp ? gpb : 0;
 }
@@ -574,34 +588,36 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
   WarmStore ws{nullptr, nullptr, nullptr, nullptr, 0, 0};
   if (wsp) ws = *wsp;
   const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax);
-  const int gpb = groups_per_block(G, slice);
+  const int gpb = groups_per_block(G, slice, cfg.tpb);
   if (gpb == 0) return cudaErrorInvalidConfiguration;
   const size_t smem = slice * gpb;
   unsigned grid = 1;
   cudaError_t e;
   const bool screen = cfg.mode == 1 && cand != nullptr;
+  const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
+  if (nobj <= 0) return cudaSuccess;
   if (screen) {
     // centroid blocks: enough (object, block) items to fill the GPU
-    const long long want = (long long)cfg.sms * 96;
-    int NB = (int)std::min<long long>(std::max<long long>(1, (want + ob.count - 1) / ob.count),
+    const long long want = (long long)cfg.sms * std::min(std::max(cfg.ipsm, 8), 256);
+    int NB = (int)std::min<long long>(std::max<long long>(1, (want + nobj - 1) / nobj),
                                       std::max(1, K / 8));
     const int KB = (K + NB - 1) / NB;
     NB = (K + KB - 1) / KB;
     // scratch layout: [queue counter: 4 ints][merged lists: count*9][items]
     unsigned long long* queue = reinterpret_cast<unsigned long long*>(cand);
     int* merged = cand + 4;
-    int* items = merged + ((ob.count * 9 + 3) & ~3LL);
+    int* items = merged + ((ob.count * 9 + 3) & ~3LL);  // merged is indexed by object
     e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    e = launch_cfg(k_screen<G, NPL>, smem, gpb * G, cfg.sms, ob.count * (long long)NB, gpb, &grid);
+    e = launch_cfg(k_screen<G, NPL>, smem, gpb * G, cfg.sms, nobj * (long long)NB, gpb, &grid);
     if (e != cudaSuccess) return e;
     k_screen<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, KB, NB, cfg, slice, items,
                                                   queue, ws, d_err);
-    const unsigned mb = (unsigned)std::min<long long>((ob.count + 255) / 256, 4096);
-    k_merge<<<mb, 256, 0, st>>>(items, ob.count, NB, merged);
+    const unsigned mb = (unsigned)std::min<long long>((nobj + 255) / 256, 4096);
+    k_merge<<<mb, 256, 0, st>>>(items, nobj, NB, cfg.oidx, merged);
     note_launches(2);
   }
-  e = launch_cfg(k_exact<G, NPL>, smem, gpb * G, cfg.sms, ob.count, gpb, &grid);
+  e = launch_cfg(k_exact<G, NPL>, smem, gpb * G, cfg.sms, nobj, gpb, &grid);
   if (e != cudaSuccess) return e;
   WarmStore wx = ws;
   if (!screen) wx.par8 = nullptr;
@@ -656,6 +672,14 @@ cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, in
   D2_BINS(X)
 #undef X
   return cudaErrorInvalidValue;
+}
+
+cudaError_t bin_objects(const ObjView& ob, int nmax, int* bins_out, cudaStream_t st) {
+  if (ob.count <= 0) return cudaSuccess;
+  const unsigned b = (unsigned)std::min<long long>((ob.count + 255) / 256, 4096);
+  k_bin_of<<<b, 256, 0, st>>>(ob.off, ob.count, nmax, bins_out);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t cost_matrix(const ObjView& ob, const CentView& cv, long long i, long long j, int mode,

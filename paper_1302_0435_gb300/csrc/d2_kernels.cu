@@ -85,6 +85,138 @@ __device__ T build_cost(const Grp<G>& g, T* C, int m, int n, const void* xl, int
   return cmax;
 }
 
+// ---------------------------------------------------------- start order --
+// The cold-start basis is the northwest staircase taken in the order of
+// the supports' projections onto the object's principal direction (in 1-D
+// that staircase is the optimal monotone coupling; in d dimensions it is a
+// start close to it along the dominant axis).
+
+// inclusive prefix of per-id masses (from the by-id inclusive prefix `pre`)
+// in the order id_of[0..cnt)
+template <int G>
+__device__ void prefix_in_order(const Grp<G>& g, const long long* pre, const int* id_of, int cnt,
+                                long long* out) {
+  long long carry = 0;
+  for (int base = 0; base < cnt; base += G) {
+    const int r = base + g.lane;
+    long long v = 0;
+    if (r < cnt) {
+      const int id = id_of[r];
+      v = pre[id] - (id > 0 ? pre[id - 1] : 0LL);
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      const long long u = __shfl_up_sync(g.mask, v, o, G);
+      if (g.lane >= o) v += u;
+    }
+    v += carry;
+    if (r < cnt) out[r] = v;
+    carry = __shfl_sync(g.mask, v, G - 1, G);
+  }
+  g.sync();
+}
+
+// stable ranks of proj[0..cnt) (ties to the smaller index)
+template <int G>
+__device__ void rank_by_proj(const Grp<G>& g, const float* proj, int cnt, int* rank, int* id) {
+  for (int a = g.lane; a < cnt; a += G) {
+    const float v = proj[a];
+    int r = 0;
+    for (int b = 0; b < cnt; ++b) {
+      const float u = proj[b];
+      r += (u < v || (u == v && b < a)) ? 1 : 0;
+    }
+    rank[a] = r;
+    id[r] = a;
+  }
+  g.sync();
+}
+
+// Object side: weighted mean, principal direction by power iteration from
+// the farthest support, row ranks and rank-order prefix masses.
+template <int G>
+__device__ void order_rows(const Grp<G>& g, const PairMem<float>& s, const ObjView& ob, long long o0,
+                           int m, int d) {
+  const float wscale = (float)kInvMass;
+  for (int k = g.lane; k < d; k += G) {
+    float acc = 0.f;
+    for (int a = 0; a < m; ++a) {
+      const float pa = (float)(s.P[a] - (a > 0 ? s.P[a - 1] : 0LL)) * wscale;
+      acc = fmaf(pa, ldx<float>(ob.loc, ob.ldt, (o0 + a) * d + k), acc);
+    }
+    s.mu[k] = acc;
+  }
+  g.sync();
+  // start: the support farthest from the mean (largest weighted deviation)
+  float best = -1.f;
+  int bi = 0;
+  for (int a = g.lane; a < m; a += G) {
+    float dev = 0.f;
+    for (int k = 0; k < d; ++k) {
+      const float x = ldx<float>(ob.loc, ob.ldt, (o0 + a) * d + k) - s.mu[k];
+      dev = fmaf(x, x, dev);
+    }
+    dev *= (float)(s.P[a] - (a > 0 ? s.P[a - 1] : 0LL)) * wscale;
+    if (dev > best) { best = dev; bi = a; }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const float ob2 = gshfl_xor<G>(g, best, o);
+    const int oi = gshfl_xor<G>(g, bi, o);
+    if (ob2 > best || (ob2 == best && oi < bi)) { best = ob2; bi = oi; }
+  }
+  for (int k = g.lane; k < d; k += G) s.dir[k] = ldx<float>(ob.loc, ob.ldt, (o0 + bi) * d + k) - s.mu[k];
+  g.sync();
+  for (int it = 0; it < 6; ++it) {
+    for (int a = g.lane; a < m; a += G) {
+      float dot = 0.f;
+      for (int k = 0; k < d; ++k) dot = fmaf(ldx<float>(ob.loc, ob.ldt, (o0 + a) * d + k) - s.mu[k], s.dir[k], dot);
+      s.proj[a] = dot * (float)(s.P[a] - (a > 0 ? s.P[a - 1] : 0LL)) * wscale;
+    }
+    g.sync();
+    float nrm = 0.f;
+    float vk[8];
+    int nk = 0;
+    for (int k = g.lane; k < d; k += G) {
+      float acc = 0.f;
+      for (int a = 0; a < m; ++a) acc = fmaf(s.proj[a], ldx<float>(ob.loc, ob.ldt, (o0 + a) * d + k) - s.mu[k], acc);
+      if (nk < 8) vk[nk++] = acc;
+      nrm = fmaf(acc, acc, nrm);
+    }
+    nrm = gsum<G>(g, nrm);
+    g.sync();
+    const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
+    nk = 0;
+    for (int k = g.lane; k < d; k += G) {
+      if (nk < 8) s.dir[k] = inv > 0.f ? vk[nk] * inv : s.dir[k];
+      ++nk;
+    }
+    g.sync();
+  }
+  for (int a = g.lane; a < m; a += G) {
+    float dot = 0.f;
+    for (int k = 0; k < d; ++k) dot = fmaf(ldx<float>(ob.loc, ob.ldt, (o0 + a) * d + k) - s.mu[k], s.dir[k], dot);
+    s.proj[a] = dot;
+  }
+  g.sync();
+  rank_by_proj<G>(g, s.proj, m, s.rrank, s.rid);
+  prefix_in_order<G>(g, s.P, s.rid, m, s.Pr);
+}
+
+// Centroid side: column ranks along the object's direction and their
+// rank-order prefix masses (s.Q holds the centroid's by-id prefix).
+template <int G>
+__device__ void order_cols(const Grp<G>& g, const PairMem<float>& s, const float* y32, int n, int d) {
+  for (int r = g.lane; r < n; r += G) {
+    float dot = 0.f;
+    for (int k = 0; k < d; ++k) dot = fmaf(y32[(long long)r * d + k] - s.mu[k], s.dir[k], dot);
+    s.proj[r] = dot;
+  }
+  g.sync();
+  rank_by_proj<G>(g, s.proj, n, s.crank, s.cid);
+  prefix_in_order<G>(g, s.Q, s.cid, n, s.Qr);
+}
+
 template <int G>
 __device__ bool load_obj_prefix(const Grp<G>& g, const ObjView& ob, long long o0, int m,
                                 long long* P) {
@@ -123,8 +255,12 @@ __device__ __forceinline__ int solve_exact(const Grp<G>& g, const PairMem<double
     const float c32 = build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
                                            cv.loc32 + c0 * cv.d, cv.d);
     Simplex<float, G, NPL> S32(s32, m, n, g);
-    if (S32.solve(cap, tol32(c32), &piv) == kStInvalid) { *piv_out += piv; return kStInvalid; }
+    order_rows<G>(g, s32, ob, o0, m, cv.d);
+    order_cols<G>(g, s32, cv.loc32 + c0 * cv.d, n, cv.d);
+    S32.init_northwest_ranked();
+    if (S32.run(cap, tol32(c32), &piv) == kStInvalid) { *piv_out += piv; return kStInvalid; }
     S.t = S32.t;
+    S.root = S32.root;
     g.sync();
   }
   const double cmax = build_cost<double, G>(g, s.cost, m, n, ob.loc, ob.ldt, o0,
@@ -200,7 +336,7 @@ __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
       const long long c0 = cv.off[j];
       const int n = (int)(cv.off[j + 1] - c0);
       if (m >= 1 && m <= cfg.mmax && n >= 1 && n <= cfg.nmax && m + n <= G * NPL) {
-        PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax);
+        PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax, cv.d);
         if (load_obj_prefix<G>(g, ob, o0, m, s64.P)) {
           Simplex<double, G, NPL> S(s64, m, n, g);
           st = solve_exact<G, NPL>(g, s64, S, ob, o0, m, cv, c0, n, cfg.budget, cfg.mode == 1,
@@ -249,7 +385,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
   extern __shared__ __align__(16) unsigned char smem[];
   Grp<G> g;
   unsigned char* base = smem + (threadIdx.x / G) * slice;
-  const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax);
+  const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax, cv.d);
   int* cand = s32.sc;                                  // [8]
   float* clo = reinterpret_cast<float*>(s32.sc + 8);   // [8]
   int n_scr = 0, p_scr = 0;
@@ -269,6 +405,8 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
     const int m = (int)(ob.off[i + 1] - o0);
     const long long cb = (i / seg_size) * (long long)K;
     bool ok = m >= 1 && m <= cfg.mmax && cb + K <= cv.K && load_obj_prefix<G>(g, ob, o0, m, s32.P);
+    const bool cold = !(ws.par8 && ws.warm);
+    if (ok && cold) order_rows<G>(g, s32, ob, o0, m, cv.d);
     int ncand = 0;
     bool all = false;
     float best_hi = FLT_MAX;
@@ -282,12 +420,13 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       Simplex<float, G, NPL> S(s32, m, n, g);
       const long long wt = (i * (long long)K + j) * ws.ns;
       int st;
-      if (ws.par8 && ws.warm) {
+      if (!cold) {
         S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
-        st = S.run(cfg.budget * (m + n), tol32(cmax), &p_scr, false);
       } else {
-        st = S.solve(cfg.budget * (m + n), tol32(cmax), &p_scr, false);
+        order_cols<G>(g, s32, cv.loc32 + c0 * cv.d, n, cv.d);
+        S.init_northwest_ranked();
       }
+      st = S.run(cfg.budget * (m + n), tol32(cmax), &p_scr, false);
       if (ws.par8) {
         // always leave a valid basis for the next round
         if (st == kStInvalid) S.init_northwest();
@@ -385,7 +524,7 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
   Grp<G> g;
   const int gpb = blockDim.x / G;
   unsigned char* base = smem + (threadIdx.x / G) * slice;
-  const PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax);
+  const PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax, cv.d);
   int n_ex = 0, p_ex = 0;
   const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
   for (long long tt = (long long)blockIdx.x * gpb + threadIdx.x / G; tt < nobj;
@@ -567,7 +706,7 @@ static cudaError_t mallows_pairs_g(const ObjView& ob, const CentView& cv, const 
                                    const long long* pcen, long long npairs, const SolveCfg& cfg,
                                    double* dist2, FlowOut fo, int* status, int* d_err,
                                    cudaStream_t st) {
-  const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax);
+  const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax, cv.d);
   const int gpb = groups_per_block(G, slice);
   if (gpb == 0) return cudaErrorInvalidConfiguration;
   const size_t smem = slice * gpb;
@@ -587,7 +726,7 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
                             const WarmStore* wsp) {
   WarmStore ws{nullptr, nullptr, nullptr, nullptr, 0, 0};
   if (wsp) ws = *wsp;
-  const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax);
+  const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax, cv.d);
   const int gpb = groups_per_block(G, slice, cfg.tpb);
   if (gpb == 0) return cudaErrorInvalidConfiguration;
   const size_t smem = slice * gpb;

@@ -104,13 +104,27 @@ struct PairMem {
   T* acc0;            // [N]
   T* acc1;            // [N]
   int* sc;            // [16] group scalars
+  // projection order of the start basis (see order_rows / order_cols)
+  int* rrank;         // [mmax] row -> rank
+  int* rid;           // [mmax] rank -> row
+  int* crank;         // [nmax] column -> rank
+  int* cid;           // [nmax] rank -> column
+  long long* Pr;      // [mmax] prefix masses in rank order
+  long long* Qr;      // [nmax]
+  float* dir;         // [dmax] principal direction of the object
+  float* mu;          // [dmax] weighted mean of the object
+  float* proj;        // [max(mmax,nmax)] projections
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline size_t pair_mem_bytes(int mmax, int nmax) {
+__host__ __device__ inline size_t pair_mem_bytes(int mmax, int nmax, int dmax = 256) {
   const size_t N = (size_t)(mmax + nmax);
+  const size_t mx = (size_t)(mmax > nmax ? mmax : nmax);
   size_t b = 0;
+  b += align_up((size_t)mmax * 4, 16) * 2 + align_up((size_t)nmax * 4, 16) * 2;  // ranks
+  b += align_up((size_t)mmax * 8, 16) + align_up((size_t)nmax * 8, 16);          // Pr Qr
+  b += align_up((size_t)dmax * 4, 16) * 2 + align_up(mx * 4, 16);               // dir mu proj
   b += align_up((size_t)mmax * nmax * 8, 16);  // cost
   b += align_up(N * 8, 16);                    // pot
   b += align_up(N * 4, 16) * 2;                // pos sz
@@ -126,10 +140,20 @@ __host__ __device__ inline size_t pair_mem_bytes(int mmax, int nmax) {
 }
 
 template <typename T>
-__device__ inline PairMem<T> carve(unsigned char* base, int mmax, int nmax) {
+__device__ inline PairMem<T> carve(unsigned char* base, int mmax, int nmax, int dmax = 256) {
   const size_t N = (size_t)(mmax + nmax);
+  const size_t mx = (size_t)(mmax > nmax ? mmax : nmax);
   PairMem<T> s;
   unsigned char* p = base;
+  s.rrank = reinterpret_cast<int*>(p); p += align_up((size_t)mmax * 4, 16);
+  s.rid = reinterpret_cast<int*>(p); p += align_up((size_t)mmax * 4, 16);
+  s.crank = reinterpret_cast<int*>(p); p += align_up((size_t)nmax * 4, 16);
+  s.cid = reinterpret_cast<int*>(p); p += align_up((size_t)nmax * 4, 16);
+  s.Pr = reinterpret_cast<long long*>(p); p += align_up((size_t)mmax * 8, 16);
+  s.Qr = reinterpret_cast<long long*>(p); p += align_up((size_t)nmax * 8, 16);
+  s.dir = reinterpret_cast<float*>(p); p += align_up((size_t)dmax * 4, 16);
+  s.mu = reinterpret_cast<float*>(p); p += align_up((size_t)dmax * 4, 16);
+  s.proj = reinterpret_cast<float*>(p); p += align_up(mx * 4, 16);
   s.cost = reinterpret_cast<T*>(p); p += align_up((size_t)mmax * nmax * 8, 16);
   s.pot = reinterpret_cast<T*>(p); p += align_up(N * 8, 16);
   s.pos = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
@@ -159,6 +183,8 @@ __device__ inline PairMem<T2> recast(const PairMem<T1>& s) {
   o.acc0 = reinterpret_cast<T2*>(s.acc0);
   o.acc1 = reinterpret_cast<T2*>(s.acc1);
   o.sc = s.sc;
+  o.rrank = s.rrank; o.rid = s.rid; o.crank = s.crank; o.cid = s.cid; o.Pr = s.Pr; o.Qr = s.Qr;
+  o.dir = s.dir; o.mu = s.mu; o.proj = s.proj;
   return o;
 }
 
@@ -244,6 +270,7 @@ struct Simplex {
   int a0, r0, sq, sr;
   int cand = -1;     // this lane's candidate cell from the last full pricing
   int cand_a = 0, cand_r = 0;
+  int root = 0;      // the tree root: the node at preorder position 0
 
   __device__ __forceinline__ Simplex(const PairMem<T>& s_, int m_, int n_, const Grp<G>& g_)
       : s(s_), m(m_), n(n_), N(m_ + n_), g(g_) {
@@ -273,6 +300,7 @@ struct Simplex {
   // re(a) = first r with Q_r >= P_a.  As a tree rooted at row 0, a node's
   // preorder position is the step at which the path first touches it.
   __device__ __forceinline__ void init_northwest() {
+    root = 0;
     const long long* P = s.P;
     const long long* Q = s.Q;
 #pragma unroll
@@ -334,6 +362,75 @@ struct Simplex {
     g.sync();
   }
 
+  // The same northwest staircase taken in rank order: rows and columns are
+  // visited in the order of their projections (rrank/crank, prefix masses
+  // Pr/Qr in that order, see order_rows/order_cols).  Node ids stay the
+  // real rows and columns; only the visiting order changes, so the result
+  // is again a spanning-tree basis with its basic flows.
+  __device__ __forceinline__ void init_northwest_ranked() {
+    root = s.rid[0];
+    const long long* P = s.Pr;
+    const long long* Q = s.Qr;
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int a = node_of(k);
+      if (a < m) {
+        const int ra = s.rrank[a];
+        int e = n - 1;
+        if (ra < m - 1) {
+          int lo = 0, hi = n - 1;
+          const long long key = P[ra];
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (Q[mid] >= key) hi = mid; else lo = mid + 1;
+          }
+          e = lo;
+        }
+        s.re[ra] = e;
+      }
+    }
+    g.sync();
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y < m) {
+        const int a = s.rrank[y];
+        if (a == 0) {
+          t.par[k] = -1; t.pos[k] = 0; t.sz[k] = N; t.flow[k] = 0;
+        } else {
+          const int c = s.re[a - 1];
+          const long long lo = max(P[a - 1], c > 0 ? Q[c - 1] : 0LL);
+          const long long hi = min(P[a], Q[c]);
+          t.par[k] = m + s.cid[c];
+          t.pos[k] = a + c + 1;
+          t.flow[k] = hi > lo ? hi - lo : 0;
+          t.sz[k] = (s.re[a] == c) ? 1 : N - (a + c + 1);
+        }
+      } else if (y < N) {
+        const int r = s.crank[y - m];
+        int af = 0;
+        if (r > 0) {
+          const long long key = Q[r - 1];
+          int lo = 0, hi = m - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (P[mid] <= key) lo = mid + 1; else hi = mid;
+          }
+          af = lo;
+        }
+        const long long lo = max(af > 0 ? P[af - 1] : 0LL, r > 0 ? Q[r - 1] : 0LL);
+        const long long hi = min(P[af], Q[r]);
+        t.par[k] = s.rid[af];
+        t.pos[k] = af + r + 1;
+        t.flow[k] = hi > lo ? hi - lo : 0;
+        const bool spine = (af < m - 1) && (s.re[af] == r);
+        t.sz[k] = spine ? N - (af + r + 1) : 1;
+      }
+      if (y < N) { s.pos[y] = t.pos[k]; s.sz[y] = t.sz[k]; }
+    }
+    g.sync();
+  }
+
   // Potentials from the tree: pot(root) = 0, pot(y) = c(y,par y) - pot(par y),
   // by pointer jumping: pot(y) = acc(y) + (-1)^parity(y) * pot(anc(y)).
   __device__ __forceinline__ void refresh_potentials() {
@@ -343,10 +440,10 @@ struct Simplex {
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
       const int y = node_of(k);
-      if (y == 0) { pa[0] = 0; aa[0] = T(0); }
+      if (y == root) { pa[y] = y; aa[y] = T(0); }   // the root points at itself
       else if (y < N) {
         const int p = t.par[k];
-        if (p < 0 || p >= N || (y < m) == (p < m)) { lbad = true; pa[y] = 0; aa[y] = T(0); }
+        if (p < 0 || p >= N || (y < m) == (p < m)) { lbad = true; pa[y] = root; aa[y] = T(0); }
         else { pa[y] = p | (1 << 16); aa[y] = s.cost[edge_idx(y, p)]; }
       }
     }
@@ -361,7 +458,7 @@ struct Simplex {
         if (y < N) {
           const int code = pa[y];
           const int an = code & 0xffff;
-          if (an != 0) {
+          if (an != root) {
             const int c2 = pa[an];
             const T v = aa[an];
             const int par1 = code >> 16;
@@ -387,6 +484,8 @@ struct Simplex {
     g.sync();
   }
 
+  // Pricing over the lane's cells t = lane, lane+G, ...  Returns the
+  // entering cell key ((row << 8) | col) or -1, and its reduced cost.
   // order-preserving map of a value to an unsigned key (smaller value ->
   // smaller key), so group minima can use the integer reduction unit
   __device__ __forceinline__ static unsigned okey(float v) {
@@ -694,7 +793,7 @@ struct Simplex {
     for (int k = 0; k < NPL; ++k) {
       const int y = node_of(k);
       if (y < N) {
-        par8[y] = (unsigned char)(t.par[k] & 0xff);
+        par8[y] = (unsigned char)(t.par[k] & 0xff);  // root: 255, recognised by pos 0
         pos8[y] = (unsigned char)t.pos[k];
         sz8[y] = (unsigned char)t.sz[k];
         flow[y] = t.flow[k];
@@ -705,18 +804,21 @@ struct Simplex {
   // so its flows are still the basic solution).
   __device__ __forceinline__ void load_tree(const unsigned char* par8, const unsigned char* pos8,
                                             const unsigned char* sz8, const long long* flow) {
+    int r0 = INT_MAX;
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
       const int y = node_of(k);
       if (y < N) {
-        t.par[k] = y == 0 ? -1 : (int)par8[y];
         t.pos[k] = pos8[y];
+        t.par[k] = t.pos[k] == 0 ? -1 : (int)par8[y];
         t.sz[k] = sz8[y];
         t.flow[k] = flow[y];
         s.pos[y] = t.pos[k];
         s.sz[y] = t.sz[k];
+        if (t.pos[k] == 0) r0 = y;
       }
     }
+    root = (int)__reduce_min_sync(g.mask, (unsigned)r0);
     g.sync();
   }
 
@@ -727,23 +829,25 @@ struct Simplex {
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
       const int y = node_of(k);
-      if (y > 0 && y < N)
-        acc += (A)((double)t.flow[k] * kInvMass) * (A)s.cost[edge_idx(y, t.par[k])];
+      if (y < N && y != root)
+        acc += ((A)t.flow[k] * (A)kInvMass) * (A)s.cost[edge_idx(y, t.par[k])];
     }
     return gsum<G>(g, acc);
   }
 
-  // Basis flows as (cell, w) records: entry y-1 for node y != root.
+  // Basis flows as (cell, w) records: one entry per node but the root
+  // (entry y, or y-1 past the root).
   __device__ __forceinline__ void write_flows(int* cell, double* w, long long stride) const {
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
       const int y = node_of(k);
-      if (y > 0 && y < N) {
+      if (y < N && y != root) {
         const int p = t.par[k];
         const int row = y < m ? y : p;
         const int col = y < m ? p - m : y - m;
-        cell[y - 1] = (row << 16) | col;
-        w[y - 1] = (double)t.flow[k] * kInvMass;
+        const int e = y < root ? y : y - 1;
+        cell[e] = (row << 16) | col;
+        w[e] = (double)t.flow[k] * kInvMass;
       }
     }
     for (long long e = N - 1 + g.lane; e < stride; e += G) {

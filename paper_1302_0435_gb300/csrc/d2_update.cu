@@ -110,7 +110,17 @@ __device__ __forceinline__ double round_to(double v, int dt) {
   return v;
 }
 
-// one block per centroid; dynamic smem: num [n*d] doubles + den [n]
+constexpr int kChunkMembers = 8;  // members staged per step
+constexpr int kMaxStride = 127;
+
+// One block per centroid.  Members (objects assigned to it, increasing
+// index) are staged kChunkMembers at a time: their flow entries' centroid
+// support r, object row and coefficient omega_i * w go to shared memory;
+// then every (r, k) slot of the numerator sums, in entry order, the
+// entries of its column r (coef * v^(a)_k) in FP64; the k == 0 slot also
+// sums the denominator.  The order of every sum is fixed, so results are
+// deterministic.  Dynamic smem: num [n*d] + den [n] doubles, then the
+// staged entries.
 __global__ void k_accumulate(ObjView ob, const double* omega, FlowOut fo, const int* order,
                              const long long* start, const long long* coff, int d, int cent_ldt,
                              float* loc32, double* loc64) {
@@ -120,26 +130,42 @@ __global__ void k_accumulate(ObjView ob, const double* omega, FlowOut fo, const 
   const int n = (int)(coff[g + 1] - c0);
   double* num = acc;
   double* den = acc + (size_t)n * d;
-  for (int t = threadIdx.x; t < n * d; t += blockDim.x) num[t] = 0.0;
+  double* e_coef = den + n;
+  long long* e_row = reinterpret_cast<long long*>(e_coef + kChunkMembers * kMaxStride);
+  int* e_r = reinterpret_cast<int*>(e_row + kChunkMembers * kMaxStride);
+  const int stride = (int)(fo.stride < kMaxStride ? fo.stride : kMaxStride);
+  const int slots = n * d;
+  for (int t = threadIdx.x; t < slots; t += blockDim.x) num[t] = 0.0;
   for (int t = threadIdx.x; t < n; t += blockDim.x) den[t] = 0.0;
-  __syncthreads();
   const long long b = start[g], e = start[g + 1];
-  for (long long t = b; t < e; ++t) {
-    const long long i = order[t];
-    const double om = omega ? omega[i] : 1.0;
-    const long long o0 = ob.off[i];
-    const int m = (int)(ob.off[i + 1] - o0);
-    const int* cell = fo.cell + i * fo.stride;
-    const double* w = fo.w + i * fo.stride;
-    for (long long q = 0; q < fo.stride; ++q) {
-      const int cl = cell[q];
-      if (cl < 0) break;
+  for (long long c = b; c < e; c += kChunkMembers) {
+    const int cm = (int)(e - c < kChunkMembers ? e - c : kChunkMembers);
+    __syncthreads();
+    for (int q = threadIdx.x; q < cm * stride; q += blockDim.x) {
+      const int mi = q / stride, qq = q - mi * stride;
+      const long long i = order[c + mi];
+      const long long o0 = ob.off[i];
+      const int m = (int)(ob.off[i + 1] - o0);
+      const int cl = fo.cell[i * fo.stride + qq];
       const int a = cl >> 16, r = cl & 0xffff;
-      if (a >= m || r >= n) continue;  // not a cell of this pair: ignored
-      const double coef = om * w[q];
-      for (int k = threadIdx.x; k < d; k += blockDim.x)
-        num[r * d + k] = fma(coef, ldloc(ob.loc, ob.ldt, (o0 + a) * d + k), num[r * d + k]);
-      if (threadIdx.x == 0) den[r] += coef;
+      const bool ok = cl >= 0 && a < m && r < n;  // other entries are ignored
+      e_r[q] = ok ? r : -1;
+      e_row[q] = o0 + a;
+      e_coef[q] = ok ? (omega ? omega[i] : 1.0) * fo.w[i * fo.stride + qq] : 0.0;
+    }
+    __syncthreads();
+    const int ne = cm * stride;
+    for (int t = threadIdx.x; t < slots; t += blockDim.x) {
+      const int r = t / d, k = t - r * d;
+      double sn = num[t], sd = (k == 0) ? den[r] : 0.0;
+      for (int q = 0; q < ne; ++q) {
+        if (e_r[q] != r) continue;
+        const double cf = e_coef[q];
+        sn = fma(cf, ldloc(ob.loc, ob.ldt, e_row[q] * d + k), sn);
+        if (k == 0) sd += cf;
+      }
+      num[t] = sn;
+      if (k == 0) den[r] = sd;
     }
   }
   __syncthreads();
@@ -197,7 +223,8 @@ cudaError_t update_locations(const ObjView& ob, const double* omega, const int* 
   note_launches(5);
   if (!fo.cell) return cudaGetLastError();  // sort only
   // largest centroid support bounds the accumulator size
-  const size_t smem = ((size_t)64 * d + 64) * sizeof(double);
+  const size_t smem = ((size_t)64 * d + 64) * sizeof(double) +
+                      (size_t)kChunkMembers * kMaxStride * (8 + 8 + 4);
   e = cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_accumulate<<<(unsigned)KT, 128, smem, st>>>(ob, omega, fo, order, start, coff, d, cent_ldt,

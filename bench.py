@@ -62,6 +62,13 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate(step_seconds, pairs_per_rank_step, steps, ws):
+    """Whole-job throughput over ranks: max of the ranks' timed totals,
+    units all ranks processed (weak scaling: each rank its own workload)."""
+    t = reduce_max(float(sum(step_seconds)), ws)
+    return pairs_per_rank_step * steps * ws / t, t
+
+
 def reduce_max(x, ws):
     if ws == 1:
         return x
@@ -304,8 +311,7 @@ def run_ours(args):
     barrier(ws)
     launches = d2.d2_get_stats()["kernel_launches"] - launches0
     clk = clocks.stop()
-    t_total = reduce_max(sum(times), ws)
-    value = ppstep * args.steps * ws / t_total
+    value, t_total = aggregate(times, ppstep, args.steps, ws)
 
     # dominant kernel: k_assign over the full bag set against one segment's K centroids
     lab1 = torch.empty(w["N"], dtype=torch.int32, device=dev)
@@ -414,13 +420,17 @@ def serve_measure(dev, n_requests=60, lam_fracs=(0.8,), n_sat=24, seed=1005):
         srv.poll(t)
     sat_dt = time.perf_counter() - t0
     sat_pairs = sum(b.count for b in burst) * K / sat_dt
-    sat_rps = n_sat / sat_dt
+    # the request law's mean size (log-uniform on [1, 4096]) sets the
+    # request rate that offers a given fraction of the saturated pairs/s
+    mean_bags = (4096.0 - 1.0) / np.log(4096.0)
+    sat_rps = sat_pairs / (mean_bags * K)
     out = {"workload": "serving: K=1024 resident centroids (n=32, d=32), requests log-uniform "
                        "1-4096 bags of 4-64 supports", "slots": 8,
            "saturated_pairs_per_s": sat_pairs, "saturated_requests_per_s": sat_rps, "levels": []}
     for frac in lam_fracs:
         lam = frac * sat_rps
         reqs = [d2.bags_from_synth(synth.serving_request(rng, means)) for _ in range(n_requests)]
+        offered = sum(b.count for b in reqs) * K
         gaps = rng.exponential(1.0 / lam, size=n_requests)
         lat = []
         tickets = []
@@ -449,6 +459,7 @@ def serve_measure(dev, n_requests=60, lam_fracs=(0.8,), n_sat=24, seed=1005):
         wall = time.perf_counter() - t_start
         lat = np.array(lat)
         out["levels"].append({"lambda_frac": frac, "requests": n_requests,
+                              "offered_pairs": int(offered), "lambda_per_s": lam,
                               "p50_ms": float(np.percentile(lat, 50)),
                               "p99_ms": float(np.percentile(lat, 99)),
                               "pairs_per_s": sum(b.count for b in reqs) * K / wall})

@@ -69,6 +69,16 @@ extern "C" {
                             every centroid the FP32 error bound cannot rule
                             out, so labels and dist2 are FP64-exact. */
 
+/* d2_cost_matrix only: the FP32 tile the tensor-core contraction gives
+   (||x||^2 + ||y||^2 - 2 x.y over BF16 operands with FP32 accumulation),
+   widened to FP64.  Needs BF16 objects and dim a multiple of 16 in 16..256. */
+#define D2_PREC_TC 3
+
+/* tensor-core ground costs for the FP32 screen of d2_assign (d2_config.cost_tc) */
+#define D2_TC_AUTO 0  /* on for BF16 objects with dim a multiple of 16 in 64..256 */
+#define D2_TC_OFF 1   /* the screen builds its FP32 tiles with SIMT FMAs */
+#define D2_TC_ON 2    /* on for BF16 objects with dim a multiple of 16 in 16..256 */
+
 /* Limits of the current kernels. */
 #define D2_MAX_SUPPORT 64   /* supports per bag (objects and centroids) */
 #define D2_MAX_DIM 256      /* vector dimension d */
@@ -96,7 +106,10 @@ typedef struct {
     int32_t precision;          /* D2_PREC_* ; 0 = AUTO */
     int32_t pivot_budget;       /* pivots per pair = pivot_budget*(m+n); 0 = 64 */
     int32_t group_lanes;        /* lanes per pair: 0 = autotune, or 1/2/4/8/16/32 */
-    int32_t reserved[5];
+    int32_t cost_tc;            /* D2_TC_* ; 0 = AUTO */
+    int32_t tile_budget_mib;    /* device memory for tensor-core cost tiles;
+                                   0 = min(32 GiB, 40% of free memory) */
+    int32_t reserved[3];
 } d2_config;
 
 /*
@@ -150,7 +163,10 @@ int d2_get_centroids(d2_ctx* ctx, double* loc_out, double* w_out, int64_t* off_o
  * Eq. (D2opt)): C[a*n_j + r] = ||v_i^(a) - z_j^(r)||^2 for object i of
  * `objs` and resident centroid j, as the kernels compute it in `precision`
  * (D2_PREC_FP64: FP64 explicit differences; D2_PREC_FP32: the FP32 tile the
- * FP32 solver prices with, widened to FP64).  C: m_i*n_j doubles.
+ * FP32 solver prices with, widened to FP64; D2_PREC_TC: the tensor-core tile
+ * the FP32 screen of d2_assign reads when cost_tc is on, D2_EUNSUPPORTED if
+ * the objects are not BF16 or dim is not a multiple of 16 in 16..256).
+ * C: m_i*n_j doubles.
  */
 int d2_cost_matrix(d2_ctx* ctx, const d2_bags* objs, int64_t i, int64_t j, int32_t precision,
                    double* C);

@@ -29,7 +29,7 @@ enum Slot {
   // level driver
   kLvDataLoc, kLvDataW, kLvDataOff, kLvOmega, kLvOmegaNew, kLvC, kLvCT, kLvLab, kLvD2,
   kLvCLoc32, kLvCLoc64, kLvCQ, kLvCW, kLvCOff, kLvTmp, kCand, kWarmMeta, kWarmFlow, kBins,
-  kBinSort, kTuneLab, kTuneD2,
+  kBinSort, kTuneLab, kTuneD2, kTcTile, kTcRow, kTcSrc, kTcNx, kTcDel,
   kSlots
 };
 
@@ -55,6 +55,13 @@ struct d2_ctx {
   double* c_w64 = nullptr;
   long long* c_off = nullptr;
   std::vector<long long> h_coff;
+  // BF16 copy of the resident centroids for the tensor-core contraction
+  // (dimension a multiple of 16 in 16..256), rebuilt when the set changes
+  void* c_yb = nullptr;
+  float* c_yn = nullptr;
+  float* c_cn = nullptr;
+  float* c_cd = nullptr;
+  bool tc_stale = true;
   // scratch
   Buf slot[kSlots];
   int* d_err = nullptr;
@@ -90,6 +97,23 @@ void* grow(d2_ctx* c, int s, size_t bytes, int* rc) {
     return nullptr;
   }
   b.n = want;
+  return b.p;
+}
+
+// As grow, without the slack (for buffers sized to a memory budget).
+void* grow_exact(d2_ctx* c, int s, size_t bytes, int* rc) {
+  Buf& b = c->slot[s];
+  if (bytes == 0) bytes = 16;
+  if (b.n >= bytes) return b.p;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.n = 0;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *rc = D2_ENOMEM;
+    return nullptr;
+  }
+  b.n = bytes;
   return b.p;
 }
 
@@ -223,6 +247,9 @@ int read_err(d2_ctx* c, int* bits) {
 void free_centroids(d2_ctx* c) {
   cudaFree(c->c_loc32); cudaFree(c->c_loc64); cudaFree(c->c_Q); cudaFree(c->c_w64); cudaFree(c->c_off);
   c->c_loc32 = nullptr; c->c_loc64 = nullptr; c->c_Q = nullptr; c->c_w64 = nullptr; c->c_off = nullptr;
+  cudaFree(c->c_yb); cudaFree(c->c_yn); cudaFree(c->c_cn); cudaFree(c->c_cd);
+  c->c_yb = nullptr; c->c_yn = nullptr; c->c_cn = nullptr; c->c_cd = nullptr;
+  c->tc_stale = true;
   c->K = c->Tc = 0;
   c->h_coff.clear();
 }
@@ -319,11 +346,12 @@ int make_bins(d2_ctx* c, const ObjView& v, int nmax, Bins* b) {
 // its autotuned launch shape.  ws may be null.
 int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, int K, int mode,
                int mmax, const double* om, int* lab, double* d2o, double* terms, FlowOut fo,
-               int* cand, const d2k::WarmStore* ws, const Bins& bins) {
+               int* cand, const d2k::WarmStore* ws, const Bins& bins,
+               const d2k::TcWork* tw = nullptr) {
   const int nmax = std::max(c->nmax, 1);
   SolveCfg base = solve_cfg(c, mode, mmax);
   if (!bins.binned) {
-    CK(d2k::assign(v, cv, seg, K, base, om, lab, d2o, terms, fo, cand, c->d_err, c->stream, ws));
+    CK(d2k::assign(v, cv, seg, K, base, om, lab, d2o, terms, fo, cand, c->d_err, c->stream, ws, tw));
     return D2_OK;
   }
   for (int b = 3; b >= 0; --b) {
@@ -338,7 +366,8 @@ int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, i
     if (it == c->tuned.end() && c->cfg.group_lanes == 0 && mode == 1 && cnt >= 8192) {
       // autotune on a sample of this bin: threads per block x screening items per SM
       SolveCfg t = cfg;
-      t.nobj = 2048;
+      // a sample of about 2^17 pairs, at least 256 objects
+      t.nobj = std::min<long long>(cnt, std::max<long long>(256, (1LL << 17) / std::max(K, 1)));
       int rc = D2_OK;
       int* tl = static_cast<int*>(grow(c, kTuneLab, (size_t)v.count * 4, &rc));
       double* td = static_cast<double*>(grow(c, kTuneD2, (size_t)v.count * 8, &rc));
@@ -356,7 +385,7 @@ int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, i
           t.ipsm = ip;
           CK(cudaEventRecord(e0, c->stream));
           CK(d2k::assign(v, cv, seg, K, t, om, tl, td, nullptr, FlowOut{nullptr, nullptr, 0}, cand,
-                         c->d_err, c->stream, nullptr));
+                         c->d_err, c->stream, nullptr, tw));
           CK(cudaEventRecord(e1, c->stream));
           CK(cudaEventSynchronize(e1));
           float ms = 0.f;
@@ -372,8 +401,69 @@ int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, i
       cfg.tpb = it->second.first;
       cfg.ipsm = it->second.second;
     }
-    CK(d2k::assign(v, cv, seg, K, cfg, om, lab, d2o, terms, fo, cand, c->d_err, c->stream, ws));
+    CK(d2k::assign(v, cv, seg, K, cfg, om, lab, d2o, terms, fo, cand, c->d_err, c->stream, ws, tw));
   }
+  return D2_OK;
+}
+
+// The tensor-core copy of the resident centroids, built on first use after
+// the set changed.
+int tc_cents(d2_ctx* c, d2k::TcCents* out) {
+  const long long ncols = d2k::tc_cols(c->Tc);
+  if (c->tc_stale) {
+    cudaFree(c->c_yb); cudaFree(c->c_yn); cudaFree(c->c_cn); cudaFree(c->c_cd);
+    c->c_yb = nullptr; c->c_yn = nullptr; c->c_cn = nullptr; c->c_cd = nullptr;
+    if (cudaMalloc(&c->c_yb, (size_t)ncols * c->d * 2) != cudaSuccess ||
+        cudaMalloc(&c->c_yn, (size_t)ncols * 4) != cudaSuccess ||
+        cudaMalloc(&c->c_cn, (size_t)c->K * 4) != cudaSuccess ||
+        cudaMalloc(&c->c_cd, (size_t)c->K * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return D2_ENOMEM;
+    }
+    int rc = D2_OK;
+    double* del = static_cast<double*>(grow(c, kTcDel, (size_t)ncols * 8, &rc));
+    if (rc != D2_OK) return rc;
+    CK(d2k::tc_prep_centroids(c->c_loc64, c->c_off, c->K, c->Tc, c->d, c->c_yb, c->c_yn, del,
+                              c->c_cn, c->c_cd, c->stream));
+    c->tc_stale = false;
+  }
+  out->yb = c->c_yb;
+  out->yn = c->c_yn;
+  out->cn = c->c_cn;
+  out->cd = c->c_cd;
+  out->ncols = ncols;
+  return D2_OK;
+}
+
+// Whether d2_assign screens with tensor-core tiles for these objects.
+bool tc_wanted(const d2_ctx* c, const d2_bags* objs, const ObjView& v, int mode) {
+  if (c->cfg.cost_tc == D2_TC_OFF || mode != 1) return false;
+  if (objs->loc_dtype != D2_BF16 || !d2k::tc_dim_ok(c->d)) return false;
+  if (c->cfg.cost_tc != D2_TC_ON && c->d < 64) return false;
+  return (reinterpret_cast<uintptr_t>(v.loc) & 15) == 0;
+}
+
+// Tile buffers for `rows` tile rows at most (capped by the budget).
+int tc_work(d2_ctx* c, long long rows, int mmax, d2k::TcWork* w) {
+  int rc = tc_cents(c, &w->cents);
+  if (rc != D2_OK) return rc;
+  size_t budget = (size_t)c->cfg.tile_budget_mib << 20;
+  if (c->cfg.tile_budget_mib <= 0) {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    budget = std::min<size_t>((size_t)32 << 30, fr / 5 * 2);
+  }
+  const size_t row_bytes = (size_t)w->cents.ncols * 4;
+  long long cap = (long long)(budget / row_bytes);
+  cap = std::min(cap, rows);
+  if (cap < mmax) return D2_ENOMEM;  // not even one object of mmax rows fits
+  w->C = static_cast<float*>(grow_exact(c, kTcTile, (size_t)cap * row_bytes, &rc));
+  if (rc != D2_OK) return rc;
+  w->trow = static_cast<long long*>(grow(c, kTcRow, (size_t)(cap + 1) * 8, &rc));
+  w->rowsrc = static_cast<long long*>(grow(c, kTcSrc, (size_t)cap * 8, &rc));
+  w->nx = static_cast<float*>(grow(c, kTcNx, (size_t)cap * 4, &rc));
+  if (rc != D2_OK) return rc;
+  w->rows_cap = cap;
   return D2_OK;
 }
 
@@ -555,8 +645,24 @@ int d2_cost_matrix(d2_ctx* c, const d2_bags* objs, int64_t i, int64_t j, int32_t
   bool host;
   rc = stage_out(c, C, (size_t)(m * n), kOutD2, &dC, &host);
   if (rc != D2_OK) return rc;
-  const int mode = precision == D2_PREC_FP32 ? 1 : 0;
-  CK(d2k::cost_matrix(v, resident_view(c), i, j, mode, dC, c->stream));
+  if (precision == D2_PREC_TC) {
+    if (objs->loc_dtype != D2_BF16 || !d2k::tc_dim_ok(c->d) ||
+        (reinterpret_cast<uintptr_t>(v.loc) & 15) != 0)
+      return D2_EUNSUPPORTED;
+    d2k::TcWork tw;
+    if ((rc = tc_work(c, m, (int)m, &tw))) return rc;
+    const long long c0 = c->h_coff[j];
+    const int ct0 = (int)(c0 / 256), ct1 = (int)((c0 + n - 1) / 256);
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    CK(d2k::tc_chunk(v, tw, nullptr, i, 1, (int)m, ct0, ct1 - ct0 + 1, c->d_err, c->stream));
+    CK(d2k::tc_extract(tw.C, tw.cents.ncols, (int)m, c0, (int)n, dC, c->stream));
+    int bits = 0;
+    if ((rc = read_err(c, &bits))) return rc;
+    if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
+  } else {
+    const int mode = precision == D2_PREC_FP32 ? 1 : 0;
+    CK(d2k::cost_matrix(v, resident_view(c), i, j, mode, dC, c->stream));
+  }
   if (host) CK(cudaMemcpyAsync(C, dC, (size_t)(m * n) * 8, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return D2_OK;
@@ -603,6 +709,7 @@ int d2_mallows_batch(d2_ctx* c, const d2_bags* objs, const int64_t* pair_obj, co
   if (h4) CK(cudaMemcpyAsync(flows->w, fo.w, (size_t)(npairs * fo.stride) * 8, cudaMemcpyDeviceToHost, c->stream));
   int bits = 0;
   if ((rc = read_err(c, &bits))) return rc;
+  if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
   if (bits & d2k::kErrInvalid) return D2_EINVAL;
   if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
   return D2_OK;
@@ -652,8 +759,12 @@ int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labe
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   Bins bins;
   if (want_bins(c, N, mmax) && (rc = make_bins(c, v, c->nmax, &bins))) return rc;
-  if ((rc = run_assign(c, v, resident_view(c), N, (int)c->K, mode_for(c, objs->loc_dtype), mmax, om,
-                       dl, dd, terms, fo, cand, nullptr, bins)))
+  const int mode = mode_for(c, objs->loc_dtype);
+  d2k::TcWork tw;
+  const bool tc = tc_wanted(c, objs, v, mode);
+  if (tc && (rc = tc_work(c, N * (long long)mmax, mmax, &tw))) return rc;
+  if ((rc = run_assign(c, v, resident_view(c), N, (int)c->K, mode, mmax, om, dl, dd, terms, fo,
+                       cand, nullptr, bins, tc ? &tw : nullptr)))
     return rc;
   if (eps_total) {
     double* de = static_cast<double*>(grow(c, kEpsOut, 8, &rc));
@@ -667,6 +778,7 @@ int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labe
   if (h4) CK(cudaMemcpyAsync(flows->w, fo.w, (size_t)(N * fo.stride) * 8, cudaMemcpyDeviceToHost, c->stream));
   int bits = 0;
   if ((rc = read_err(c, &bits))) return rc;
+  if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
   if (bits & d2k::kErrInvalid) return D2_EINVAL;
   if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
   return D2_OK;
@@ -729,10 +841,12 @@ int d2_update_locations(d2_ctx* c, const d2_bags* objs, const double* omega, con
   }
   void* scr = grow(c, kUpd, d2k::update_scratch_bytes(N, c->K), &rc);
   if (rc != D2_OK) return rc;
+  c->tc_stale = true;
   CK(d2k::update_locations(v, om, dl, N, (int)c->K, fo, c->K, c->c_off, c->d, c->cent_ldt,
                            c->c_loc32, c->c_loc64, scr, c->stream));
   int bits = 0;
   if ((rc = read_err(c, &bits))) return rc;
+  if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
   if (bits & d2k::kErrInvalid) return D2_EINVAL;
   if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
   return D2_OK;
@@ -917,6 +1031,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
   }
   int bits = 0;
   if ((rc = read_err(c, &bits))) return rc;
+  if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
   if (bits & d2k::kErrInvalid) return D2_EINVAL;
   if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
   return D2_OK;

@@ -46,6 +46,45 @@ struct WarmStore {
   int warm;
 };
 
+// FP32 ground-cost tiles made ahead of the screen by the tensor-core
+// contraction (d2_tc.cu) for the objects of one chunk: row R of C holds
+// ||x||^2 + ||y||^2 - 2 x.y of tile row R (an object support) against every
+// centroid support column.  Launch object tt owns rows trow[tt] ..
+// trow[tt+1]; the cost of its support a against centroid support row c0+r
+// is C[(trow[tt]+a)*ldc + (c0 - col0) + r].  C == nullptr: the screen builds
+// its tiles itself.
+struct TileView {
+  const float* C = nullptr;
+  const long long* trow = nullptr;  // [nobj+1]
+  const float* nx = nullptr;        // [rows] ||x||^2 of each tile row (FP32)
+  const float* cn = nullptr;        // [K] max ||y^||^2 over each centroid's BF16 supports
+  const float* cd = nullptr;        // [K] max ||y - y^|| over each centroid's supports
+  long long ldc = 0;
+  long long col0 = 0;
+};
+
+// Resident centroids rounded to BF16 for the contraction, with the data of
+// its error bound (see TileView).
+struct TcCents {
+  const void* yb = nullptr;  // [ncols][d] BF16 (rows >= Tc are zero)
+  const float* yn = nullptr;  // [ncols] ||y^||^2 in FP32
+  const float* cn = nullptr;  // [K]
+  const float* cd = nullptr;  // [K]
+  long long ncols = 0;        // centroid support rows rounded up to the tile width
+};
+
+// Per-call buffers of the tensor-core screen: the tile buffer and the row
+// maps of one chunk (a chunk of c objects of at most mmax supports has
+// c*mmax <= rows_cap; trow holds rows_cap+1 entries).
+struct TcWork {
+  TcCents cents;
+  float* C = nullptr;
+  long long* trow = nullptr;    // [rows_cap+1]
+  long long* rowsrc = nullptr;  // [rows_cap]
+  float* nx = nullptr;          // [rows_cap]
+  long long rows_cap = 0;       // tile rows the buffers hold (C: rows_cap*ncols floats)
+};
+
 // Launch-wide solver settings.
 struct SolveCfg {
   int mode;        // 0: FP64 throughout; 1: FP32 screen/pivots + FP64 certify
@@ -55,12 +94,14 @@ struct SolveCfg {
   int sms;         // SM count
   int tpb = 128;   // threads per block of the solver kernels (64 or 128)
   int ipsm = 96;   // screening work items per SM the centroid blocks aim for
-  const int* oidx = nullptr;  // objects of this launch (nullptr: 0..count-1)
+  const int* oidx = nullptr;  // objects of this launch (nullptr: obase..obase+nobj-1)
   long long nobj = -1;        // entries of oidx (-1: all ob.count objects)
+  long long obase = 0;        // first object when oidx is nullptr
+  TileView tile;              // precomputed FP32 tiles of the screen (optional)
 };
 
 // Error bits raised by kernels into a device int.
-enum : int { kErrInvalid = 1, kErrNotConverged = 2 };
+enum : int { kErrInvalid = 1, kErrNotConverged = 2, kErrTimeout = 4 };
 
 cudaError_t scan_bags(const long long* off, long long count, int* d_info, cudaStream_t st);
 cudaError_t prep_centroids(const void* loc, int ldt, const void* w, int wdt, const long long* off,
@@ -76,14 +117,39 @@ cudaError_t mallows_pairs(const ObjView& ob, const CentView& cv, const long long
 cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, int K,
                    const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
                    double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st,
-                   const WarmStore* ws = nullptr);
+                   const WarmStore* ws = nullptr, const TcWork* tw = nullptr);
+
+// ---- tensor-core ground cost (d2_tc.cu) ----
+// Whether the contraction supports dimension d (a multiple of 16 in 16..256).
+inline bool tc_dim_ok(int d) { return d >= 16 && d <= 256 && d % 16 == 0; }
+inline long long tc_cols(long long Tc) { return (Tc + 255) / 256 * 256; }
+// BF16 copies, FP32 squared norms and rounding bounds of the resident
+// centroids (loc64: [Tc][d]); yb [ncols][d], yn [ncols], ydel [ncols] FP64
+// scratch, cn/cd [K].
+cudaError_t tc_prep_centroids(const double* loc64, const long long* off, long long K, long long Tc,
+                              int d, void* yb, float* yn, double* ydel, float* cn, float* cd,
+                              cudaStream_t st);
+// Tiles of one chunk: objects oidx[0..cnt) (or obase..obase+cnt-1) with
+// supports of at most mmax rows (others get no rows); fills w.trow,
+// w.rowsrc, w.nx and C rows [0, trow[cnt]) x columns of col tiles
+// [ct0, ct0+nct) (nct = -1: all).  Objects' loc must be BF16.
+cudaError_t tc_chunk(const ObjView& ob, const TcWork& w, const int* oidx, long long obase,
+                     long long cnt, int mmax, int ct0, int nct, int* d_err, cudaStream_t st);
+// Copy rows [0,m) x columns [c0, c0+n) of a chunk's tile to FP64.
+cudaError_t tc_extract(const float* C, long long ldc, int m, long long c0, int n, double* out,
+                       cudaStream_t st);
 // ints of assign scratch for `count` objects and K centroids per object:
 // queue counter, merged lists [count*9], and per-(object, centroid block)
 // items; a launch over nobj <= count objects makes at most
 // nobj*ceil(want/nobj) <= want + count items, want <= sms*256.
+// The screen keeps up to kCandCap candidates per (object, centroid block)
+// item and per object; more means the object is certified against all K.
+constexpr int kCandCap = 16;
+constexpr int kItemInts = 2 + 2 * kCandCap;  // count, centroids, lower ends, best upper end
+constexpr int kMergedInts = 1 + kCandCap;    // count, centroids
 inline long long assign_scratch_ints(long long count, long long K, int sms = 160) {
   (void)K;
-  return 4 + ((count * 9 + 3) & ~3LL) + (count + (long long)sms * 256) * 18 + 4;
+  return 4 + ((count * kMergedInts + 3) & ~3LL) + (count + (long long)sms * 256) * kItemInts + 4;
 }
 cudaError_t cost_matrix(const ObjView& ob, const CentView& cv, long long i, long long j, int mode,
                         double* C, cudaStream_t st);

@@ -368,14 +368,57 @@ __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
 // tolerance 2^-20 * max cost and the drift of the incrementally updated
 // FP32 potentials, refreshed every 64 pivots); every centroid whose interval
 // [D32_j - err_j, D32_j + err_j] reaches below the smallest upper end is a
-// candidate.
+// candidate.  With tensor-core tiles (cfg.tile) the bound adds the tile's
+// own error, see tc_bound.
 // Work items are (object i, centroid block jb) with blocks of KB centroids,
 // so small batches still fill the GPU; lane groups take items from an
-// atomic counter (persistent kernel).  Output per item (18 ints at
-// item*18): count (-1: more than 8, -2: invalid object), 8 candidate
-// indices in increasing order, their 8 lower ends (float bits), and the
-// block's smallest upper end (float bits).
-constexpr int kItemInts = 18;
+// atomic counter (persistent kernel).  Output per item (kItemInts ints at
+// item*kItemInts): count (-1: more than kCandCap, -2: invalid object),
+// kCandCap candidate indices in increasing order, their lower ends (float
+// bits), and the block's smallest upper end (float bits).
+
+// FP32 cost tile of one pair from a chunk's precomputed tile rows (see
+// TileView): row a of the pair is row a of src, columns 0..n-1.  Returns
+// the tile maximum (group-uniform).
+template <int G>
+__device__ __forceinline__ float load_tile(const Grp<G>& g, float* C, int m, int n,
+                                           const float* __restrict__ src, long long ldc) {
+  const int mn = m * n;
+  const int q = G / n, rem = G - (G / n) * n;
+  int a = g.lane / n, r = g.lane - (g.lane / n) * n;
+  float cmax = 0.f;
+#pragma unroll 4
+  for (int t = g.lane; t < mn; t += G) {
+    const float v = __ldg(src + (long long)a * ldc + r);
+    C[t] = v;
+    cmax = fmaxf(cmax, v);
+    r += rem; a += q;
+    if (r >= n) { r -= n; ++a; }
+  }
+  cmax = gmax<G>(g, cmax);
+  g.sync();
+  return cmax;
+}
+
+// Bound on |C^ - C| for every cell of a tensor-core tile (C^ = the FP32
+// tile of ||x||^2 + ||y^||^2 - 2 x.y^ over BF16 x and y^ = BF16(y)), from the
+// largest FP32 squared norms nxm (object rows) and cn (centroid rows) and
+// the largest rounding distance cd = max ||y - y^||:
+//   accumulation of d exact products in FP32 by the tensor cores, modelled
+//   as at most one unit in the last place of sum|x_k y^_k| <= ||x|| ||y^||
+//   lost by every aligned addend (d products plus one accumulator per
+//   block of at least 4 products: <= 1.25 d units of 2^-23), taken twice:
+//   d * 2^-22; the two FP32 norm sums and the final FMA ((d+3) * 2^-24);
+//   both relative to ||x||^2 + ||y^||^2 >= 2 ||x|| ||y^||; then the move from
+//   y^ back to y: | ||x-y^||^2 - ||x-y||^2 | <= (2(||x|| + ||y^||) + cd) cd.
+// Since a pair's flows sum to 1, the same bound holds for the objective of
+// any basis, hence for the optimum.
+__device__ __forceinline__ float tc_bound(int d, float nxm, float cn, float cd) {
+  const float rel = (float)d * 0x1p-22f + (float)(d + 3) * 0x1p-24f;
+  const float e1 = rel * (nxm + cn);
+  const float e2 = (2.f * (sqrtf(nxm) + sqrtf(cn)) + 2.f * cd) * cd;
+  return (e1 + e2) * (1.f + 0x1p-10f);
+}
 
 template <int G, int NPL>
 __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, CentView cv, long long seg_size, int K,
@@ -386,8 +429,8 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
   Grp<G> g;
   unsigned char* base = smem + (threadIdx.x / G) * slice;
   const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax, cv.d);
-  int* cand = s32.sc;                                  // [8]
-  float* clo = reinterpret_cast<float*>(s32.sc + 8);   // [8]
+  int* cand = s32.sc;                                          // [kCandCap]
+  float* clo = reinterpret_cast<float*>(s32.sc + kCandCap);    // [kCandCap]
   int n_scr = 0, p_scr = 0;
   const float rel = (float)(cv.d + 3) * 0x1p-24f + 0x1p-17f;
   const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
@@ -398,7 +441,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
     item = __shfl_sync(g.mask, item, 0, G);
     if (item >= total) break;
     const long long tt = (long long)(item / NB);
-    const long long i = cfg.oidx ? (long long)cfg.oidx[tt] : tt;
+    const long long i = cfg.oidx ? (long long)cfg.oidx[tt] : cfg.obase + tt;
     const int jb = (int)(item - (unsigned long long)tt * NB);
     const int j0 = jb * KB, j1 = min(K, j0 + KB);
     const long long o0 = ob.off[i];
@@ -407,6 +450,14 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
     bool ok = m >= 1 && m <= cfg.mmax && cb + K <= cv.K && load_obj_prefix<G>(g, ob, o0, m, s32.P);
     const bool cold = !(ws.par8 && ws.warm);
     if (ok && cold) order_rows<G>(g, s32, ob, o0, m, cv.d);
+    const bool tcp = cfg.tile.C != nullptr;
+    long long trow0 = 0;
+    float nxm = 0.f;
+    if (ok && tcp) {
+      trow0 = cfg.tile.trow[tt];
+      for (int a = g.lane; a < m; a += G) nxm = fmaxf(nxm, cfg.tile.nx[trow0 + a]);
+      nxm = gmax<G>(g, nxm);
+    }
     int ncand = 0;
     bool all = false;
     float best_hi = FLT_MAX;
@@ -415,8 +466,11 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       const int n = (int)(cv.off[cb + j + 1] - c0);
       if (n < 1 || n > cfg.nmax || m + n > G * NPL) { ok = false; break; }
       load_cent_prefix<G>(g, cv, c0, n, s32.Q);
-      const float cmax = build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
-                                              cv.loc32 + c0 * cv.d, cv.d);
+      const float cmax =
+          tcp ? load_tile<G>(g, s32.cost, m, n,
+                             cfg.tile.C + trow0 * cfg.tile.ldc + (c0 - cfg.tile.col0), cfg.tile.ldc)
+              : build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0, cv.loc32 + c0 * cv.d,
+                                     cv.d);
       Simplex<float, G, NPL> S(s32, m, n, g);
       const long long wt = (i * (long long)K + j) * ws.ns;
       int st;
@@ -435,10 +489,11 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       ++n_scr;
       if (st != kStOk) all = true;  // no bound: let the exact pass decide
       const float D = S.template objective<float>();
-      const float e = D * rel + cmax * 0x1p-14f;
+      float e = D * rel + cmax * 0x1p-14f;
+      if (tcp) e += tc_bound(cv.d, nxm, cfg.tile.cn[cb + j], cfg.tile.cd[cb + j]);
       const float lo = D - e, hi = D + e;
       if (lo <= best_hi) {
-        if (ncand < 8) {
+        if (ncand < kCandCap) {
           if (g.lane == 0) { cand[ncand] = j; clo[ncand] = lo; }
           ++ncand;
         } else {
@@ -465,24 +520,25 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
     int* out = items_out + item * kItemInts;
     if (g.lane == 0) {
       out[0] = !ok ? -2 : (all ? -1 : ncand);
-      out[17] = __float_as_int(best_hi);
+      out[2 * kCandCap + 1] = __float_as_int(best_hi);
     }
-    if (g.lane >= 1 && g.lane <= 8) {
+    if (g.lane >= 1 && g.lane <= kCandCap) {
       out[g.lane] = (g.lane <= ncand) ? cand[g.lane - 1] : -1;
-      out[8 + g.lane] = __float_as_int((g.lane <= ncand) ? clo[g.lane - 1] : FLT_MAX);
+      out[kCandCap + g.lane] = __float_as_int((g.lane <= ncand) ? clo[g.lane - 1] : FLT_MAX);
     }
     g.sync();
   }
   if (g.lane == 0) add_stats(n_scr, p_scr, 0, 0);
 }
 
-// Per object: merge its NB block lists into one candidate list (count, 8
-// indices increasing) at cand[i*9]: keep the block candidates whose lower
-// end reaches the smallest upper end over all blocks.
-__global__ void k_merge(const int* items, long long N, int NB, const int* oidx, int* cand) {
+// Per object: merge its NB block lists into one candidate list (count,
+// kCandCap indices increasing) at cand[i*kMergedInts]: keep the block
+// candidates whose lower end reaches the smallest upper end over all blocks.
+__global__ void k_merge(const int* items, long long N, int NB, const int* oidx, long long obase,
+                        int* cand) {
   for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < N;
        tt += (long long)gridDim.x * blockDim.x) {
-    const long long i = oidx ? (long long)oidx[tt] : tt;
+    const long long i = oidx ? (long long)oidx[tt] : obase + tt;
     const int* it = items + tt * NB * kItemInts;
     float best_hi = FLT_MAX;
     int state = 0;  // 0 ok, -1 all, -2 invalid
@@ -490,21 +546,21 @@ __global__ void k_merge(const int* items, long long N, int NB, const int* oidx, 
       const int c = it[b * kItemInts];
       if (c == -2) state = -2;
       else if (c == -1 && state == 0) state = -1;
-      best_hi = fminf(best_hi, __int_as_float(it[b * kItemInts + 17]));
+      best_hi = fminf(best_hi, __int_as_float(it[b * kItemInts + 2 * kCandCap + 1]));
     }
     int cnt = 0;
-    int* out = cand + i * 9;
+    int* out = cand + i * kMergedInts;
     if (state == 0) {
       for (int b = 0; b < NB && state == 0; ++b) {
         const int* blk = it + b * kItemInts;
         for (int c = 0; c < blk[0]; ++c) {
-          if (__int_as_float(blk[9 + c]) <= best_hi) {
-            if (cnt < 8) out[1 + cnt] = blk[1 + c];
+          if (__int_as_float(blk[kCandCap + 1 + c]) <= best_hi) {
+            if (cnt < kCandCap) out[1 + cnt] = blk[1 + c];
             ++cnt;
           }
         }
       }
-      if (cnt > 8) state = -1;
+      if (cnt > kCandCap) state = -1;
     }
     out[0] = state == 0 ? cnt : state;
   }
@@ -529,14 +585,14 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
   const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
   for (long long tt = (long long)blockIdx.x * gpb + threadIdx.x / G; tt < nobj;
        tt += (long long)gridDim.x * gpb) {
-    const long long i = cfg.oidx ? (long long)cfg.oidx[tt] : tt;
+    const long long i = cfg.oidx ? (long long)cfg.oidx[tt] : cfg.obase + tt;
     const long long o0 = ob.off[i];
     const int m = (int)(ob.off[i + 1] - o0);
     const long long cb = (i / seg_size) * (long long)K;
     int best_j = -1;
     double best = nan("");
     int st = kStOk;
-    const int cnt = cand_in ? cand_in[i * 9] : -1;
+    const int cnt = cand_in ? cand_in[i * kMergedInts] : -1;
     const bool okm = m >= 1 && m <= cfg.mmax && cb + K <= cv.K && cnt != -2;
     if (!okm || !load_obj_prefix<G>(g, ob, o0, m, s64.P)) {
       st = kStInvalid;
@@ -544,7 +600,7 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
       const bool all = cnt < 0;
       const int count = all ? K : cnt;
       for (int c = 0; c < count; ++c) {
-        const int j = all ? c : cand_in[i * 9 + 1 + c];
+        const int j = all ? c : cand_in[i * kMergedInts + 1 + c];
         const long long c0 = cv.off[cb + j];
         const int n = (int)(cv.off[cb + j + 1] - c0);
         if (j < 0 || j >= K || n < 1 || n > cfg.nmax || m + n > G * NPL) { st = kStInvalid; break; }
@@ -723,7 +779,7 @@ template <int G, int NPL>
 static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg_size, int K,
                             const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
                             double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st,
-                            const WarmStore* wsp) {
+                            const WarmStore* wsp, const TcWork* tw) {
   WarmStore ws{nullptr, nullptr, nullptr, nullptr, 0, 0};
   if (wsp) ws = *wsp;
   const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax, cv.d);
@@ -736,25 +792,55 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
   const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
   if (nobj <= 0) return cudaSuccess;
   if (screen) {
-    // centroid blocks: enough (object, block) items to fill the GPU
-    const long long want = (long long)cfg.sms * std::min(std::max(cfg.ipsm, 8), 256);
-    int NB = (int)std::min<long long>(std::max<long long>(1, (want + nobj - 1) / nobj),
-                                      std::max(1, K / 8));
-    const int KB = (K + NB - 1) / NB;
-    NB = (K + KB - 1) / KB;
-    // scratch layout: [queue counter: 4 ints][merged lists: count*9][items]
+    // scratch layout: [queue counter: 4 ints][merged lists: count*kMergedInts][items]
     unsigned long long* queue = reinterpret_cast<unsigned long long*>(cand);
     int* merged = cand + 4;
-    int* items = merged + ((ob.count * 9 + 3) & ~3LL);  // merged is indexed by object
-    e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-    e = launch_cfg(k_screen<G, NPL>, smem, gpb * G, cfg.sms, nobj * (long long)NB, gpb, &grid);
-    if (e != cudaSuccess) return e;
-    k_screen<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, KB, NB, cfg, slice, items,
+    int* items = merged + ((ob.count * kMergedInts + 3) & ~3LL);  // merged is indexed by object
+    // one screening launch over objects [t0, t0+cnt) of this launch
+    auto screen_part = [&](const SolveCfg& sc, long long cnt) -> cudaError_t {
+      // centroid blocks: enough (object, block) items to fill the GPU
+      const long long want = (long long)sc.sms * std::min(std::max(sc.ipsm, 8), 256);
+      int NB = (int)std::min<long long>(std::max<long long>(1, (want + cnt - 1) / cnt),
+                                        std::max(1, K / 8));
+      const int KB = (K + NB - 1) / NB;
+      NB = (K + KB - 1) / KB;
+      cudaError_t e2 = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
+      if (e2 != cudaSuccess) return e2;
+      unsigned g2 = 1;
+      e2 = launch_cfg(k_screen<G, NPL>, smem, gpb * G, sc.sms, cnt * (long long)NB, gpb, &g2);
+      if (e2 != cudaSuccess) return e2;
+      k_screen<G, NPL><<<g2, gpb * G, smem, st>>>(ob, cv, seg_size, K, KB, NB, sc, slice, items,
                                                   queue, ws, d_err);
-    const unsigned mb = (unsigned)std::min<long long>((nobj + 255) / 256, 4096);
-    k_merge<<<mb, 256, 0, st>>>(items, nobj, NB, cfg.oidx, merged);
-    note_launches(2);
+      const unsigned mb = (unsigned)std::min<long long>((cnt + 255) / 256, 4096);
+      k_merge<<<mb, 256, 0, st>>>(items, cnt, NB, sc.oidx, sc.obase, merged);
+      note_launches(2);
+      return cudaGetLastError();
+    };
+    if (tw && tw->C && cfg.mmax <= 64) {
+      // tensor-core tiles, chunk by chunk within the tile buffer
+      const long long per = std::max<long long>(1, tw->rows_cap / cfg.mmax);
+      for (long long t0 = 0; t0 < nobj; t0 += per) {
+        const long long cnt = std::min(per, nobj - t0);
+        SolveCfg sc = cfg;
+        sc.oidx = cfg.oidx ? cfg.oidx + t0 : nullptr;
+        sc.obase = cfg.oidx ? 0 : cfg.obase + t0;
+        sc.nobj = cnt;
+        e = tc_chunk(ob, *tw, sc.oidx, sc.obase, cnt, cfg.mmax, 0, -1, d_err, st);
+        if (e != cudaSuccess) return e;
+        sc.tile.C = tw->C;
+        sc.tile.trow = tw->trow;
+        sc.tile.nx = tw->nx;
+        sc.tile.cn = tw->cents.cn;
+        sc.tile.cd = tw->cents.cd;
+        sc.tile.ldc = tw->cents.ncols;
+        sc.tile.col0 = 0;
+        e = screen_part(sc, cnt);
+        if (e != cudaSuccess) return e;
+      }
+    } else {
+      e = screen_part(cfg, nobj);
+      if (e != cudaSuccess) return e;
+    }
   }
   e = launch_cfg(k_exact<G, NPL>, smem, gpb * G, cfg.sms, nobj, gpb, &grid);
   if (e != cudaSuccess) return e;
@@ -801,13 +887,13 @@ cudaError_t mallows_pairs(const ObjView& ob, const CentView& cv, const long long
 cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, int K,
                    const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
                    double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st,
-                   const WarmStore* ws) {
+                   const WarmStore* ws, const TcWork* tw) {
   if (ob.count <= 0) return cudaSuccess;
   int G, NP;
   if (!pick_shape(cfg.mmax, cfg.nmax, cfg.group, &G, &NP)) return cudaErrorInvalidValue;
 #define X(g_, n_)                                                                            \
   if (G == g_ && NP == n_)                                                                  \
-    return assign_g<g_, n_>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, cand, d_err, st, ws);
+    return assign_g<g_, n_>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, cand, d_err, st, ws, tw);
   D2_BINS(X)
 #undef X
   return cudaErrorInvalidValue;

@@ -103,7 +103,7 @@ struct PairMem {
   int* pj1;           // [N]
   T* acc0;            // [N]
   T* acc1;            // [N]
-  int* sc;            // [16] group scalars
+  int* sc;            // [32] group scalars
   // projection order of the start basis (see order_rows / order_cols)
   int* rrank;         // [mmax] row -> rank
   int* rid;           // [mmax] rank -> row
@@ -135,7 +135,7 @@ __host__ __device__ inline size_t pair_mem_bytes(int mmax, int nmax, int dmax = 
   b += align_up((size_t)mmax * 4, 16);         // re
   b += align_up(N * 4, 16) * 2;                // pj0 pj1
   b += align_up(N * 8, 16) * 2;                // acc0 acc1
-  b += 64;                                     // sc
+  b += 128;                                    // sc: 32 group scalars
   return align_up(b, 128);
 }
 

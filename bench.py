@@ -487,14 +487,20 @@ def serve_measure(dev, n_requests=60, lam_fracs=(0.8,), n_sat=24, seed=1005):
 
 
 def run_profile_case(args):
-    """Small case for ncu captures: two d2_assign launches of the image-like
-    law (N=20,000 bags against K=64 centroids), device buffers."""
+    """Small case for ncu captures: two d2_assign launches, device buffers,
+    of the image-like law (N=20,000 bags against K=64 centroids) or of the
+    high-dimension law (BF16 d=128 descriptors against K=512 centroids of 64
+    supports: the screen reads tensor-core cost tiles)."""
     import torch
     from paper_1302_0435_gb300 import build, d2, synth
     build.build()
     d2.load()
-    objs, cents = synth.image_like(N=args.profile_n, K=WORKLOAD["K"])
-    ctx = d2.Context(0)
+    if args.profile_workload == "high_dim":
+        objs, cents = synth.high_dim(N=args.profile_n, K=512)
+        ctx = d2.Context(0, tile_budget_mib=1024)  # keep a capture to about 1 GB of tiles
+    else:
+        objs, cents = synth.image_like(N=args.profile_n, K=WORKLOAD["K"])
+        ctx = d2.Context(0)
     d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
     ob = d2.bags_from_synth(objs, device="cuda:0")
     lab = torch.empty(objs.count, dtype=torch.int32, device="cuda:0")
@@ -519,6 +525,7 @@ def main():
                     help="serving sweep at 0.5/0.8/0.95 of saturation (own JSON line)")
     ap.add_argument("--profile", action="store_true", help="small k_assign case for ncu")
     ap.add_argument("--profile-n", type=int, default=20000)
+    ap.add_argument("--profile-workload", default="image_like", choices=["image_like", "high_dim"])
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args)

@@ -420,7 +420,7 @@ __device__ __forceinline__ float tc_bound(int d, float nxm, float cn, float cd) 
   return (e1 + e2) * (1.f + 0x1p-10f);
 }
 
-template <int G, int NPL>
+template <int G, int NPL, bool TC>
 __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, CentView cv, long long seg_size, int K,
                                                 int KB, int NB, SolveCfg cfg, size_t slice,
                                                 int* items_out, unsigned long long* queue,
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
     bool ok = m >= 1 && m <= cfg.mmax && cb + K <= cv.K && load_obj_prefix<G>(g, ob, o0, m, s32.P);
     const bool cold = !(ws.par8 && ws.warm);
     if (ok && cold) order_rows<G>(g, s32, ob, o0, m, cv.d);
-    const bool tcp = cfg.tile.C != nullptr;
+    constexpr bool tcp = TC;  // FP32 tiles precomputed by the tensor cores (cfg.tile)
     long long trow0 = 0;
     float nxm = 0.f;
     if (ok && tcp) {
@@ -466,11 +466,13 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       const int n = (int)(cv.off[cb + j + 1] - c0);
       if (n < 1 || n > cfg.nmax || m + n > G * NPL) { ok = false; break; }
       load_cent_prefix<G>(g, cv, c0, n, s32.Q);
-      const float cmax =
-          tcp ? load_tile<G>(g, s32.cost, m, n,
-                             cfg.tile.C + trow0 * cfg.tile.ldc + (c0 - cfg.tile.col0), cfg.tile.ldc)
-              : build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0, cv.loc32 + c0 * cv.d,
-                                     cv.d);
+      float cmax;
+      if constexpr (TC)
+        cmax = load_tile<G>(g, s32.cost, m, n,
+                            cfg.tile.C + trow0 * cfg.tile.ldc + (c0 - cfg.tile.col0), cfg.tile.ldc);
+      else
+        cmax = build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0, cv.loc32 + c0 * cv.d,
+                                    cv.d);
       Simplex<float, G, NPL> S(s32, m, n, g);
       const long long wt = (i * (long long)K + j) * ws.ns;
       int st;
@@ -490,7 +492,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       if (st != kStOk) all = true;  // no bound: let the exact pass decide
       const float D = S.template objective<float>();
       float e = D * rel + cmax * 0x1p-14f;
-      if (tcp) e += tc_bound(cv.d, nxm, cfg.tile.cn[cb + j], cfg.tile.cd[cb + j]);
+      if constexpr (TC) e += tc_bound(cv.d, nxm, cfg.tile.cn[cb + j], cfg.tile.cd[cb + j]);
       const float lo = D - e, hi = D + e;
       if (lo <= best_hi) {
         if (ncand < kCandCap) {
@@ -807,10 +809,17 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
       cudaError_t e2 = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
       if (e2 != cudaSuccess) return e2;
       unsigned g2 = 1;
-      e2 = launch_cfg(k_screen<G, NPL>, smem, gpb * G, sc.sms, cnt * (long long)NB, gpb, &g2);
-      if (e2 != cudaSuccess) return e2;
-      k_screen<G, NPL><<<g2, gpb * G, smem, st>>>(ob, cv, seg_size, K, KB, NB, sc, slice, items,
-                                                  queue, ws, d_err);
+      if (sc.tile.C) {
+        e2 = launch_cfg(k_screen<G, NPL, true>, smem, gpb * G, sc.sms, cnt * (long long)NB, gpb, &g2);
+        if (e2 != cudaSuccess) return e2;
+        k_screen<G, NPL, true><<<g2, gpb * G, smem, st>>>(ob, cv, seg_size, K, KB, NB, sc, slice,
+                                                          items, queue, ws, d_err);
+      } else {
+        e2 = launch_cfg(k_screen<G, NPL, false>, smem, gpb * G, sc.sms, cnt * (long long)NB, gpb, &g2);
+        if (e2 != cudaSuccess) return e2;
+        k_screen<G, NPL, false><<<g2, gpb * G, smem, st>>>(ob, cv, seg_size, K, KB, NB, sc, slice,
+                                                           items, queue, ws, d_err);
+      }
       const unsigned mb = (unsigned)std::min<long long>((cnt + 255) / 256, 4096);
       k_merge<<<mb, 256, 0, st>>>(items, cnt, NB, sc.oidx, sc.obase, merged);
       note_launches(2);

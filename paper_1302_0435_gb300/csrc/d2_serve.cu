@@ -1,11 +1,16 @@
 // d2_serve.cu -- continuous-batching server for assignment requests
 // (Alg. 2 Step 2 against a resident centroid set).  A worker thread admits
-// queued requests into slots as slots and device memory free up; each slot
-// owns a CUDA stream and grow-only device/pinned buffers, so requests that
-// arrive while others are on the GPU start at once and their kernels
-// overlap with the running ones.  Each request's labels and distances are
-// computed by the same deterministic per-pair solver as d2_assign, so a
-// result does not depend on what else is in flight.
+// queued requests (smallest first) into slots as slots and device memory
+// free up; each slot owns two CUDA streams (high and low priority) and
+// grow-only device/pinned buffers, so requests that arrive while others are
+// on the GPU start at once and their kernels overlap with the running ones.
+// A request runs as a sequence of bounded chunks (about 2^17 pairs each) of
+// its bags, binned on the host by the nodes per lane their trees need; small
+// requests go to high-priority streams, so their blocks are dispatched as
+// soon as the chunk on the GPU drains instead of after a whole large request.
+// Each request's labels and distances are computed by the same
+// deterministic per-pair solver as d2_assign, so a result does not depend
+// on what else is in flight or on the chunking.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,12 +31,20 @@
 
 namespace {
 
+constexpr long long kChunkPairs = 1LL << 17;  // pairs per chunk launch
+constexpr int kSmallChunks = 2;                // requests of at most this many chunks: high priority
+
 struct Request {
   long long ticket = 0;
   long long count = 0;
   int dim = 0, ldt = 0, wdt = 0, mmax = 0;
   std::vector<unsigned char> loc, w;
   std::vector<long long> off;
+  // bags grouped by node bin (b: m + nmax <= 32(b+1)), index order inside
+  std::vector<int> order;
+  long long bstart[5] = {0, 0, 0, 0, 0};
+  int bmmax[4] = {0, 0, 0, 0};
+  long long chunks = 0;
   // results
   std::vector<int> labels;
   std::vector<double> dist2;
@@ -42,7 +55,9 @@ struct Request {
 };
 
 struct Slot {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;     // low priority
+  cudaStream_t stream_hi = nullptr;  // high priority
+  cudaStream_t cur = nullptr;        // the stream of the request in flight
   cudaEvent_t ev = nullptr;
   std::shared_ptr<Request> req;
   bool staging = false;
@@ -50,6 +65,7 @@ struct Slot {
   void* d_loc = nullptr; size_t n_loc = 0;
   void* d_w = nullptr; size_t n_w = 0;
   long long* d_off = nullptr; size_t n_off = 0;
+  int* d_order = nullptr; size_t n_order = 0;
   int* d_lab = nullptr; size_t n_lab = 0;
   double* d_d2 = nullptr; size_t n_d2 = 0;
   int* d_cand = nullptr; size_t n_cand = 0;
@@ -119,11 +135,13 @@ bool d2_server::launch(Slot& s, const std::shared_ptr<Request>& r) {
   const size_t b_loc = (size_t)T * r->dim * esz(r->ldt);
   const size_t b_w = (size_t)T * esz(r->wdt);
   const size_t b_off = (size_t)(N + 1) * 8;
-  const size_t b_in = b_loc + b_w + b_off;
+  const size_t b_ord = (size_t)N * 4;
+  const size_t b_in = b_loc + b_w + b_off + b_ord;
   const size_t b_out = (size_t)N * 4 + (size_t)N * 8 + 16;
   if (!grow_dev(reinterpret_cast<unsigned char**>(&s.d_loc), &s.n_loc, std::max<size_t>(b_loc, 16)) ||
       !grow_dev(reinterpret_cast<unsigned char**>(&s.d_w), &s.n_w, std::max<size_t>(b_w, 16)) ||
-      !grow_dev(&s.d_off, &s.n_off, b_off) || !grow_dev(&s.d_lab, &s.n_lab, (size_t)N * 4 + 16) ||
+      !grow_dev(&s.d_off, &s.n_off, b_off) || !grow_dev(&s.d_order, &s.n_order, b_ord + 16) ||
+      !grow_dev(&s.d_lab, &s.n_lab, (size_t)N * 4 + 16) ||
       !grow_dev(&s.d_d2, &s.n_d2, (size_t)N * 8 + 16) ||
       !grow_dev(&s.d_cand, &s.n_cand, (size_t)d2k::assign_scratch_ints(N, K, sms) * 4 + 16) ||
       !grow_host(&s.h_in, &s.n_in, b_in) ||
@@ -132,10 +150,14 @@ bool d2_server::launch(Slot& s, const std::shared_ptr<Request>& r) {
   std::memcpy(s.h_in, r->loc.data(), b_loc);
   std::memcpy(s.h_in + b_loc, r->w.data(), b_w);
   std::memcpy(s.h_in + b_loc + b_w, r->off.data(), b_off);
-  cudaMemsetAsync(s.d_err, 0, sizeof(int), s.stream);
-  cudaMemcpyAsync(s.d_loc, s.h_in, b_loc, cudaMemcpyHostToDevice, s.stream);
-  cudaMemcpyAsync(s.d_w, s.h_in + b_loc, b_w, cudaMemcpyHostToDevice, s.stream);
-  cudaMemcpyAsync(s.d_off, s.h_in + b_loc + b_w, b_off, cudaMemcpyHostToDevice, s.stream);
+  std::memcpy(s.h_in + b_loc + b_w + b_off, r->order.data(), b_ord);
+  s.cur = r->chunks <= kSmallChunks ? s.stream_hi : s.stream;
+  cudaStream_t st = s.cur;
+  cudaMemsetAsync(s.d_err, 0, sizeof(int), st);
+  cudaMemcpyAsync(s.d_loc, s.h_in, b_loc, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s.d_w, s.h_in + b_loc, b_w, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s.d_off, s.h_in + b_loc + b_w, b_off, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(s.d_order, s.h_in + b_loc + b_w + b_off, b_ord, cudaMemcpyHostToDevice, st);
   d2k::ObjView ob;
   ob.loc = s.d_loc;
   ob.w = s.d_w;
@@ -147,21 +169,32 @@ bool d2_server::launch(Slot& s, const std::shared_ptr<Request>& r) {
   d2k::SolveCfg cfg;
   cfg.mode = (r->ldt == D2_F64) ? 0 : mode;
   cfg.group = 32;
-  cfg.mmax = r->mmax;
   cfg.nmax = nmax;
   cfg.budget = budget_pivots;
   cfg.sms = sms;
   d2k::FlowOut fo{nullptr, nullptr, 0};
-  cudaError_t e = d2k::assign(ob, cv, N, (int)K, cfg, nullptr, s.d_lab, s.d_d2, nullptr, fo,
-                              s.d_cand, s.d_err, s.stream);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return false;
+  // bounded chunks, bin by bin (largest trees first); one stream, so the
+  // chunks of a request run in order and share its scratch
+  const long long per = std::max<long long>(1, kChunkPairs / std::max<long long>(K, 1));
+  for (int b = 3; b >= 0; --b) {
+    const long long b0 = r->bstart[b], b1 = r->bstart[b + 1];
+    for (long long t0 = b0; t0 < b1; t0 += per) {
+      d2k::SolveCfg cc = cfg;
+      cc.mmax = r->bmmax[b];
+      cc.oidx = s.d_order + t0;
+      cc.nobj = std::min(per, b1 - t0);
+      cudaError_t e = d2k::assign(ob, cv, N, (int)K, cc, nullptr, s.d_lab, s.d_d2, nullptr, fo,
+                                  s.d_cand, s.d_err, st);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+    }
   }
-  cudaMemcpyAsync(s.h_out, s.d_lab, (size_t)N * 4, cudaMemcpyDeviceToHost, s.stream);
-  cudaMemcpyAsync(s.h_out + (size_t)N * 4, s.d_d2, (size_t)N * 8, cudaMemcpyDeviceToHost, s.stream);
-  cudaMemcpyAsync(s.h_err, s.d_err, sizeof(int), cudaMemcpyDeviceToHost, s.stream);
-  cudaEventRecord(s.ev, s.stream);
+  cudaMemcpyAsync(s.h_out, s.d_lab, (size_t)N * 4, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(s.h_out + (size_t)N * 4, s.d_d2, (size_t)N * 8, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(s.h_err, s.d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaEventRecord(s.ev, st);
   return cudaGetLastError() == cudaSuccess;
 }
 
@@ -197,15 +230,19 @@ void d2_server::run() {
       progressed = true;
       cv_done.notify_all();
     }
-    // admissions: free slot and memory budget (staging runs unlocked)
+    // admissions: free slot and memory budget (staging runs unlocked);
+    // the smallest queued request goes first (ties: arrival order)
     while (!queue.empty()) {
-      std::shared_ptr<Request> r = queue.front();
+      auto pick = queue.begin();
+      for (auto q = queue.begin(); q != queue.end(); ++q)
+        if ((*q)->count < (*pick)->count) pick = q;
+      std::shared_ptr<Request> r = *pick;
       Slot* free_slot = nullptr;
       for (Slot& s : slots)
         if (!s.req && !s.staging) { free_slot = &s; break; }
       if (!free_slot) break;
       if (mem_inflight > 0 && mem_inflight + r->bytes > mem_budget) break;
-      queue.pop_front();
+      queue.erase(pick);
       free_slot->staging = true;
       mem_inflight += r->bytes;
       lk.unlock();
@@ -260,9 +297,15 @@ extern "C" int d2_server_create(d2_server** out, d2_ctx* ctx, int32_t nslots, in
   }
   sv->mem_budget = mem_budget > 0 ? (size_t)mem_budget : ((size_t)8 << 30);
   cudaSetDevice(sv->device);
+  int prio_lo = 0, prio_hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+    cudaGetLastError();
+    prio_lo = prio_hi = 0;
+  }
   sv->slots.resize(nslots);
   for (Slot& s : sv->slots) {
-    if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&s.stream_hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&s.d_err, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(reinterpret_cast<void**>(&s.h_err), sizeof(int)) != cudaSuccess) {
@@ -270,6 +313,7 @@ extern "C" int d2_server_create(d2_server** out, d2_ctx* ctx, int32_t nslots, in
       sv->stop = true;
       for (Slot& t : sv->slots) {
         if (t.stream) cudaStreamDestroy(t.stream);
+        if (t.stream_hi) cudaStreamDestroy(t.stream_hi);
         if (t.ev) cudaEventDestroy(t.ev);
         if (t.d_err) cudaFree(t.d_err);
         if (t.h_err) cudaFreeHost(t.h_err);
@@ -305,6 +349,23 @@ extern "C" int d2_server_submit(d2_server* sv, const d2_bags* objs, int64_t* tic
     mmax = std::max<int>(mmax, (int)m);
   }
   if (mmax + sv->nmax > 128) return D2_EUNSUPPORTED;
+  // stable partition of the bags by node bin
+  r->order.resize(N);
+  long long cnt[4] = {0, 0, 0, 0};
+  for (long long i = 0; i < N; ++i) {
+    const int m = (int)(objs->off[i + 1] - objs->off[i]);
+    const int b = (m + sv->nmax + 31) / 32 - 1;
+    ++cnt[b];
+    r->bmmax[b] = std::max(r->bmmax[b], m);
+  }
+  for (int b = 0; b < 4; ++b) r->bstart[b + 1] = r->bstart[b] + cnt[b];
+  long long fill[4] = {r->bstart[0], r->bstart[1], r->bstart[2], r->bstart[3]};
+  for (long long i = 0; i < N; ++i) {
+    const int m = (int)(objs->off[i + 1] - objs->off[i]);
+    r->order[fill[(m + sv->nmax + 31) / 32 - 1]++] = (int)i;
+  }
+  const long long per = std::max<long long>(1, kChunkPairs / std::max<long long>(sv->K, 1));
+  for (int b = 0; b < 4; ++b) r->chunks += (cnt[b] + per - 1) / per;
   r->count = N;
   r->dim = objs->dim;
   r->ldt = objs->loc_dtype;
@@ -315,7 +376,7 @@ extern "C" int d2_server_submit(d2_server* sv, const d2_bags* objs, int64_t* tic
   r->loc.assign(static_cast<const unsigned char*>(objs->loc), static_cast<const unsigned char*>(objs->loc) + b_loc);
   r->w.assign(static_cast<const unsigned char*>(objs->w), static_cast<const unsigned char*>(objs->w) + b_w);
   r->off.assign(objs->off, objs->off + N + 1);
-  r->bytes = b_loc + b_w + (size_t)(N + 1) * 8 + (size_t)N * (4 + 8) +
+  r->bytes = b_loc + b_w + (size_t)(N + 1) * 8 + (size_t)N * (4 + 4 + 8) +
              (size_t)d2k::assign_scratch_ints(N, sv->K, sv->sms) * 4;
   r->t_submit = std::chrono::steady_clock::now();
   {
@@ -370,9 +431,12 @@ extern "C" int d2_server_destroy(d2_server* sv) {
   cudaSetDevice(sv->device);
   for (Slot& s : sv->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.stream_hi) cudaStreamSynchronize(s.stream_hi);
     if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.stream_hi) cudaStreamDestroy(s.stream_hi);
     if (s.ev) cudaEventDestroy(s.ev);
-    cudaFree(s.d_loc); cudaFree(s.d_w); cudaFree(s.d_off); cudaFree(s.d_lab); cudaFree(s.d_d2);
+    cudaFree(s.d_loc); cudaFree(s.d_w); cudaFree(s.d_off); cudaFree(s.d_order); cudaFree(s.d_lab);
+    cudaFree(s.d_d2);
     cudaFree(s.d_cand); cudaFree(s.d_err);
     if (s.h_in) cudaFreeHost(s.h_in);
     if (s.h_out) cudaFreeHost(s.h_out);

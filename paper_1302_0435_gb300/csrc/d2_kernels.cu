@@ -69,15 +69,88 @@ __device__ __forceinline__ T cost_cells(const Grp<G>& g, T* C, int m, int n, con
   return cmax;
 }
 
+// The same tile for FP32 bags when n divides the group and d is a small
+// compile-time constant: lane l keeps centroid support r = l mod n in
+// registers and takes rows a = l/n, l/n + G/n, ...; the object row is read
+// with vector loads where its alignment allows.  Same operations in the same
+// order as cost_cells, so the tile is bitwise the same.
+template <int D, int G>
+__device__ __forceinline__ float cost_cells_fixed(const Grp<G>& g, float* C, int m, int n,
+                                                  const float* __restrict__ x,
+                                                  const float* __restrict__ yl) {
+  const int step = G / n;
+  const int r = g.lane - (g.lane / n) * n;
+  float y[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) y[k] = yl[r * D + k];
+  float cmax = 0.f;
+  for (int a = g.lane / n; a < m; a += step) {
+    const float* xr = x + (long long)a * D;
+    float acc = 0.f;
+    if constexpr (D % 4 == 0) {
+#pragma unroll
+      for (int k = 0; k < D; k += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(xr + k);
+        float df = v.x - y[k];
+        acc = fmaf(df, df, acc);
+        df = v.y - y[k + 1];
+        acc = fmaf(df, df, acc);
+        df = v.z - y[k + 2];
+        acc = fmaf(df, df, acc);
+        df = v.w - y[k + 3];
+        acc = fmaf(df, df, acc);
+      }
+    } else if constexpr (D % 2 == 0) {
+#pragma unroll
+      for (int k = 0; k < D; k += 2) {
+        const float2 v = *reinterpret_cast<const float2*>(xr + k);
+        float df = v.x - y[k];
+        acc = fmaf(df, df, acc);
+        df = v.y - y[k + 1];
+        acc = fmaf(df, df, acc);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float df = xr[k] - y[k];
+        acc = fmaf(df, df, acc);
+      }
+    }
+    C[a * n + r] = acc;
+    cmax = acc > cmax ? acc : cmax;
+  }
+  return cmax;
+}
+
 // Ground-cost tile of Eq. (D2opt): C[a*n+r] = sum_k (x_ak - y_rk)^2, by
 // explicit differences accumulated with FMA in coordinate order.  Returns
 // the tile maximum (group-uniform).
-template <typename T, int G>
+template <typename T, int G, int DMAX = 32>
 __device__ T build_cost(const Grp<G>& g, T* C, int m, int n, const void* xl, int xdt,
                         long long xrow0, const T* yl, int d) {
   T cmax;
   const long long o = xrow0 * (long long)d;
-  if (xdt == 1) cmax = cost_cells<T, float, G>(g, C, m, n, static_cast<const float*>(xl) + o, yl, d);
+  bool done = false;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 bags, n dividing the group, common small d: register-resident
+    // centroid supports (vector loads need 8- or 16-byte aligned rows)
+    const float* xf = static_cast<const float*>(xl) + o;
+    const uintptr_t al = reinterpret_cast<uintptr_t>(xf);
+    if (xdt == 1 && n <= G && G % n == 0) {
+      done = true;
+      if (d == 6 && (al & 7) == 0) cmax = cost_cells_fixed<6, G>(g, C, m, n, xf, yl);
+      else if (d == 3) cmax = cost_cells_fixed<3, G>(g, C, m, n, xf, yl);
+      else if constexpr (DMAX >= 32) {
+        if (d == 16 && (al & 15) == 0) cmax = cost_cells_fixed<16, G>(g, C, m, n, xf, yl);
+        else if (d == 32 && (al & 15) == 0) cmax = cost_cells_fixed<32, G>(g, C, m, n, xf, yl);
+        else done = false;
+      } else {
+        done = false;
+      }
+    }
+  }
+  if (done) {
+  } else if (xdt == 1) cmax = cost_cells<T, float, G>(g, C, m, n, static_cast<const float*>(xl) + o, yl, d);
   else if (xdt == 0) cmax = cost_cells<T, double, G>(g, C, m, n, static_cast<const double*>(xl) + o, yl, d);
   else cmax = cost_cells<T, __nv_bfloat16, G>(g, C, m, n, static_cast<const __nv_bfloat16*>(xl) + o, yl, d);
   cmax = gmax<G>(g, cmax);
@@ -252,7 +325,7 @@ __device__ __forceinline__ int solve_exact(const Grp<G>& g, const PairMem<double
   int piv = 0;
   if (fp32_start) {
     const PairMem<float> s32 = recast<float>(s);
-    const float c32 = build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
+    const float c32 = build_cost<float, G, 8>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
                                            cv.loc32 + c0 * cv.d, cv.d);
     Simplex<float, G, NPL> S32(s32, m, n, g);
     order_rows<G>(g, s32, ob, o0, m, cv.d);
@@ -471,8 +544,8 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
         cmax = load_tile<G>(g, s32.cost, m, n,
                             cfg.tile.C + trow0 * cfg.tile.ldc + (c0 - cfg.tile.col0), cfg.tile.ldc);
       else
-        cmax = build_cost<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0, cv.loc32 + c0 * cv.d,
-                                    cv.d);
+        cmax = build_cost<float, G, (NPL <= 1 ? 8 : 32)>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
+                                                         cv.loc32 + c0 * cv.d, cv.d);
       Simplex<float, G, NPL> S(s32, m, n, g);
       const long long wt = (i * (long long)K + j) * ws.ns;
       int st;

@@ -495,6 +495,24 @@ def run_profile_case(args):
     from paper_1302_0435_gb300 import build, d2, synth
     build.build()
     d2.load()
+    if args.profile_workload == "image_level":
+        # the benchmark step's level driver on profile_n bags (segments of
+        # 5,000, 10 rounds): k_screen launches after the first are warm
+        # rounds replayed from the CUDA graph
+        objs, cents = synth.image_like(N=args.profile_n, K=WORKLOAD["K"])
+        ctx = d2.Context(0)
+        d2.d2_set_stream(ctx, torch.cuda.current_stream())
+        d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
+        ob = d2.bags_from_synth(objs, device="cuda:0")
+        K = WORKLOAD["K"]
+        out_loc = torch.empty((cents.loc.shape[0], objs.dim), dtype=torch.float64, device="cuda:0")
+        out_w = torch.empty(K, dtype=torch.float64, device="cuda:0")
+        lab = torch.empty(objs.count, dtype=torch.int32, device="cuda:0")
+        rc = d2.d2_cluster_level(ctx, ob, K, WORKLOAD["seg"], WORKLOAD["iters"], out_loc, out_w, lab)
+        d2.d2_sync(ctx)
+        ctx.close()
+        print("profile case done: cluster_level rc=%d on %d bags" % (rc, objs.count))
+        return 0 if rc == 0 else 1
     if args.profile_workload == "high_dim":
         objs, cents = synth.high_dim(N=args.profile_n, K=512)
         ctx = d2.Context(0, tile_budget_mib=1024)  # keep a capture to about 1 GB of tiles
@@ -525,7 +543,8 @@ def main():
                     help="serving sweep at 0.5/0.8/0.95 of saturation (own JSON line)")
     ap.add_argument("--profile", action="store_true", help="small k_assign case for ncu")
     ap.add_argument("--profile-n", type=int, default=20000)
-    ap.add_argument("--profile-workload", default="image_like", choices=["image_like", "high_dim"])
+    ap.add_argument("--profile-workload", default="image_like",
+                    choices=["image_like", "image_level", "high_dim"])
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args)

@@ -434,6 +434,36 @@ struct Simplex {
   // Potentials from the tree: pot(root) = 0, pot(y) = c(y,par y) - pot(par y),
   // by pointer jumping: pot(y) = acc(y) + (-1)^parity(y) * pot(anc(y)).
   __device__ __forceinline__ void refresh_potentials() {
+    if constexpr (NPL == 1 && G == 32) {
+      // one node per lane: the same pointer jumping through shuffles
+      const int y = g.lane;
+      int code = y;
+      T acc = T(0);
+      bool lbad = false;
+      if (y < N && y != root) {
+        const int p = t.par[0];
+        if (p < 0 || p >= N || (y < m) == (p < m)) { lbad = true; code = root; }
+        else { code = p | (1 << 16); acc = s.cost[edge_idx(y, p)]; }
+      }
+      if (gany<G>(g, lbad)) bad = true;
+      for (int round = 0;; ++round) {
+        if (round > 9) { bad = true; break; }  // depth < 32 needs <= 6 rounds
+        const int an = code & 0xffff;
+        const int c2 = __shfl_sync(g.mask, code, an);
+        const T v = __shfl_sync(g.mask, acc, an);
+        const bool mv = y < N && an != root;
+        if (mv) {
+          const int par1 = code >> 16;
+          acc = par1 ? acc - v : acc + v;
+          code = (c2 & 0xffff) | ((par1 ^ (c2 >> 16)) << 16);
+        }
+        if (!gany<G>(g, mv)) break;
+      }
+      pot[0] = acc;
+      if (y < N) s.pot[y] = acc;
+      g.sync();
+      return;
+    }
     int* pa = s.pj0; int* pb = s.pj1;
     T* aa = s.acc0; T* ab = s.acc1;
     bool lbad = false;

@@ -110,17 +110,18 @@ __device__ __forceinline__ double round_to(double v, int dt) {
   return v;
 }
 
-constexpr int kChunkMembers = 8;  // members staged per step
+constexpr int kStageEntries = 1024;  // flow entries staged per step
 constexpr int kMaxStride = 127;
 
 // One block per centroid.  Members (objects assigned to it, increasing
-// index) are staged kChunkMembers at a time: their flow entries' centroid
-// support r, object row and coefficient omega_i * w go to shared memory;
-// then every (r, k) slot of the numerator sums, in entry order, the
-// entries of its column r (coef * v^(a)_k) in FP64; the k == 0 slot also
-// sums the denominator.  The order of every sum is fixed, so results are
-// deterministic.  Dynamic smem: num [n*d] + den [n] doubles, then the
-// staged entries.
+// index) are staged as many whole members at a time as fit kStageEntries
+// flow entries: each entry's centroid support r, object row and coefficient
+// omega_i * w go to shared memory, and one warp lists the entries of every
+// column r in entry order (a stable counting sort by r).  Then every (r, k)
+// slot of the numerator sums, in entry order, the entries of its column
+// (coef * v^(a)_k) in FP64; the k == 0 slot also sums the denominator.  The
+// order of every sum is fixed, so results are deterministic.  Dynamic smem:
+// num [n*d] + den [n] doubles, then the staged entries and column lists.
 __global__ void k_accumulate(ObjView ob, const double* omega, FlowOut fo, const int* order,
                              const long long* start, const long long* coff, int d, int cent_ldt,
                              float* loc32, double* loc64) {
@@ -131,15 +132,19 @@ __global__ void k_accumulate(ObjView ob, const double* omega, FlowOut fo, const 
   double* num = acc;
   double* den = acc + (size_t)n * d;
   double* e_coef = den + n;
-  long long* e_row = reinterpret_cast<long long*>(e_coef + kChunkMembers * kMaxStride);
-  int* e_r = reinterpret_cast<int*>(e_row + kChunkMembers * kMaxStride);
+  long long* e_row = reinterpret_cast<long long*>(e_coef + kStageEntries);
+  int* e_r = reinterpret_cast<int*>(e_row + kStageEntries);
+  int* blist = e_r + kStageEntries;
+  int* bend = blist + kStageEntries;  // [n+1]
   const int stride = (int)(fo.stride < kMaxStride ? fo.stride : kMaxStride);
+  const int per = kStageEntries / stride;
   const int slots = n * d;
+  const int lane = threadIdx.x & 31;
   for (int t = threadIdx.x; t < slots; t += blockDim.x) num[t] = 0.0;
   for (int t = threadIdx.x; t < n; t += blockDim.x) den[t] = 0.0;
   const long long b = start[g], e = start[g + 1];
-  for (long long c = b; c < e; c += kChunkMembers) {
-    const int cm = (int)(e - c < kChunkMembers ? e - c : kChunkMembers);
+  for (long long c = b; c < e; c += per) {
+    const int cm = (int)(e - c < per ? e - c : per);
     __syncthreads();
     for (int q = threadIdx.x; q < cm * stride; q += blockDim.x) {
       const int mi = q / stride, qq = q - mi * stride;
@@ -155,11 +160,38 @@ __global__ void k_accumulate(ObjView ob, const double* omega, FlowOut fo, const 
     }
     __syncthreads();
     const int ne = cm * stride;
+    if (threadIdx.x < 32) {
+      // counts per column, then starts, then a stable scatter in entry order
+      for (int r = lane; r <= n; r += 32) bend[r] = 0;
+      __syncwarp();
+      for (int base = 0; base < ne; base += 32) {
+        const int q = base + lane;
+        const int rr = q < ne ? e_r[q] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, rr);
+        if (rr >= 0 && lane == __ffs(peers) - 1) bend[rr + 1] += __popc(peers);
+        __syncwarp();
+      }
+      if (lane == 0)
+        for (int r = 0; r < n; ++r) bend[r + 1] += bend[r];
+      __syncwarp();
+      for (int base = 0; base < ne; base += 32) {
+        const int q = base + lane;
+        const int rr = q < ne ? e_r[q] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, rr);
+        if (rr >= 0) blist[bend[rr] + __popc(peers & ((1u << lane) - 1u))] = q;
+        __syncwarp();
+        if (rr >= 0 && lane == __ffs(peers) - 1) bend[rr] += __popc(peers);
+        __syncwarp();
+      }
+      // column r now spans blist[(r ? bend[r-1] : 0) .. bend[r])
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < slots; t += blockDim.x) {
       const int r = t / d, k = t - r * d;
       double sn = num[t], sd = (k == 0) ? den[r] : 0.0;
-      for (int q = 0; q < ne; ++q) {
-        if (e_r[q] != r) continue;
+      const int lo = r > 0 ? bend[r - 1] : 0, hi = bend[r];
+      for (int x = lo; x < hi; ++x) {
+        const int q = blist[x];
         const double cf = e_coef[q];
         sn = fma(cf, ldloc(ob.loc, ob.ldt, e_row[q] * d + k), sn);
         if (k == 0) sd += cf;
@@ -224,7 +256,7 @@ cudaError_t update_locations(const ObjView& ob, const double* omega, const int* 
   if (!fo.cell) return cudaGetLastError();  // sort only
   // largest centroid support bounds the accumulator size
   const size_t smem = ((size_t)64 * d + 64) * sizeof(double) +
-                      (size_t)kChunkMembers * kMaxStride * (8 + 8 + 4);
+                      (size_t)kStageEntries * (8 + 8 + 4 + 4) + 65 * 4;
   e = cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_accumulate<<<(unsigned)KT, 128, smem, st>>>(ob, omega, fo, order, start, coff, d, cent_ldt,

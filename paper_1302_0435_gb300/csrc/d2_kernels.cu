@@ -538,7 +538,9 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       const long long c0 = cv.off[cb + j];
       const int n = (int)(cv.off[cb + j + 1] - c0);
       if (n < 1 || n > cfg.nmax || m + n > G * NPL) { ok = false; break; }
-      load_cent_prefix<G>(g, cv, c0, n, s32.Q);
+      // warm bases carry their flows (the larger instantiations load Q
+      // regardless: fewer live values across the solve)
+      if (cold || NPL > 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
       float cmax;
       if constexpr (TC)
         cmax = load_tile<G>(g, s32.cost, m, n,
@@ -558,7 +560,10 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       st = S.run(cfg.budget * (m + n), tol32(cmax), &p_scr, false);
       if (ws.par8) {
         // always leave a valid basis for the next round
-        if (st == kStInvalid) S.init_northwest();
+        if (st == kStInvalid) {
+          if (!cold && NPL == 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
+          S.init_northwest();
+        }
         S.store_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
       }
       ++n_scr;

@@ -546,6 +546,26 @@ struct Simplex {
   // negative reduced cost (ties to the smallest cell).  Also records the
   // lane's best cell as its candidate for the following pivots.
   __device__ __forceinline__ void scan_full(T& best, int& cell) {
+    if (NPL == 1 && sr == 0) {
+      // n divides the group: this lane's cells share column r0 (rows a0,
+      // a0 + sq, ...), so its column potential stays in a register (small
+      // trees only: the larger instantiations keep their register budget)
+      const T vr = s.pot[m + r0];
+      best = T(0);
+      int bi = -1, ba = 0;
+      for (int a = a0, i = g.lane; a < m; a += sq, i += G) {
+        const T d = s.cost[i] - s.pot[a] - vr;
+        const bool better = d < best;
+        best = better ? d : best;
+        bi = better ? i : bi;
+        ba = better ? a : ba;
+      }
+      cell = bi >= 0 ? key_rc(ba, r0) : INT_MAX;
+      cand = bi;
+      cand_a = ba;
+      cand_r = r0;
+      return;
+    }
     const int mn = m * n;
     int a = a0, r = r0;
     best = T(0);

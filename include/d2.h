@@ -79,6 +79,12 @@ extern "C" {
 #define D2_TC_OFF 1   /* the screen builds its FP32 tiles with SIMT FMAs */
 #define D2_TC_ON 2    /* on for BF16 objects with dim a multiple of 16 in 16..256 */
 
+/* cold-start basis of the simplex (d2_config.start_rule) */
+#define D2_START_AUTO 0    /* the autotuner times both on large batches; otherwise
+                              Vogel for centroids of 64 supports, else RANKED */
+#define D2_START_RANKED 1  /* northwest staircase in principal-direction order */
+#define D2_START_VOGEL 2   /* Vogel's approximation (largest-penalty line first) */
+
 /* Limits of the current kernels. */
 #define D2_MAX_SUPPORT 64   /* supports per bag (objects and centroids) */
 #define D2_MAX_DIM 256      /* vector dimension d */
@@ -109,7 +115,8 @@ typedef struct {
     int32_t cost_tc;            /* D2_TC_* ; 0 = AUTO */
     int32_t tile_budget_mib;    /* device memory for tensor-core cost tiles;
                                    0 = min(32 GiB, 40% of free memory) */
-    int32_t reserved[3];
+    int32_t start_rule;         /* D2_START_* ; 0 = AUTO */
+    int32_t reserved[2];
 } d2_config;
 
 /*

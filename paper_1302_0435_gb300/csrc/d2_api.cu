@@ -67,9 +67,9 @@ struct d2_ctx {
   int* d_err = nullptr;
   int* d_info = nullptr;
   int* h_pin = nullptr;  // pinned host ints
-  // autotuned launch shape per (nodes-per-lane bin, K, m bound, n bound, d,
-  // mode): threads per block and screening items per SM
-  std::map<std::tuple<int, long long, int, int, int, int>, std::pair<int, int>> tuned;
+  // autotuned launch per (nodes-per-lane bin, K, m bound, n bound, d, mode):
+  // threads per block, screening items per SM, cold-start rule
+  std::map<std::tuple<int, long long, int, int, int, int>, std::tuple<int, int, int>> tuned;
   int tuning_runs = 0;
 };
 
@@ -214,6 +214,15 @@ int mode_for(const d2_ctx* c, int obj_ldt) {
   return 1;
 }
 
+// Cold-start rule when nothing was timed: Vogel's approximation pays for
+// its bookkeeping on wide centroids (64 supports), the ranked staircase
+// elsewhere.
+int start_default(const d2_ctx* c) {
+  if (c->cfg.start_rule == D2_START_VOGEL) return 1;
+  if (c->cfg.start_rule == D2_START_RANKED) return 0;
+  return c->nmax >= 64 ? 1 : 0;
+}
+
 SolveCfg solve_cfg(const d2_ctx* c, int mode, int mmax) {
   SolveCfg s;
   s.mode = mode;
@@ -223,6 +232,7 @@ SolveCfg solve_cfg(const d2_ctx* c, int mode, int mmax) {
   s.nmax = std::max(c->nmax, 1);
   s.budget = c->cfg.pivot_budget > 0 ? c->cfg.pivot_budget : 64;
   s.sms = c->sms;
+  s.start = start_default(c);
   return s;
 }
 
@@ -375,22 +385,38 @@ int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, i
       cudaEvent_t e0, e1;
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
+      auto time_one = [&](const SolveCfg& tc, float* ms) -> int {
+        CK(cudaEventRecord(e0, c->stream));
+        CK(d2k::assign(v, cv, seg, K, tc, om, tl, td, nullptr, FlowOut{nullptr, nullptr, 0}, cand,
+                       c->d_err, c->stream, nullptr, tw));
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        *ms = 0.f;
+        cudaEventElapsedTime(ms, e0, e1);
+        return D2_OK;
+      };
+      // cold-start rule first (default shape), unless the caller fixed it
+      if (c->cfg.start_rule == D2_START_AUTO) {
+        float best_s = 1e30f;
+        for (int sr = 0; sr < 2; ++sr) {
+          t.start = sr;
+          float ms = 0.f;
+          if ((rc = time_one(t, &ms))) return rc;
+          if (ms < best_s) { best_s = ms; cfg.start = sr; }
+        }
+      }
+      t.start = cfg.start;
       float best = 1e30f;
-      std::pair<int, int> pick(128, 96);
+      std::tuple<int, int, int> pick(128, 96, cfg.start);
       const int tpbs[2] = {64, 128};
       const int ipsms[3] = {48, 96, 192};
       for (int tp : tpbs)
         for (int ip : ipsms) {
           t.tpb = tp;
           t.ipsm = ip;
-          CK(cudaEventRecord(e0, c->stream));
-          CK(d2k::assign(v, cv, seg, K, t, om, tl, td, nullptr, FlowOut{nullptr, nullptr, 0}, cand,
-                         c->d_err, c->stream, nullptr, tw));
-          CK(cudaEventRecord(e1, c->stream));
-          CK(cudaEventSynchronize(e1));
           float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (ms < best) { best = ms; pick = std::make_pair(tp, ip); }
+          if ((rc = time_one(t, &ms))) return rc;
+          if (ms < best) { best = ms; pick = std::make_tuple(tp, ip, cfg.start); }
         }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
@@ -398,8 +424,9 @@ int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, i
       it = c->tuned.emplace(key, pick).first;
     }
     if (it != c->tuned.end()) {
-      cfg.tpb = it->second.first;
-      cfg.ipsm = it->second.second;
+      cfg.tpb = std::get<0>(it->second);
+      cfg.ipsm = std::get<1>(it->second);
+      cfg.start = std::get<2>(it->second);
     }
     CK(d2k::assign(v, cv, seg, K, cfg, om, lab, d2o, terms, fo, cand, c->d_err, c->stream, ws, tw));
   }
@@ -479,7 +506,7 @@ bool want_bins(const d2_ctx* c, long long count, int mmax) {
 
 namespace d2k {
 CentView ctx_centroids(const d2_ctx* c, int* nmax, int* d, int* device, int* mode, int* budget,
-                       int* sms, long long* K) {
+                       int* sms, long long* K, int* start) {
   *nmax = c->nmax;
   *d = c->d;
   *device = c->device;
@@ -487,6 +514,7 @@ CentView ctx_centroids(const d2_ctx* c, int* nmax, int* d, int* device, int* mod
   *budget = c->cfg.pivot_budget > 0 ? c->cfg.pivot_budget : 64;
   *sms = c->sms;
   *K = c->K;
+  *start = start_default(c);
   return resident_view(c);
 }
 }  // namespace d2k

@@ -97,6 +97,7 @@ struct SolveCfg {
   const int* oidx = nullptr;  // objects of this launch (nullptr: obase..obase+nobj-1)
   long long nobj = -1;        // entries of oidx (-1: all ob.count objects)
   long long obase = 0;        // first object when oidx is nullptr
+  int start = 0;              // cold start basis: 0 ranked northwest staircase, 1 Vogel
   TileView tile;              // precomputed FP32 tiles of the screen (optional)
 };
 
@@ -118,6 +119,24 @@ cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, in
                    const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
                    double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st,
                    const WarmStore* ws = nullptr, const TcWork* tw = nullptr);
+
+// ---- solver launches, one translation unit per nodes-per-lane shape ----
+#define D2_NPL_DECL(N)                                                                         \
+  cudaError_t assign_npl##N(const ObjView& ob, const CentView& cv, long long seg_size, int K,  \
+                            const SolveCfg& cfg, const double* omega, int* labels,           \
+                            double* dist2, double* eps_terms, FlowOut fo, int* cand,           \
+                            int* d_err, cudaStream_t st, const WarmStore* ws,                 \
+                            const TcWork* tw);                                                 \
+  cudaError_t mallows_pairs_npl##N(const ObjView& ob, const CentView& cv,                     \
+                                   const long long* pobj, const long long* pcen,              \
+                                   long long npairs, const SolveCfg& cfg, double* dist2,       \
+                                   FlowOut fo, int* status, int* d_err, cudaStream_t st);     \
+  cudaError_t stats_npl##N(long long out[4]);
+D2_NPL_DECL(1)
+D2_NPL_DECL(2)
+D2_NPL_DECL(3)
+D2_NPL_DECL(4)
+#undef D2_NPL_DECL
 
 // ---- tensor-core ground cost (d2_tc.cu) ----
 // Whether the contraction supports dimension d (a multiple of 16 in 16..256).

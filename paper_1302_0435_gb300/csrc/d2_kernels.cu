@@ -1,7 +1,9 @@
-// d2_kernels.cu -- CUDA kernels of the assignment step for sm_103a:
-// bag validation, centroid preparation, per-pair Mallows distance
-// (Eq. (D2opt) with z fixed), nearest-centroid assignment (Alg. 2 Step 2)
-// and single-pair cost matrices.
+// d2_kernels.cu -- the small kernels of the assignment step for sm_103a
+// (bag validation, centroid preparation, node bins, single-pair cost
+// matrices, fixed-order sums) and the dispatch of the solver launches
+// (per-pair Mallows distance, Eq. (D2opt) with z fixed; nearest-centroid
+// assignment, Alg. 2 Step 2) to the units d2_npl1..4.cu that instantiate
+// them for 1..4 tree nodes per lane.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -13,341 +15,9 @@
 #include "d2_internal.h"
 #include "d2_solver.cuh"
 
+#include "d2_solve.cuh"
+
 namespace d2k {
-
-// Solver activity counters: pairs screened, their pivots, pairs solved
-// exactly, their pivots.  Accumulated once per lane group per launch.
-__device__ unsigned long long g_solver_stats[4];
-
-__device__ __forceinline__ void add_stats(unsigned long long a, unsigned long long b,
-                                          unsigned long long c, unsigned long long d) {
-  if (a) atomicAdd(&g_solver_stats[0], a);
-  if (b) atomicAdd(&g_solver_stats[1], b);
-  if (c) atomicAdd(&g_solver_stats[2], c);
-  if (d) atomicAdd(&g_solver_stats[3], d);
-}
-
-// ---------------------------------------------------------------- loads --
-
-template <typename T>
-__device__ __forceinline__ T ldx(const void* p, int dt, long long idx) {
-  if (dt == 0) return (T)(static_cast<const double*>(p)[idx]);
-  if (dt == 1) return (T)(static_cast<const float*>(p)[idx]);
-  return (T)__bfloat162float(static_cast<const __nv_bfloat16*>(p)[idx]);
-}
-
-template <typename T> __device__ __forceinline__ T cvt(float v) { return (T)v; }
-template <typename T> __device__ __forceinline__ T cvt(double v) { return (T)v; }
-template <typename T> __device__ __forceinline__ T cvt(__nv_bfloat16 v) { return (T)__bfloat162float(v); }
-
-__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
-
-// Ground-cost tile of Eq. (D2opt): C[a*n+r] = sum_k (x_ak - y_rk)^2, by
-// explicit differences accumulated with FMA in coordinate order.  Returns
-// the tile maximum (group-uniform).
-template <typename T, typename X, int G>
-__device__ __forceinline__ T cost_cells(const Grp<G>& g, T* C, int m, int n, const X* x, const T* yl,
-                                        int d) {
-  const int mn = m * n;
-  const int q = G / n, rem = G - (G / n) * n;
-  int a = g.lane / n, r = g.lane - (g.lane / n) * n;
-  T cmax = T(0);
-  for (int t = g.lane; t < mn; t += G) {
-    const T* yr = yl + (long long)r * d;
-    const X* xr = x + (long long)a * d;
-    T acc = T(0);
-    for (int k = 0; k < d; ++k) {
-      const T df = cvt<T>(xr[k]) - yr[k];
-      acc = fmaT(df, df, acc);
-    }
-    C[t] = acc;
-    cmax = acc > cmax ? acc : cmax;
-    r += rem; a += q;
-    if (r >= n) { r -= n; ++a; }
-  }
-  return cmax;
-}
-
-// The same tile for FP32 bags when n divides the group and d is a small
-// compile-time constant: lane l keeps centroid support r = l mod n in
-// registers and takes rows a = l/n, l/n + G/n, ...; the object row is read
-// with vector loads where its alignment allows.  Same operations in the same
-// order as cost_cells, so the tile is bitwise the same.
-template <int D, int G>
-__device__ __forceinline__ float cost_cells_fixed(const Grp<G>& g, float* C, int m, int n,
-                                                  const float* __restrict__ x,
-                                                  const float* __restrict__ yl) {
-  const int step = G / n;
-  const int r = g.lane - (g.lane / n) * n;
-  float y[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) y[k] = yl[r * D + k];
-  float cmax = 0.f;
-  for (int a = g.lane / n; a < m; a += step) {
-    const float* xr = x + (long long)a * D;
-    float acc = 0.f;
-    if constexpr (D % 4 == 0) {
-#pragma unroll
-      for (int k = 0; k < D; k += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(xr + k);
-        float df = v.x - y[k];
-        acc = fmaf(df, df, acc);
-        df = v.y - y[k + 1];
-        acc = fmaf(df, df, acc);
-        df = v.z - y[k + 2];
-        acc = fmaf(df, df, acc);
-        df = v.w - y[k + 3];
-        acc = fmaf(df, df, acc);
-      }
-    } else if constexpr (D % 2 == 0) {
-#pragma unroll
-      for (int k = 0; k < D; k += 2) {
-        const float2 v = *reinterpret_cast<const float2*>(xr + k);
-        float df = v.x - y[k];
-        acc = fmaf(df, df, acc);
-        df = v.y - y[k + 1];
-        acc = fmaf(df, df, acc);
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const float df = xr[k] - y[k];
-        acc = fmaf(df, df, acc);
-      }
-    }
-    C[a * n + r] = acc;
-    cmax = acc > cmax ? acc : cmax;
-  }
-  return cmax;
-}
-
-// Ground-cost tile of Eq. (D2opt): C[a*n+r] = sum_k (x_ak - y_rk)^2, by
-// explicit differences accumulated with FMA in coordinate order.  Returns
-// the tile maximum (group-uniform).
-template <typename T, int G, int DMAX = 32>
-__device__ T build_cost(const Grp<G>& g, T* C, int m, int n, const void* xl, int xdt,
-                        long long xrow0, const T* yl, int d) {
-  T cmax;
-  const long long o = xrow0 * (long long)d;
-  bool done = false;
-  if constexpr (sizeof(T) == 4) {
-    // FP32 bags, n dividing the group, common small d: register-resident
-    // centroid supports (vector loads need 8- or 16-byte aligned rows)
-    const float* xf = static_cast<const float*>(xl) + o;
-    const uintptr_t al = reinterpret_cast<uintptr_t>(xf);
-    if (xdt == 1 && n <= G && G % n == 0) {
-      done = true;
-      if (d == 6 && (al & 7) == 0) cmax = cost_cells_fixed<6, G>(g, C, m, n, xf, yl);
-      else if (d == 3) cmax = cost_cells_fixed<3, G>(g, C, m, n, xf, yl);
-      else if constexpr (DMAX >= 32) {
-        if (d == 16 && (al & 15) == 0) cmax = cost_cells_fixed<16, G>(g, C, m, n, xf, yl);
-        else if (d == 32 && (al & 15) == 0) cmax = cost_cells_fixed<32, G>(g, C, m, n, xf, yl);
-        else done = false;
-      } else {
-        done = false;
-      }
-    }
-  }
-  if (done) {
-  } else if (xdt == 1) cmax = cost_cells<T, float, G>(g, C, m, n, static_cast<const float*>(xl) + o, yl, d);
-  else if (xdt == 0) cmax = cost_cells<T, double, G>(g, C, m, n, static_cast<const double*>(xl) + o, yl, d);
-  else cmax = cost_cells<T, __nv_bfloat16, G>(g, C, m, n, static_cast<const __nv_bfloat16*>(xl) + o, yl, d);
-  cmax = gmax<G>(g, cmax);
-  g.sync();
-  return cmax;
-}
-
-// ---------------------------------------------------------- start order --
-// The cold-start basis is the northwest staircase taken in the order of
-// the supports' projections onto the object's principal direction (in 1-D
-// that staircase is the optimal monotone coupling; in d dimensions it is a
-// start close to it along the dominant axis).
-
-// inclusive prefix of per-id masses (from the by-id inclusive prefix `pre`)
-// in the order id_of[0..cnt)
-template <int G>
-__device__ void prefix_in_order(const Grp<G>& g, const long long* pre, const int* id_of, int cnt,
-                                long long* out) {
-  long long carry = 0;
-  for (int base = 0; base < cnt; base += G) {
-    const int r = base + g.lane;
-    long long v = 0;
-    if (r < cnt) {
-      const int id = id_of[r];
-      v = pre[id] - (id > 0 ? pre[id - 1] : 0LL);
-    }
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) {
-      const long long u = __shfl_up_sync(g.mask, v, o, G);
-      if (g.lane >= o) v += u;
-    }
-    v += carry;
-    if (r < cnt) out[r] = v;
-    carry = __shfl_sync(g.mask, v, G - 1, G);
-  }
-  g.sync();
-}
-
-// stable ranks of proj[0..cnt) (ties to the smaller index)
-template <int G>
-__device__ void rank_by_proj(const Grp<G>& g, const float* proj, int cnt, int* rank, int* id) {
-  for (int a = g.lane; a < cnt; a += G) {
-    const float v = proj[a];
-    int r = 0;
-    for (int b = 0; b < cnt; ++b) {
-      const float u = proj[b];
-      r += (u < v || (u == v && b < a)) ? 1 : 0;
-    }
-    rank[a] = r;
-    id[r] = a;
-  }
-  g.sync();
-}
-
-// Object side: weighted mean, principal direction by power iteration from
-// the farthest support, row ranks and rank-order prefix masses.
-template <int G>
-__device__ void order_rows(const Grp<G>& g, const PairMem<float>& s, const ObjView& ob, long long o0,
-                           int m, int d) {
-  const float wscale = (float)kInvMass;
-  for (int k = g.lane; k < d; k += G) {
-    float acc = 0.f;
-    for (int a = 0; a < m; ++a) {
-      const float pa = (float)(s.P[a] - (a > 0 ? s.P[a - 1] : 0LL)) * wscale;
-      acc = fmaf(pa, ldx<float>(ob.loc, ob.ldt, (o0 + a) * d + k), acc);
-    }
-    s.mu[k] = acc;
-  }
-  g.sync();
-  // start: the support farthest from the mean (largest weighted deviation)
-  float best = -1.f;
-  int bi = 0;
-  for (int a = g.lane; a < m; a += G) {
-    float dev = 0.f;
-    for (int k = 0; k < d; ++k) {
-      const float x = ldx<float>(ob.loc, ob.ldt, (o0 + a) * d + k) - s.mu[k];
-      dev = fmaf(x, x, dev);
-    }
-    dev *= (float)(s.P[a] - (a > 0 ? s.P[a - 1] : 0LL)) * wscale;
-    if (dev > best) { best = dev; bi = a; }
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    const float ob2 = gshfl_xor<G>(g, best, o);
-    const int oi = gshfl_xor<G>(g, bi, o);
-    if (ob2 > best || (ob2 == best && oi < bi)) { best = ob2; bi = oi; }
-  }
-  for (int k = g.lane; k < d; k += G) s.dir[k] = ldx<float>(ob.loc, ob.ldt, (o0 + bi) * d + k) - s.mu[k];
-  g.sync();
-  for (int it = 0; it < 6; ++it) {
-    for (int a = g.lane; a < m; a += G) {
-      float dot = 0.f;
-      for (int k = 0; k < d; ++k) dot = fmaf(ldx<float>(ob.loc, ob.ldt, (o0 + a) * d + k) - s.mu[k], s.dir[k], dot);
-      s.proj[a] = dot * (float)(s.P[a] - (a > 0 ? s.P[a - 1] : 0LL)) * wscale;
-    }
-    g.sync();
-    float nrm = 0.f;
-    float vk[8];
-    int nk = 0;
-    for (int k = g.lane; k < d; k += G) {
-      float acc = 0.f;
-      for (int a = 0; a < m; ++a) acc = fmaf(s.proj[a], ldx<float>(ob.loc, ob.ldt, (o0 + a) * d + k) - s.mu[k], acc);
-      if (nk < 8) vk[nk++] = acc;
-      nrm = fmaf(acc, acc, nrm);
-    }
-    nrm = gsum<G>(g, nrm);
-    g.sync();
-    const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
-    nk = 0;
-    for (int k = g.lane; k < d; k += G) {
-      if (nk < 8) s.dir[k] = inv > 0.f ? vk[nk] * inv : s.dir[k];
-      ++nk;
-    }
-    g.sync();
-  }
-  for (int a = g.lane; a < m; a += G) {
-    float dot = 0.f;
-    for (int k = 0; k < d; ++k) dot = fmaf(ldx<float>(ob.loc, ob.ldt, (o0 + a) * d + k) - s.mu[k], s.dir[k], dot);
-    s.proj[a] = dot;
-  }
-  g.sync();
-  rank_by_proj<G>(g, s.proj, m, s.rrank, s.rid);
-  prefix_in_order<G>(g, s.P, s.rid, m, s.Pr);
-}
-
-// Centroid side: column ranks along the object's direction and their
-// rank-order prefix masses (s.Q holds the centroid's by-id prefix).
-template <int G>
-__device__ void order_cols(const Grp<G>& g, const PairMem<float>& s, const float* y32, int n, int d) {
-  for (int r = g.lane; r < n; r += G) {
-    float dot = 0.f;
-    for (int k = 0; k < d; ++k) dot = fmaf(y32[(long long)r * d + k] - s.mu[k], s.dir[k], dot);
-    s.proj[r] = dot;
-  }
-  g.sync();
-  rank_by_proj<G>(g, s.proj, n, s.crank, s.cid);
-  prefix_in_order<G>(g, s.Q, s.cid, n, s.Qr);
-}
-
-template <int G>
-__device__ bool load_obj_prefix(const Grp<G>& g, const ObjView& ob, long long o0, int m,
-                                long long* P) {
-  if (ob.wdt == 0) return load_prefix<G>(g, static_cast<const double*>(ob.w) + o0, m, P);
-  return load_prefix<G>(g, static_cast<const float*>(ob.w) + o0, m, P);
-}
-
-template <int G>
-__device__ void load_cent_prefix(const Grp<G>& g, const CentView& cv, long long c0, int n,
-                                 long long* Q) {
-  for (int r = g.lane; r < n; r += G) Q[r] = cv.Qpre[c0 + r];
-  g.sync();
-}
-
-// Tolerances on the most negative reduced cost accepted as optimal.
-__device__ __forceinline__ double tol64(double cmax) { return cmax * 0x1p-43; }
-__device__ __forceinline__ float tol32(float cmax) { return cmax * 0x1p-20f; }
-
-// Exact solve of pair (object at o0/m, centroid at c0/n) into the tree
-// registers `tr`.  With fp32_start the basis is first driven to FP32
-// optimality on the FP32 tile (cheap pivots); the same tree and integer
-// flows then continue on the FP64 tile with FP64 potentials until no FP64
-// reduced cost is below -tol64, so the result is FP64-optimal either way.
-// *obj: FP64 objective.
-template <int G, int NPL>
-__device__ __forceinline__ int solve_exact(const Grp<G>& g, const PairMem<double>& s,
-                                           Simplex<double, G, NPL>& S, const ObjView& ob,
-                                           long long o0, int m, const CentView& cv, long long c0,
-                                           int n, int budget, bool fp32_start, double* obj,
-                                           int* piv_out) {
-  load_cent_prefix<G>(g, cv, c0, n, s.Q);
-  const int cap = budget * (m + n);
-  int piv = 0;
-  if (fp32_start) {
-    const PairMem<float> s32 = recast<float>(s);
-    const float c32 = build_cost<float, G, 8>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
-                                           cv.loc32 + c0 * cv.d, cv.d);
-    Simplex<float, G, NPL> S32(s32, m, n, g);
-    order_rows<G>(g, s32, ob, o0, m, cv.d);
-    order_cols<G>(g, s32, cv.loc32 + c0 * cv.d, n, cv.d);
-    S32.init_northwest_ranked();
-    if (S32.run(cap, tol32(c32), &piv) == kStInvalid) { *piv_out += piv; return kStInvalid; }
-    S.t = S32.t;
-    S.root = S32.root;
-    g.sync();
-  }
-  const double cmax = build_cost<double, G>(g, s.cost, m, n, ob.loc, ob.ldt, o0,
-                                            cv.loc64 + c0 * cv.d, cv.d);
-  S.set_dims(m, n);
-  S.bad = false;
-  if (!fp32_start) S.init_northwest();
-  const int st = S.run(cap, tol64(cmax), &piv);
-  *obj = S.template objective<double>();
-  *piv_out += piv;
-  return st;
-}
-
-// -------------------------------------------------------------- kernels --
 
 __global__ void k_scan_bags(const long long* off, long long count, int* info) {
   for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < count;
@@ -386,341 +56,6 @@ __global__ void k_prep_centroids(const void* loc, int ldt, const void* w, int wd
       loc32[c0 * d + e] = (float)v;
     }
   }
-}
-
-template <int G, int NPL>
-__global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
-                                                       const long long* pobj, const long long* pcen,
-                                                       long long npairs, SolveCfg cfg, size_t slice,
-                                                       double* dist2, FlowOut fo, int* status, int* err) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Grp<G> g;
-  const int gpb = blockDim.x / G;
-  unsigned char* base = smem + (threadIdx.x / G) * slice;
-  int n_pairs = 0, n_piv = 0;
-  for (long long t = (long long)blockIdx.x * gpb + threadIdx.x / G; t < npairs;
-       t += (long long)gridDim.x * gpb) {
-    const long long i = pobj[t], j = pcen[t];
-    int st = kStInvalid;
-    double res = nan("");
-    if (i >= 0 && i < ob.count && j >= 0 && j < cv.K) {
-      const long long o0 = ob.off[i];
-      const int m = (int)(ob.off[i + 1] - o0);
-      const long long c0 = cv.off[j];
-      const int n = (int)(cv.off[j + 1] - c0);
-      if (m >= 1 && m <= cfg.mmax && n >= 1 && n <= cfg.nmax && m + n <= G * NPL) {
-        PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax, cv.d);
-        if (load_obj_prefix<G>(g, ob, o0, m, s64.P)) {
-          Simplex<double, G, NPL> S(s64, m, n, g);
-          st = solve_exact<G, NPL>(g, s64, S, ob, o0, m, cv, c0, n, cfg.budget, cfg.mode == 1,
-                                   &res, &n_piv);
-          ++n_pairs;
-          if (fo.cell && st != kStInvalid)
-            S.write_flows(fo.cell + t * fo.stride, fo.w + t * fo.stride, fo.stride);
-        }
-      }
-    }
-    if (g.lane == 0) {
-      dist2[t] = res;
-      if (status) status[t] = st == kStOk ? 0 : (st == kStNotConverged ? -3 : -1);
-      if (st == kStInvalid) atomicOr(err, kErrInvalid);
-      if (st == kStNotConverged) atomicOr(err, kErrNotConverged);
-    }
-    g.sync();
-  }
-  if (g.lane == 0) add_stats(0, 0, n_pairs, n_piv);
-}
-
-// Nearest centroid, Alg. 2 Step 2, in two kernels.  Object i uses the
-// centroids [(i/seg_size)*K, (i/seg_size)*K + K) of the set.
-//
-// k_screen: every centroid is solved with an FP32 tile and FP32 pivots.
-// The FP32 objective D32_j has a bound err_j on its distance to the FP64
-// optimum (cost rounding (d+3)*2^-24 relative, summation 2^-17 relative,
-// basis optimality 2^-14 * max cost absolute, which covers the stopping
-// tolerance 2^-20 * max cost and the drift of the incrementally updated
-// FP32 potentials, refreshed every 64 pivots); every centroid whose interval
-// [D32_j - err_j, D32_j + err_j] reaches below the smallest upper end is a
-// candidate.  With tensor-core tiles (cfg.tile) the bound adds the tile's
-// own error, see tc_bound.
-// Work items are (object i, centroid block jb) with blocks of KB centroids,
-// so small batches still fill the GPU; lane groups take items from an
-// atomic counter (persistent kernel).  Output per item (kItemInts ints at
-// item*kItemInts): count (-1: more than kCandCap, -2: invalid object),
-// kCandCap candidate indices in increasing order, their lower ends (float
-// bits), and the block's smallest upper end (float bits).
-
-// FP32 cost tile of one pair from a chunk's precomputed tile rows (see
-// TileView): row a of the pair is row a of src, columns 0..n-1.  Returns
-// the tile maximum (group-uniform).
-template <int G>
-__device__ __forceinline__ float load_tile(const Grp<G>& g, float* C, int m, int n,
-                                           const float* __restrict__ src, long long ldc) {
-  const int mn = m * n;
-  const int q = G / n, rem = G - (G / n) * n;
-  int a = g.lane / n, r = g.lane - (g.lane / n) * n;
-  float cmax = 0.f;
-#pragma unroll 4
-  for (int t = g.lane; t < mn; t += G) {
-    const float v = __ldg(src + (long long)a * ldc + r);
-    C[t] = v;
-    cmax = fmaxf(cmax, v);
-    r += rem; a += q;
-    if (r >= n) { r -= n; ++a; }
-  }
-  cmax = gmax<G>(g, cmax);
-  g.sync();
-  return cmax;
-}
-
-// Bound on |C^ - C| for every cell of a tensor-core tile (C^ = the FP32
-// tile of ||x||^2 + ||y^||^2 - 2 x.y^ over BF16 x and y^ = BF16(y)), from the
-// largest FP32 squared norms nxm (object rows) and cn (centroid rows) and
-// the largest rounding distance cd = max ||y - y^||:
-//   accumulation of d exact products in FP32 by the tensor cores, modelled
-//   as at most one unit in the last place of sum|x_k y^_k| <= ||x|| ||y^||
-//   lost by every aligned addend (d products plus one accumulator per
-//   block of at least 4 products: <= 1.25 d units of 2^-23), taken twice:
-//   d * 2^-22; the two FP32 norm sums and the final FMA ((d+3) * 2^-24);
-//   both relative to ||x||^2 + ||y^||^2 >= 2 ||x|| ||y^||; then the move from
-//   y^ back to y: | ||x-y^||^2 - ||x-y||^2 | <= (2(||x|| + ||y^||) + cd) cd.
-// Since a pair's flows sum to 1, the same bound holds for the objective of
-// any basis, hence for the optimum.
-__device__ __forceinline__ float tc_bound(int d, float nxm, float cn, float cd) {
-  const float rel = (float)d * 0x1p-22f + (float)(d + 3) * 0x1p-24f;
-  const float e1 = rel * (nxm + cn);
-  const float e2 = (2.f * (sqrtf(nxm) + sqrtf(cn)) + 2.f * cd) * cd;
-  return (e1 + e2) * (1.f + 0x1p-10f);
-}
-
-template <int G, int NPL, bool TC>
-__global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, CentView cv, long long seg_size, int K,
-                                                int KB, int NB, SolveCfg cfg, size_t slice,
-                                                int* items_out, unsigned long long* queue,
-                                                WarmStore ws, int* err) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Grp<G> g;
-  unsigned char* base = smem + (threadIdx.x / G) * slice;
-  const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax, cv.d);
-  int* cand = s32.sc;                                          // [kCandCap]
-  float* clo = reinterpret_cast<float*>(s32.sc + kCandCap);    // [kCandCap]
-  int n_scr = 0, p_scr = 0;
-  const float rel = (float)(cv.d + 3) * 0x1p-24f + 0x1p-17f;
-  const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
-  const unsigned long long total = (unsigned long long)nobj * NB;
-  for (;;) {
-    unsigned long long item = 0;
-    if (g.lane == 0) item = atomicAdd(queue, 1ull);
-    item = __shfl_sync(g.mask, item, 0, G);
-    if (item >= total) break;
-    const long long tt = (long long)(item / NB);
-    const long long i = cfg.oidx ? (long long)cfg.oidx[tt] : cfg.obase + tt;
-    const int jb = (int)(item - (unsigned long long)tt * NB);
-    const int j0 = jb * KB, j1 = min(K, j0 + KB);
-    const long long o0 = ob.off[i];
-    const int m = (int)(ob.off[i + 1] - o0);
-    const long long cb = (i / seg_size) * (long long)K;
-    bool ok = m >= 1 && m <= cfg.mmax && cb + K <= cv.K && load_obj_prefix<G>(g, ob, o0, m, s32.P);
-    const bool cold = !(ws.par8 && ws.warm);
-    if (ok && cold) order_rows<G>(g, s32, ob, o0, m, cv.d);
-    constexpr bool tcp = TC;  // FP32 tiles precomputed by the tensor cores (cfg.tile)
-    long long trow0 = 0;
-    float nxm = 0.f;
-    if (ok && tcp) {
-      trow0 = cfg.tile.trow[tt];
-      for (int a = g.lane; a < m; a += G) nxm = fmaxf(nxm, cfg.tile.nx[trow0 + a]);
-      nxm = gmax<G>(g, nxm);
-    }
-    int ncand = 0;
-    bool all = false;
-    float best_hi = FLT_MAX;
-    for (int j = j0; ok && j < j1; ++j) {
-      const long long c0 = cv.off[cb + j];
-      const int n = (int)(cv.off[cb + j + 1] - c0);
-      if (n < 1 || n > cfg.nmax || m + n > G * NPL) { ok = false; break; }
-      // warm bases carry their flows (the larger instantiations load Q
-      // regardless: fewer live values across the solve)
-      if (cold || NPL > 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
-      float cmax;
-      if constexpr (TC)
-        cmax = load_tile<G>(g, s32.cost, m, n,
-                            cfg.tile.C + trow0 * cfg.tile.ldc + (c0 - cfg.tile.col0), cfg.tile.ldc);
-      else
-        cmax = build_cost<float, G, (NPL <= 1 ? 8 : 32)>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
-                                                         cv.loc32 + c0 * cv.d, cv.d);
-      Simplex<float, G, NPL> S(s32, m, n, g);
-      const long long wt = (i * (long long)K + j) * ws.ns;
-      int st;
-      if (!cold) {
-        S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
-      } else {
-        order_cols<G>(g, s32, cv.loc32 + c0 * cv.d, n, cv.d);
-        S.init_northwest_ranked();
-      }
-      st = S.run(cfg.budget * (m + n), tol32(cmax), &p_scr, false);
-      if (ws.par8) {
-        // always leave a valid basis for the next round
-        if (st == kStInvalid) {
-          if (!cold && NPL == 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
-          S.init_northwest();
-        }
-        S.store_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
-      }
-      ++n_scr;
-      if (st != kStOk) all = true;  // no bound: let the exact pass decide
-      const float D = S.template objective<float>();
-      float e = D * rel + cmax * 0x1p-14f;
-      if constexpr (TC) e += tc_bound(cv.d, nxm, cfg.tile.cn[cb + j], cfg.tile.cd[cb + j]);
-      const float lo = D - e, hi = D + e;
-      if (lo <= best_hi) {
-        if (ncand < kCandCap) {
-          if (g.lane == 0) { cand[ncand] = j; clo[ncand] = lo; }
-          ++ncand;
-        } else {
-          all = true;
-        }
-      }
-      g.sync();
-      if (hi < best_hi) {
-        best_hi = hi;
-        int k2 = 0;
-        for (int c = 0; c < ncand; ++c) {
-          const int cj = cand[c];
-          const float cl = clo[c];
-          g.sync();
-          if (cl <= best_hi) {
-            if (g.lane == 0) { cand[k2] = cj; clo[k2] = cl; }
-            ++k2;
-          }
-          g.sync();
-        }
-        ncand = k2;
-      }
-    }
-    int* out = items_out + item * kItemInts;
-    if (g.lane == 0) {
-      out[0] = !ok ? -2 : (all ? -1 : ncand);
-      out[2 * kCandCap + 1] = __float_as_int(best_hi);
-    }
-    if (g.lane >= 1 && g.lane <= kCandCap) {
-      out[g.lane] = (g.lane <= ncand) ? cand[g.lane - 1] : -1;
-      out[kCandCap + g.lane] = __float_as_int((g.lane <= ncand) ? clo[g.lane - 1] : FLT_MAX);
-    }
-    g.sync();
-  }
-  if (g.lane == 0) add_stats(n_scr, p_scr, 0, 0);
-}
-
-// Per object: merge its NB block lists into one candidate list (count,
-// kCandCap indices increasing) at cand[i*kMergedInts]: keep the block
-// candidates whose lower end reaches the smallest upper end over all blocks.
-__global__ void k_merge(const int* items, long long N, int NB, const int* oidx, long long obase,
-                        int* cand) {
-  for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < N;
-       tt += (long long)gridDim.x * blockDim.x) {
-    const long long i = oidx ? (long long)oidx[tt] : obase + tt;
-    const int* it = items + tt * NB * kItemInts;
-    float best_hi = FLT_MAX;
-    int state = 0;  // 0 ok, -1 all, -2 invalid
-    for (int b = 0; b < NB; ++b) {
-      const int c = it[b * kItemInts];
-      if (c == -2) state = -2;
-      else if (c == -1 && state == 0) state = -1;
-      best_hi = fminf(best_hi, __int_as_float(it[b * kItemInts + 2 * kCandCap + 1]));
-    }
-    int cnt = 0;
-    int* out = cand + i * kMergedInts;
-    if (state == 0) {
-      for (int b = 0; b < NB && state == 0; ++b) {
-        const int* blk = it + b * kItemInts;
-        for (int c = 0; c < blk[0]; ++c) {
-          if (__int_as_float(blk[kCandCap + 1 + c]) <= best_hi) {
-            if (cnt < kCandCap) out[1 + cnt] = blk[1 + c];
-            ++cnt;
-          }
-        }
-      }
-      if (cnt > kCandCap) state = -1;
-    }
-    out[0] = state == 0 ? cnt : state;
-  }
-}
-
-// k_exact: the candidates of each object (all K for mode 0, for
-// count -1, or where the FP32 screen could not run) are solved to FP64
-// optimality; the label is the smallest-index minimum of those FP64
-// values, so it agrees with an all-FP64 argmin.
-template <int G, int NPL>
-__global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long long seg_size, int K,
-                                               SolveCfg cfg, size_t slice, const int* cand_in,
-                                               const double* omega, int* labels, double* dist2,
-                                               double* eps_terms, FlowOut fo, WarmStore ws,
-                                               int* err) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Grp<G> g;
-  const int gpb = blockDim.x / G;
-  unsigned char* base = smem + (threadIdx.x / G) * slice;
-  const PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax, cv.d);
-  int n_ex = 0, p_ex = 0;
-  const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
-  for (long long tt = (long long)blockIdx.x * gpb + threadIdx.x / G; tt < nobj;
-       tt += (long long)gridDim.x * gpb) {
-    const long long i = cfg.oidx ? (long long)cfg.oidx[tt] : cfg.obase + tt;
-    const long long o0 = ob.off[i];
-    const int m = (int)(ob.off[i + 1] - o0);
-    const long long cb = (i / seg_size) * (long long)K;
-    int best_j = -1;
-    double best = nan("");
-    int st = kStOk;
-    const int cnt = cand_in ? cand_in[i * kMergedInts] : -1;
-    const bool okm = m >= 1 && m <= cfg.mmax && cb + K <= cv.K && cnt != -2;
-    if (!okm || !load_obj_prefix<G>(g, ob, o0, m, s64.P)) {
-      st = kStInvalid;
-    } else {
-      const bool all = cnt < 0;
-      const int count = all ? K : cnt;
-      for (int c = 0; c < count; ++c) {
-        const int j = all ? c : cand_in[i * kMergedInts + 1 + c];
-        const long long c0 = cv.off[cb + j];
-        const int n = (int)(cv.off[cb + j + 1] - c0);
-        if (j < 0 || j >= K || n < 1 || n > cfg.nmax || m + n > G * NPL) { st = kStInvalid; break; }
-        double D;
-        Simplex<double, G, NPL> S(s64, m, n, g);
-        int s2;
-        if (ws.par8 && cand_in && !all) {
-          // the screen just saved this pair's FP32-optimal basis: continue in FP64
-          const long long wt = (i * (long long)K + j) * ws.ns;
-          load_cent_prefix<G>(g, cv, c0, n, s64.Q);
-          const double cmax = build_cost<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
-                                                    cv.loc64 + c0 * cv.d, cv.d);
-          S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
-          s2 = S.run(cfg.budget * (m + n), tol64(cmax), &p_ex);
-          D = S.template objective<double>();
-        } else {
-          s2 = solve_exact<G, NPL>(g, s64, S, ob, o0, m, cv, c0, n, cfg.budget, cfg.mode == 1, &D,
-                                   &p_ex);
-        }
-        ++n_ex;
-        if (s2 != kStOk) st = s2;
-        if (s2 == kStInvalid) break;
-        if (best_j < 0 || D < best) {
-          best = D;
-          best_j = j;
-          if (fo.cell) S.write_flows(fo.cell + i * fo.stride, fo.w + i * fo.stride, fo.stride);
-        }
-        g.sync();
-      }
-    }
-    if (g.lane == 0) {
-      labels[i] = st == kStInvalid ? -1 : best_j;
-      dist2[i] = st == kStInvalid ? nan("") : best;
-      if (eps_terms) eps_terms[i] = (omega ? omega[i] : 1.0) * dist2[i];
-      if (st == kStInvalid) atomicOr(err, kErrInvalid);
-      if (st == kStNotConverged) atomicOr(err, kErrNotConverged);
-    }
-    g.sync();
-  }
-  if (g.lane == 0) add_stats(0, 0, n_ex, p_ex);
 }
 
 __global__ void k_bin_of(const long long* off, long long count, int nmax, int* bins) {
@@ -778,11 +113,17 @@ static unsigned long long g_launches = 0;
 void note_launches(long long k) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
 long long launches() { return (long long)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
+// Sum of the solver counters of the units that hold the solver kernels.
 cudaError_t solver_stats(long long out[4]) {
-  unsigned long long v[4] = {0, 0, 0, 0};
-  cudaError_t e = cudaMemcpyFromSymbol(v, g_solver_stats, sizeof(v));
-  for (int i = 0; i < 4; ++i) out[i] = (long long)v[i];
-  return e;
+  cudaError_t (*const units[4])(long long*) = {stats_npl1, stats_npl2, stats_npl3, stats_npl4};
+  for (int i = 0; i < 4; ++i) out[i] = 0;
+  for (auto f : units) {
+    long long v[4];
+    const cudaError_t e = f(v);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < 4; ++i) out[i] += v[i];
+  }
+  return cudaSuccess;
 }
 
 int device_sms(int dev) {
@@ -807,135 +148,6 @@ cudaError_t prep_centroids(const void* loc, int ldt, const void* w, int wdt, con
   const long long blocks = (K + 3) / 4;
   k_prep_centroids<32><<<(unsigned)(blocks < 65535 ? blocks : 65535), 128, 0, st>>>(
       loc, ldt, w, wdt, off, K, d, loc32, loc64, Qpre, w64, d_err);
-  note_launches(1);
-  return cudaGetLastError();
-}
-
-// Groups per block: up to 128 threads, whole warps only, within the
-// 227 KB shared-memory limit of a block.  0 if one warp does not fit.
-static int groups_per_block(int G, size_t slice, int tpb = 128) {
-  const size_t limit = 227 * 1024;
-  const int per_warp = 32 / G;
-  int gpb = (tpb >= 32 && tpb <= 128 ? tpb : 128) / G;
-  while (gpb >= per_warp && (size_t)gpb * slice > limit) gpb -= per_warp;
-  return gpb >= per_warp ? gpb : 0;
-}
-
-template <typename KernelT>
-static cudaError_t launch_cfg(KernelT kern, size_t smem, int threads, int sms, long long work,
-                              int gpb, unsigned* grid) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  long long need = (work + gpb - 1) / gpb;
-  long long cap = (long long)per_sm * sms;
-  long long gsz = need < cap ? need : cap;
-  *grid = (unsigned)(gsz > 0 ? gsz : 1);
-  return cudaSuccess;
-}
-
-template <int G, int NPL>
-static cudaError_t mallows_pairs_g(const ObjView& ob, const CentView& cv, const long long* pobj,
-                                   const long long* pcen, long long npairs, const SolveCfg& cfg,
-                                   double* dist2, FlowOut fo, int* status, int* d_err,
-                                   cudaStream_t st) {
-  const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax, cv.d);
-  const int gpb = groups_per_block(G, slice);
-  if (gpb == 0) return cudaErrorInvalidConfiguration;
-  const size_t smem = slice * gpb;
-  unsigned grid = 1;
-  cudaError_t e = launch_cfg(k_mallows_pairs<G, NPL>, smem, gpb * G, cfg.sms, npairs, gpb, &grid);
-  if (e != cudaSuccess) return e;
-  k_mallows_pairs<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, pobj, pcen, npairs, cfg, slice,
-                                                            dist2, fo, status, d_err);
-  note_launches(1);
-  return cudaGetLastError();
-}
-
-template <int G, int NPL>
-static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg_size, int K,
-                            const SolveCfg& cfg, const double* omega, int* labels, double* dist2,
-                            double* eps_terms, FlowOut fo, int* cand, int* d_err, cudaStream_t st,
-                            const WarmStore* wsp, const TcWork* tw) {
-  WarmStore ws{nullptr, nullptr, nullptr, nullptr, 0, 0};
-  if (wsp) ws = *wsp;
-  const size_t slice = pair_mem_bytes(cfg.mmax, cfg.nmax, cv.d);
-  const int gpb = groups_per_block(G, slice, cfg.tpb);
-  if (gpb == 0) return cudaErrorInvalidConfiguration;
-  const size_t smem = slice * gpb;
-  unsigned grid = 1;
-  cudaError_t e;
-  const bool screen = cfg.mode == 1 && cand != nullptr;
-  const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
-  if (nobj <= 0) return cudaSuccess;
-  if (screen) {
-    // scratch layout: [queue counter: 4 ints][merged lists: count*kMergedInts][items]
-    unsigned long long* queue = reinterpret_cast<unsigned long long*>(cand);
-    int* merged = cand + 4;
-    int* items = merged + ((ob.count * kMergedInts + 3) & ~3LL);  // merged is indexed by object
-    // one screening launch over objects [t0, t0+cnt) of this launch
-    auto screen_part = [&](const SolveCfg& sc, long long cnt) -> cudaError_t {
-      // centroid blocks: enough (object, block) items to fill the GPU
-      const long long want = (long long)sc.sms * std::min(std::max(sc.ipsm, 8), 256);
-      int NB = (int)std::min<long long>(std::max<long long>(1, (want + cnt - 1) / cnt),
-                                        std::max(1, K / 8));
-      const int KB = (K + NB - 1) / NB;
-      NB = (K + KB - 1) / KB;
-      cudaError_t e2 = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
-      if (e2 != cudaSuccess) return e2;
-      unsigned g2 = 1;
-      if (sc.tile.C) {
-        e2 = launch_cfg(k_screen<G, NPL, true>, smem, gpb * G, sc.sms, cnt * (long long)NB, gpb, &g2);
-        if (e2 != cudaSuccess) return e2;
-        k_screen<G, NPL, true><<<g2, gpb * G, smem, st>>>(ob, cv, seg_size, K, KB, NB, sc, slice,
-                                                          items, queue, ws, d_err);
-      } else {
-        e2 = launch_cfg(k_screen<G, NPL, false>, smem, gpb * G, sc.sms, cnt * (long long)NB, gpb, &g2);
-        if (e2 != cudaSuccess) return e2;
-        k_screen<G, NPL, false><<<g2, gpb * G, smem, st>>>(ob, cv, seg_size, K, KB, NB, sc, slice,
-                                                           items, queue, ws, d_err);
-      }
-      const unsigned mb = (unsigned)std::min<long long>((cnt + 255) / 256, 4096);
-      k_merge<<<mb, 256, 0, st>>>(items, cnt, NB, sc.oidx, sc.obase, merged);
-      note_launches(2);
-      return cudaGetLastError();
-    };
-    if (tw && tw->C && cfg.mmax <= 64) {
-      // tensor-core tiles, chunk by chunk within the tile buffer
-      const long long per = std::max<long long>(1, tw->rows_cap / cfg.mmax);
-      for (long long t0 = 0; t0 < nobj; t0 += per) {
-        const long long cnt = std::min(per, nobj - t0);
-        SolveCfg sc = cfg;
-        sc.oidx = cfg.oidx ? cfg.oidx + t0 : nullptr;
-        sc.obase = cfg.oidx ? 0 : cfg.obase + t0;
-        sc.nobj = cnt;
-        e = tc_chunk(ob, *tw, sc.oidx, sc.obase, cnt, cfg.mmax, 0, -1, d_err, st);
-        if (e != cudaSuccess) return e;
-        sc.tile.C = tw->C;
-        sc.tile.trow = tw->trow;
-        sc.tile.nx = tw->nx;
-        sc.tile.cn = tw->cents.cn;
-        sc.tile.cd = tw->cents.cd;
-        sc.tile.ldc = tw->cents.ncols;
-        sc.tile.col0 = 0;
-        e = screen_part(sc, cnt);
-        if (e != cudaSuccess) return e;
-      }
-    } else {
-      e = screen_part(cfg, nobj);
-      if (e != cudaSuccess) return e;
-    }
-  }
-  e = launch_cfg(k_exact<G, NPL>, smem, gpb * G, cfg.sms, nobj, gpb, &grid);
-  if (e != cudaSuccess) return e;
-  WarmStore wx = ws;
-  if (!screen) wx.par8 = nullptr;
-  k_exact<G, NPL><<<grid, gpb * G, smem, st>>>(ob, cv, seg_size, K, cfg, slice,
-                                               screen ? cand + 4 : nullptr, omega, labels, dist2,
-                                               eps_terms, fo, wx, d_err);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -965,7 +177,7 @@ cudaError_t mallows_pairs(const ObjView& ob, const CentView& cv, const long long
   if (!pick_shape(cfg.mmax, cfg.nmax, cfg.group, &G, &NP)) return cudaErrorInvalidValue;
 #define X(g_, n_)                                                                          \
   if (G == g_ && NP == n_)                                                                \
-    return mallows_pairs_g<g_, n_>(ob, cv, pobj, pcen, npairs, cfg, dist2, fo, status, d_err, st);
+    return mallows_pairs_npl##n_(ob, cv, pobj, pcen, npairs, cfg, dist2, fo, status, d_err, st);
   D2_BINS(X)
 #undef X
   return cudaErrorInvalidValue;
@@ -980,7 +192,7 @@ cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, in
   if (!pick_shape(cfg.mmax, cfg.nmax, cfg.group, &G, &NP)) return cudaErrorInvalidValue;
 #define X(g_, n_)                                                                            \
   if (G == g_ && NP == n_)                                                                  \
-    return assign_g<g_, n_>(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, cand, d_err, st, ws, tw);
+    return assign_npl##n_(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, cand, d_err, st, ws, tw);
   D2_BINS(X)
 #undef X
   return cudaErrorInvalidValue;

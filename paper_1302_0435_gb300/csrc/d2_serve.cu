@@ -111,7 +111,7 @@ struct d2_server {
   d2_ctx* ctx = nullptr;
   int device = 0;
   d2k::CentView cv{};
-  int nmax = 0, d = 0, mode = 1, budget_pivots = 64, sms = 1;
+  int nmax = 0, d = 0, mode = 1, budget_pivots = 64, sms = 1, start = 0;
   long long K = 0;
   size_t mem_budget = 0, mem_inflight = 0;
   std::vector<Slot> slots;
@@ -172,6 +172,7 @@ bool d2_server::launch(Slot& s, const std::shared_ptr<Request>& r) {
   cfg.nmax = nmax;
   cfg.budget = budget_pivots;
   cfg.sms = sms;
+  cfg.start = start;
   d2k::FlowOut fo{nullptr, nullptr, 0};
   // bounded chunks, bin by bin (largest trees first); one stream, so the
   // chunks of a request run in order and share its scratch
@@ -278,7 +279,7 @@ void d2_server::run() {
 // The context's resident centroid set (read-only while a server runs).
 namespace d2k {
 CentView ctx_centroids(const d2_ctx* c, int* nmax, int* d, int* device, int* mode, int* budget,
-                       int* sms, long long* K);
+                       int* sms, long long* K, int* start);
 }
 
 extern "C" int d2_server_create(d2_server** out, d2_ctx* ctx, int32_t nslots, int64_t mem_budget) {
@@ -289,7 +290,7 @@ extern "C" int d2_server_create(d2_server** out, d2_ctx* ctx, int32_t nslots, in
   sv->ctx = ctx;
   int mode = 1;
   sv->cv = d2k::ctx_centroids(ctx, &sv->nmax, &sv->d, &sv->device, &mode, &sv->budget_pivots, &sv->sms,
-                              &sv->K);
+                              &sv->K, &sv->start);
   sv->mode = mode;
   if (sv->K == 0) {
     delete sv;

@@ -294,6 +294,233 @@ struct Simplex {
     return y < m ? key_rc(y, p - m) : key_rc(p, y - m);
   }
 
+  // ---- Vogel start --------------------------------------------------
+  // Smallest and second smallest alive cost of column r over the alive
+  // rows `ra` (ties to the smaller row), by this lane alone.
+  __device__ __forceinline__ void vogel_col_scan(int r, unsigned long long ra, T& v1, int& i1,
+                                                 T& v2, int& i2) const {
+    v1 = v2 = T(INFINITY);
+    i1 = i2 = -1;
+    for (unsigned long long b = ra; b; b &= b - 1) {
+      const int a = __ffsll((long long)b) - 1;
+      const T c = s.cost[a * n + r];
+      if (c < v1) { v2 = v1; i2 = i1; v1 = c; i1 = a; }
+      else if (c < v2) { v2 = c; i2 = a; }
+    }
+  }
+  // The same for row a over the alive columns `ca`, by the whole warp; every
+  // lane gets the result.
+  __device__ __forceinline__ void vogel_row_scan(int a, unsigned long long ca, T& v1, int& i1,
+                                                 T& v2, int& i2) const {
+    T b1 = T(INFINITY), b2 = T(INFINITY);
+    int j1 = INT_MAX, j2 = INT_MAX;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = g.lane + 32 * h;
+      if (r < n && ((ca >> r) & 1ull)) {
+        const T c = s.cost[a * n + r];
+        if (c < b1) { b2 = b1; j2 = j1; b1 = c; j1 = r; }
+        else if (c < b2) { b2 = c; j2 = r; }
+      }
+    }
+    // smallest (value, column) over the warp
+    T m1 = b1;
+    int k1 = j1;
+    gmin_val_key(m1, k1);
+    // second: the best entry other than (m1, k1): the owner offers its own
+    // second, everyone else their first
+    T o = (j1 == k1) ? b2 : b1;
+    int ko = (j1 == k1) ? j2 : j1;
+    gmin_val_key(o, ko);
+    v1 = m1; i1 = k1; v2 = o; i2 = (ko == INT_MAX) ? -1 : ko;
+  }
+  // Vogel's approximation: at every step the line (row or column) with the
+  // largest penalty -- the gap between its two smallest alive costs; ties to
+  // the smaller line, rows before columns -- gives its cheapest alive cell
+  // as much flow as both ends still hold; the end that runs out (the row on
+  // a tie) leaves.  Flows are the int64 masses, so the start is exactly
+  // feasible.  Tree: every removed line hangs from the other end of the cell
+  // that removed it, the last line standing is the root; sizes follow the
+  // removal order and preorder positions its reverse.  m, n <= 64, G = 32.
+  __device__ void init_vogel() {
+    static_assert(G == 32, "Vogel start: one warp per pair");
+    long long* mass = s.pflow;  // remaining mass of a line; its edge flow once removed
+    int* par = s.pj0;
+    int* ord = s.pj1;
+    int* szs = s.ppos;
+    int* poss = s.psz;
+    int* offs = s.pnode;
+    for (int y = g.lane; y < N; y += G) {
+      long long v;
+      if (y < m) v = s.P[y] - (y > 0 ? s.P[y - 1] : 0LL);
+      else {
+        const int r = y - m;
+        v = s.Q[r] - (r > 0 ? s.Q[r - 1] : 0LL);
+      }
+      mass[y] = v;
+      par[y] = -1;
+      szs[y] = 1;
+      offs[y] = 0;
+    }
+    unsigned long long ra = (m >= 64) ? ~0ull : ((1ull << m) - 1ull);
+    unsigned long long ca = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
+    // per-lane state of rows and columns lane, lane + 32
+    T rv1[2], rv2[2], cv1[2], cv2[2];
+    int ri1[2], ri2[2], ci1[2], ci2[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      rv1[h] = rv2[h] = cv1[h] = cv2[h] = T(INFINITY);
+      ri1[h] = ri2[h] = ci1[h] = ci2[h] = -1;
+      const int r = g.lane + 32 * h;
+      if (r < n) vogel_col_scan(r, ra, cv1[h], ci1[h], cv2[h], ci2[h]);
+    }
+    for (int a = 0; a < m; ++a) {
+      T v1, v2;
+      int i1, i2;
+      vogel_row_scan(a, ca, v1, i1, v2, i2);
+      if ((a & 31) == g.lane) {
+        const int h = a >> 5;
+        rv1[h] = v1; ri1[h] = i1; rv2[h] = v2; ri2[h] = i2;
+      }
+    }
+    g.sync();
+    int tcount = 0;
+    int guard = 0;
+    while (__popcll(ra) > 1 && __popcll(ca) > 1) {
+      if (++guard > 2 * 128) { bad = true; break; }
+      // the largest penalty (float keys: larger gap -> larger key)
+      unsigned best = 0u;
+      int bline = INT_MAX;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int a = g.lane + 32 * h;
+        if (a < m && ((ra >> a) & 1ull)) {
+          const unsigned k = __float_as_uint((float)(rv2[h] - rv1[h]));
+          if (k > best || (k == best && a < bline)) { best = k; bline = a; }
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = g.lane + 32 * h;
+        if (r < n && ((ca >> r) & 1ull)) {
+          const unsigned k = __float_as_uint((float)(cv2[h] - cv1[h]));
+          if (k > best || (k == best && m + r < bline)) { best = k; bline = m + r; }
+        }
+      }
+      const unsigned wbest = __reduce_max_sync(g.mask, best);
+      const int L = (int)__reduce_min_sync(g.mask, best == wbest ? (unsigned)bline : 0xffffffffu);
+      // its cheapest alive cell, from the owner lane
+      int a, r;
+      if (L < m) {
+        a = L;
+        const int h = a >> 5;
+        r = __shfl_sync(g.mask, h ? ri1[1] : ri1[0], a & 31);
+      } else {
+        r = L - m;
+        const int h = r >> 5;
+        a = __shfl_sync(g.mask, h ? ci1[1] : ci1[0], r & 31);
+      }
+      if (a < 0 || r < 0) { bad = true; break; }
+      const long long ma = mass[a], mr = mass[m + r];
+      const bool row_leaves = ma <= mr;
+      const long long f = row_leaves ? ma : mr;
+      g.sync();
+      if (g.lane == 0) {
+        if (row_leaves) { mass[m + r] = mr - f; par[a] = m + r; ord[tcount] = a; }
+        else { mass[a] = ma - f; par[m + r] = a; ord[tcount] = m + r; }
+      }
+      ++tcount;
+      if (row_leaves) {
+        ra &= ~(1ull << a);
+        // columns whose two smallest included row a
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = g.lane + 32 * h;
+          if (c < n && ((ca >> c) & 1ull) && (ci1[h] == a || ci2[h] == a))
+            vogel_col_scan(c, ra, cv1[h], ci1[h], cv2[h], ci2[h]);
+        }
+      } else {
+        ca &= ~(1ull << r);
+        // rows whose two smallest included column r, one warp-wide rescan each
+        unsigned long long hit = 0ull;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int b = g.lane + 32 * h;
+          const bool p = b < m && ((ra >> b) & 1ull) && (ri1[h] == r || ri2[h] == r);
+          hit |= (unsigned long long)__ballot_sync(g.mask, p) << (32 * h);
+        }
+        for (; hit; hit &= hit - 1) {
+          const int b = __ffsll((long long)hit) - 1;
+          T v1, v2;
+          int i1, i2;
+          vogel_row_scan(b, ca, v1, i1, v2, i2);
+          if ((b & 31) == g.lane) {
+            const int h = b >> 5;
+            rv1[h] = v1; ri1[h] = i1; rv2[h] = v2; ri2[h] = i2;
+          }
+        }
+      }
+      g.sync();
+    }
+    // one line of one kind is left: it takes all remaining cells and is the root
+    int rt;
+    if (__popcll(ra) == 1) {
+      rt = __ffsll((long long)ra) - 1;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = g.lane + 32 * h;
+        if (c < n && ((ca >> c) & 1ull)) {
+          par[m + c] = rt;
+          ord[tcount + __popcll(ca & ((1ull << c) - 1ull))] = m + c;
+        }
+      }
+      tcount += __popcll(ca);
+    } else {
+      rt = m + __ffsll((long long)ca) - 1;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int b = g.lane + 32 * h;
+        if (b < m && ((ra >> b) & 1ull)) {
+          par[b] = rt;
+          ord[tcount + __popcll(ra & ((1ull << b) - 1ull))] = b;
+        }
+      }
+      tcount += __popcll(ra);
+    }
+    if (tcount != N - 1 || __popcll(ra) < 1 || __popcll(ca) < 1) bad = true;
+    g.sync();
+    if (!bad && g.lane == 0) {
+      // subtree sizes: children leave before their parents
+      for (int q = 0; q < N - 1; ++q) {
+        const int y = ord[q];
+        szs[par[y]] += szs[y];
+      }
+      // preorder positions: parents are placed before their children
+      poss[rt] = 0;
+      for (int q = N - 2; q >= 0; --q) {
+        const int y = ord[q];
+        const int p = par[y];
+        poss[y] = poss[p] + 1 + offs[p];
+        offs[p] += szs[y];
+      }
+    }
+    g.sync();
+    root = rt;
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y < N) {
+        t.par[k] = (y == rt) ? -1 : par[y];
+        t.pos[k] = poss[y];
+        t.sz[k] = szs[y];
+        t.flow[k] = (y == rt) ? 0LL : mass[y];
+        s.pos[y] = t.pos[k];
+        s.sz[y] = t.sz[k];
+      }
+    }
+    g.sync();
+  }
+
   // Northwest-corner basis: the staircase path from cell (0,0) to (m-1,n-1)
   // that moves down when the current row's cumulative mass is reached
   // (P_a <= Q_r), else right.  Row a spans columns [re(a-1), re(a)] with

@@ -18,6 +18,7 @@ D2_ETIMEOUT, D2_ECUDA, D2_EUNSUPPORTED, D2_ENOCENTROIDS = -4, -5, -6, -7
 D2_F64, D2_F32, D2_BF16 = 0, 1, 2
 D2_PREC_AUTO, D2_PREC_FP64, D2_PREC_FP32, D2_PREC_TC = 0, 1, 2, 3
 D2_TC_AUTO, D2_TC_OFF, D2_TC_ON = 0, 1, 2
+D2_START_AUTO, D2_START_RANKED, D2_START_VOGEL = 0, 1, 2
 MAX_SUPPORT = 64
 
 EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_strerror",
@@ -36,7 +37,8 @@ class D2Bags(ctypes.Structure):
 class D2Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("pivot_budget", ctypes.c_int32),
                 ("group_lanes", ctypes.c_int32), ("cost_tc", ctypes.c_int32),
-                ("tile_budget_mib", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("tile_budget_mib", ctypes.c_int32), ("start_rule", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class D2Flows(ctypes.Structure):
@@ -162,10 +164,10 @@ class Context:
     """d2_ctx_create / d2_ctx_destroy."""
 
     def __init__(self, device=0, precision=D2_PREC_AUTO, pivot_budget=0, group_lanes=0,
-                 cost_tc=D2_TC_AUTO, tile_budget_mib=0):
+                 cost_tc=D2_TC_AUTO, tile_budget_mib=0, start_rule=D2_START_AUTO):
         lib = load()
         self.h = ctypes.c_void_p()
-        cfg = D2Config(precision, pivot_budget, group_lanes, cost_tc, tile_budget_mib)
+        cfg = D2Config(precision, pivot_budget, group_lanes, cost_tc, tile_budget_mib, start_rule)
         _check(lib.d2_ctx_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)), "d2_ctx_create")
         self._cents = None
 

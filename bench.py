@@ -392,7 +392,7 @@ def run_ours(args):
     return 0
 
 
-def serve_measure(dev, n_requests=60, lam_fracs=(0.8,), n_sat=24, seed=1005):
+def serve_measure(dev, n_requests=150, lam_fracs=(0.8,), n_sat=24, seed=1005):
     """Serving workload: Poisson arrivals of assignment requests (log-uniform
     1-4096 bags of 4-64 supports, d=32) against K=1024 resident centroids of
     32 supports, through the continuous-batching server.  Saturated

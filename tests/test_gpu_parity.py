@@ -45,9 +45,9 @@ def rand_pairs(rng, count, mrange, d, alpha=1.0, spread=2.0):
     return out
 
 
-def gpu_pairs(d2, objs, cents, pi, pj, precision=0, group=0, flows=False):
+def gpu_pairs(d2, objs, cents, pi, pj, precision=0, group=0, flows=False, start_rule=0):
     import torch
-    ctx = d2.Context(0, precision=precision, group_lanes=group)
+    ctx = d2.Context(0, precision=precision, group_lanes=group, start_rule=start_rule)
     d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
     ob = d2.bags_from_synth(objs, device="cuda:0")
     po = torch.as_tensor(np.asarray(pi, dtype=np.int64), device="cuda:0")
@@ -348,3 +348,99 @@ def test_binned_autotuned_assign_is_bitwise_unbinned(d2, oracle_mod):
     _check_assign(oracle_mod, sub, cents, big["labels"][idx], big["dist2"][idx])
     big["ctx"].close()
     small["ctx"].close()
+
+
+# ---- cold-start rules on trees of more than one node per lane (m+n > 32) ----
+
+@pytest.mark.parametrize("rule", ["ranked", "vogel"])
+def test_mallows_start_rules_large(d2, oracle_mod, rule):
+    rng = np.random.default_rng(77 if rule == "vogel" else 78)
+    objs_l = rand_pairs(rng, 24, (20, 65), 6, alpha=0.7)
+    cents_l = rand_pairs(rng, 6, (20, 65), 6)
+    objs = make_bags(objs_l, np.float32, np.float32)
+    cents = make_bags(cents_l, np.float32, np.float32)
+    pi, pj = all_pairs(objs.count, cents.count)
+    r = d2.D2_START_VOGEL if rule == "vogel" else d2.D2_START_RANKED
+    got, st, rc, (cell, w) = gpu_pairs(d2, objs, cents, pi, pj, precision=2, flows=True,
+                                       start_rule=r)
+    assert rc == 0 and (st == 0).all()
+    ref = oracle_mod.mallows_pairs(objs, cents, pi, pj, nthreads=8)
+    assert_d2_close(got, ref)
+    _check_plans(oracle_mod, objs, cents, pi, pj, cell, w, ref)
+
+
+def _lattice_pairs(rng, count, mrange, d):
+    """Integer-lattice supports (many equal costs), weights with equal, zero
+    and repeated entries (many equal partial sums and degenerate bases)."""
+    out = []
+    for t in range(count):
+        m = int(rng.integers(*mrange))
+        x = rng.integers(0, 3, size=(m, d)).astype(np.float64)
+        kind = t % 3
+        if kind == 0:
+            w = np.full(m, 1.0 / m)
+        elif kind == 1:
+            w = rng.integers(0, 3, size=m).astype(np.float64)
+            if w.sum() == 0:
+                w[0] = 1.0
+        else:
+            w = np.repeat(rng.dirichlet(np.ones((m + 1) // 2)), 2)[:m]
+        out.append((x, w))
+    return out
+
+
+def test_vogel_degenerate_lattices(d2, oracle_mod):
+    rng = np.random.default_rng(79)
+    objs = make_bags(_lattice_pairs(rng, 18, (30, 65), 2), np.float32, np.float32)
+    cents = make_bags(_lattice_pairs(rng, 6, (30, 65), 2), np.float32, np.float32)
+    pi, pj = all_pairs(objs.count, cents.count)
+    got, st, rc, (cell, w) = gpu_pairs(d2, objs, cents, pi, pj, precision=2, flows=True,
+                                       start_rule=d2.D2_START_VOGEL)
+    assert rc == 0 and (st == 0).all()
+    ref = oracle_mod.mallows_pairs(objs, cents, pi, pj, nthreads=8)
+    assert_d2_close(got, ref)
+    _check_plans(oracle_mod, objs, cents, pi, pj, cell, w, ref)
+
+
+def _check_plans(oracle_mod, objs, cents, pi, pj, cell, w, ref):
+    """Each returned plan meets both marginals within 1e-12 and costs D^2."""
+    for t in range(len(pi)):
+        x, p = oracle_mod.bag(objs, int(pi[t]))
+        y, q = oracle_mod.bag(cents, int(pj[t]))
+        p = p / p.sum()
+        q = q / q.sum()
+        ok = cell[t] >= 0
+        a = cell[t][ok] >> 16
+        r = cell[t][ok] & 0xFFFF
+        f = w[t][ok]
+        assert (f >= -1e-15).all()
+        assert np.abs(np.bincount(a, weights=f, minlength=len(p)) - p).max() <= 1e-12
+        assert np.abs(np.bincount(r, weights=f, minlength=len(q)) - q).max() <= 1e-12
+        c = np.sum((x[a] - y[r]) ** 2, axis=1)
+        assert abs(float(np.dot(f, c)) - ref[t]) <= 1e-9 * max(ref[t], 1e-12)
+
+
+def test_assign_start_rules_agree(d2, oracle_mod):
+    """The screen's cold start changes the path, not the answer."""
+    import torch
+    objs, cents = synth.uneven(N=3000, K=24, seed=1203)
+    out = {}
+    for rule in (d2.D2_START_RANKED, d2.D2_START_VOGEL):
+        ctx = d2.Context(0, start_rule=rule)
+        d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
+        ob = d2.bags_from_synth(objs, device="cuda:0")
+        lab = torch.empty(objs.count, dtype=torch.int32, device="cuda:0")
+        dist = torch.empty(objs.count, dtype=torch.float64, device="cuda:0")
+        assert d2.d2_assign(ctx, ob, lab, dist) == d2.D2_OK
+        d2.d2_sync(ctx)
+        out[rule] = (lab.cpu().numpy(), dist.cpu().numpy())
+        ctx.close()
+    (la, da), (lb, db) = out[d2.D2_START_RANKED], out[d2.D2_START_VOGEL]
+    for i in np.nonzero(la != lb)[0]:
+        assert abs(da[i] - db[i]) <= TIE * max(da[i], db[i])
+    assert np.allclose(da, db, rtol=1e-12, atol=0)
+    idx = np.sort(np.random.default_rng(3).choice(objs.count, size=40, replace=False))
+    big = np.argsort(-objs.sizes(), kind="stable")[:8]
+    idx = np.unique(np.concatenate([idx, big]))
+    lo, do_ = oracle_mod.assign(objs.subset(idx), cents, nthreads=8)
+    assert_d2_close(db[idx], do_)

@@ -838,14 +838,24 @@ struct Simplex {
     return c == INT_MAX ? -1 : c;
   }
 
-  // Entering cell: first the lanes' candidates from the last full scan are
-  // re-priced with the current potentials (one cell per lane); only when
-  // none is below -tol is the whole tile scanned again.  Returns the cell
-  // key ((row << 8) | col) or -1 if no reduced cost is below -tol.
+  // Entering cell: on trees of one node per lane, the most negative reduced
+  // cost of the whole tile; otherwise the lanes' candidates from the last
+  // full scan are first re-priced with the current potentials (one cell per
+  // lane), and only when none is below -tol is the whole tile scanned again.
+  // Returns the cell key ((row << 8) | col) or -1 if no reduced cost is
+  // below -tol.
   __device__ __forceinline__ int price(bool bland, T tol, T& dbest) {
     if (bland) return price_bland(tol, dbest);
     T best = T(0);
     int cell = INT_MAX;
+    if constexpr (NPL == 1) {
+      // small tiles (at most 8 cells per lane at 16 x 16): the full Dantzig
+      // scan every pivot costs less than the pivots a candidate list adds
+      scan_full(best, cell);
+      gmin_val_key(best, cell);
+      dbest = best;
+      return (best < -tol && cell != INT_MAX) ? cell : -1;
+    }
     if (cand >= 0) {
       best = s.cost[cand] - s.pot[cand_a] - s.pot[m + cand_r];
       cell = key_rc(cand_a, cand_r);

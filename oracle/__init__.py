@@ -297,7 +297,89 @@ def _slice_bags(b, lo, hi):
     return _Bags(np.asarray(b.loc[s:e]), np.asarray(b.w[s:e]), o[lo:hi + 1] - s)
 
 
-def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, nthreads=1):
+def _take_bags(b, idx):
+    """Bags idx of b (in the given order), repacked."""
+    o = np.asarray(b.off, dtype=np.int64)
+    idx = np.asarray(idx, dtype=np.int64)
+    rows = [np.arange(o[i], o[i + 1]) for i in idx]
+    rows = np.concatenate(rows) if rows else np.zeros(0, dtype=np.int64)
+    sizes = o[idx + 1] - o[idx]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return _Bags(np.asarray(b.loc)[rows], np.asarray(b.w)[rows], off)
+
+
+def _uniform_bag(b, i):
+    """Bag i of b as a centroid of the constrained form: its supports with
+    uniform weights 1/s (Alg. 2 Step 3*)."""
+    x, _ = bag(b, i)
+    return _Bags(x.copy(), np.full(len(x), 1.0 / len(x)), np.array([0, len(x)], dtype=np.int64))
+
+
+def _join_bags(parts):
+    locs = np.concatenate([np.asarray(p.loc, dtype=np.float64).reshape(len(p.w), -1) for p in parts])
+    ws = np.concatenate([np.asarray(p.w, dtype=np.float64) for p in parts])
+    offs = np.concatenate([[0], np.cumsum([len(p.w) for p in parts])]).astype(np.int64)
+    return _Bags(locs, ws, offs)
+
+
+def split_binary(objs, omega, members, iters, nthreads=1):
+    """One binary split of the initial data segmentation (Alg. 3 Step 1, the
+    constrained D2-clustering of Alg. 2 with Step 3* and k = 2).
+
+    Start: z_1 is the first member's bag and z_2 the member's bag with the
+    largest D^2 to z_1 (ties to the earlier member), both with uniform
+    weights.  Then assign (Alg. 2 Step 2); up to `iters` times update the
+    locations with the weights held fixed (Eq. (WeightedUpdate)) and assign
+    again, stopping early when the labels repeat.  Returns the members
+    labelled 0 and 1; if one side is empty, the first and second halves.
+    """
+    members = np.asarray(members, dtype=np.int64)
+    sub = _take_bags(objs, members)
+    om = np.ones(len(members)) if omega is None else _f64(omega)[members]
+    z1 = _uniform_bag(sub, 0)
+    _, d1 = assign(sub, z1, nthreads=nthreads)
+    i2 = int(np.argmax(d1))  # first index of the largest value
+    cents = _join_bags([z1, _uniform_bag(sub, i2)])
+    lab, _ = assign(sub, cents, nthreads=nthreads)
+    for _ in range(int(iters)):
+        fo, fa, fr, fw = assigned_flows(sub, cents, lab)
+        cents = _Bags(update_locations(sub, om, lab, fo, fa, fr, fw, cents), cents.w, cents.off)
+        new, _ = assign(sub, cents, nthreads=nthreads)
+        if np.array_equal(new, lab):
+            break
+        lab = new
+    a, b = members[lab == 0], members[lab == 1]
+    if len(a) == 0 or len(b) == 0:
+        h = len(members) // 2
+        a, b = members[:h], members[h:]
+    return a, b
+
+
+def segment(objs, omega, tau, iters, nthreads=1):
+    """Initial data segmentation of Alg. 3 Step 1: repeatedly split the
+    segment holding the most objects (ties: the one created first) into two
+    with split_binary, until no segment holds more than tau objects.  A split
+    keeps the first part in the parent's place and appends the second.
+    Returns (segment id per object [N] int64, number of segments); segments
+    are numbered in increasing order of their smallest member."""
+    N = len(objs.off) - 1
+    segs = [np.arange(N, dtype=np.int64)]
+    while True:
+        big = max(range(len(segs)), key=lambda k: (len(segs[k]), -k))
+        if len(segs[big]) <= tau:
+            break
+        a, b = split_binary(objs, omega, segs[big], iters, nthreads=nthreads)
+        segs[big] = a
+        segs.append(b)
+    order = sorted(range(len(segs)), key=lambda k: int(segs[k][0]))
+    seg_id = np.empty(N, dtype=np.int64)
+    for new_id, k in enumerate(order):
+        seg_id[segs[k]] = new_id
+    return seg_id, len(segs)
+
+
+def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, nthreads=1,
+                  segmentation="slices", split_iters=10):
     """Alg. 3 level loop with the segment-wise weighted D2-clustering of
     Alg. 2 (constrained update, Step 3*) inside each segment.
 
@@ -310,6 +392,10 @@ def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, n
     Stops after the level that fits in one segment.  After each update the
     locations are rounded to loc_round (e.g. np.float32) when given, so that
     every level's data keep the input location precision.
+    segmentation="constrained" forms each level's segments with the binary
+    constrained D2 splits of Alg. 3 Step 1 (segment(), split_iters rounds per
+    split) instead of contiguous slices; segment mu's labels are offset by
+    mu*K (Eq. (UpdateLabel) with its index list L_mu).
 
     Returns (centroid locations [K*n, d] float64, centroid weights [K],
     labels [N] int64)."""
@@ -322,12 +408,16 @@ def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, n
     C = np.arange(N0, dtype=np.int64)
     while True:
         n_l = len(data.off) - 1
-        M = 1 if n_l <= seg_size else int(math.ceil(n_l / seg_size))
+        if segmentation == "constrained" and n_l > seg_size:
+            seg_id, M = segment(data, om, seg_size, split_iters, nthreads=nthreads)
+            members = [np.nonzero(seg_id == mu)[0] for mu in range(M)]
+        else:
+            M = 1 if n_l <= seg_size else int(math.ceil(n_l / seg_size))
+            members = [np.arange(mu * seg_size, min((mu + 1) * seg_size, n_l)) for mu in range(M)]
         seg_labels, seg_cents = [], []
         for mu in range(M):
-            lo, hi = mu * seg_size, min((mu + 1) * seg_size, n_l)
-            seg = _slice_bags(data, lo, hi)
-            om_seg = om[lo:hi]
+            seg = _take_bags(data, members[mu])
+            om_seg = om[members[mu]]
             cents = _Bags(_f64(init_cents.loc).copy(), _f64(init_cents.w).copy(),
                           _i64(init_cents.off).copy())
             lab = None
@@ -342,7 +432,9 @@ def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, n
                 lab, _ = assign(seg, cents, nthreads=nthreads)
             seg_labels.append(lab)
             seg_cents.append(cents)
-        C_tilde = np.concatenate(update_label(seg_labels, [K] * M))
+        C_tilde = np.empty(n_l, dtype=np.int64)
+        for mu, lab_mu in zip(range(M), update_label(seg_labels, [K] * M)):
+            C_tilde[members[mu]] = lab_mu
         C = update_global_label(C, C_tilde)
         w_new = propagate_weights(C_tilde, om, M * K)
         if M == 1:

@@ -85,6 +85,10 @@ extern "C" {
 #define D2_START_RANKED 1  /* northwest staircase in principal-direction order */
 #define D2_START_VOGEL 2   /* Vogel's approximation (largest-penalty line first) */
 
+/* segments of d2_cluster_level (d2_config.segmentation) */
+#define D2_SEG_SLICES 0       /* contiguous slices of seg_size objects */
+#define D2_SEG_CONSTRAINED 1  /* the binary constrained D2 splits of d2_segment */
+
 /* Limits of the current kernels. */
 #define D2_MAX_SUPPORT 64   /* supports per bag (objects and centroids) */
 #define D2_MAX_DIM 256      /* vector dimension d */
@@ -116,7 +120,9 @@ typedef struct {
     int32_t tile_budget_mib;    /* device memory for tensor-core cost tiles;
                                    0 = min(32 GiB, 40% of free memory) */
     int32_t start_rule;         /* D2_START_* ; 0 = AUTO */
-    int32_t reserved[2];
+    int32_t segmentation;       /* D2_SEG_* : how d2_cluster_level forms segments */
+    int32_t split_iters;        /* update rounds per binary split of D2_SEG_CONSTRAINED;
+                                   0 = 10 */
 } d2_config;
 
 /*
@@ -216,6 +222,23 @@ int d2_assign(d2_ctx* ctx, const d2_bags* objs, const double* omega, int32_t* la
  */
 int d2_update_locations(d2_ctx* ctx, const d2_bags* objs, const double* omega,
                         const int32_t* labels, const d2_flows* flows);
+
+/*
+ * Initial data segmentation (Alg. 3 Step 1): split the bags into segments of
+ * at most tau bags by repeated binary splits of the largest segment (ties:
+ * the one formed first).  A split is a constrained D2-clustering with k = 2
+ * (Alg. 2 with Step 3*): start centroids are the segment's first bag and
+ * the bag with the largest D^2 to it (ties: the first), both with uniform
+ * weights; then assign, and up to `iters` times update the locations with
+ * the weights held fixed (Eq. (WeightedUpdate) with omega, NULL = 1) and
+ * assign again, stopping when the labels repeat.  The first part keeps the
+ * parent's place; a split with an empty side halves the segment instead.
+ * seg_id [count] (host or device) receives the segment of every bag,
+ * segments numbered by their smallest bag; *n_segments their number.
+ * Needs no resident centroids.
+ */
+int d2_segment(d2_ctx* ctx, const d2_bags* objs, const double* omega, int64_t tau,
+               int32_t iters, int32_t* seg_id, int64_t* n_segments);
 
 /*
  * One hierarchical clustering job in the manner of Alg. 3 on one GPU:

@@ -30,6 +30,9 @@ enum Slot {
   kLvDataLoc, kLvDataW, kLvDataOff, kLvOmega, kLvOmegaNew, kLvC, kLvCT, kLvLab, kLvD2,
   kLvCLoc32, kLvCLoc64, kLvCQ, kLvCW, kLvCOff, kLvTmp, kCand, kWarmMeta, kWarmFlow, kBins,
   kBinSort, kTuneLab, kTuneD2, kTcTile, kTcRow, kTcSrc, kTcNx, kTcDel,
+  // initial data segmentation
+  kSgMem, kSgOff, kSgLoc, kSgW, kSgOm, kSgCLoc, kSgCW, kSgCOff, kSgC32, kSgC64, kSgCQ, kSgCW64,
+  kSgLab, kSgD2, kSgCell, kSgFw, kSgUpd, kSgCand, kSgOut, kLvSegof,
   kSlots
 };
 
@@ -295,10 +298,11 @@ __global__ void k_replicate(const float* l32, const double* l64, const long long
 }
 
 // C~ = label + segment*K (Eq. (UpdateLabel)); C = C~[C] (Eq. (UpdateGlobalLabel))
-__global__ void k_merge_labels(const int* lab, long long n_l, long long seg, int K, int* ct) {
+__global__ void k_merge_labels(const int* lab, long long n_l, long long seg, const int* segof,
+                               int K, int* ct) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_l;
        i += (long long)gridDim.x * blockDim.x)
-    ct[i] = lab[i] < 0 ? -1 : (int)((i / seg) * K + lab[i]);
+    ct[i] = lab[i] < 0 ? -1 : (int)((segof ? (long long)segof[i] : i / seg) * K + lab[i]);
 }
 __global__ void k_compose(int* C, long long N, const int* ct) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -335,7 +339,9 @@ int make_bins(d2_ctx* c, const ObjView& v, int nmax, Bins* b) {
   if (rc != D2_OK) return rc;
   CK(d2k::bin_objects(v, nmax, bins, c->stream));
   d2k::FlowOut none{nullptr, nullptr, 0};
-  CK(d2k::update_locations(v, nullptr, bins, N, 4, none, 4, nullptr, v.d, 0, nullptr, nullptr, scr,
+  ObjView flat = v;  // the bin sort is one group of 4 labels, whatever the segments
+  flat.segof = nullptr;
+  CK(d2k::update_locations(flat, nullptr, bins, N, 4, none, 4, nullptr, v.d, 0, nullptr, nullptr, scr,
                            c->stream));
   // scratch layout of the sort: counts | tot | start | order | ...
   const long long nchunks = (N + 1023) / 1024;
@@ -491,6 +497,131 @@ int tc_work(d2_ctx* c, long long rows, int mmax, d2k::TcWork* w) {
   w->nx = static_cast<float*>(grow(c, kTcNx, (size_t)cap * 4, &rc));
   if (rc != D2_OK) return rc;
   w->rows_cap = cap;
+  return D2_OK;
+}
+
+// Initial data segmentation of Alg. 3 Step 1 on the device view v (see
+// d2_segment in d2.h): largest-first binary splits, each a constrained
+// D2-clustering with k = 2 (farthest-bag start, uniform centroid weights held
+// fixed, at most `iters` update rounds, early stop when the labels repeat).
+// Writes the segment of every object to segof (device, [v.count]); segments
+// are numbered by their smallest member.
+int segment_impl(d2_ctx* c, const ObjView& v, int mmax, const double* om, long long tau, int iters,
+                 int* segof, long long* M_out) {
+  const long long N = v.count;
+  int rc = D2_OK;
+  const size_t lsz = esize(v.ldt), wsz = esize(v.wdt);
+  const long long rows_cap = N * (long long)mmax;
+  const long long stride = 2LL * mmax - 1;
+  int* dmem = static_cast<int*>(grow(c, kSgMem, (size_t)N * 4, &rc));
+  long long* soff = static_cast<long long*>(grow(c, kSgOff, (size_t)(N + 1) * 8, &rc));
+  void* sloc = grow(c, kSgLoc, (size_t)rows_cap * v.d * lsz, &rc);
+  void* sw = grow(c, kSgW, (size_t)rows_cap * wsz, &rc);
+  double* som = static_cast<double*>(grow(c, kSgOm, (size_t)N * 8, &rc));
+  double* zloc = static_cast<double*>(grow(c, kSgCLoc, (size_t)2 * mmax * v.d * 8, &rc));
+  double* zw = static_cast<double*>(grow(c, kSgCW, (size_t)2 * mmax * 8, &rc));
+  long long* zoff = static_cast<long long*>(grow(c, kSgCOff, 3 * 8, &rc));
+  float* z32 = static_cast<float*>(grow(c, kSgC32, (size_t)2 * mmax * v.d * 4, &rc));
+  double* z64 = static_cast<double*>(grow(c, kSgC64, (size_t)2 * mmax * v.d * 8, &rc));
+  long long* zQ = static_cast<long long*>(grow(c, kSgCQ, (size_t)2 * mmax * 8, &rc));
+  double* zw64 = static_cast<double*>(grow(c, kSgCW64, (size_t)2 * mmax * 8, &rc));
+  int* lab = static_cast<int*>(grow(c, kSgLab, (size_t)N * 4, &rc));
+  double* dd = static_cast<double*>(grow(c, kSgD2, (size_t)N * 8, &rc));
+  int* fcell = static_cast<int*>(grow(c, kSgCell, (size_t)(N * stride) * 4, &rc));
+  double* fw = static_cast<double*>(grow(c, kSgFw, (size_t)(N * stride) * 8, &rc));
+  void* uscr = grow(c, kSgUpd, d2k::update_scratch_bytes(N, 2), &rc);
+  int* cand = static_cast<int*>(grow(c, kSgCand, (size_t)d2k::assign_scratch_ints(N, 2, c->sms) * 4, &rc));
+  if (rc != D2_OK) return rc;
+  SolveCfg cfg = solve_cfg(c, mode_for(c, v.ldt), mmax);
+  cfg.nmax = mmax;  // the split centroids are bags of the data
+  cfg.start = c->cfg.start_rule == D2_START_VOGEL ? 1
+            : c->cfg.start_rule == D2_START_RANKED ? 0 : (mmax >= 64 ? 1 : 0);
+  const FlowOut fo{fcell, fw, stride};
+  std::vector<std::vector<int>> segs(1, std::vector<int>((size_t)N));
+  for (long long i = 0; i < N; ++i) segs[0][(size_t)i] = (int)i;
+  std::vector<double> hd;
+  std::vector<int> hl, hl2;
+  auto check = [&]() -> int {
+    int bits = 0;
+    int r = read_err(c, &bits);
+    if (r != D2_OK) return r;
+    if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
+    if (bits & d2k::kErrInvalid) return D2_EINVAL;
+    if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
+    return D2_OK;
+  };
+  for (;;) {
+    size_t big = 0;
+    for (size_t k = 1; k < segs.size(); ++k)
+      if (segs[k].size() > segs[big].size()) big = k;
+    if ((long long)segs[big].size() <= tau) break;
+    if ((long long)segs.size() > N) return D2_EINVAL;  // every split makes progress
+    const std::vector<int> S = segs[big];
+    const long long cnt = (long long)S.size();
+    CK(cudaMemcpyAsync(dmem, S.data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(d2k::seg_gather(v, dmem, cnt, om, soff, sloc, sw, som, c->stream));
+    ObjView sub;
+    sub.loc = sloc;
+    sub.w = sw;
+    sub.off = soff;
+    sub.count = cnt;
+    sub.d = v.d;
+    sub.ldt = v.ldt;
+    sub.wdt = v.wdt;
+    auto set_cents = [&](int i0, int i1, int K) -> int {
+      CK(d2k::seg_cents(sub, i0, i1, K, zloc, zw, zoff, c->stream));
+      CK(d2k::prep_centroids(zloc, D2_F64, zw, D2_F64, zoff, K, v.d, z32, z64, zQ, zw64, c->d_err,
+                             c->stream));
+      return D2_OK;
+    };
+    auto solve = [&](int K) -> int {
+      const CentView zc{z32, z64, zQ, zoff, K, v.d};
+      CK(d2k::assign(sub, zc, cnt, K, cfg, nullptr, lab, dd, nullptr, fo, cand, c->d_err,
+                     c->stream));
+      return check();
+    };
+    auto labels_to = [&](std::vector<int>& h) -> int {
+      h.resize((size_t)cnt);
+      CK(cudaMemcpyAsync(h.data(), lab, (size_t)cnt * 4, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      return D2_OK;
+    };
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    // start: the first member, then the member farthest from it
+    if ((rc = set_cents(0, 0, 1)) || (rc = solve(1))) return rc;
+    hd.resize((size_t)cnt);
+    CK(cudaMemcpyAsync(hd.data(), dd, (size_t)cnt * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int i2 = 0;
+    for (long long t = 1; t < cnt; ++t)
+      if (hd[(size_t)t] > hd[(size_t)i2]) i2 = (int)t;
+    if ((rc = set_cents(0, i2, 2)) || (rc = solve(2)) || (rc = labels_to(hl))) return rc;
+    for (int r = 0; r < iters; ++r) {
+      CK(d2k::update_locations(sub, som, lab, cnt, 2, fo, 2, zoff, v.d, D2_F64, z32, z64, uscr,
+                               c->stream));
+      if ((rc = solve(2)) || (rc = labels_to(hl2))) return rc;
+      if (hl2 == hl) break;
+      hl.swap(hl2);
+    }
+    std::vector<int> a, b;
+    for (long long t = 0; t < cnt; ++t) (hl[(size_t)t] == 0 ? a : b).push_back(S[(size_t)t]);
+    if (a.empty() || b.empty()) {
+      const long long h = cnt / 2;
+      a.assign(S.begin(), S.begin() + h);
+      b.assign(S.begin() + h, S.end());
+    }
+    segs[big] = std::move(a);
+    segs.push_back(std::move(b));
+  }
+  std::vector<size_t> order(segs.size());
+  for (size_t k = 0; k < segs.size(); ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return segs[x][0] < segs[y][0]; });
+  std::vector<int> hs((size_t)N);
+  for (size_t id = 0; id < order.size(); ++id)
+    for (int i : segs[order[id]]) hs[(size_t)i] = (int)id;
+  CK(cudaMemcpyAsync(segof, hs.data(), (size_t)N * 4, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *M_out = (long long)segs.size();
   return D2_OK;
 }
 
@@ -880,6 +1011,31 @@ int d2_update_locations(d2_ctx* c, const d2_bags* objs, const double* omega, con
   return D2_OK;
 }
 
+int d2_segment(d2_ctx* c, const d2_bags* objs, const double* omega, int64_t tau, int32_t iters,
+               int32_t* seg_id, int64_t* n_segments) {
+  if (!c || !bags_ok(objs) || tau < 1 || iters < 0 || !seg_id || !n_segments) return D2_EINVAL;
+  const long long N = objs->count;
+  if (N < 1) return D2_EINVAL;
+  cudaSetDevice(c->device);
+  int rc = D2_OK;
+  ObjView v;
+  if ((rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v))) return rc;
+  int mmax = 0;
+  if ((rc = scan(c, v, &mmax))) return rc;
+  const double* om;
+  if ((rc = stage_in(c, omega, (size_t)N, kOmega, &om))) return rc;
+  int* ds;
+  bool host = false;
+  if ((rc = stage_out(c, seg_id, (size_t)N, kSgOut, &ds, &host))) return rc;
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  long long M = 0;
+  if ((rc = segment_impl(c, v, mmax, om, tau, iters, ds, &M))) return rc;
+  if (host) CK(cudaMemcpyAsync(seg_id, ds, (size_t)N * 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *n_segments = M;
+  return D2_OK;
+}
+
 int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t K, int64_t seg_size,
                      int32_t iters, double* out_loc, double* out_cent_weight, int32_t* labels) {
   if (!c || !bags_ok(objs) || K < 1 || iters < 0 || !out_loc || !out_cent_weight || !labels)
@@ -918,7 +1074,17 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
   int cur_mmax = mmax;
   for (int level = 0;; ++level) {
     const long long n_l = cur.count;
-    const long long M = n_l <= seg_size ? 1 : (n_l + seg_size - 1) / seg_size;
+    cur.segof = nullptr;
+    long long M = n_l <= seg_size ? 1 : (n_l + seg_size - 1) / seg_size;
+    if (c->cfg.segmentation == D2_SEG_CONSTRAINED && n_l > seg_size) {
+      // this level's segments from the binary constrained D2 splits
+      int* segof = static_cast<int*>(grow(c, kLvSegof, (size_t)n_l * 4, &rc));
+      if (rc != D2_OK) return rc;
+      const int si = c->cfg.split_iters > 0 ? c->cfg.split_iters : 10;
+      if ((rc = segment_impl(c, cur, cur_mmax, om, seg_size, si, segof, &M))) return rc;
+      cur.segof = segof;
+      CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    }
     const long long seg = M == 1 ? n_l : seg_size;
     const long long KT = M * K;
     // centroid sets of this level: M copies of the resident set
@@ -1021,7 +1187,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     CK(d2k::update_locations(cur, om, lab, seg, K, sort_only, KT, loff, d, c->cent_ldt, l32, l64,
                              scr, c->stream));
     CK(d2k::group_weight_sum(om, n_l, KT, scr, wnew, c->stream));
-    k_merge_labels<<<blocks_for(n_l), 256, 0, c->stream>>>(lab, n_l, seg, K, ct);
+    k_merge_labels<<<blocks_for(n_l), 256, 0, c->stream>>>(lab, n_l, seg, cur.segof, K, ct);
     k_compose<<<blocks_for(N0), 256, 0, c->stream>>>(C, N0, ct);
     d2k::note_launches(2);
     CK(cudaGetLastError());

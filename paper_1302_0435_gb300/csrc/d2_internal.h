@@ -16,7 +16,13 @@ struct ObjView {
   int d;
   int ldt;  // 0 f64, 1 f32, 2 bf16
   int wdt;  // 0 f64, 1 f32
+  // segment of each object (nullptr: object i is in segment i / seg_size)
+  const int* segof = nullptr;
 };
+
+__host__ __device__ inline long long seg_of(const ObjView& ob, long long i, long long seg_size) {
+  return ob.segof ? (long long)ob.segof[i] : i / seg_size;
+}
 
 struct CentView {
   const float* loc32;    // [T][d] FP32 copy (exact for FP32/BF16 centroids)
@@ -138,6 +144,18 @@ D2_NPL_DECL(3)
 D2_NPL_DECL(4)
 #undef D2_NPL_DECL
 
+// ---- initial data segmentation helpers (d2_segment.cu) ----
+// Gather bags members[0..cnt) of v into a compact view: off_out [cnt+1],
+// loc_out / w_out in v's element types (room for all their rows), om_out
+// [cnt] (1 where om_in is nullptr).
+cudaError_t seg_gather(const ObjView& v, const int* members, long long cnt, const double* om_in,
+                       long long* off_out, void* loc_out, void* w_out, double* om_out,
+                       cudaStream_t st);
+// K (1 or 2) start centroids from bags i0 (, i1) of v: FP64 locations,
+// uniform FP64 weights, offsets [K+1].
+cudaError_t seg_cents(const ObjView& v, int i0, int i1, int K, double* cloc, double* cw,
+                      long long* coff, cudaStream_t st);
+
 // ---- tensor-core ground cost (d2_tc.cu) ----
 // Whether the contraction supports dimension d (a multiple of 16 in 16..256).
 inline bool tc_dim_ok(int d) { return d >= 16 && d <= 256 && d % 16 == 0; }
@@ -177,7 +195,7 @@ cudaError_t sum_fixed_order(const double* v, long long n, double* out, cudaStrea
 // Location update (Eq. (WeightedUpdate)): objects grouped by label with a
 // stable counting sort, then one block per centroid sums its members in
 // object-index order.  labels index the centroid set `cv` (seg_size/K map
-// an object's local label to a global centroid: g = (i/seg_size)*K + label).
+// an object's local label to a global centroid: g = seg_of(i)*K + label).
 struct UpdateScratch {
   int* chunk_counts;   // [nchunks * KT]
   long long* start;    // [KT+1]

@@ -401,7 +401,8 @@ __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
 }
 
 // Nearest centroid, Alg. 2 Step 2, in two kernels.  Object i uses the
-// centroids [(i/seg_size)*K, (i/seg_size)*K + K) of the set.
+// centroids [seg(i)*K, seg(i)*K + K) of the set (seg(i) = i/seg_size, or
+// the object's entry of ob.segof).
 //
 // k_screen: every centroid is solved with an FP32 tile and FP32 pivots.
 // The FP32 objective D32_j has a bound err_j on its distance to the FP64
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
     const int j0 = jb * KB, j1 = min(K, j0 + KB);
     const long long o0 = ob.off[i];
     const int m = (int)(ob.off[i + 1] - o0);
-    const long long cb = (i / seg_size) * (long long)K;
+    const long long cb = seg_of(ob, i, seg_size) * (long long)K;
     bool ok = m >= 1 && m <= cfg.mmax && cb + K <= cv.K && load_obj_prefix<G>(g, ob, o0, m, s32.P);
     const bool cold = !(ws.par8 && ws.warm);
     // the cold-start rule is a compile-time choice (ST: 0 ranked staircase,
@@ -642,7 +643,7 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
     const long long i = cfg.oidx ? (long long)cfg.oidx[tt] : cfg.obase + tt;
     const long long o0 = ob.off[i];
     const int m = (int)(ob.off[i + 1] - o0);
-    const long long cb = (i / seg_size) * (long long)K;
+    const long long cb = seg_of(ob, i, seg_size) * (long long)K;
     int best_j = -1;
     double best = nan("");
     int st = kStOk;

@@ -18,12 +18,12 @@ constexpr int kChunk = 1024;
 
 __host__ __device__ inline size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
-__global__ void k_global_label(const int* labels, long long N, long long seg_size, int K,
-                               long long KT, int* gl) {
+__global__ void k_global_label(const int* labels, long long N, long long seg_size, const int* segof,
+                               int K, long long KT, int* gl) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     const int l = labels[i];
-    const long long g = (i / seg_size) * (long long)K + l;
+    const long long g = (segof ? (long long)segof[i] : i / seg_size) * (long long)K + l;
     gl[i] = (l < 0 || l >= K || g >= KT) ? -1 : (int)g;
   }
 }
@@ -246,7 +246,7 @@ cudaError_t update_locations(const ObjView& ob, const double* omega, const int* 
   cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)nchunks * KT * 4, st);
   if (e != cudaSuccess) return e;
   const unsigned gb = (unsigned)((N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096);
-  k_global_label<<<gb, 256, 0, st>>>(labels, N, seg_size, K, KT, gl);
+  k_global_label<<<gb, 256, 0, st>>>(labels, N, seg_size, ob.segof, K, KT, gl);
   k_chunk_hist<<<(unsigned)nchunks, 256, 0, st>>>(gl, N, KT, counts);
   const unsigned kb = (unsigned)((KT + 255) / 256);
   k_label_prefix<<<kb, 256, 0, st>>>(counts, nchunks, KT, tot);

@@ -19,13 +19,14 @@ D2_F64, D2_F32, D2_BF16 = 0, 1, 2
 D2_PREC_AUTO, D2_PREC_FP64, D2_PREC_FP32, D2_PREC_TC = 0, 1, 2, 3
 D2_TC_AUTO, D2_TC_OFF, D2_TC_ON = 0, 1, 2
 D2_START_AUTO, D2_START_RANKED, D2_START_VOGEL = 0, 1, 2
+D2_SEG_SLICES, D2_SEG_CONSTRAINED = 0, 1
 MAX_SUPPORT = 64
 
 EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_strerror",
            "d2_version", "d2_set_centroids", "d2_get_centroids", "d2_cost_matrix",
            "d2_mallows_batch", "d2_assign", "d2_update_locations", "d2_cluster_level",
            "d2_get_stats", "d2_update_locations_noalloc", "d2_server_create", "d2_server_submit",
-           "d2_server_poll", "d2_server_stats", "d2_server_destroy"]
+           "d2_server_poll", "d2_server_stats", "d2_server_destroy", "d2_segment"]
 
 
 class D2Bags(ctypes.Structure):
@@ -38,7 +39,7 @@ class D2Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("pivot_budget", ctypes.c_int32),
                 ("group_lanes", ctypes.c_int32), ("cost_tc", ctypes.c_int32),
                 ("tile_budget_mib", ctypes.c_int32), ("start_rule", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("segmentation", ctypes.c_int32), ("split_iters", ctypes.c_int32)]
 
 
 class D2Flows(ctypes.Structure):
@@ -88,6 +89,7 @@ def load(path=None):
     lib.d2_update_locations.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, ctypes.POINTER(D2Flows)]
     lib.d2_cluster_level.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i32, i64, i32, vp, vp, vp]
     lib.d2_get_stats.argtypes = [ctypes.POINTER(D2Stats)]
+    lib.d2_segment.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i64, i32, vp, ctypes.POINTER(i64)]
     lib.d2_server_create.argtypes = [ctypes.POINTER(vp), vp, i32, i64]
     lib.d2_server_submit.argtypes = [vp, ctypes.POINTER(D2Bags), ctypes.POINTER(i64)]
     lib.d2_server_poll.argtypes = [vp, i64, vp, vp, ctypes.POINTER(ctypes.c_double), i32]
@@ -164,10 +166,12 @@ class Context:
     """d2_ctx_create / d2_ctx_destroy."""
 
     def __init__(self, device=0, precision=D2_PREC_AUTO, pivot_budget=0, group_lanes=0,
-                 cost_tc=D2_TC_AUTO, tile_budget_mib=0, start_rule=D2_START_AUTO):
+                 cost_tc=D2_TC_AUTO, tile_budget_mib=0, start_rule=D2_START_AUTO,
+                 segmentation=D2_SEG_SLICES, split_iters=0):
         lib = load()
         self.h = ctypes.c_void_p()
-        cfg = D2Config(precision, pivot_budget, group_lanes, cost_tc, tile_budget_mib, start_rule)
+        cfg = D2Config(precision, pivot_budget, group_lanes, cost_tc, tile_budget_mib, start_rule,
+                       segmentation, split_iters)
         _check(lib.d2_ctx_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)), "d2_ctx_create")
         self._cents = None
 
@@ -264,6 +268,17 @@ def d2_cluster_level(ctx, objs, K, seg_size, iters, out_loc, out_cent_weight, la
     if rc not in (D2_OK, D2_ENOTCONVERGED):
         _check(rc, "d2_cluster_level")
     return rc
+
+
+def d2_segment(ctx, objs, tau, iters, omega=None, seg_id=None):
+    """Initial data segmentation (Alg. 3 Step 1).  Returns (seg_id array,
+    number of segments); seg_id may be a caller buffer (numpy or device
+    tensor of int32)."""
+    out = seg_id if seg_id is not None else np.empty(objs.count, dtype=np.int32)
+    m = ctypes.c_int64()
+    _check(load().d2_segment(ctx.h, ctypes.byref(objs.s), _ptr(omega), int(tau), int(iters),
+                             _ptr(out), ctypes.byref(m)), "d2_segment")
+    return out, m.value
 
 
 def d2_get_stats():

@@ -66,3 +66,14 @@ def test_layout_of_config_structs():
     assert ctypes.sizeof(d2.D2Bags) == 48
     assert ctypes.sizeof(d2.D2Config) == 32
     assert ctypes.sizeof(d2.D2Flows) == 24
+
+
+def test_every_called_entry_point_has_a_ctypes_signature():
+    """A call without argtypes passes 64-bit pointers and sizes as C int."""
+    import re
+    from pathlib import Path
+    src = (Path(__file__).resolve().parents[1] / "paper_1302_0435_gb300" / "d2.py").read_text()
+    called = set(re.findall(r"load\(\)\.(d2_\w+)\(", src))
+    declared = set(re.findall(r"lib\.(d2_\w+)\.argtypes", src))
+    no_args = {"d2_version"}  # takes no arguments
+    assert called - declared - no_args == set()

@@ -32,7 +32,7 @@ enum Slot {
   kBinSort, kTuneLab, kTuneD2, kTcTile, kTcRow, kTcSrc, kTcNx, kTcDel,
   // initial data segmentation
   kSgMem, kSgOff, kSgLoc, kSgW, kSgOm, kSgCLoc, kSgCW, kSgCOff, kSgC32, kSgC64, kSgCQ, kSgCW64,
-  kSgLab, kSgD2, kSgCell, kSgFw, kSgUpd, kSgCand, kSgOut, kLvSegof,
+  kSgLab, kSgD2, kSgCell, kSgFw, kSgUpd, kSgCand, kSgOut, kLvSegof, kSgPart, kUpdPart, kLvPart,
   kSlots
 };
 
@@ -531,6 +531,8 @@ int segment_impl(d2_ctx* c, const ObjView& v, int mmax, const double* om, long l
   double* fw = static_cast<double*>(grow(c, kSgFw, (size_t)(N * stride) * 8, &rc));
   void* uscr = grow(c, kSgUpd, d2k::update_scratch_bytes(N, 2), &rc);
   int* cand = static_cast<int*>(grow(c, kSgCand, (size_t)d2k::assign_scratch_ints(N, 2, c->sms) * 4, &rc));
+  const size_t spart_n = d2k::update_part_bytes(N, 2, v.d);
+  double* spart = static_cast<double*>(grow(c, kSgPart, spart_n, &rc));
   if (rc != D2_OK) return rc;
   SolveCfg cfg = solve_cfg(c, mode_for(c, v.ldt), mmax);
   cfg.nmax = mmax;  // the split centroids are bags of the data
@@ -598,7 +600,7 @@ int segment_impl(d2_ctx* c, const ObjView& v, int mmax, const double* om, long l
     if ((rc = set_cents(0, i2, 2)) || (rc = solve(2)) || (rc = labels_to(hl))) return rc;
     for (int r = 0; r < iters; ++r) {
       CK(d2k::update_locations(sub, som, lab, cnt, 2, fo, 2, zoff, v.d, D2_F64, z32, z64, uscr,
-                               c->stream));
+                               c->stream, spart, spart_n));
       if ((rc = solve(2)) || (rc = labels_to(hl2))) return rc;
       if (hl2 == hl) break;
       hl.swap(hl2);
@@ -999,10 +1001,12 @@ int d2_update_locations(d2_ctx* c, const d2_bags* objs, const double* omega, con
     if ((rc = resolve_assigned(c, v, dl, mmax, resident_view(c), &fo))) return rc;
   }
   void* scr = grow(c, kUpd, d2k::update_scratch_bytes(N, c->K), &rc);
+  const size_t upart_n = d2k::update_part_bytes(N, c->K, c->d);
+  double* upart = static_cast<double*>(grow(c, kUpdPart, upart_n, &rc));
   if (rc != D2_OK) return rc;
   c->tc_stale = true;
   CK(d2k::update_locations(v, om, dl, N, (int)c->K, fo, c->K, c->c_off, c->d, c->cent_ldt,
-                           c->c_loc32, c->c_loc64, scr, c->stream));
+                           c->c_loc32, c->c_loc64, scr, c->stream, upart, upart_n));
   int bits = 0;
   if ((rc = read_err(c, &bits))) return rc;
   if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
@@ -1103,6 +1107,8 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     fo.cell = static_cast<int*>(grow(c, kFlowCell, (size_t)(n_l * stride) * 4, &rc));
     fo.w = static_cast<double*>(grow(c, kFlowW, (size_t)(n_l * stride) * 8, &rc));
     void* scr = grow(c, kUpd, d2k::update_scratch_bytes(n_l, KT), &rc);
+    const size_t lpart_n = d2k::update_part_bytes(n_l, KT, d);
+    double* lpart = static_cast<double*>(grow(c, kLvPart, lpart_n, &rc));
     int* cand = static_cast<int*>(grow(c, kCand, (size_t)d2k::assign_scratch_ints(n_l, K, c->sms) * 4, &rc));
     if (rc != D2_OK) return rc;
     k_replicate<<<blocks_for(M * Tc), 256, 0, c->stream>>>(c->c_loc32, c->c_loc64, c->c_Q, c->c_w64,
@@ -1154,7 +1160,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
       cudaError_t ue = cudaSuccess;
       if (rc2 == D2_OK && it < iters)
         ue = d2k::update_locations(cur, om, lab, seg, K, fo, KT, loff, d, c->cent_ldt, l32, l64, scr,
-                                   c->stream);
+                                   c->stream, lpart, lpart_n);
       if (capturing) {
         cudaGraph_t graph = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
@@ -1172,7 +1178,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
             return rc;
           if (it < iters)
             CK(d2k::update_locations(cur, om, lab, seg, K, fo, KT, loff, d, c->cent_ldt, l32, l64,
-                                     scr, c->stream));
+                                     scr, c->stream, lpart, lpart_n));
         } else {
           CK(cudaGraphLaunch(gexec, c->stream));
         }

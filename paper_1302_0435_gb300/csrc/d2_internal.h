@@ -203,10 +203,20 @@ struct UpdateScratch {
   int* seg_label;      // [N] global centroid per object
 };
 size_t update_scratch_bytes(long long N, long long KT);
+// Blocks per centroid of the accumulation: about 512 members each, at most 64.
+inline long long update_parts(long long N, long long KT) {
+  const long long u = (N + KT * 512 - 1) / (KT * 512);
+  return u < 1 ? 1 : (u > 64 ? 64 : u);
+}
+// Room for the per-part sums (0: one block per centroid suffices).
+size_t update_part_bytes(long long N, long long KT, int d);
+// part / part_bytes (optional): room for the per-part sums of large
+// clusters (update_part_bytes); without it one block sums each centroid.
 cudaError_t update_locations(const ObjView& ob, const double* omega, const int* labels,
                              long long seg_size, int K, const FlowOut& fo, long long KT,
                              const long long* coff, int d, int cent_ldt, float* loc32,
-                             double* loc64, void* scratch, cudaStream_t st);
+                             double* loc64, void* scratch, cudaStream_t st,
+                             double* part = nullptr, size_t part_bytes = 0);
 
 // After update_locations (or update_locations with fo.cell == nullptr, which
 // only sorts): per centroid sum of omega over its members, object order.

@@ -122,9 +122,14 @@ constexpr int kMaxStride = 127;
 // (coef * v^(a)_k) in FP64; the k == 0 slot also sums the denominator.  The
 // order of every sum is fixed, so results are deterministic.  Dynamic smem:
 // num [n*d] + den [n] doubles, then the staged entries and column lists.
+//
+// Large clusters are split over U blocks (blockIdx.y = part p takes the p-th
+// of U equal runs of the members); with U > 1 each part writes its sums to
+// `part` and k_accumulate_sum adds the parts in part order, so the result is
+// still deterministic.
 __global__ void k_accumulate(ObjView ob, const double* omega, FlowOut fo, const int* order,
                              const long long* start, const long long* coff, int d, int cent_ldt,
-                             float* loc32, double* loc64) {
+                             float* loc32, double* loc64, int U, double* part) {
   extern __shared__ __align__(16) double acc[];
   const long long g = blockIdx.x;
   const long long c0 = coff[g];
@@ -142,7 +147,10 @@ __global__ void k_accumulate(ObjView ob, const double* omega, FlowOut fo, const 
   const int lane = threadIdx.x & 31;
   for (int t = threadIdx.x; t < slots; t += blockDim.x) num[t] = 0.0;
   for (int t = threadIdx.x; t < n; t += blockDim.x) den[t] = 0.0;
-  const long long b = start[g], e = start[g + 1];
+  const long long gb = start[g], ge = start[g + 1];
+  const long long len = (ge - gb + U - 1) / U;
+  const long long b = gb + (long long)blockIdx.y * len;
+  const long long e = b + len < ge ? b + len : ge;
   for (long long c = b; c < e; c += per) {
     const int cm = (int)(e - c < per ? e - c : per);
     __syncthreads();
@@ -201,10 +209,39 @@ __global__ void k_accumulate(ObjView ob, const double* omega, FlowOut fo, const 
     }
   }
   __syncthreads();
+  if (U > 1) {
+    double* out = part + ((size_t)g * U + blockIdx.y) * ((size_t)64 * d + 64);
+    for (int t = threadIdx.x; t < n * d; t += blockDim.x) out[t] = num[t];
+    for (int t = threadIdx.x; t < n; t += blockDim.x) out[(size_t)64 * d + t] = den[t];
+    return;
+  }
   for (int t = threadIdx.x; t < n * d; t += blockDim.x) {
     const int r = t / d;
     if (den[r] > 0.0) {
       const double v = round_to(num[t] / den[r], cent_ldt);
+      loc64[c0 * d + t] = v;
+      loc32[c0 * d + t] = (float)v;
+    }
+  }
+}
+
+// The parts of each centroid added in part order, then the new locations.
+__global__ void k_accumulate_sum(const long long* coff, int d, int cent_ldt, int U,
+                                 const double* part, float* loc32, double* loc64) {
+  const long long g = blockIdx.x;
+  const long long c0 = coff[g];
+  const int n = (int)(coff[g + 1] - c0);
+  const size_t ps = (size_t)64 * d + 64;
+  const double* in = part + (size_t)g * U * ps;
+  for (int t = threadIdx.x; t < n * d; t += blockDim.x) {
+    const int r = t / d;
+    double sn = 0.0, sd = 0.0;
+    for (int q = 0; q < U; ++q) {
+      sn += in[q * ps + t];
+      sd += in[q * ps + (size_t)64 * d + r];
+    }
+    if (sd > 0.0) {
+      const double v = round_to(sn / sd, cent_ldt);
       loc64[c0 * d + t] = v;
       loc32[c0 * d + t] = (float)v;
     }
@@ -230,10 +267,16 @@ size_t update_scratch_bytes(long long N, long long KT) {
          al((size_t)N * 4) * 2;
 }
 
+size_t update_part_bytes(long long N, long long KT, int d) {
+  const long long U = update_parts(N, KT);
+  return U > 1 ? (size_t)(KT * U) * ((size_t)64 * d + 64) * sizeof(double) : 0;
+}
+
 cudaError_t update_locations(const ObjView& ob, const double* omega, const int* labels,
                              long long seg_size, int K, const FlowOut& fo, long long KT,
                              const long long* coff, int d, int cent_ldt, float* loc32,
-                             double* loc64, void* scratch, cudaStream_t st) {
+                             double* loc64, void* scratch, cudaStream_t st, double* part,
+                             size_t part_bytes) {
   const long long N = ob.count;
   if (N <= 0 || KT <= 0) return cudaSuccess;
   const long long nchunks = (N + kChunk - 1) / kChunk;
@@ -259,9 +302,17 @@ cudaError_t update_locations(const ObjView& ob, const double* omega, const int* 
                       (size_t)kStageEntries * (8 + 8 + 4 + 4) + 65 * 4;
   e = cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_accumulate<<<(unsigned)KT, 128, smem, st>>>(ob, omega, fo, order, start, coff, d, cent_ldt,
-                                                loc32, loc64);
+  // several blocks per centroid when the clusters are large (few centroids,
+  // many members) and the caller gave room for the parts
+  int U = (int)update_parts(N, KT);
+  if (!part || part_bytes < update_part_bytes(N, KT, d)) U = 1;
+  k_accumulate<<<dim3((unsigned)KT, (unsigned)U), 128, smem, st>>>(
+      ob, omega, fo, order, start, coff, d, cent_ldt, loc32, loc64, U, part);
   note_launches(1);
+  if (U > 1) {
+    k_accumulate_sum<<<(unsigned)KT, 128, 0, st>>>(coff, d, cent_ldt, U, part, loc32, loc64);
+    note_launches(1);
+  }
   return cudaGetLastError();
 }
 

@@ -74,10 +74,11 @@ def test_uneven_full_assign(d2, oracle_mod):
     _check_sample(oracle_mod, objs, cents, lab, dist, _sample(np.random.default_rng(2), objs, 400, 12))
 
 
-def test_high_dim_full_k(d2, oracle_mod):
-    objs, cents = synth.high_dim(N=1500)              # BF16 d=128, full K=512 of 64 supports
-    lab, dist = _assign_device(d2, objs, cents)
-    _check_sample(oracle_mod, objs, cents, lab, dist, _sample(np.random.default_rng(3), objs, 60, 4))
+def test_high_dim_full_size(d2, oracle_mod):
+    objs, cents = synth.high_dim()                    # 100,000 BF16 bags, d=128, K=512 of 64 supports
+    lab, dist = _assign_device(d2, objs, cents)       # tensor-core tiles, Vogel start
+    assert ((lab >= 0) & (lab < cents.count)).all()
+    _check_sample(oracle_mod, objs, cents, lab, dist, _sample(np.random.default_rng(3), objs, 40, 4))
 
 
 def test_serving_full_k(d2, oracle_mod):

@@ -157,6 +157,36 @@ def _bag_arrays(b):
     return loc, _f64(b.w), _i64(b.off)
 
 
+def mallows_table(xs, wx, ys, wy, table):
+    """Mallows distance with a custom ground cost between symbols (the
+    sequence variant of Eq. (D2opt): the squared Euclidean distance between
+    supports is replaced by a pairwise symbol distance, here any
+    nonnegative table[A][A]).  xs, ys: integer symbol ids of the supports.
+    Weights are normalised first.  Returns (D2, flow)."""
+    xs = np.asarray(xs, dtype=np.int64).ravel()
+    ys = np.asarray(ys, dtype=np.int64).ravel()
+    C = _f64(table)[np.ix_(xs, ys)]
+    p = normalise(wx)
+    q = normalise(wy)
+    v, w, _, _, _ = transport(C, p, q)
+    return v, w
+
+
+def assign_table(objs, cents, table):
+    """Alg. 2 Step 2 with the symbol cost table: labels (ties to the smallest
+    j) and D^2 of every bag; supports are symbol ids (dim 1)."""
+    N = len(objs.off) - 1
+    K = len(cents.off) - 1
+    allm = np.empty((N, K))
+    for i in range(N):
+        x, wx = bag(objs, i)
+        for j in range(K):
+            y, wy = bag(cents, j)
+            allm[i, j] = mallows_table(x, wx, y, wy, table)[0]
+    lab = np.argmin(allm, axis=1)  # first minimum
+    return lab.astype(np.int32), allm[np.arange(N), lab], allm
+
+
 def bag(b, i):
     """Rows of bag i as (loc [m, d], w [m]) in float64."""
     lo, hi = int(b.off[i]), int(b.off[i + 1])

@@ -172,6 +172,19 @@ int d2_get_centroids(d2_ctx* ctx, double* loc_out, double* w_out, int64_t* off_o
                      int64_t* k_out, int64_t* t_out);
 
 /*
+ * Symbol ground costs (the sequence variant of Eq. (D2opt)): with a table
+ * set, supports are symbol ids (dim 1, integer values in [0, A)) and the
+ * cost between symbols s and t is table[s*A + t] instead of the squared
+ * Euclidean distance; Mallows distances, labels and plans are computed as
+ * before.  table: [A][A] FP64, nonnegative and finite, host or device,
+ * copied.  A = 0 (or table NULL) removes it.  The resident centroids, and
+ * every later batch, must be symbol ids (else D2_EINVAL).  Symbolic
+ * supports are not moved: d2_update_locations and d2_cluster_level return
+ * D2_EUNSUPPORTED while a table is set.  A*A at most 2^26.
+ */
+int d2_set_cost_table(d2_ctx* ctx, const double* table, int32_t A);
+
+/*
  * Ground-cost matrix of one pair (the objective coefficients of
  * Eq. (D2opt)): C[a*n_j + r] = ||v_i^(a) - z_j^(r)||^2 for object i of
  * `objs` and resident centroid j, as the kernels compute it in `precision`

@@ -65,6 +65,10 @@ struct d2_ctx {
   float* c_cn = nullptr;
   float* c_cd = nullptr;
   bool tc_stale = true;
+  // symbol ground-cost table (A > 0): FP64 and FP32 copies of [A][A]
+  double* tab64 = nullptr;
+  float* tab32 = nullptr;
+  int A = 0;
   // scratch
   Buf slot[kSlots];
   int* d_err = nullptr;
@@ -247,7 +251,22 @@ CentView resident_view(const d2_ctx* c) {
   v.off = c->c_off;
   v.K = c->K;
   v.d = c->d;
+  v.tab32 = c->tab32;
+  v.tab64 = c->tab64;
+  v.A = c->A;
   return v;
+}
+
+// With a symbol table set: the bags must be one-dimensional symbol ids in
+// [0, A); raises kErrInvalid otherwise (read at the end of the call).
+int check_bag_symbols(d2_ctx* c, const ObjView& v) {
+  if (c->A <= 0) return D2_OK;
+  if (v.d != 1) return D2_EINVAL;
+  long long T = 0;
+  CK(cudaMemcpyAsync(&T, v.off + v.count, 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(d2k::check_symbols(v.loc, v.ldt, T, c->A, c->d_err, c->stream));
+  return D2_OK;
 }
 
 int read_err(d2_ctx* c, int* bits) {
@@ -702,6 +721,7 @@ int d2_ctx_destroy(d2_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_centroids(c);
+  cudaFree(c->tab64); cudaFree(c->tab32);
   for (auto& b : c->slot) if (b.p) cudaFree(b.p);
   if (c->d_err) cudaFree(c->d_err);
   if (c->d_info) cudaFree(c->d_info);
@@ -763,12 +783,57 @@ int d2_set_centroids(d2_ctx* c, const d2_bags* b) {
     free_centroids(c);
     return D2_EINVAL;
   }
+  if (c->A > 0) {  // a symbol table is set: the centroids must be symbol ids
+    if (d != 1) { free_centroids(c); return D2_EINVAL; }
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    CK(d2k::check_symbols(c->c_loc64, D2_F64, Tc, c->A, c->d_err, c->stream));
+    if ((rc = read_err(c, &bits))) return rc;
+    if (bits) { free_centroids(c); return D2_EINVAL; }
+  }
   c->K = b->count;
   c->Tc = Tc;
   c->d = d;
   c->nmax = nmax;
   c->cent_ldt = b->loc_dtype;
   c->h_coff = h;
+  return D2_OK;
+}
+
+int d2_set_cost_table(d2_ctx* c, const double* table, int32_t A) {
+  if (!c || A < 0 || (A > 0 && !table)) return D2_EINVAL;
+  cudaSetDevice(c->device);
+  if (A == 0 || !table) {
+    cudaFree(c->tab64); cudaFree(c->tab32);
+    c->tab64 = nullptr; c->tab32 = nullptr; c->A = 0;
+    return D2_OK;
+  }
+  if ((long long)A * A > (1LL << 26)) return D2_EUNSUPPORTED;
+  std::vector<double> h((size_t)A * A);
+  CK(cudaMemcpy(h.data(), table, h.size() * 8, cudaMemcpyDefault));
+  std::vector<float> h32(h.size());
+  for (size_t t = 0; t < h.size(); ++t) {
+    if (!(h[t] >= 0.0) || std::isinf(h[t])) return D2_EINVAL;  // nonnegative, finite
+    h32[t] = (float)h[t];
+  }
+  if (c->K > 0) {  // the resident centroids must already be symbol ids
+    if (c->d != 1) return D2_EINVAL;
+    std::vector<double> loc((size_t)c->Tc);
+    CK(cudaMemcpy(loc.data(), c->c_loc64, loc.size() * 8, cudaMemcpyDeviceToHost));
+    for (double x : loc)
+      if (!(x >= 0.0 && x < (double)A && x == std::floor(x))) return D2_EINVAL;
+  }
+  cudaFree(c->tab64); cudaFree(c->tab32);
+  c->tab64 = nullptr; c->tab32 = nullptr; c->A = 0;
+  if (cudaMalloc(&c->tab64, h.size() * 8) != cudaSuccess ||
+      cudaMalloc(&c->tab32, h.size() * 4) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->tab64); cudaFree(c->tab32);
+    c->tab64 = nullptr; c->tab32 = nullptr;
+    return D2_ENOMEM;
+  }
+  CK(cudaMemcpy(c->tab64, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->tab32, h32.data(), h32.size() * 4, cudaMemcpyHostToDevice));
+  c->A = A;
   return D2_OK;
 }
 
@@ -822,7 +887,12 @@ int d2_cost_matrix(d2_ctx* c, const d2_bags* objs, int64_t i, int64_t j, int32_t
     if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
   } else {
     const int mode = precision == D2_PREC_FP32 ? 1 : 0;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    if ((rc = check_bag_symbols(c, v))) return rc;
     CK(d2k::cost_matrix(v, resident_view(c), i, j, mode, dC, c->stream));
+    int bits = 0;
+    if ((rc = read_err(c, &bits))) return rc;
+    if (bits & d2k::kErrInvalid) return D2_EINVAL;
   }
   if (host) CK(cudaMemcpyAsync(C, dC, (size_t)(m * n) * 8, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -862,6 +932,7 @@ int d2_mallows_batch(d2_ctx* c, const d2_bags* objs, const int64_t* pair_obj, co
       return rc;
   }
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  if ((rc = check_bag_symbols(c, v))) return rc;
   const SolveCfg cfg = solve_cfg(c, mode_for(c, objs->loc_dtype), mmax);
   CK(d2k::mallows_pairs(v, resident_view(c), po, pc, npairs, cfg, dd, fo, ds, c->d_err, c->stream));
   if (h1) CK(cudaMemcpyAsync(dist2, dd, (size_t)npairs * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -918,6 +989,7 @@ int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labe
   int* cand = static_cast<int*>(grow(c, kCand, (size_t)d2k::assign_scratch_ints(N, c->K, c->sms) * 4, &rc));
   if (rc != D2_OK) return rc;
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  if ((rc = check_bag_symbols(c, v))) return rc;
   Bins bins;
   if (want_bins(c, N, mmax) && (rc = make_bins(c, v, c->nmax, &bins))) return rc;
   const int mode = mode_for(c, objs->loc_dtype);
@@ -972,6 +1044,7 @@ int d2_update_locations(d2_ctx* c, const d2_bags* objs, const double* omega, con
                         const d2_flows* flows) {
   if (!c || !bags_ok(objs) || !labels) return D2_EINVAL;
   if (c->K == 0) return D2_ENOCENTROIDS;
+  if (c->A > 0) return D2_EUNSUPPORTED;  // symbolic supports are not moved
   if (objs->dim != c->d) return D2_EINVAL;
   const long long N = objs->count;
   if (N == 0) return D2_OK;
@@ -1045,6 +1118,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
   if (!c || !bags_ok(objs) || K < 1 || iters < 0 || !out_loc || !out_cent_weight || !labels)
     return D2_EINVAL;
   if (c->K == 0) return D2_ENOCENTROIDS;
+  if (c->A > 0) return D2_EUNSUPPORTED;  // symbolic supports are not moved
   if (c->K != K || objs->dim != c->d || seg_size <= K) return D2_EINVAL;
   const long long N0 = objs->count;
   if (N0 < 1) return D2_EINVAL;

@@ -31,6 +31,11 @@ struct CentView {
   const long long* off;  // [K+1]
   long long K;           // number of centroids in the set
   int d;
+  // symbol ground costs (A > 0): supports are symbol ids (d = 1) and the
+  // cost of symbols (s, t) is tab[s*A + t] instead of the squared distance
+  const float* tab32 = nullptr;
+  const double* tab64 = nullptr;
+  int A = 0;
 };
 
 struct FlowOut {
@@ -143,6 +148,11 @@ D2_NPL_DECL(2)
 D2_NPL_DECL(3)
 D2_NPL_DECL(4)
 #undef D2_NPL_DECL
+
+// Raise kErrInvalid into d_err unless every location of the T supports is
+// an integer symbol id in [0, A) (d = 1).
+cudaError_t check_symbols(const void* loc, int ldt, long long T, int A, int* d_err,
+                          cudaStream_t st);
 
 // ---- initial data segmentation helpers (d2_segment.cu) ----
 // Gather bags members[0..cnt) of v into a compact view: off_out [cnt+1],

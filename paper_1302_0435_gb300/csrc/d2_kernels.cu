@@ -75,7 +75,12 @@ __global__ void k_cost_matrix(ObjView ob, CentView cv, long long i, long long j,
   const int n = (int)(cv.off[j + 1] - c0);
   for (int t = threadIdx.x; t < m * n; t += blockDim.x) {
     const int a = t / n, r = t % n;
-    if (mode == 0) {
+    if (cv.A) {  // symbol table (ids checked before the launch; clamped reads)
+      int xs = (int)ldx<double>(ob.loc, ob.ldt, o0 + a), ys = (int)cv.loc64[c0 + r];
+      xs = xs < 0 ? 0 : (xs >= cv.A ? cv.A - 1 : xs);
+      ys = ys < 0 ? 0 : (ys >= cv.A ? cv.A - 1 : ys);
+      C[t] = mode == 0 ? cv.tab64[xs * cv.A + ys] : (double)cv.tab32[xs * cv.A + ys];
+    } else if (mode == 0) {
       double acc = 0.0;
       for (int k = 0; k < cv.d; ++k) {
         const double df = ldx<double>(ob.loc, ob.ldt, (o0 + a) * cv.d + k) - cv.loc64[(c0 + r) * cv.d + k];
@@ -90,6 +95,14 @@ __global__ void k_cost_matrix(ObjView ob, CentView cv, long long i, long long j,
       }
       C[t] = (double)acc;
     }
+  }
+}
+
+__global__ void k_check_symbols(const void* loc, int ldt, long long T, int A, int* err) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double v = ldx<double>(loc, ldt, t);
+    if (!(v >= 0.0 && v < (double)A && v == floor(v))) atomicOr(err, kErrInvalid);
   }
 }
 
@@ -209,6 +222,15 @@ cudaError_t bin_objects(const ObjView& ob, int nmax, int* bins_out, cudaStream_t
 cudaError_t cost_matrix(const ObjView& ob, const CentView& cv, long long i, long long j, int mode,
                         double* C, cudaStream_t st) {
   k_cost_matrix<<<1, 256, 0, st>>>(ob, cv, i, j, mode, C);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t check_symbols(const void* loc, int ldt, long long T, int A, int* d_err,
+                          cudaStream_t st) {
+  if (T <= 0) return cudaSuccess;
+  const unsigned b = (unsigned)std::min<long long>((T + 255) / 256, 4096);
+  k_check_symbols<<<b, 256, 0, st>>>(loc, ldt, T, A, d_err);
   note_launches(1);
   return cudaGetLastError();
 }

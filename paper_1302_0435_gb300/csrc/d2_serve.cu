@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -350,6 +351,16 @@ extern "C" int d2_server_submit(d2_server* sv, const d2_bags* objs, int64_t* tic
     mmax = std::max<int>(mmax, (int)m);
   }
   if (mmax + sv->nmax > 128) return D2_EUNSUPPORTED;
+  if (sv->cv.A > 0) {  // symbol ground costs: one-dimensional symbol ids in [0, A)
+    if (objs->dim != 1) return D2_EINVAL;
+    for (long long t = 0; t < T; ++t) {
+      double x;
+      if (objs->loc_dtype == D2_F64) x = static_cast<const double*>(objs->loc)[t];
+      else if (objs->loc_dtype == D2_F32) x = static_cast<const float*>(objs->loc)[t];
+      else return D2_EINVAL;
+      if (!(x >= 0.0 && x < (double)sv->cv.A && x == std::floor(x))) return D2_EINVAL;
+    }
+  }
   // stable partition of the bags by node bin
   r->order.resize(N);
   long long cnt[4] = {0, 0, 0, 0};

@@ -162,6 +162,33 @@ __device__ T build_cost(const Grp<G>& g, T* C, int m, int n, const void* xl, int
   return cmax;
 }
 
+// Ground-cost tile from a symbol table (the sequence variant of Eq. (D2opt)):
+// C[a*n+r] = tab[x_a*A + y_r] with x, y symbol ids (d = 1).  Ids are checked
+// before the launch; the clamp only keeps reads inside the table.  Returns
+// the tile maximum (group-uniform).
+template <typename T, int G>
+__device__ T build_cost_tab(const Grp<G>& g, T* C, int m, int n, const void* xl, int xdt,
+                            long long xrow0, const T* ysym, const T* tab, int A) {
+  const int mn = m * n;
+  const int q = G / n, rem = G - (G / n) * n;
+  int a = g.lane / n, r = g.lane - (g.lane / n) * n;
+  T cmax = T(0);
+  for (int t = g.lane; t < mn; t += G) {
+    int xs = (int)ldx<T>(xl, xdt, xrow0 + a);
+    int ys = (int)ysym[r];
+    xs = xs < 0 ? 0 : (xs >= A ? A - 1 : xs);
+    ys = ys < 0 ? 0 : (ys >= A ? A - 1 : ys);
+    const T c = tab[xs * A + ys];
+    C[t] = c;
+    cmax = c > cmax ? c : cmax;
+    r += rem; a += q;
+    if (r >= n) { r -= n; ++a; }
+  }
+  cmax = gmax<G>(g, cmax);
+  g.sync();
+  return cmax;
+}
+
 // ---------------------------------------------------------- start order --
 // The cold-start basis is the northwest staircase taken in the order of
 // the supports' projections onto the object's principal direction (in 1-D
@@ -329,8 +356,11 @@ __device__ __forceinline__ int solve_exact(const Grp<G>& g, const PairMem<double
   int piv = 0;
   if (fp32_start) {
     const PairMem<float> s32 = recast<float>(s);
-    const float c32 = build_cost<float, G, 8>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
-                                           cv.loc32 + c0 * cv.d, cv.d);
+    const float c32 =
+        cv.A ? build_cost_tab<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0, cv.loc32 + c0,
+                                        cv.tab32, cv.A)
+             : build_cost<float, G, 8>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
+                                       cv.loc32 + c0 * cv.d, cv.d);
     Simplex<float, G, NPL> S32(s32, m, n, g);
     if constexpr (ST == 1) {
       S32.init_vogel();
@@ -344,8 +374,11 @@ __device__ __forceinline__ int solve_exact(const Grp<G>& g, const PairMem<double
     S.root = S32.root;
     g.sync();
   }
-  const double cmax = build_cost<double, G>(g, s.cost, m, n, ob.loc, ob.ldt, o0,
-                                            cv.loc64 + c0 * cv.d, cv.d);
+  const double cmax =
+      cv.A ? build_cost_tab<double, G>(g, s.cost, m, n, ob.loc, ob.ldt, o0, cv.loc64 + c0,
+                                       cv.tab64, cv.A)
+           : build_cost<double, G>(g, s.cost, m, n, ob.loc, ob.ldt, o0, cv.loc64 + c0 * cv.d,
+                                   cv.d);
   S.set_dims(m, n);
   S.bad = false;
   if (!fp32_start) S.init_northwest();
@@ -518,6 +551,9 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       if constexpr (TC)
         cmax = load_tile<G>(g, s32.cost, m, n,
                             cfg.tile.C + trow0 * cfg.tile.ldc + (c0 - cfg.tile.col0), cfg.tile.ldc);
+      else if (cv.A)
+        cmax = build_cost_tab<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0, cv.loc32 + c0,
+                                        cv.tab32, cv.A);
       else
         cmax = build_cost<float, G, (NPL <= 1 ? 8 : 32)>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
                                                          cv.loc32 + c0 * cv.d, cv.d);
@@ -666,8 +702,11 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
           // the screen just saved this pair's FP32-optimal basis: continue in FP64
           const long long wt = (i * (long long)K + j) * ws.ns;
           load_cent_prefix<G>(g, cv, c0, n, s64.Q);
-          const double cmax = build_cost<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
-                                                    cv.loc64 + c0 * cv.d, cv.d);
+          const double cmax =
+              cv.A ? build_cost_tab<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
+                                               cv.loc64 + c0, cv.tab64, cv.A)
+                   : build_cost<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
+                                           cv.loc64 + c0 * cv.d, cv.d);
           S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
           s2 = S.run(cfg.budget * (m + n), tol64(cmax), &p_ex);
           D = S.template objective<double>();

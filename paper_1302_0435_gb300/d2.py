@@ -26,7 +26,8 @@ EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_st
            "d2_version", "d2_set_centroids", "d2_get_centroids", "d2_cost_matrix",
            "d2_mallows_batch", "d2_assign", "d2_update_locations", "d2_cluster_level",
            "d2_get_stats", "d2_update_locations_noalloc", "d2_server_create", "d2_server_submit",
-           "d2_server_poll", "d2_server_stats", "d2_server_destroy", "d2_segment"]
+           "d2_server_poll", "d2_server_stats", "d2_server_destroy", "d2_segment",
+           "d2_set_cost_table"]
 
 
 class D2Bags(ctypes.Structure):
@@ -90,6 +91,7 @@ def load(path=None):
     lib.d2_cluster_level.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i32, i64, i32, vp, vp, vp]
     lib.d2_get_stats.argtypes = [ctypes.POINTER(D2Stats)]
     lib.d2_segment.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i64, i32, vp, ctypes.POINTER(i64)]
+    lib.d2_set_cost_table.argtypes = [vp, vp, i32]
     lib.d2_server_create.argtypes = [ctypes.POINTER(vp), vp, i32, i64]
     lib.d2_server_submit.argtypes = [vp, ctypes.POINTER(D2Bags), ctypes.POINTER(i64)]
     lib.d2_server_poll.argtypes = [vp, i64, vp, vp, ctypes.POINTER(ctypes.c_double), i32]
@@ -268,6 +270,17 @@ def d2_cluster_level(ctx, objs, K, seg_size, iters, out_loc, out_cent_weight, la
     if rc not in (D2_OK, D2_ENOTCONVERGED):
         _check(rc, "d2_cluster_level")
     return rc
+
+
+def d2_set_cost_table(ctx, table):
+    """Symbol ground costs: table [A, A] FP64 (numpy or tensor); None removes."""
+    if table is None:
+        _check(load().d2_set_cost_table(ctx.h, None, 0), "d2_set_cost_table")
+        return
+    if isinstance(table, np.ndarray):
+        table = np.ascontiguousarray(table, dtype=np.float64)
+    A = int(table.shape[0])
+    _check(load().d2_set_cost_table(ctx.h, _ptr(table), A), "d2_set_cost_table")
 
 
 def d2_segment(ctx, objs, tau, iters, omega=None, seg_id=None):

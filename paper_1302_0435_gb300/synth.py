@@ -195,6 +195,40 @@ def serving_request(rng, means, size=None):
     return _pack(sizes, loc, w, "f32", "f32")
 
 
+def sequence_like(N=100_000, K=64, A=20, seed=1006, classes=3):
+    """Sequence-style bags (the protein experiment's shape): each bag is the
+    histogram of a symbol sequence (length 100-600) drawn from one of
+    `classes` class profiles over A symbols; its supports are the symbols
+    present (ids stored as FP32, dim 1), weights their frequencies.
+    Centroids: K such histograms.  Table: a substitution-style symbol
+    distance D(s, t) = -(log P(s|t) + log P(t|s)) from a random symmetric
+    similarity (softmax rows), nonnegative.  Returns (objs, cents, table)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    prof = rng.dirichlet(np.full(A, 0.6), size=classes)
+
+    def hist_bags(count):
+        cls = rng.integers(0, classes, size=count)
+        lens = rng.integers(100, 601, size=count)
+        syms, ws, sizes = [], [], []
+        for c, L in zip(cls, lens):
+            cnt = rng.multinomial(L, prof[c])
+            nz = np.nonzero(cnt)[0]
+            syms.append(nz.astype(np.float32))
+            ws.append((cnt[nz] / L).astype(np.float32))
+            sizes.append(len(nz))
+        return _pack(np.asarray(sizes, dtype=np.int64), np.concatenate(syms).reshape(-1, 1),
+                     np.concatenate(ws), "f32", "f32")
+
+    objs = hist_bags(N)
+    cents = hist_bags(K)
+    e = rng.normal(size=(A, 6))
+    sim = -((e[:, None, :] - e[None, :, :]) ** 2).sum(-1) / 4.0
+    P = np.exp(sim)
+    P /= P.sum(axis=1, keepdims=True)
+    table = -(np.log(P) + np.log(P).T)
+    return objs, cents, table
+
+
 CONFIGS = {
     "plain_small": plain_small,
     "image_like": image_like,

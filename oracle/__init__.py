@@ -187,6 +187,19 @@ def assign_table(objs, cents, table):
     return lab.astype(np.int32), allm[np.arange(N), lab], allm
 
 
+def assign_multi(objs_list, cents_list, nthreads=1):
+    """Alg. 2 Step 2 with the combined distance of several bag types
+    (Eq. (imgdist)): D^2(I_i, Z_j) = sum_b D^2(U_i^b, Z_j^b); labels with
+    ties to the smallest j.  objs_list[b] / cents_list[b] hold bag type b of
+    every object / centroid.  Returns (labels, summed D^2, summed matrix)."""
+    tot = None
+    for objs, cents in zip(objs_list, cents_list):
+        _, _, allm = assign(objs, cents, nthreads=nthreads, return_all=True)
+        tot = allm if tot is None else tot + allm
+    lab = np.argmin(tot, axis=1)
+    return lab.astype(np.int32), tot[np.arange(tot.shape[0]), lab], tot
+
+
 def bag(b, i):
     """Rows of bag i as (loc [m, d], w [m]) in float64."""
     lo, hi = int(b.off[i]), int(b.off[i + 1])

@@ -195,6 +195,29 @@ def serving_request(rng, means, size=None):
     return _pack(sizes, loc, w, "f32", "f32")
 
 
+def image_two_bags(N=200_000, K=64, seed=1007, n=16, components=32):
+    """Two bag types per image (the paper's colour and texture bags): each
+    object draws one mixture component and, from it, a colour bag (d = 3)
+    and a texture bag (d = 3) of 8-16 supports each, Dirichlet(0.5)
+    weights, FP32.  Centroids: K of each type with n supports and uniform
+    weights.  Returns ([colour objs, texture objs], [colour cents,
+    texture cents])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out_o, out_c = [], []
+    means = [rng.uniform(-5.0, 5.0, size=(components, 3)) for _ in range(2)]
+    comp = rng.integers(0, components, size=N)
+    for t in range(2):
+        sizes = rng.integers(8, 17, size=N).astype(np.int64)
+        loc = (means[t][np.repeat(comp, sizes)] + rng.normal(0, 1.0, size=(int(sizes.sum()), 3)))
+        w = _dirichlet_ragged(rng, sizes, 0.5, np.float32)
+        out_o.append(_pack(sizes, loc.astype(np.float32), w, "f32", "f32"))
+        ccomp = rng.integers(0, components, size=K)
+        cl = means[t][np.repeat(ccomp, n)] + rng.normal(0, 1.0, size=(K * n, 3))
+        out_c.append(_pack(np.full(K, n, dtype=np.int64), cl.astype(np.float32),
+                           np.full(K * n, 1.0 / n, np.float32), "f32", "f32"))
+    return out_o, out_c
+
+
 def sequence_like(N=100_000, K=64, A=20, seed=1006, classes=3):
     """Sequence-style bags (the protein experiment's shape): each bag is the
     histogram of a symbol sequence (length 100-600) drawn from one of

@@ -237,6 +237,21 @@ int d2_update_locations(d2_ctx* ctx, const d2_bags* objs, const double* omega,
                         const int32_t* labels, const d2_flows* flows);
 
 /*
+ * Nearest centroid under the combined distance of several bag types
+ * (Eq. (imgdist)): object i is B bags, one per type, and
+ * D^2(I_i, Z_j) = sum_b D^2(U_i^b, Z_j^b).  ctxs[b] holds type b's resident
+ * centroids (all on one device, all with the same K; one context per type);
+ * objs[b] holds type b's bag of every object (same count).  labels [count]
+ * and dist2 [count] (the summed FP64 D^2; ties to the smallest j), host or
+ * device.  Each type's FP32 screen bounds every pair; the candidates of the
+ * summed bounds are solved exactly by every type.  Each type's centroids
+ * are then updated on their own (d2_update_locations on ctxs[b] with these
+ * labels).  B at most 8.
+ */
+int d2_assign_multi(d2_ctx* const* ctxs, int32_t B, const d2_bags* objs, int32_t* labels,
+                    double* dist2);
+
+/*
  * Initial data segmentation (Alg. 3 Step 1): split the bags into segments of
  * at most tau bags by repeated binary splits of the largest segment (ties:
  * the one formed first).  A split is a constrained D2-clustering with k = 2

@@ -33,6 +33,8 @@ enum Slot {
   // initial data segmentation
   kSgMem, kSgOff, kSgLoc, kSgW, kSgOm, kSgCLoc, kSgCW, kSgCOff, kSgC32, kSgC64, kSgCQ, kSgCW64,
   kSgLab, kSgD2, kSgCell, kSgFw, kSgUpd, kSgCand, kSgOut, kLvSegof, kSgPart, kUpdPart, kLvPart,
+  // combined distance of several bag types
+  kMbPair, kMbTmpLab, kMbTmpD2, kMbCnt, kMbStart, kMbPObj, kMbPCen, kMbD2, kMbSt,
   kSlots
 };
 
@@ -1085,6 +1087,100 @@ int d2_update_locations(d2_ctx* c, const d2_bags* objs, const double* omega, con
   if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
   if (bits & d2k::kErrInvalid) return D2_EINVAL;
   if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
+  return D2_OK;
+}
+
+int d2_assign_multi(d2_ctx* const* ctxs, int32_t B, const d2_bags* objs, int32_t* labels,
+                    double* dist2) {
+  if (!ctxs || B < 1 || B > d2k::kMaxBagTypes || !objs || !labels || !dist2) return D2_EINVAL;
+  d2_ctx* c = ctxs[0];
+  if (!c) return D2_EINVAL;
+  const long long N = objs[0].count;
+  for (int b = 0; b < B; ++b) {
+    d2_ctx* cb = ctxs[b];
+    if (!cb || !bags_ok(&objs[b])) return D2_EINVAL;
+    if (cb->K == 0) return D2_ENOCENTROIDS;
+    if (cb->device != c->device || cb->K != c->K || objs[b].count != N || objs[b].dim != cb->d)
+      return D2_EINVAL;
+    for (int a = 0; a < b; ++a)
+      if (ctxs[a] == cb) return D2_EINVAL;  // one context per bag type
+  }
+  if (N == 0) return D2_OK;
+  cudaSetDevice(c->device);
+  const int K = (int)c->K;
+  int rc = D2_OK;
+  ObjView v[d2k::kMaxBagTypes];
+  int mmax[d2k::kMaxBagTypes];
+  d2k::MultiScreen ms{};
+  ms.B = B;
+  auto check = [](d2_ctx* cx) -> int {
+    int bits = 0;
+    int r = read_err(cx, &bits);
+    if (r != D2_OK) return r;
+    if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
+    if (bits & d2k::kErrInvalid) return D2_EINVAL;
+    if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
+    return D2_OK;
+  };
+  // 1. every type screens every pair: FP32 value and its bound
+  for (int b = 0; b < B; ++b) {
+    d2_ctx* cb = ctxs[b];
+    if ((rc = stage_bags(cb, &objs[b], kObjOff, kObjLoc, kObjW, &v[b]))) return rc;
+    if ((rc = scan(cb, v[b], &mmax[b]))) return rc;
+    float* pair = static_cast<float*>(grow(cb, kMbPair, (size_t)N * K * 2 * 4, &rc));
+    int* cand = static_cast<int*>(grow(cb, kCand, (size_t)d2k::assign_scratch_ints(N, K, cb->sms) * 4, &rc));
+    int* tl = static_cast<int*>(grow(cb, kMbTmpLab, (size_t)N * 4, &rc));
+    double* td = static_cast<double*>(grow(cb, kMbTmpD2, (size_t)N * 8, &rc));
+    if (rc != D2_OK) return rc;
+    CK(cudaMemsetAsync(cb->d_err, 0, sizeof(int), cb->stream));
+    if ((rc = check_bag_symbols(cb, v[b]))) return rc;
+    SolveCfg cfg = solve_cfg(cb, 1, mmax[b]);  // the FP32 screen, whatever the data type
+    cfg.pair_out = pair;
+    cfg.screen_only = true;
+    CK(d2k::assign(v[b], resident_view(cb), N, K, cfg, nullptr, tl, td, nullptr,
+                   FlowOut{nullptr, nullptr, 0}, cand, cb->d_err, cb->stream));
+    if ((rc = check(cb))) return rc;
+    ms.pair[b] = pair;
+  }
+  // 2. candidates from the summed intervals, listed as pairs
+  long long* cnt = static_cast<long long*>(grow(c, kMbCnt, (size_t)N * 8, &rc));
+  long long* start = static_cast<long long*>(grow(c, kMbStart, (size_t)(N + 1) * 8, &rc));
+  if (rc != D2_OK) return rc;
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CK(d2k::multi_candidates(ms, N, K, cnt, start, c->d_err, c->stream));
+  long long P = 0;
+  CK(cudaMemcpyAsync(&P, start + N, 8, cudaMemcpyDeviceToHost, c->stream));
+  if ((rc = check(c))) return rc;
+  long long* pobj = static_cast<long long*>(grow(c, kMbPObj, (size_t)std::max(P, 1LL) * 8, &rc));
+  long long* pcen = static_cast<long long*>(grow(c, kMbPCen, (size_t)std::max(P, 1LL) * 8, &rc));
+  double* dd = static_cast<double*>(grow(c, kMbD2, (size_t)std::max(P, 1LL) * B * 8, &rc));
+  int* pst = static_cast<int*>(grow(c, kMbSt, (size_t)std::max(P, 1LL) * 4, &rc));
+  if (rc != D2_OK) return rc;
+  CK(d2k::multi_fill(ms, N, K, start, pobj, pcen, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  // 3. every type solves the listed pairs exactly
+  d2k::MultiExact mx{};
+  mx.B = B;
+  for (int b = 0; b < B; ++b) {
+    d2_ctx* cb = ctxs[b];
+    CK(cudaMemsetAsync(cb->d_err, 0, sizeof(int), cb->stream));
+    const SolveCfg cfg = solve_cfg(cb, mode_for(cb, objs[b].loc_dtype), mmax[b]);
+    if (P > 0)
+      CK(d2k::mallows_pairs(v[b], resident_view(cb), pobj, pcen, P, cfg, dd + (size_t)b * P,
+                            FlowOut{nullptr, nullptr, 0}, pst, cb->d_err, cb->stream));
+    if ((rc = check(cb))) return rc;
+    mx.d2[b] = dd + (size_t)b * P;
+  }
+  // 4. labels from the summed exact values
+  int* dl;
+  double* dD;
+  bool h1 = false, h2 = false;
+  if ((rc = stage_out(c, labels, (size_t)N, kOutLab, &dl, &h1))) return rc;
+  if ((rc = stage_out(c, dist2, (size_t)N, kOutD2, &dD, &h2))) return rc;
+  CK(d2k::multi_argmin(N, start, pcen, mx, dl, dD, c->stream));
+  if (h1) CK(cudaMemcpyAsync(labels, dl, (size_t)N * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (h2) CK(cudaMemcpyAsync(dist2, dD, (size_t)N * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return D2_OK;
 }
 

@@ -109,6 +109,11 @@ struct SolveCfg {
   long long nobj = -1;        // entries of oidx (-1: all ob.count objects)
   long long obase = 0;        // first object when oidx is nullptr
   int start = 0;              // cold start basis: 0 ranked northwest staircase, 1 Vogel
+  // per-pair screen output (optional): pair_out[2*(i*K + j)] = FP32 value,
+  // [..+1] = its error bound (+inf when the screen could not bound it, NaN
+  // for an invalid bag); screen_only: no FP64 certification launch
+  float* pair_out = nullptr;
+  bool screen_only = false;
   TileView tile;              // precomputed FP32 tiles of the screen (optional)
 };
 
@@ -153,6 +158,26 @@ D2_NPL_DECL(4)
 // an integer symbol id in [0, A) (d = 1).
 cudaError_t check_symbols(const void* loc, int ldt, long long T, int A, int* d_err,
                           cudaStream_t st);
+
+// ---- combined distance of several bag types (d2_multi.cu) ----
+constexpr int kMaxBagTypes = 8;
+struct MultiScreen {  // per type: the screen's pair values and bounds [N*K*2]
+  const float* pair[kMaxBagTypes];
+  int B;
+};
+struct MultiExact {  // per type: exact D^2 of the listed pairs
+  const double* d2[kMaxBagTypes];
+  int B;
+};
+// Candidate counts per object (cnt [N]) and their offsets (start [N+1]).
+cudaError_t multi_candidates(const MultiScreen& ms, long long N, int K, long long* cnt,
+                             long long* start, int* d_err, cudaStream_t st);
+// The listed pairs (object, centroid), objects in order, centroids increasing.
+cudaError_t multi_fill(const MultiScreen& ms, long long N, int K, const long long* start,
+                       long long* pobj, long long* pcen, cudaStream_t st);
+// Label and summed D^2 of every object from its listed pairs' exact values.
+cudaError_t multi_argmin(long long N, const long long* start, const long long* pcen,
+                         const MultiExact& mx, int* labels, double* dist2, cudaStream_t st);
 
 // ---- initial data segmentation helpers (d2_segment.cu) ----
 // Gather bags members[0..cnt) of v into a compact view: off_out [cnt+1],

@@ -582,6 +582,11 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       const float D = S.template objective<float>();
       float e = D * rel + cmax * 0x1p-14f;
       if constexpr (TC) e += tc_bound(cv.d, nxm, cfg.tile.cn[cb + j], cfg.tile.cd[cb + j]);
+      if (cfg.pair_out && g.lane == 0) {
+        float* po = cfg.pair_out + 2 * (i * (long long)K + j);
+        po[0] = D;
+        po[1] = st != kStOk ? INFINITY : e;
+      }
       const float lo = D - e, hi = D + e;
       if (lo <= best_hi) {
         if (ncand < kCandCap) {
@@ -608,6 +613,8 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
         ncand = k2;
       }
     }
+    if (!ok && cfg.pair_out && g.lane == 0)
+      for (int j = j0; j < j1; ++j) cfg.pair_out[2 * (i * (long long)K + j)] = NAN;
     int* out = items_out + item * kItemInts;
     if (g.lane == 0) {
       out[0] = !ok ? -2 : (all ? -1 : ncand);
@@ -857,6 +864,7 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
       if (e != cudaSuccess) return e;
     }
   }
+  if (screen && cfg.screen_only) return cudaGetLastError();
   e = launch_cfg(k_exact<G, NPL, ST>, smem, gpb * G, cfg.sms, nobj, gpb, &grid);
   if (e != cudaSuccess) return e;
   WarmStore wx = ws;

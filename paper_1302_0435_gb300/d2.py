@@ -27,7 +27,7 @@ EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_st
            "d2_mallows_batch", "d2_assign", "d2_update_locations", "d2_cluster_level",
            "d2_get_stats", "d2_update_locations_noalloc", "d2_server_create", "d2_server_submit",
            "d2_server_poll", "d2_server_stats", "d2_server_destroy", "d2_segment",
-           "d2_set_cost_table"]
+           "d2_set_cost_table", "d2_assign_multi"]
 
 
 class D2Bags(ctypes.Structure):
@@ -92,6 +92,7 @@ def load(path=None):
     lib.d2_get_stats.argtypes = [ctypes.POINTER(D2Stats)]
     lib.d2_segment.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i64, i32, vp, ctypes.POINTER(i64)]
     lib.d2_set_cost_table.argtypes = [vp, vp, i32]
+    lib.d2_assign_multi.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(D2Bags), vp, vp]
     lib.d2_server_create.argtypes = [ctypes.POINTER(vp), vp, i32, i64]
     lib.d2_server_submit.argtypes = [vp, ctypes.POINTER(D2Bags), ctypes.POINTER(i64)]
     lib.d2_server_poll.argtypes = [vp, i64, vp, vp, ctypes.POINTER(ctypes.c_double), i32]
@@ -281,6 +282,18 @@ def d2_set_cost_table(ctx, table):
         table = np.ascontiguousarray(table, dtype=np.float64)
     A = int(table.shape[0])
     _check(load().d2_set_cost_table(ctx.h, _ptr(table), A), "d2_set_cost_table")
+
+
+def d2_assign_multi(ctxs, objs_list, labels, dist2):
+    """Combined distance of several bag types: ctxs[b] holds type b's
+    centroids, objs_list[b] type b's bags (BagsRef)."""
+    B = len(ctxs)
+    hs = (ctypes.c_void_p * B)(*[c.h for c in ctxs])
+    bags = (D2Bags * B)(*[o.s for o in objs_list])
+    rc = load().d2_assign_multi(hs, B, bags, _ptr(labels), _ptr(dist2))
+    if rc not in (D2_OK, D2_ENOTCONVERGED):
+        _check(rc, "d2_assign_multi")
+    return rc
 
 
 def d2_segment(ctx, objs, tau, iters, omega=None, seg_id=None):

@@ -14,13 +14,17 @@ Contents (each function cites the passage it follows):
                      Eq. (UpdateLabel), Eq. (UpdateGlobalLabel) and the
                      weight rule of the weighted D2-clustering section.
   cluster_level      Alg. 3 levels with the segment-wise Alg. 2 loop.
+  joint_lp, update_weights
+                     Alg. 1 Step 1: the LP of Eq. (WeightedD2) over the
+                     centroid weights and all flows of a cluster (HiGHS).
 
 Bags are passed as any object with attributes ``loc`` ([T, d] array),
 ``w`` ([T]) and ``off`` ([N+1] int64, bag b = rows off[b]:off[b+1]).
 Every function converts to float64 first.
 
-Parity pins for every function live in tests/test_oracle_pins.py and
-tests/test_oracle_update_level.py; no function here is "parity unpinned".
+Parity pins for every function live in tests/test_oracle_*.py (the joint
+LP of Alg. 1 Step 1 in tests/test_oracle_joint.py); no function here is
+"parity unpinned".
 """
 import ctypes
 import math
@@ -419,6 +423,84 @@ def segment(objs, omega, tau, iters, nthreads=1):
     for new_id, k in enumerate(order):
         seg_id[segs[k]] = new_id
     return seg_id, len(segs)
+
+
+def joint_lp(costs, qs, omega):
+    """Alg. 1 Step 1 for one cluster: with the support locations z^(r) fixed,
+    minimise Eq. (WeightedD2), sum_i omega_i sum_{r,a} c^(i)_{ra} w^(i)_{ra},
+    over the centroid weights p_z and every member's flows w^(i), under the
+    constraints of Eq. (D2opt): sum_r p_r = 1, sum_a w^(i)_{ra} = p_r for
+    every member i and support r, sum_r w^(i)_{ra} = q^(i)_a, p, w >= 0.
+    The LP is written out whole (variables p first, then each member's
+    w^(i) row-major in (r, a)) and handed to a library dual simplex (HiGHS
+    through scipy) at tight tolerances.  costs[i]: [s', t_i] array of
+    c^(i)_{ra}; qs[i]: member i's normalised weights; omega: [n'].
+    Returns (epsilon, p) with p clamped at 0."""
+    from scipy.optimize import linprog
+    from scipy.sparse import coo_matrix
+    s = costs[0].shape[0]
+    nvar = s + sum(c.size for c in costs)
+    obj = np.zeros(nvar)
+    ri, ci, vals, rhs = [], [], [], []
+    row = 0
+    ri += [0] * s
+    ci += list(range(s))
+    vals += [1.0] * s
+    rhs.append(1.0)
+    row = 1
+    col = s
+    for c, q, om in zip(costs, qs, omega):
+        c = np.asarray(c, dtype=np.float64)
+        t = c.shape[1]
+        obj[col:col + c.size] = om * c.ravel()
+        for r in range(s):                       # sum_a w_ra - p_r = 0
+            ri += [row] * (t + 1)
+            ci += list(range(col + r * t, col + (r + 1) * t)) + [r]
+            vals += [1.0] * t + [-1.0]
+            rhs.append(0.0)
+            row += 1
+        for a in range(t):                       # sum_r w_ra = q_a
+            ri += [row] * s
+            ci += list(range(col + a, col + c.size, t))
+            vals += [1.0] * s
+            rhs.append(float(q[a]))
+            row += 1
+        col += c.size
+    A = coo_matrix((vals, (ri, ci)), shape=(row, nvar)).tocsr()
+    res = linprog(obj, A_eq=A, b_eq=np.array(rhs), bounds=(0, None), method="highs-ds",
+                  options=dict(primal_feasibility_tolerance=1e-10,
+                               dual_feasibility_tolerance=1e-10))
+    if res.status != 0:
+        raise RuntimeError("joint LP: " + res.message)
+    return float(res.fun), np.maximum(res.x[:s], 0.0)
+
+
+def update_weights(objs, omega, labels, cents):
+    """Alg. 1 Step 1 for every cluster (Eq. (WeightedD2) under the
+    constraints of Eq. (D2opt)): the new centroid weights p_z of each
+    centroid j, from its members i with C(i) = j, with the supports of z_j
+    fixed.  Empty clusters keep their weights and get epsilon 0.  Returns
+    (weights [sum n_j] float64, epsilon [K])."""
+    xl, xw, xo = _bag_arrays(objs)
+    yl, yw, yo = _bag_arrays(cents)
+    N = xo.size - 1
+    K = yo.size - 1
+    om = np.ones(N) if omega is None else _f64(omega)
+    lab = np.asarray(labels, dtype=np.int64)
+    wout = yw.copy()
+    eps = np.zeros(K)
+    for j in range(K):
+        mem = np.nonzero(lab == j)[0]
+        if mem.size == 0:
+            continue
+        z = yl[yo[j]:yo[j + 1]]
+        cs, qs = [], []
+        for i in mem:
+            x = xl[xo[i]:xo[i + 1]]
+            cs.append(cost(z, x))
+            qs.append(normalise(xw[xo[i]:xo[i + 1]]))
+        eps[j], wout[yo[j]:yo[j + 1]] = joint_lp(cs, qs, om[mem])
+    return wout, eps
 
 
 def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, nthreads=1,

@@ -92,6 +92,7 @@ extern "C" {
 /* Limits of the current kernels. */
 #define D2_MAX_SUPPORT 64   /* supports per bag (objects and centroids) */
 #define D2_MAX_DIM 256      /* vector dimension d */
+#define D2_JOINT_MAX_ITER 4096  /* rounds of d2_update_weights */
 
 /*
  * A ragged batch of bags in CSR form.  Bag b owns supports
@@ -235,6 +236,36 @@ int d2_assign(d2_ctx* ctx, const d2_bags* objs, const double* omega, int32_t* la
  */
 int d2_update_locations(d2_ctx* ctx, const d2_bags* objs, const double* omega,
                         const int32_t* labels, const d2_flows* flows);
+
+/*
+ * Centroid weights of Alg. 1 Step 1: for every cluster j, with the support
+ * locations z_j^(r) fixed, the weights p_j and all member flows that solve
+ * the joint LP of Eq. (WeightedD2) under the constraints of Eq. (D2opt)
+ * (omega NULL = 1):
+ *     min_{p_j, w} sum_{i:C(i)=j} omega_i sum_{r,a} w^(i)_{r,a} c(z_j^(r), v_i^(a))
+ *     s.t. sum_r p_jr = 1, sum_a w^(i)_{r,a} = p_jr, sum_r w^(i)_{r,a} = q_i^(a), p, w >= 0.
+ * Replaces the resident centroid weights by the optimal p_j (d2_get_centroids
+ * reads them back).  Given p_j the LP separates into the members' own
+ * transportation LPs, so a following d2_update_locations (Alg. 1 Step 2,
+ * Eq. (WeightedUpdate)) with the same labels moves the supports with
+ * optimal flows of the joint LP.  Method: exact member solves give one
+ * supporting cut of the objective per round (LP duality), and Kelley's
+ * cutting-plane rounds choose the next p_j; a cluster stops when its best
+ * objective and the cut model's lower bound agree within relative gap `tol`
+ * (e.g. 1e-9), or after max_iter rounds (1..D2_JOINT_MAX_ITER) with the best
+ * weights found.  labels: [count] cluster of every object (host or device;
+ * labels outside [0, K) are ignored).  eps_out [K] (may be NULL): the
+ * objective of Eq. (WeightedD2) at the new weights; iters_out [K] (may be
+ * NULL): rounds used (0 for an empty cluster, whose weights are kept).
+ * Works with a symbol cost table too (weights move, supports do not).
+ * Device memory: about K * max_iter * (n_max + 1) doubles of cuts.
+ * Returns D2_ENOTCONVERGED if any cluster was not certified within
+ * max_iter rounds (its weights are still the best found), D2_EUNSUPPORTED
+ * for centroids of more than 64 supports.
+ */
+int d2_update_weights(d2_ctx* ctx, const d2_bags* objs, const double* omega,
+                      const int32_t* labels, int32_t max_iter, double tol, double* eps_out,
+                      int32_t* iters_out);
 
 /*
  * Nearest centroid under the combined distance of several bag types

@@ -35,6 +35,8 @@ enum Slot {
   kSgLab, kSgD2, kSgCell, kSgFw, kSgUpd, kSgCand, kSgOut, kLvSegof, kSgPart, kUpdPart, kLvPart,
   // combined distance of several bag types
   kMbPair, kMbTmpLab, kMbTmpD2, kMbCnt, kMbStart, kMbPObj, kMbPCen, kMbD2, kMbSt,
+  // joint weights (Alg. 1 Step 1)
+  kJState, kJPot, kJPStart, kJEps, kJIters,
   kSlots
 };
 
@@ -1087,6 +1089,99 @@ int d2_update_locations(d2_ctx* c, const d2_bags* objs, const double* omega, con
   if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
   if (bits & d2k::kErrInvalid) return D2_EINVAL;
   if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
+  return D2_OK;
+}
+
+int d2_update_weights(d2_ctx* c, const d2_bags* objs, const double* omega, const int32_t* labels,
+                      int32_t max_iter, double tol, double* eps_out, int32_t* iters_out) {
+  if (!c || !bags_ok(objs) || !labels || max_iter < 1 || max_iter > D2_JOINT_MAX_ITER ||
+      !(tol >= 0.0 && tol < 1.0))
+    return D2_EINVAL;
+  if (c->K == 0) return D2_ENOCENTROIDS;
+  if (objs->dim != c->d) return D2_EINVAL;
+  if (c->nmax > d2k::kMaxJointN) return D2_EUNSUPPORTED;
+  cudaSetDevice(c->device);
+  const long long N = objs->count, K = c->K;
+  int rc = D2_OK;
+  ObjView v;
+  if ((rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v))) return rc;
+  int mmax = 0;
+  if ((rc = scan(c, v, &mmax))) return rc;
+  if ((rc = check_bag_symbols(c, v))) return rc;
+  const double* om;
+  const int* dl;
+  if ((rc = stage_in(c, omega, (size_t)N, kOmega, &om))) return rc;
+  if ((rc = stage_in(c, labels, (size_t)N, kLabelsIn, &dl))) return rc;
+  double* eps_d;
+  int* it_d;
+  bool eps_h, it_h;
+  if ((rc = stage_out(c, eps_out, (size_t)K, kJEps, &eps_d, &eps_h)) ||
+      (rc = stage_out(c, reinterpret_cast<int*>(iters_out), (size_t)K, kJIters, &it_d, &it_h)))
+    return rc;
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  // members of every cluster, increasing object index
+  void* scr = grow(c, kUpd, d2k::update_scratch_bytes(std::max(N, 1LL), K), &rc);
+  const int nmax = std::max(c->nmax, 1);
+  const int itmax = max_iter;
+  void* jmem = grow(c, kJState, d2k::joint_state_bytes(K, c->Tc, nmax, itmax), &rc);
+  long long* pobj = static_cast<long long*>(grow(c, kPairObj, (size_t)std::max(N, 1LL) * 8, &rc));
+  long long* pcen = static_cast<long long*>(grow(c, kPairCen, (size_t)std::max(N, 1LL) * 8, &rc));
+  double* W = static_cast<double*>(grow(c, kOutD2, (size_t)std::max(N, 1LL) * 8, &rc));
+  int* pst = static_cast<int*>(grow(c, kOutStatus, (size_t)std::max(N, 1LL) * 4, &rc));
+  double* pot = static_cast<double*>(grow(c, kJPot, (size_t)std::max(N, 1LL) * nmax * 8, &rc));
+  long long* pstart = static_cast<long long*>(grow(c, kJPStart, (size_t)(K + 1) * 8, &rc));
+  if (rc != D2_OK) return rc;
+  const long long* start;
+  const int* order;
+  if (N > 0) {
+    FlowOut none{nullptr, nullptr, 0};
+    CK(d2k::update_locations(v, nullptr, dl, N, (int)K, none, K, c->c_off, c->d, c->cent_ldt,
+                             c->c_loc32, c->c_loc64, scr, c->stream));
+    d2k::sorted_groups(scr, N, K, &start, &order);
+  } else {
+    long long* z = static_cast<long long*>(scr);  // no members: start = 0
+    CK(cudaMemsetAsync(z, 0, (size_t)(K + 1) * 8, c->stream));
+    start = z;
+    order = nullptr;
+  }
+  d2k::JointView jv = d2k::joint_view(jmem, K, c->Tc, nmax, itmax, tol);
+  CK(d2k::joint_init(jv, start, c->c_off, c->c_w64, c->stream));
+  SolveCfg cfg = solve_cfg(c, mode_for(c, v.ldt), mmax);
+  FlowOut fo{nullptr, nullptr, 0};
+  fo.pot = pot;
+  fo.pstride = nmax;
+  const CentView cv = resident_view(c);
+  long long* hP = reinterpret_cast<long long*>(c->h_pin + 4);
+  for (int it = 0; it < itmax; ++it) {
+    if (it > 0)  // the weights chosen by the last master solve
+      CK(d2k::prep_centroids(c->c_loc64, D2_F64, jv.wnext, D2_F64, c->c_off, K, c->d, c->c_loc32,
+                             c->c_loc64, c->c_Q, c->c_w64, c->d_err, c->stream));
+    CK(d2k::joint_list(jv, order, start, pstart, pobj, pcen, c->stream));
+    CK(cudaMemcpyAsync(hP, pstart + K, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const long long P = *hP;
+    if (P == 0) break;
+    CK(d2k::mallows_pairs(v, cv, pobj, pcen, P, cfg, W, fo, pst, c->d_err, c->stream));
+    CK(d2k::joint_round(jv, pstart, pobj, om, W, pot, nmax, pst, c->c_off, c->c_w64, c->stream));
+  }
+  int* jst = reinterpret_cast<int*>(pst);  // per-cluster status, reusing the pair status room
+  if ((size_t)std::max(N, 1LL) < (size_t)K) {
+    jst = static_cast<int*>(grow(c, kOutStatus, (size_t)K * 4, &rc));
+    if (rc != D2_OK) return rc;
+  }
+  CK(d2k::joint_finish(jv, c->c_off, eps_d, it_d, jst, c->stream));
+  CK(d2k::prep_centroids(c->c_loc64, D2_F64, jv.wnext, D2_F64, c->c_off, K, c->d, c->c_loc32,
+                         c->c_loc64, c->c_Q, c->c_w64, c->d_err, c->stream));
+  if (eps_h) CK(cudaMemcpyAsync(eps_out, eps_d, (size_t)K * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (it_h) CK(cudaMemcpyAsync(iters_out, it_d, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<int> hs((size_t)K);
+  CK(cudaMemcpyAsync(hs.data(), jst, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
+  int bits = 0;
+  if ((rc = read_err(c, &bits))) return rc;
+  if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
+  if (bits & d2k::kErrInvalid) return D2_EINVAL;
+  for (int s : hs)
+    if (s == 2 || s == 4) return D2_ENOTCONVERGED;
   return D2_OK;
 }
 

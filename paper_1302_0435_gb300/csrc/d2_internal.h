@@ -42,6 +42,11 @@ struct FlowOut {
   int* cell;
   double* w;
   long long stride;
+  // optional (mallows_pairs only): the FP64 potentials of the centroid
+  // supports of each solved pair, pot[t*pstride + r], from the final basis
+  // (c(a, r) - u_a - v_r >= 0 on every cell, = 0 on the basis)
+  double* pot = nullptr;
+  long long pstride = 0;
 };
 
 // Saved optimal bases of every (object, centroid) pair of an assign call,
@@ -252,6 +257,50 @@ cudaError_t update_locations(const ObjView& ob, const double* omega, const int* 
                              const long long* coff, int d, int cent_ldt, float* loc32,
                              double* loc64, void* scratch, cudaStream_t st,
                              double* part = nullptr, size_t part_bytes = 0);
+
+// After update_locations with fo.cell == nullptr (the sort only): the
+// members of group g are order[start[g] .. start[g+1]), increasing index.
+void sorted_groups(void* scratch, long long N, long long KT, const long long** start,
+                   const int** order);
+
+// Alg. 1 Step 1 (d2_joint.cu): per-cluster state of the cutting-plane
+// solve of the joint LP of Eq. (WeightedD2).  Cuts per unit of the
+// cluster's total omega: cutA [K][itmax][nmax], cutB [K][itmax].
+constexpr int kMaxJointN = 64;
+struct JointView {
+  double* cutA;
+  double* cutB;
+  int* bvar;        // [K][nmax+1] optimal basis of each cluster's master LP
+  int* nk;          // [K] cuts so far
+  int* status;      // [K] 0 active, 1 certified, 2 round cap, 3 empty, 4 failed
+  double* F;        // [K] F at this round's weights, per unit omega
+  double* ub;       // [K] best F seen
+  double* lb;       // [K] the master's lower bound
+  double* omsum;    // [K] total omega of the cluster
+  double* scale;    // [K] master scaling
+  double* pbest;    // [Tc] weights of the best F
+  double* wnext;    // [Tc] weights for the next round (final: the result)
+  unsigned long long* pivots;  // master pivots, summed
+  long long K;
+  int itmax;
+  int nmax;
+  double tol;
+};
+size_t joint_state_bytes(long long K, long long Tc, int nmax, int itmax);
+JointView joint_view(void* mem, long long K, long long Tc, int nmax, int itmax, double tol);
+cudaError_t joint_init(const JointView& jv, const long long* start, const long long* coff,
+                       const double* w64, cudaStream_t st);
+// pair list (object, cluster) of the active clusters; pstart [K+1]
+cudaError_t joint_list(const JointView& jv, const int* order, const long long* start,
+                       long long* pstart, long long* pobj, long long* pcen, cudaStream_t st);
+// cut of this round from the member solves (W, potentials, status per pair),
+// then one master solve per active cluster: next weights into wnext
+cudaError_t joint_round(const JointView& jv, const long long* pstart, const long long* pobj,
+                        const double* omega, const double* W, const double* pot,
+                        long long pstride, const int* pst, const long long* coff,
+                        const double* w64, cudaStream_t st);
+cudaError_t joint_finish(const JointView& jv, const long long* coff, double* eps, int* iters,
+                         int* status, cudaStream_t st);
 
 // After update_locations (or update_locations with fo.cell == nullptr, which
 // only sorts): per centroid sum of omega over its members, object order.

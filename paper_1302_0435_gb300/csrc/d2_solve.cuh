@@ -419,6 +419,8 @@ __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
           ++n_pairs;
           if (fo.cell && st != kStInvalid)
             S.write_flows(fo.cell + t * fo.stride, fo.w + t * fo.stride, fo.stride);
+          if (fo.pot && st == kStOk)  // potentials of the final, freshly priced basis
+            for (int r = g.lane; r < n; r += G) fo.pot[t * fo.pstride + r] = s64.pot[m + r];
         }
       }
     }

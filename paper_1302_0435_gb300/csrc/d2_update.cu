@@ -316,6 +316,16 @@ cudaError_t update_locations(const ObjView& ob, const double* omega, const int* 
   return cudaGetLastError();
 }
 
+void sorted_groups(void* scratch, long long N, long long KT, const long long** start,
+                   const int** order) {
+  const long long nchunks = (N + kChunk - 1) / kChunk;
+  unsigned char* p = static_cast<unsigned char*>(scratch);
+  p += al((size_t)nchunks * KT * 4);
+  p += al((size_t)(KT + 1) * 8);
+  *start = reinterpret_cast<const long long*>(p); p += al((size_t)(KT + 1) * 8);
+  *order = reinterpret_cast<const int*>(p);
+}
+
 cudaError_t group_weight_sum(const double* omega, long long N, long long KT, void* scratch,
                              double* out, cudaStream_t st) {
   const long long nchunks = (N + kChunk - 1) / kChunk;

@@ -27,7 +27,7 @@ EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_st
            "d2_mallows_batch", "d2_assign", "d2_update_locations", "d2_cluster_level",
            "d2_get_stats", "d2_update_locations_noalloc", "d2_server_create", "d2_server_submit",
            "d2_server_poll", "d2_server_stats", "d2_server_destroy", "d2_segment",
-           "d2_set_cost_table", "d2_assign_multi"]
+           "d2_set_cost_table", "d2_assign_multi", "d2_update_weights"]
 
 
 class D2Bags(ctypes.Structure):
@@ -93,6 +93,8 @@ def load(path=None):
     lib.d2_segment.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i64, i32, vp, ctypes.POINTER(i64)]
     lib.d2_set_cost_table.argtypes = [vp, vp, i32]
     lib.d2_assign_multi.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(D2Bags), vp, vp]
+    lib.d2_update_weights.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, i32, ctypes.c_double,
+                                      vp, vp]
     lib.d2_server_create.argtypes = [ctypes.POINTER(vp), vp, i32, i64]
     lib.d2_server_submit.argtypes = [vp, ctypes.POINTER(D2Bags), ctypes.POINTER(i64)]
     lib.d2_server_poll.argtypes = [vp, i64, vp, vp, ctypes.POINTER(ctypes.c_double), i32]
@@ -262,6 +264,19 @@ def d2_update_locations(ctx, objs, labels, omega=None, flows=None):
                                     ctypes.byref(f) if f else None)
     if rc not in (D2_OK, D2_ENOTCONVERGED):
         _check(rc, "d2_update_locations")
+    return rc
+
+
+def d2_update_weights(ctx, objs, labels, max_iter=512, tol=1e-9, omega=None, eps=None,
+                      iters=None):
+    """Alg. 1 Step 1: resident centroid weights from the joint LP of
+    Eq. (WeightedD2).  eps [K] float64 / iters [K] int32 outputs are
+    optional.  Returns D2_OK, or D2_ENOTCONVERGED if a cluster was not
+    certified within max_iter rounds."""
+    rc = load().d2_update_weights(ctx.h, ctypes.byref(objs.s), _ptr(omega), _ptr(labels),
+                                  int(max_iter), float(tol), _ptr(eps), _ptr(iters))
+    if rc not in (D2_OK, D2_ENOTCONVERGED):
+        _check(rc, "d2_update_weights")
     return rc
 
 

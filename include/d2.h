@@ -392,7 +392,9 @@ int d2_update_locations_noalloc(const d2_bags* objs, const double* omega, const 
  * Counters of this process's library activity (diagnostics, not a paper
  * quantity), monotonic since library load: kernels launched; pair LPs
  * solved on the FP32 screening path and their simplex pivots; pair LPs
- * solved to FP64 optimality and their pivots (FP32 warm start + FP64).
+ * solved to FP64 optimality and their pivots (FP32 warm start + FP64);
+ * cutting-plane rounds of d2_update_weights (summed over calls) and the
+ * pivots of its per-cluster master LPs.
  * Reading the device counters synchronises the current device.
  */
 typedef struct {
@@ -401,7 +403,9 @@ typedef struct {
     int64_t pivots_screened;
     int64_t pairs_exact;
     int64_t pivots_exact;
-    int64_t reserved[3];
+    int64_t joint_rounds;
+    int64_t joint_master_pivots;
+    int64_t reserved[1];
 } d2_stats;
 int d2_get_stats(d2_stats* out);
 

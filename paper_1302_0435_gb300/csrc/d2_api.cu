@@ -1123,7 +1123,8 @@ int d2_update_weights(d2_ctx* c, const d2_bags* objs, const double* omega, const
   void* scr = grow(c, kUpd, d2k::update_scratch_bytes(std::max(N, 1LL), K), &rc);
   const int nmax = std::max(c->nmax, 1);
   const int itmax = max_iter;
-  void* jmem = grow(c, kJState, d2k::joint_state_bytes(K, c->Tc, nmax, itmax), &rc);
+  const int G = d2k::joint_groups(nmax);
+  void* jmem = grow(c, kJState, d2k::joint_state_bytes(K, c->Tc, nmax, itmax, G), &rc);
   long long* pobj = static_cast<long long*>(grow(c, kPairObj, (size_t)std::max(N, 1LL) * 8, &rc));
   long long* pcen = static_cast<long long*>(grow(c, kPairCen, (size_t)std::max(N, 1LL) * 8, &rc));
   double* W = static_cast<double*>(grow(c, kOutD2, (size_t)std::max(N, 1LL) * 8, &rc));
@@ -1144,7 +1145,7 @@ int d2_update_weights(d2_ctx* c, const d2_bags* objs, const double* omega, const
     start = z;
     order = nullptr;
   }
-  d2k::JointView jv = d2k::joint_view(jmem, K, c->Tc, nmax, itmax, tol);
+  d2k::JointView jv = d2k::joint_view(jmem, K, c->Tc, nmax, itmax, G, tol);
   CK(d2k::joint_init(jv, start, c->c_off, c->c_w64, c->stream));
   SolveCfg cfg = solve_cfg(c, mode_for(c, v.ldt), mmax);
   FlowOut fo{nullptr, nullptr, 0};
@@ -1163,6 +1164,7 @@ int d2_update_weights(d2_ctx* c, const d2_bags* objs, const double* omega, const
     if (P == 0) break;
     CK(d2k::mallows_pairs(v, cv, pobj, pcen, P, cfg, W, fo, pst, c->d_err, c->stream));
     CK(d2k::joint_round(jv, pstart, pobj, om, W, pot, nmax, pst, c->c_off, c->c_w64, c->stream));
+    d2k::joint_note(1, 0);
   }
   int* jst = reinterpret_cast<int*>(pst);  // per-cluster status, reusing the pair status room
   if ((size_t)std::max(N, 1LL) < (size_t)K) {
@@ -1170,6 +1172,10 @@ int d2_update_weights(d2_ctx* c, const d2_bags* objs, const double* omega, const
     if (rc != D2_OK) return rc;
   }
   CK(d2k::joint_finish(jv, c->c_off, eps_d, it_d, jst, c->stream));
+  unsigned long long* hpiv = reinterpret_cast<unsigned long long*>(c->h_pin + 4);
+  CK(cudaMemcpyAsync(hpiv, jv.pivots, 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  d2k::joint_note(0, (long long)*hpiv);
   CK(d2k::prep_centroids(c->c_loc64, D2_F64, jv.wnext, D2_F64, c->c_off, K, c->d, c->c_loc32,
                          c->c_loc64, c->c_Q, c->c_w64, c->d_err, c->stream));
   if (eps_h) CK(cudaMemcpyAsync(eps_out, eps_d, (size_t)K * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -1506,6 +1512,7 @@ int d2_get_stats(d2_stats* out) {
   if (!out) return D2_EINVAL;
   std::memset(out, 0, sizeof(*out));
   out->kernel_launches = d2k::launches();
+  d2k::joint_counters(&out->joint_rounds, &out->joint_master_pivots);
   long long v[4];
   if (d2k::solver_stats(v) == cudaSuccess) {
     out->pairs_screened = v[0];

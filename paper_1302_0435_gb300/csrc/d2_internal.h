@@ -265,12 +265,33 @@ void sorted_groups(void* scratch, long long N, long long KT, const long long** s
 
 // Alg. 1 Step 1 (d2_joint.cu): per-cluster state of the cutting-plane
 // solve of the joint LP of Eq. (WeightedD2).  Cuts per unit of the
-// cluster's total omega: cutA [K][itmax][nmax], cutB [K][itmax].
+// cluster's total omega, G member groups per round:
+// cutA [K][itmax][G][nmax], cutB [K][itmax][G].
 constexpr int kMaxJointN = 64;
+constexpr int kMaxJointR = 80;  // master rows: groups + supports (shared memory)
+// Target master size: more groups mean fewer cutting-plane rounds but a
+// costlier FP64 master per round (200,000 image-like bags in 64 clusters of
+// 16 supports: 16 / 32 / 64 groups take 120 / 86 / 60 rounds and 0.96 /
+// 0.83 / 0.95 s).
+#ifndef D2_JOINT_RTARGET
+#define D2_JOINT_RTARGET 48
+#endif
+// Cut groups for centroids of up to nmax supports: a power of two dividing
+// 128, at most 64, with groups + nmax <= max(target, nmax + 16), within
+// kMaxJointR.
+inline int joint_groups(int nmax) {
+  int cap = D2_JOINT_RTARGET > nmax + 16 ? D2_JOINT_RTARGET : nmax + 16;
+  if (cap > kMaxJointR) cap = kMaxJointR;
+  int G = 64;
+  while (G > 1 && G + nmax > cap) G >>= 1;
+  return G;
+}
 struct JointView {
   double* cutA;
   double* cutB;
-  int* bvar;        // [K][nmax+1] optimal basis of each cluster's master LP
+  int* bvar;        // [K][G+nmax] optimal basis of each cluster's master LP
+  double* binv;     // [K][(G+nmax)^2] its inverse, kept between rounds
+  int* since;       // [K] pivots since that inverse was last refactored
   int* nk;          // [K] cuts so far
   int* status;      // [K] 0 active, 1 certified, 2 round cap, 3 empty, 4 failed
   double* F;        // [K] F at this round's weights, per unit omega
@@ -284,10 +305,12 @@ struct JointView {
   long long K;
   int itmax;
   int nmax;
+  int G;
   double tol;
 };
-size_t joint_state_bytes(long long K, long long Tc, int nmax, int itmax);
-JointView joint_view(void* mem, long long K, long long Tc, int nmax, int itmax, double tol);
+size_t joint_state_bytes(long long K, long long Tc, int nmax, int itmax, int G);
+JointView joint_view(void* mem, long long K, long long Tc, int nmax, int itmax, int G,
+                     double tol);
 cudaError_t joint_init(const JointView& jv, const long long* start, const long long* coff,
                        const double* w64, cudaStream_t st);
 // pair list (object, cluster) of the active clusters; pstart [K+1]
@@ -301,6 +324,9 @@ cudaError_t joint_round(const JointView& jv, const long long* pstart, const long
                         const double* w64, cudaStream_t st);
 cudaError_t joint_finish(const JointView& jv, const long long* coff, double* eps, int* iters,
                          int* status, cudaStream_t st);
+// process-wide counters of d2_update_weights: rounds and master pivots
+void joint_note(long long rounds, long long pivots);
+void joint_counters(int64_t* rounds, int64_t* pivots);
 
 // After update_locations (or update_locations with fo.cell == nullptr, which
 // only sorts): per centroid sum of omega over its members, object order.

@@ -10,16 +10,22 @@
 // W_i(p') >= q_i.u + p'.v for every p' (with equality at the solved p).  So
 // one round of member solves yields one supporting cut of F:
 //   F(p') >= a.p' + b,  a = sum_i omega_i v_i,  b = sum_i omega_i (W_i - p.v_i).
-// The rounds follow Kelley's cutting-plane method: the next p minimises the
-// largest cut over the simplex, a small LP solved here per cluster by a
-// revised primal simplex on its dual, where each new cut enters as a new
-// column and the previous optimal basis stays feasible.  The model minimum
-// is a lower bound of min F, the best F seen an upper bound; a cluster stops
-// when the two agree to the requested relative gap, and keeps the weights of
-// the upper bound.  Cuts are stored per unit of the cluster's total omega.
+// The members are dealt round-robin (in increasing object order) into G
+// groups, and each group's sum gets its own cut, F_g(p') >= a_g.p' + b_g,
+// so the model of F = sum_g F_g is far tighter than one aggregate cut per
+// round (Kelley's cutting-plane method with disaggregated cuts).  The next
+// p minimises sum_g max_k (a_gk.p + b_gk) over the simplex, a small LP
+// solved per cluster by a revised primal simplex on its dual, where the
+// new cuts enter as new columns and the previous optimal basis stays
+// feasible.  The model minimum is a lower bound of min F, the best F seen
+// an upper bound; a cluster stops when the two agree to the requested
+// relative gap, and keeps the weights of the upper bound.  Cuts are stored
+// per unit of the cluster's total omega.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cfloat>
+#include <climits>
 #include <cmath>
 
 #include "d2_internal.h"
@@ -102,10 +108,12 @@ __global__ void k_joint_fill(const int* order, const long long* start, const int
   }
 }
 
-// One block per active cluster: the cut of this round and F at its p.  Each
-// thread sums a fixed stride of the members into its own shared row, then
-// column c is summed over the rows in order (deterministic).  Row layout:
-// a_0..a_{n-1}, F, b, omega.
+// One block per active cluster: this round's G group cuts and F at its p.
+// Member t of the cluster (sorted order) belongs to group t % G, and G
+// divides the block size, so every thread's members lie in one group.
+// Each thread sums its members into its own shared row, then column c of
+// group g is summed over that group's rows in thread order
+// (deterministic).  Row layout: a_0..a_{n-1}, F, b, omega.
 __global__ void k_joint_cut(JointView jv, const long long* pstart, const long long* pobj,
                             const double* omega, const double* W, const double* pot,
                             long long pstride, const int* pst, const long long* coff,
@@ -116,6 +124,7 @@ __global__ void k_joint_cut(JointView jv, const long long* pstart, const long lo
   const long long c0 = coff[j];
   const int n = (int)(coff[j + 1] - c0);
   const int cols = n + 3;
+  const int G = jv.G;
   double* my = rows + (size_t)threadIdx.x * cols;
   for (int c = 0; c < cols; ++c) my[c] = 0.0;
   int bad = 0;
@@ -139,48 +148,63 @@ __global__ void k_joint_cut(JointView jv, const long long* pstart, const long lo
     if (threadIdx.x == 0) jv.status[j] = kJFail;
     return;
   }
-  __shared__ double tot[kMaxJointN + 3];
-  for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < (int)blockDim.x; ++k) s += rows[(size_t)k * cols + c];
-    tot[c] = s;
+  // totals of the cluster (F, omega) first: every row in order
+  __shared__ double tot_s[2];
+  if (threadIdx.x < 2) {
+    const int c = n + (threadIdx.x == 0 ? 0 : 2);
+    double acc = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) acc += rows[(size_t)k * cols + c];
+    tot_s[threadIdx.x] = acc;
   }
   __syncthreads();
-  const double Om = tot[n + 2];
+  const double Om = tot_s[1];
   const int kk = jv.nk[j];
-  double* a = jv.cutA + ((size_t)j * jv.itmax + kk) * jv.nmax;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) a[r] = tot[r] / Om;
+  const int per = (int)blockDim.x / G;  // rows of a group: threads g, g+G, ...
+  for (int e = threadIdx.x; e < G * (n + 1); e += blockDim.x) {
+    const int g = e / (n + 1), c = e - g * (n + 1);
+    const int col = c < n ? c : n + 1;  // a_r, then b
+    double acc = 0.0;
+    for (int k = 0; k < per; ++k) acc += rows[(size_t)(g + k * G) * cols + col];
+    if (c < n) jv.cutA[(((size_t)j * jv.itmax + kk) * G + g) * jv.nmax + c] = acc / Om;
+    else jv.cutB[((size_t)j * jv.itmax + kk) * G + g] = acc / Om;
+  }
   if (threadIdx.x == 0) {
-    jv.cutB[(size_t)j * jv.itmax + kk] = tot[n + 1] / Om;
-    jv.F[j] = tot[n] / Om;
+    jv.F[j] = tot_s[0] / Om;
     jv.omsum[j] = Om;
   }
 }
 
 // ---- the master LP -----------------------------------------------------
-// Model: min theta s.t. theta >= a_k.p + b_k (k < nk), sum p = 1, p >= 0.
-// Solved through its dual, with R = n + 1 rows:
-//   max sum_k b_k mu_k + nu
-//   s.t. sum_k mu_k = 1                              (row 0)
-//        nu - sum_k a_kr mu_k + sigma_r = 0          (row 1 + r)
+// Model: min sum_g theta_g s.t. theta_g >= a_gk.p + b_gk (every round k < nk
+// and group g), sum p = 1, p >= 0.  Solved through its dual, with
+// R = G + n rows:
+//   max sum_{k,g} b_gk mu_gk + nu
+//   s.t. sum_k mu_gk = 1                              (row g < G)
+//        nu - sum_{k,g} a_gk,r mu_gk + sigma_r = 0    (row G + r)
 //        mu, sigma >= 0, nu free (always basic).
-// The simplex multipliers of the optimal basis are (theta, p).  Variable ids:
-// mu_k = k, sigma_r = kSig + r, nu = kNu.  Cuts enter scaled by 1/S (S: the
-// largest entry of the first cut) so the matrix entries are O(1).
-constexpr int kSig = 1 << 20;
+// The simplex multipliers of the optimal basis are (theta_g, p).  Variable
+// ids: mu_gk = k*G + g, sigma_r = kSig + r, nu = kNu.  Cuts enter scaled by
+// 1/S (S: the largest entry of the first round's cuts) so the matrix
+// entries are O(1).  The basis and its inverse carry over from round to
+// round (new cuts are new nonbasic columns); the inverse is updated by
+// pivots and recomputed by Gauss-Jordan every kRefactor pivots.  FP64
+// throughout: the lower bound certifies the relative gap.
+constexpr int kSig = 1 << 24;
 constexpr int kNu = -1;
+constexpr int kRefactor = 64;
+constexpr int kMT = 256;  // master block size
 
 struct Master {
   const JointView& jv;
   long long j;
-  int n, R, nk;
+  int n, G, R, nk;
   double S;
-  double *Binv, *aug, *col, *y, *xB, *cB, *fac;
+  double *Binv, *aug, *col, *y, *xB, *cB, *fac, *row;
   int* bvar;
-  unsigned char* inB;
+  unsigned* inB;  // basic flags as bits: [nk*G] mu, then [n] sigma
 
   __device__ Master(const JointView& jv_, long long j_, int n_, int nk_, unsigned char* sm)
-      : jv(jv_), j(j_), n(n_), R(n_ + 1), nk(nk_) {
+      : jv(jv_), j(j_), n(n_), G(jv_.G), R(jv_.G + n_), nk(nk_) {
     double* d = reinterpret_cast<double*>(sm);
     Binv = d; d += R * R;
     aug = d; d += 2 * R * R;
@@ -189,57 +213,109 @@ struct Master {
     xB = d; d += R;
     cB = d; d += R;
     fac = d; d += R;
+    row = d; d += R;
     bvar = reinterpret_cast<int*>(d);
-    inB = reinterpret_cast<unsigned char*>(bvar + R);
+    inB = reinterpret_cast<unsigned*>(bvar + R);
   }
-  __device__ const double* cut(int k) const {
-    return jv.cutA + ((size_t)j * jv.itmax + k) * jv.nmax;
+  __device__ const double* cut(int id) const {  // id = k*G + g
+    return jv.cutA + ((size_t)j * jv.itmax * G + id) * jv.nmax;
   }
-  __device__ double cutb(int k) const { return jv.cutB[(size_t)j * jv.itmax + k]; }
+  __device__ double cutb(int id) const { return jv.cutB[(size_t)j * jv.itmax * G + id]; }
   __device__ double cost(int v) const {
     if (v == kNu) return 1.0;
     if (v >= kSig) return 0.0;
     return cutb(v) / S;
   }
-  // column of variable v into col[] (all threads call; ends synchronised)
-  __device__ void load_col(int v) {
+  __device__ int flag(int v) const { return v >= kSig ? nk * G + (v - kSig) : v; }
+  __device__ bool basic(int f) const { return (inB[f >> 5] >> (f & 31)) & 1u; }
+  __device__ void set_basic(int f, bool on) {  // one thread at a time
+    if (on) inB[f >> 5] |= 1u << (f & 31);
+    else inB[f >> 5] &= ~(1u << (f & 31));
+  }
+  // entry i of the column of variable v
+  __device__ double entry(int v, int i) const {
+    if (v == kNu) return i >= G ? 1.0 : 0.0;
+    if (v >= kSig) return i == G + (v - kSig) ? 1.0 : 0.0;
+    if (i < G) return i == v % G ? 1.0 : 0.0;
+    return -cut(v)[i - G] / S;
+  }
+  // reduced cost of nonbasic flag e (mu or sigma) and its variable id
+  __device__ double reduced(int e, int* v) const {
+    if (e < nk * G) {
+      const double* a = cut(e);
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int r = 0;
+      for (; r + 4 <= n; r += 4) {
+        s0 += y[G + r] * a[r];
+        s1 += y[G + r + 1] * a[r + 1];
+        s2 += y[G + r + 2] * a[r + 2];
+        s3 += y[G + r + 3] * a[r + 3];
+      }
+      for (; r < n; ++r) s0 += y[G + r] * a[r];
+      *v = e;
+      return (cutb(e) + ((s0 + s1) + (s2 + s3))) / S - y[e % G];
+    }
+    *v = kSig + (e - nk * G);
+    return -y[G + (e - nk * G)];
+  }
+  // xB = Binv * rhs (rhs: 1 on the G group rows), cB, and y = cB * Binv
+  __device__ void basics() {
     for (int i = threadIdx.x; i < R; i += blockDim.x) {
-      double x;
-      if (v == kNu) x = i == 0 ? 0.0 : 1.0;
-      else if (v >= kSig) x = (i == 1 + (v - kSig)) ? 1.0 : 0.0;
-      else x = i == 0 ? 1.0 : -cut(v)[i - 1] / S;
-      col[i] = x;
+      double x = 0.0;
+      for (int g = 0; g < G; ++g) x += Binv[i * R + g];
+      xB[i] = x;
+      cB[i] = cost(bvar[i]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+      double s0 = 0.0, s1 = 0.0;
+      int l = 0;
+      for (; l + 2 <= R; l += 2) {
+        s0 += cB[l] * Binv[l * R + i];
+        s1 += cB[l + 1] * Binv[(l + 1) * R + i];
+      }
+      if (l < R) s0 += cB[l] * Binv[l * R + i];
+      y[i] = s0 + s1;
     }
     __syncthreads();
   }
-  // Binv = B^-1 by Gauss-Jordan with partial pivoting on [B | I]; xB = Binv e0.
+  // Binv = B^-1 by Gauss-Jordan with partial pivoting on [B | I] (rows with
+  // a zero factor are skipped: B is mostly unit and 0/1 columns).
   __device__ bool refactor() {
     const int W2 = 2 * R;
-    for (int l = 0; l < R; ++l) {
-      const int v = bvar[l];
-      for (int i = threadIdx.x; i < R; i += blockDim.x) {
-        double x;
-        if (v == kNu) x = i == 0 ? 0.0 : 1.0;
-        else if (v >= kSig) x = (i == 1 + (v - kSig)) ? 1.0 : 0.0;
-        else x = i == 0 ? 1.0 : -cut(v)[i - 1] / S;
-        aug[i * W2 + l] = x;
-        aug[i * W2 + R + l] = i == l ? 1.0 : 0.0;
-      }
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      const int i = e / R, l = e - i * R;
+      aug[i * W2 + l] = entry(bvar[l], i);
+      aug[i * W2 + R + l] = i == l ? 1.0 : 0.0;
     }
     __syncthreads();
     __shared__ int piv_s;
     __shared__ int ok_s;
+    __shared__ double pv_s[kMT / 32];
+    __shared__ int pi_s[kMT / 32];
     if (threadIdx.x == 0) ok_s = 1;
     for (int c = 0; c < R; ++c) {
-      if (threadIdx.x == 0) {  // R <= 65: a serial pivot search is cheap
-        int best = c;
-        double bv = fabs(aug[c * W2 + c]);
-        for (int i = c + 1; i < R; ++i) {
-          const double x = fabs(aug[i * W2 + c]);
-          if (x > bv) { bv = x; best = i; }
-        }
-        piv_s = best;
-        if (!(bv > 1e-13)) ok_s = 0;
+      // pivot row: the largest |aug[i][c]|, i >= c (ties: smallest i)
+      double bv = -1.0;
+      int bi = INT_MAX;
+      for (int i = c + threadIdx.x; i < R; i += blockDim.x) {
+        const double x = fabs(aug[i * W2 + c]);
+        if (x > bv) { bv = x; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double x2 = __shfl_down_sync(0xffffffffu, bv, o);
+        const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+        if (x2 > bv || (x2 == bv && i2 < bi)) { bv = x2; bi = i2; }
+      }
+      if ((threadIdx.x & 31) == 0) { pv_s[threadIdx.x >> 5] = bv; pi_s[threadIdx.x >> 5] = bi; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double b2 = pv_s[0];
+        int i2 = pi_s[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+          if (pv_s[w] > b2 || (pv_s[w] == b2 && pi_s[w] < i2)) { b2 = pv_s[w]; i2 = pi_s[w]; }
+        piv_s = i2;
+        if (!(b2 > 1e-13) || i2 >= R) ok_s = 0;
       }
       __syncthreads();
       if (!ok_s) return false;
@@ -258,7 +334,8 @@ struct Master {
       __syncthreads();
       for (int e = threadIdx.x; e < R * W2; e += blockDim.x) {
         const int i = e / W2, k = e - i * W2;
-        if (i != c) aug[e] -= fac[i] * aug[c * W2 + k];
+        const double f = fac[i];
+        if (i != c && f != 0.0) aug[e] -= f * aug[c * W2 + k];
       }
       __syncthreads();
     }
@@ -267,28 +344,16 @@ struct Master {
       Binv[e] = aug[i * W2 + R + k];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < R; i += blockDim.x) {
-      xB[i] = Binv[i * R + 0];
-      cB[i] = cost(bvar[i]);
-    }
-    __syncthreads();
+    basics();
     return true;
-  }
-  __device__ void duals() {
-    for (int i = threadIdx.x; i < R; i += blockDim.x) {
-      double s = 0.0;
-      for (int l = 0; l < R; ++l) s += cB[l] * Binv[l * R + i];
-      y[i] = s;
-    }
-    __syncthreads();
   }
 };
 
-// Best entering candidate of the block: the largest reduced cost above tol
-// (Dantzig), or with bland the smallest variable id above tol.
-__device__ void block_pick(double d, int v, bool bland, double* sd, int* sv, double* out_d,
-                           int* out_v) {
-  // order key: Dantzig -> larger d first, then smaller id; Bland -> smaller id
+// Entering candidate of the block from each thread's (d, v): the largest d
+// (Dantzig; ties to the smaller id), or with bland the smallest id.
+// v == INT_MAX: no candidate.
+__device__ void block_pick(double d, int v, bool bland, double* sd, int* sv, int* out_v,
+                           double* out_d) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int o = 16; o > 0; o >>= 1) {
     const double d2 = __shfl_down_sync(0xffffffffu, d, o);
@@ -315,37 +380,76 @@ __device__ void block_pick(double d, int v, bool bland, double* sd, int* sv, dou
       else take = d2 > bd || (d2 == bd && v2 < bv);
       if (take) { bd = d2; bv = v2; }
     }
-    *out_d = bd;
     *out_v = bv;
+    *out_d = bd;
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(128) k_joint_master(JointView jv, const long long* coff,
+// Leaving-row order of the ratio test: the smaller ratio (within a relative
+// 1e-12), then the larger pivot element, or with bland the smaller
+// variable id.  vid == INT_MAX: no candidate yet.
+__device__ __forceinline__ bool ratio_better(double rt, double al, int vid, double r2, double a2,
+                                             int v2, bool bland) {
+  if (v2 == INT_MAX) return false;
+  if (vid == INT_MAX) return true;
+  const double eps = 1e-12 * (1.0 + rt);
+  if (r2 < rt - eps) return true;
+  if (r2 > rt + eps) return false;
+  return bland ? v2 < vid : a2 > al;
+}
+
+__device__ void block_ratio(double rt, double al, int lv, int vid, bool bland, double* sd,
+                            int* sv, int* out_l) {
+  __shared__ double sa[kMT / 32];
+  __shared__ int sl[kMT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double r2 = __shfl_down_sync(0xffffffffu, rt, o);
+    const double a2 = __shfl_down_sync(0xffffffffu, al, o);
+    const int l2 = __shfl_down_sync(0xffffffffu, lv, o);
+    const int v2 = __shfl_down_sync(0xffffffffu, vid, o);
+    if (ratio_better(rt, al, vid, r2, a2, v2, bland)) { rt = r2; al = a2; lv = l2; vid = v2; }
+  }
+  if (lane == 0) { sd[warp] = rt; sa[warp] = al; sl[warp] = lv; sv[warp] = vid; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (ratio_better(sd[0], sa[0], sv[0], sd[w], sa[w], sv[w], bland)) {
+        sd[0] = sd[w]; sa[0] = sa[w]; sl[0] = sl[w]; sv[0] = sv[w];
+      }
+    *out_l = sv[0] == INT_MAX ? INT_MAX : sl[0];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long long* coff,
                                                       const double* w64) {
   extern __shared__ __align__(16) unsigned char sm[];
   const long long j = blockIdx.x;
   if (jv.status[j] != kJActive) return;
   const long long c0 = coff[j];
   const int n = (int)(coff[j + 1] - c0);
-  const int kk = jv.nk[j];  // the cut written this round
+  const int G = jv.G;
+  const int kk = jv.nk[j];  // the round whose cuts were written
   const int nk = kk + 1;
-  __shared__ double S_s, sd[4];
-  __shared__ int sv[4], enter_s, leave_s, state_s;
-  __shared__ double dbest_s;
+  __shared__ double S_s, sd[kMT / 32], dq_s;
+  __shared__ int sv[kMT / 32], enter_s, leave_s, state_s;
   // incumbent
   const double F = jv.F[j];
   const bool better = F < jv.ub[j];
   __syncthreads();
-  if (better) {
+  if (better)
     for (int r = threadIdx.x; r < n; r += blockDim.x) jv.pbest[c0 + r] = w64[c0 + r];
-  }
   if (threadIdx.x == 0) {
     if (better) jv.ub[j] = F;
     if (kk == 0) {
-      double S = fabs(jv.cutB[(size_t)j * jv.itmax]);
-      const double* a0 = jv.cutA + (size_t)j * jv.itmax * jv.nmax;
-      for (int r = 0; r < n; ++r) S = fmax(S, fabs(a0[r]));
+      double S = 0.0;
+      for (int g = 0; g < G; ++g) {
+        S = fmax(S, fabs(jv.cutB[(size_t)j * jv.itmax * G + g]));
+        const double* a0 = jv.cutA + ((size_t)j * jv.itmax * G + g) * jv.nmax;
+        for (int r = 0; r < n; ++r) S = fmax(S, fabs(a0[r]));
+      }
       jv.scale[j] = S > 0.0 ? S : 1.0;
     }
     S_s = jv.scale[j];
@@ -354,155 +458,163 @@ __global__ void __launch_bounds__(128) k_joint_master(JointView jv, const long l
   __syncthreads();
   Master M(jv, j, n, nk, sm);
   M.S = S_s;
-  int* bv_g = jv.bvar + (size_t)j * (jv.nmax + 1);
+  const int R = M.R;
+  int* bv_g = jv.bvar + (size_t)j * (jv.G + jv.nmax);
+  double* bi_g = jv.binv + (size_t)j * (jv.G + jv.nmax) * (jv.G + jv.nmax);
   if (kk == 0) {
-    // mu_0 = 1, nu = min_r a_0r, sigma_r basic for every other r
+    // mu_g0 = 1 for every group, nu = min_r sum_g a_g0r, sigma_r basic for
+    // every other r
     if (threadIdx.x == 0) {
-      const double* a0 = M.cut(0);
       int rs = 0;
-      for (int r = 1; r < n; ++r)
-        if (a0[r] < a0[rs]) rs = r;
+      double best = INFINITY;
+      for (int r = 0; r < n; ++r) {
+        double A = 0.0;
+        for (int g = 0; g < G; ++g) A += M.cut(g)[r];
+        if (A < best) { best = A; rs = r; }
+      }
       int l = 0;
-      M.bvar[l++] = 0;
+      for (int g = 0; g < G; ++g) M.bvar[l++] = g;
       M.bvar[l++] = kNu;
       for (int r = 0; r < n; ++r)
         if (r != rs) M.bvar[l++] = kSig + r;
     }
   } else {
-    for (int l = threadIdx.x; l < M.R; l += blockDim.x) M.bvar[l] = bv_g[l];
+    for (int l = threadIdx.x; l < R; l += blockDim.x) M.bvar[l] = bv_g[l];
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) M.Binv[e] = bi_g[e];
   }
   __syncthreads();
-  const int nflag = nk + n;
-  for (int e = threadIdx.x; e < nflag; e += blockDim.x) M.inB[e] = 0;
+  const int nflag = nk * G + n;
+  for (int e = threadIdx.x; e < (nflag + 31) / 32; e += blockDim.x) M.inB[e] = 0u;
   __syncthreads();
   if (threadIdx.x == 0)
-    for (int l = 0; l < M.R; ++l) {
-      const int v = M.bvar[l];
-      if (v >= kSig) M.inB[nk + (v - kSig)] = 1;
-      else if (v >= 0) M.inB[v] = 1;
-    }
+    for (int l = 0; l < R; ++l)
+      if (M.bvar[l] != kNu) M.set_basic(M.flag(M.bvar[l]), true);
+  __syncthreads();
   int status = kJActive;
-  if (!M.refactor()) status = kJFail;
+  int since = kk == 0 ? 0 : jv.since[j];
+  if (kk == 0 || since >= kRefactor) {
+    if (!M.refactor()) status = kJFail;
+    since = 0;
+  } else {
+    M.basics();
+  }
   const double tol_d = 1e-12, tol_p = 1e-9;
-  const int cap = 50 * M.R + 4 * nk;
-  int pivots = 0, degen = 0, since = 0;
+  const int cap = 50 * R + 4 * nk * G;
+  const int fresh0 = kk * G;  // this round's cuts: flags [fresh0, nk*G), then sigma
+  int pivots = 0, degen = 0;
   bool bland = false;
   while (status == kJActive) {
-    M.duals();
-    // price every nonbasic mu_k and sigma_r
-    double bd = -INFINITY;
-    int bvv = INT_MAX;
-    for (int k = threadIdx.x; k < nk + n; k += blockDim.x) {
-      if (M.inB[k]) continue;
-      double d;
-      int v;
-      if (k < nk) {
-        const double* a = M.cut(k);
-        double s = M.cutb(k) / M.S - M.y[0];
-        for (int r = 0; r < n; ++r) s += M.y[1 + r] * (a[r] / M.S);
-        d = s;
-        v = k;
-      } else {
-        d = -M.y[1 + (k - nk)];
-        v = kSig + (k - nk);
+    // partial pricing first (this round's cuts and the sigma columns), all
+    // columns when that finds nothing or under Bland's rule
+    int q = INT_MAX;
+    for (int pass = bland ? 1 : 0; pass < 2 && q == INT_MAX; ++pass) {
+      const int lo = pass == 0 ? fresh0 : 0, hi = nflag;
+      double bd = -INFINITY;
+      int bvv = INT_MAX;
+      for (int e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        if (M.basic(e)) continue;
+        int v;
+        const double d = M.reduced(e, &v);
+        if (d > tol_d) {
+          const bool take =
+              bvv == INT_MAX || (bland ? v < bvv : (d > bd || (d == bd && v < bvv)));
+          if (take) { bd = d; bvv = v; }
+        }
       }
-      if (d > tol_d) {
-        const bool take = bvv == INT_MAX || (bland ? v < bvv : (d > bd || (d == bd && v < bvv)));
-        if (take) { bd = d; bvv = v; }
-      }
+      block_pick(bd, bvv, bland, sd, sv, &enter_s, &dq_s);
+      q = enter_s;
     }
-    block_pick(bd, bvv, bland, sd, sv, &dbest_s, &enter_s);
-    const int q = enter_s;
     if (q == INT_MAX) break;  // optimal
     if (pivots >= cap) { status = kJFail; break; }
-    M.load_col(q);
-    // alpha = Binv * col (into fac)
-    for (int i = threadIdx.x; i < M.R; i += blockDim.x) {
-      double s = 0.0;
-      for (int l = 0; l < M.R; ++l) s += M.Binv[i * M.R + l] * M.col[l];
-      M.fac[i] = s;
-    }
+    const double dq = dq_s;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) M.col[i] = M.entry(q, i);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int lv = -1;
-      double br = INFINITY, ba = 0.0;
-      for (int l = 0; l < M.R; ++l) {
-        if (M.bvar[l] == kNu) continue;
-        const double al_ = M.fac[l];
-        if (!(al_ > tol_p)) continue;
-        const double xl = M.xB[l] > 0.0 ? M.xB[l] : 0.0;
-        const double rt = xl / al_;
-        bool take;
-        if (lv < 0) take = true;
-        else if (rt < br - 1e-12 * (1.0 + br)) take = true;
-        else if (rt > br + 1e-12 * (1.0 + br)) take = false;
-        else if (bland) take = M.bvar[l] < M.bvar[lv];
-        else take = al_ > ba;
-        if (take) { lv = l; br = rt; ba = al_; }
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {  // alpha = Binv * col
+      double s0 = 0.0, s1 = 0.0;
+      int l = 0;
+      for (; l + 2 <= R; l += 2) {
+        s0 += M.Binv[i * R + l] * M.col[l];
+        s1 += M.Binv[i * R + l + 1] * M.col[l + 1];
       }
-      leave_s = lv;
-      state_s = lv < 0 ? kJFail : kJActive;  // unbounded cannot happen for a valid model
+      if (l < R) s0 += M.Binv[i * R + l] * M.col[l];
+      M.fac[i] = s0 + s1;
     }
     __syncthreads();
+    {  // ratio test over the basic rows (nu never leaves), block-wide
+      double rt = INFINITY, al_ = 0.0;
+      int lv = INT_MAX, vid = INT_MAX;
+      for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        const double a = M.fac[i];
+        if (M.bvar[i] == kNu || !(a > tol_p)) continue;
+        const double r2 = (M.xB[i] > 0.0 ? M.xB[i] : 0.0) / a;
+        if (ratio_better(rt, al_, vid, r2, a, M.bvar[i], bland)) {
+          rt = r2; al_ = a; lv = i; vid = M.bvar[i];
+        }
+      }
+      block_ratio(rt, al_, lv, vid, bland, sd, sv, &leave_s);
+      if (threadIdx.x == 0) state_s = leave_s == INT_MAX ? kJFail : kJActive;
+      __syncthreads();
+    }
     if (state_s != kJActive) { status = kJFail; break; }
     const int l = leave_s;
     const double apiv = M.fac[l];
     const double theta = (M.xB[l] > 0.0 ? M.xB[l] : 0.0) / apiv;
-    // x_B and B^-1 update
-    for (int i = threadIdx.x; i < M.R; i += blockDim.x)
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
       if (i != l) M.xB[i] -= theta * M.fac[i];
-    __syncthreads();
-    for (int e = threadIdx.x; e < M.R; e += blockDim.x) M.Binv[l * M.R + e] /= apiv;
-    __syncthreads();
-    for (int e = threadIdx.x; e < M.R * M.R; e += blockDim.x) {
-      const int i = e / M.R, k = e - i * M.R;
-      if (i != l) M.Binv[e] -= M.fac[i] * M.Binv[l * M.R + k];
+      M.row[i] = M.Binv[l * R + i] / apiv;  // new row l of Binv
     }
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      const int i = e / R, k = e - i * R;
+      M.Binv[e] = i == l ? M.row[k] : M.Binv[e] - M.fac[i] * M.row[k];
+    }
+    for (int i = threadIdx.x; i < R; i += blockDim.x) M.y[i] += dq * M.row[i];
     __syncthreads();
     if (threadIdx.x == 0) {
       const int old = M.bvar[l];
-      if (old >= kSig) M.inB[nk + (old - kSig)] = 0;
-      else if (old >= 0) M.inB[old] = 0;
-      if (q >= kSig) M.inB[nk + (q - kSig)] = 1;
-      else M.inB[q] = 1;
+      if (old != kNu) M.set_basic(M.flag(old), false);
+      M.set_basic(M.flag(q), true);
       M.bvar[l] = q;
       M.xB[l] = theta;
       M.cB[l] = M.cost(q);
     }
     __syncthreads();
     ++pivots;
-    if (theta <= 1e-15) { if (++degen > 2 * M.R) bland = true; }
+    if (theta <= 1e-15) { if (++degen > 2 * R) bland = true; }
     else { degen = 0; bland = false; }
-    if (++since >= 32) {
+    if (++since >= kRefactor) {
       since = 0;
       if (!M.refactor()) { status = kJFail; break; }
     }
   }
-  if (status == kJActive && since > 0 && !M.refactor()) status = kJFail;
-  M.duals();
-  // lower bound and the next p
-  __shared__ double psum_s;
+  M.basics();  // multipliers recomputed from the inverse for the bound
+  // lower bound sum_g theta_g and the next p
+  __shared__ double psum_s, lb_s;
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int r = 0; r < n; ++r) s += M.y[1 + r] > 0.0 ? M.y[1 + r] : 0.0;
+    double s = 0.0, t = 0.0;
+    for (int r = 0; r < n; ++r) s += M.y[G + r] > 0.0 ? M.y[G + r] : 0.0;
+    for (int g = 0; g < G; ++g) t += M.y[g];
     psum_s = s;
+    lb_s = t * M.S;
   }
   __syncthreads();
-  const double lb = M.y[0] * M.S;
+  const double lb = lb_s;
   const double ub = jv.ub[j];
   if (status == kJActive) {
     if (ub <= 0.0 || ub - lb <= jv.tol * ub) status = kJDone;
     else if (nk >= jv.itmax) status = kJCap;
     else if (!(psum_s > 0.0)) status = kJFail;
   }
-  for (int l = threadIdx.x; l < M.R; l += blockDim.x) bv_g[l] = M.bvar[l];
+  for (int i = threadIdx.x; i < R; i += blockDim.x) bv_g[i] = M.bvar[i];
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) bi_g[e] = M.Binv[e];
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    const double pr = M.y[1 + r] > 0.0 ? M.y[1 + r] : 0.0;
+    const double pr = M.y[G + r] > 0.0 ? M.y[G + r] : 0.0;
     jv.wnext[c0 + r] = status == kJActive ? pr / psum_s : jv.pbest[c0 + r];
   }
   if (threadIdx.x == 0) {
     jv.lb[j] = lb;
     jv.status[j] = status;
+    jv.since[j] = since;
     atomicAdd(jv.pivots, (unsigned long long)pivots);
   }
 }
@@ -533,29 +645,46 @@ unsigned blocks_for(long long n) {
   return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
 }
 
-size_t master_smem(int nmax, int itmax) {
-  const int R = nmax + 1;
-  return (size_t)(3 * R * R + 5 * R) * 8 + (size_t)R * 4 + (size_t)(itmax + nmax) + 16;
+size_t master_smem(int nmax, int itmax, int G) {
+  const int R = G + nmax;
+  return (size_t)(3 * R * R + 6 * R) * 8 + (size_t)R * 4 +
+         ((size_t)itmax * G + nmax + 31) / 32 * 4 + 16;
 }
+
+std::atomic<long long> g_rounds{0}, g_mpiv{0};
 
 }  // namespace
 
-size_t joint_state_bytes(long long K, long long Tc, int nmax, int itmax) {
-  return al((size_t)K * itmax * nmax * 8) + al((size_t)K * itmax * 8) +
-         al((size_t)K * (nmax + 1) * 4) + 2 * al((size_t)K * 4) + 6 * al((size_t)K * 8) +
-         2 * al((size_t)Tc * 8) + al(8);
+void joint_note(long long rounds, long long pivots) {
+  g_rounds += rounds;
+  g_mpiv += pivots;
 }
 
-JointView joint_view(void* mem, long long K, long long Tc, int nmax, int itmax, double tol) {
+void joint_counters(int64_t* rounds, int64_t* pivots) {
+  *rounds = g_rounds.load();
+  *pivots = g_mpiv.load();
+}
+
+size_t joint_state_bytes(long long K, long long Tc, int nmax, int itmax, int G) {
+  return al((size_t)K * itmax * G * nmax * 8) + al((size_t)K * itmax * G * 8) +
+         al((size_t)K * (G + nmax) * 4) + al((size_t)K * (G + nmax) * (G + nmax) * 8) +
+         3 * al((size_t)K * 4) + 6 * al((size_t)K * 8) + 2 * al((size_t)Tc * 8) + al(8);
+}
+
+JointView joint_view(void* mem, long long K, long long Tc, int nmax, int itmax, int G,
+                     double tol) {
   unsigned char* p = static_cast<unsigned char*>(mem);
   JointView v{};
   v.K = K;
   v.itmax = itmax;
   v.nmax = nmax;
+  v.G = G;
   v.tol = tol;
-  v.cutA = reinterpret_cast<double*>(p); p += al((size_t)K * itmax * nmax * 8);
-  v.cutB = reinterpret_cast<double*>(p); p += al((size_t)K * itmax * 8);
-  v.bvar = reinterpret_cast<int*>(p); p += al((size_t)K * (nmax + 1) * 4);
+  v.cutA = reinterpret_cast<double*>(p); p += al((size_t)K * itmax * G * nmax * 8);
+  v.cutB = reinterpret_cast<double*>(p); p += al((size_t)K * itmax * G * 8);
+  v.bvar = reinterpret_cast<int*>(p); p += al((size_t)K * (G + nmax) * 4);
+  v.binv = reinterpret_cast<double*>(p); p += al((size_t)K * (G + nmax) * (G + nmax) * 8);
+  v.since = reinterpret_cast<int*>(p); p += al((size_t)K * 4);
   v.nk = reinterpret_cast<int*>(p); p += al((size_t)K * 4);
   v.status = reinterpret_cast<int*>(p); p += al((size_t)K * 4);
   v.F = reinterpret_cast<double*>(p); p += al((size_t)K * 8);
@@ -593,17 +722,18 @@ cudaError_t joint_round(const JointView& jv, const long long* pstart, const long
                         const double* omega, const double* W, const double* pot,
                         long long pstride, const int* pst, const long long* coff,
                         const double* w64, cudaStream_t st) {
-  if (jv.nmax > kMaxJointN) return cudaErrorInvalidValue;
+  if (jv.nmax > kMaxJointN || jv.G < 1 || 128 % jv.G != 0 || jv.G + jv.nmax > kMaxJointR)
+    return cudaErrorInvalidValue;
   const size_t cs = (size_t)128 * (jv.nmax + 3) * 8;
   cudaError_t e = cudaFuncSetAttribute(k_joint_cut, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)cs);
   if (e != cudaSuccess) return e;
   k_joint_cut<<<(unsigned)jv.K, 128, cs, st>>>(jv, pstart, pobj, omega, W, pot, pstride, pst, coff,
                                                w64);
-  const size_t ms = master_smem(jv.nmax, jv.itmax);
+  const size_t ms = master_smem(jv.nmax, jv.itmax, jv.G);
   e = cudaFuncSetAttribute(k_joint_master, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms);
   if (e != cudaSuccess) return e;
-  k_joint_master<<<(unsigned)jv.K, 128, ms, st>>>(jv, coff, w64);
+  k_joint_master<<<(unsigned)jv.K, kMT, ms, st>>>(jv, coff, w64);
   note_launches(2);
   return cudaGetLastError();
 }

@@ -50,7 +50,8 @@ class D2Flows(ctypes.Structure):
 class D2Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("pairs_screened", ctypes.c_int64),
                 ("pivots_screened", ctypes.c_int64), ("pairs_exact", ctypes.c_int64),
-                ("pivots_exact", ctypes.c_int64), ("reserved", ctypes.c_int64 * 3)]
+                ("pivots_exact", ctypes.c_int64), ("joint_rounds", ctypes.c_int64),
+                ("joint_master_pivots", ctypes.c_int64), ("reserved", ctypes.c_int64 * 1)]
 
 
 class D2Error(RuntimeError):

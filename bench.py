@@ -150,12 +150,13 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources of the screening kernel's translation unit
+    (k_screen<32,1> is instantiated in d2_npl1.cu from these files)."""
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_1302_0435_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(cs, f), "rb") as fh:
-                h.update(fh.read())
+    for f in ("d2_npl1.cu", "d2_solve.cuh", "d2_solver.cuh", "d2_internal.h"):
+        with open(os.path.join(cs, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

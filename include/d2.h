@@ -124,6 +124,10 @@ typedef struct {
     int32_t segmentation;       /* D2_SEG_* : how d2_cluster_level forms segments */
     int32_t split_iters;        /* update rounds per binary split of D2_SEG_CONSTRAINED;
                                    0 = 10 */
+    double eps_tol;             /* d2_cluster_level: > 0 ends a level's rounds early once
+                                   the objective sum_i omega_i D^2(v_i, z_C(i)) changes by
+                                   at most eps_tol relative between rounds ("until epsilon
+                                   converges", Alg. 2 Step 4); 0 = exactly `iters` rounds */
 } d2_config;
 
 /*

@@ -504,7 +504,7 @@ def update_weights(objs, omega, labels, cents):
 
 
 def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, nthreads=1,
-                  segmentation="slices", split_iters=10):
+                  segmentation="slices", split_iters=10, eps_tol=0.0):
     """Alg. 3 level loop with the segment-wise weighted D2-clustering of
     Alg. 2 (constrained update, Step 3*) inside each segment.
 
@@ -521,6 +521,11 @@ def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, n
     constrained D2 splits of Alg. 3 Step 1 (segment(), split_iters rounds per
     split) instead of contiguous slices; segment mu's labels are offset by
     mu*K (Eq. (UpdateLabel) with its index list L_mu).
+    eps_tol > 0 ends a level's rounds after the first round r >= 1 whose
+    level objective eps_r = sum_i omega_i D^2(v_i, z_C(i)) (over all its
+    segments, from round r's assignment) is within eps_tol relative of
+    eps_{r-1} (Alg. 2 Step 4, "until epsilon converges"); the segments run
+    their rounds in step.
 
     Returns (centroid locations [K*n, d] float64, centroid weights [K],
     labels [N] int64)."""
@@ -539,24 +544,30 @@ def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, n
         else:
             M = 1 if n_l <= seg_size else int(math.ceil(n_l / seg_size))
             members = [np.arange(mu * seg_size, min((mu + 1) * seg_size, n_l)) for mu in range(M)]
-        seg_labels, seg_cents = [], []
-        for mu in range(M):
-            seg = _take_bags(data, members[mu])
-            om_seg = om[members[mu]]
-            cents = _Bags(_f64(init_cents.loc).copy(), _f64(init_cents.w).copy(),
-                          _i64(init_cents.off).copy())
-            lab = None
-            for _ in range(int(iters)):
-                lab, _ = assign(seg, cents, nthreads=nthreads)
+        segs = [_take_bags(data, members[mu]) for mu in range(M)]
+        oms = [om[members[mu]] for mu in range(M)]
+        seg_cents = [_Bags(_f64(init_cents.loc).copy(), _f64(init_cents.w).copy(),
+                           _i64(init_cents.off).copy()) for _ in range(M)]
+        seg_labels = [None] * M
+        eps_prev = None
+        for _ in range(int(iters)):
+            eps = 0.0
+            for mu in range(M):
+                seg, cents = segs[mu], seg_cents[mu]
+                lab, dist2 = assign(seg, cents, nthreads=nthreads)
+                eps += float(np.sum(oms[mu] * dist2))
                 fo, fa, fr, fw = assigned_flows(seg, cents, lab)
-                newloc = update_locations(seg, om_seg, lab, fo, fa, fr, fw, cents)
+                newloc = update_locations(seg, oms[mu], lab, fo, fa, fr, fw, cents)
                 if loc_round is not None:
                     newloc = newloc.astype(loc_round).astype(np.float64)
-                cents = _Bags(newloc, cents.w, cents.off)
-            if lab is None:
-                lab, _ = assign(seg, cents, nthreads=nthreads)
-            seg_labels.append(lab)
-            seg_cents.append(cents)
+                seg_cents[mu] = _Bags(newloc, cents.w, cents.off)
+                seg_labels[mu] = lab
+            if eps_tol > 0 and eps_prev is not None and abs(eps - eps_prev) <= eps_tol * eps:
+                break
+            eps_prev = eps
+        for mu in range(M):
+            if seg_labels[mu] is None:
+                seg_labels[mu], _ = assign(segs[mu], seg_cents[mu], nthreads=nthreads)
         C_tilde = np.empty(n_l, dtype=np.int64)
         for mu, lab_mu in zip(range(M), update_label(seg_labels, [K] * M)):
             C_tilde[members[mu]] = lab_mu

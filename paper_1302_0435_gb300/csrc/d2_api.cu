@@ -33,6 +33,7 @@ enum Slot {
   // initial data segmentation
   kSgMem, kSgOff, kSgLoc, kSgW, kSgOm, kSgCLoc, kSgCW, kSgCOff, kSgC32, kSgC64, kSgCQ, kSgCW64,
   kSgLab, kSgD2, kSgCell, kSgFw, kSgUpd, kSgCand, kSgOut, kLvSegof, kSgPart, kUpdPart, kLvPart,
+  kLvTerms, kLvEps,
   // combined distance of several bag types
   kMbPair, kMbTmpLab, kMbTmpD2, kMbCnt, kMbStart, kMbPObj, kMbPCen, kMbD2, kMbSt,
   // joint weights (Alg. 1 Step 1)
@@ -1411,7 +1412,27 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     long long glaunches = 0;
     const bool graphs = iters > 2 && c->stream != nullptr && c->stream != cudaStreamLegacy &&
                         c->stream != cudaStreamPerThread;
+    // "until epsilon converges" (eps_tol > 0): the level objective of each
+    // round's assignment, summed in a fixed order, read back before the next
+    double* lterms = nullptr;
+    double* leps = nullptr;
+    const double etol = c->cfg.eps_tol;
+    if (etol > 0.0) {
+      lterms = static_cast<double*>(grow(c, kLvTerms, (size_t)n_l * 8, &rc));
+      leps = static_cast<double*>(grow(c, kLvEps, 8, &rc));
+      if (rc != D2_OK) return rc;
+    }
+    double eps_prev = -1.0;
     for (int it = 0; it < std::max(iters, 1); ++it) {
+      if (lterms && it >= 1) {
+        CK(d2k::sum_fixed_order(lterms, n_l, leps, c->stream));
+        double* he = reinterpret_cast<double*>(c->h_pin + 6);
+        CK(cudaMemcpyAsync(he, leps, 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        const double e = *he;
+        if (eps_prev >= 0.0 && std::fabs(e - eps_prev) <= etol * e) break;
+        eps_prev = e;
+      }
       ws.warm = it > 0;
       if (gexec && it >= 2) {
         CK(cudaGraphLaunch(gexec, c->stream));
@@ -1426,7 +1447,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
       cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
       cudaStreamIsCapturing(c->stream, &cst);
       const bool capturing = cst == cudaStreamCaptureStatusActive;
-      int rc2 = run_assign(c, cur, cv, seg, K, cfg.mode, cur_mmax, om, lab, ld2, nullptr, fo, cand,
+      int rc2 = run_assign(c, cur, cv, seg, K, cfg.mode, cur_mmax, om, lab, ld2, lterms, fo, cand,
                            ws.par8 ? &ws : nullptr, bins);
       cudaError_t ue = cudaSuccess;
       if (rc2 == D2_OK && it < iters)
@@ -1444,7 +1465,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
           if (gexec) cudaGraphExecDestroy(gexec);
           gexec = nullptr;
           // run the round directly instead
-          if ((rc = run_assign(c, cur, cv, seg, K, cfg.mode, cur_mmax, om, lab, ld2, nullptr, fo,
+          if ((rc = run_assign(c, cur, cv, seg, K, cfg.mode, cur_mmax, om, lab, ld2, lterms, fo,
                                cand, ws.par8 ? &ws : nullptr, bins)))
             return rc;
           if (it < iters)

@@ -8,6 +8,9 @@
 // its bags, binned on the host by the nodes per lane their trees need; small
 // requests go to high-priority streams, so their blocks are dispatched as
 // soon as the chunk on the GPU drains instead of after a whole large request.
+// A quarter of the slots (at least one, when there are two or more) only
+// take small requests, and at most kMaxLarge large requests run at once,
+// so a burst of large requests never holds every slot.
 // Each request's labels and distances are computed by the same
 // deterministic per-pair solver as d2_assign, so a result does not depend
 // on what else is in flight or on the chunking.
@@ -34,6 +37,9 @@ namespace {
 
 constexpr long long kChunkPairs = 1LL << 17;  // pairs per chunk launch
 constexpr int kSmallChunks = 2;                // requests of at most this many chunks: high priority
+// Large requests (more chunks) in flight at once: one chunk already fills
+// the GPU, so more only stretch every large request's latency.
+constexpr int kMaxLarge = 2;
 
 struct Request {
   long long ticket = 0;
@@ -234,14 +240,23 @@ void d2_server::run() {
     }
     // admissions: free slot and memory budget (staging runs unlocked);
     // the smallest queued request goes first (ties: arrival order)
+    const int nslots = (int)slots.size();
+    const int reserved = nslots >= 2 ? std::max(1, nslots / 4) : 0;  // small requests only
     while (!queue.empty()) {
       auto pick = queue.begin();
       for (auto q = queue.begin(); q != queue.end(); ++q)
         if ((*q)->count < (*pick)->count) pick = q;
       std::shared_ptr<Request> r = *pick;
+      const bool small = r->chunks <= kSmallChunks;
+      int large = 0;
+      for (Slot& s : slots) large += (s.req && s.req->chunks > kSmallChunks) ? 1 : 0;
+      if (!small && large >= kMaxLarge) break;  // the rest of the queue is larger still
       Slot* free_slot = nullptr;
-      for (Slot& s : slots)
+      const int limit = small ? nslots : nslots - reserved;
+      for (int k = 0; k < limit; ++k) {
+        Slot& s = slots[k];
         if (!s.req && !s.staging) { free_slot = &s; break; }
+      }
       if (!free_slot) break;
       if (mem_inflight > 0 && mem_inflight + r->bytes > mem_budget) break;
       queue.erase(pick);

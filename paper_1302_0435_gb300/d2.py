@@ -40,7 +40,8 @@ class D2Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("pivot_budget", ctypes.c_int32),
                 ("group_lanes", ctypes.c_int32), ("cost_tc", ctypes.c_int32),
                 ("tile_budget_mib", ctypes.c_int32), ("start_rule", ctypes.c_int32),
-                ("segmentation", ctypes.c_int32), ("split_iters", ctypes.c_int32)]
+                ("segmentation", ctypes.c_int32), ("split_iters", ctypes.c_int32),
+                ("eps_tol", ctypes.c_double)]
 
 
 class D2Flows(ctypes.Structure):
@@ -173,11 +174,11 @@ class Context:
 
     def __init__(self, device=0, precision=D2_PREC_AUTO, pivot_budget=0, group_lanes=0,
                  cost_tc=D2_TC_AUTO, tile_budget_mib=0, start_rule=D2_START_AUTO,
-                 segmentation=D2_SEG_SLICES, split_iters=0):
+                 segmentation=D2_SEG_SLICES, split_iters=0, eps_tol=0.0):
         lib = load()
         self.h = ctypes.c_void_p()
         cfg = D2Config(precision, pivot_budget, group_lanes, cost_tc, tile_budget_mib, start_rule,
-                       segmentation, split_iters)
+                       segmentation, split_iters, float(eps_tol))
         _check(lib.d2_ctx_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)), "d2_ctx_create")
         self._cents = None
 
@@ -327,7 +328,8 @@ def d2_get_stats():
     st = D2Stats()
     _check(load().d2_get_stats(ctypes.byref(st)), "d2_get_stats")
     return {k: int(getattr(st, k)) for k in ("kernel_launches", "pairs_screened", "pivots_screened",
-                                              "pairs_exact", "pivots_exact")}
+                                              "pairs_exact", "pivots_exact", "joint_rounds",
+                                              "joint_master_pivots")}
 
 
 def d2_update_locations_noalloc(objs, labels, flows, K, cent_off, cent_loc_dtype, cent_loc64,

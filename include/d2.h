@@ -85,6 +85,13 @@ extern "C" {
 #define D2_START_RANKED 1  /* northwest staircase in principal-direction order */
 #define D2_START_VOGEL 2   /* Vogel's approximation (largest-penalty line first) */
 
+/* centroid update of d2_cluster_level's rounds (d2_config.centroid_update) */
+#define D2_UPDATE_CONSTRAINED 0  /* Alg. 2 Step 3*: support weights fixed, locations by
+                                    Eq. (WeightedUpdate) */
+#define D2_UPDATE_ALG1 1         /* Alg. 1 (weighted D2-clustering, Alg. 3 Step 2): support
+                                    weights by the joint LP (d2_update_weights), then the
+                                    locations with flows at the new weights */
+
 /* segments of d2_cluster_level (d2_config.segmentation) */
 #define D2_SEG_SLICES 0       /* contiguous slices of seg_size objects */
 #define D2_SEG_CONSTRAINED 1  /* the binary constrained D2 splits of d2_segment */
@@ -128,6 +135,10 @@ typedef struct {
                                    the objective sum_i omega_i D^2(v_i, z_C(i)) changes by
                                    at most eps_tol relative between rounds ("until epsilon
                                    converges", Alg. 2 Step 4); 0 = exactly `iters` rounds */
+    int32_t centroid_update;    /* D2_UPDATE_* ; 0 = CONSTRAINED */
+    int32_t joint_max_iter;     /* D2_UPDATE_ALG1: cutting-plane rounds per weight update;
+                                   0 = 512 */
+    double joint_tol;           /* D2_UPDATE_ALG1: relative gap of the weight LP; 0 = 1e-9 */
 } d2_config;
 
 /*
@@ -285,6 +296,18 @@ int d2_update_weights(d2_ctx* ctx, const d2_bags* objs, const double* omega,
  */
 int d2_assign_multi(d2_ctx* const* ctxs, int32_t B, const d2_bags* objs, int32_t* labels,
                     double* dist2);
+
+/*
+ * d2_cluster_level with the support weights of the result as well:
+ * out_support_w [K*n] (host or device, may be NULL).  With the default
+ * D2_UPDATE_CONSTRAINED they stay the resident set's; with D2_UPDATE_ALG1
+ * every round of every level re-solves them (Alg. 1 Step 1) and the next
+ * level's data carry them.  D2_ENOTCONVERGED when a weight LP was not
+ * certified within joint_max_iter rounds (its best weights were used).
+ */
+int d2_cluster_level_ex(d2_ctx* ctx, const d2_bags* objs, const double* omega, int32_t K,
+                        int64_t seg_size, int32_t iters, double* out_loc, double* out_support_w,
+                        double* out_cent_weight, int32_t* labels);
 
 /*
  * Initial data segmentation (Alg. 3 Step 1): split the bags into segments of

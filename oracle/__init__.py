@@ -504,7 +504,8 @@ def update_weights(objs, omega, labels, cents):
 
 
 def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, nthreads=1,
-                  segmentation="slices", split_iters=10, eps_tol=0.0):
+                  segmentation="slices", split_iters=10, eps_tol=0.0, update="constrained",
+                  return_support_weights=False):
     """Alg. 3 level loop with the segment-wise weighted D2-clustering of
     Alg. 2 (constrained update, Step 3*) inside each segment.
 
@@ -526,6 +527,11 @@ def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, n
     segments, from round r's assignment) is within eps_tol relative of
     eps_{r-1} (Alg. 2 Step 4, "until epsilon converges"); the segments run
     their rounds in step.
+    update="alg1" updates each cluster by Alg. 1 (the weighted D2-clustering
+    of Alg. 3 Step 2): Step 1 re-solves the support weights by the joint LP
+    (update_weights), Step 2 moves the supports with the members' optimal
+    flows at those weights; the next level's data carry the weights.
+    return_support_weights adds the result's support weights to the tuple.
 
     Returns (centroid locations [K*n, d] float64, centroid weights [K],
     labels [N] int64)."""
@@ -556,6 +562,9 @@ def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, n
                 seg, cents = segs[mu], seg_cents[mu]
                 lab, dist2 = assign(seg, cents, nthreads=nthreads)
                 eps += float(np.sum(oms[mu] * dist2))
+                if update == "alg1":
+                    wj, _ = update_weights(seg, oms[mu], lab, cents)
+                    cents = _Bags(cents.loc, wj, cents.off)
                 fo, fa, fr, fw = assigned_flows(seg, cents, lab)
                 newloc = update_locations(seg, oms[mu], lab, fo, fa, fr, fw, cents)
                 if loc_round is not None:
@@ -575,6 +584,8 @@ def cluster_level(objs, omega, init_cents, K, seg_size, iters, loc_round=None, n
         w_new = propagate_weights(C_tilde, om, M * K)
         if M == 1:
             c0 = seg_cents[0]
+            if return_support_weights:
+                return _f64(c0.loc), w_new, C, _f64(c0.w)
             return _f64(c0.loc), w_new, C
         locs = np.concatenate([c.loc for c in seg_cents])
         ws = np.concatenate([c.w for c in seg_cents])

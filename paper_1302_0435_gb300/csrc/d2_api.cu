@@ -37,7 +37,7 @@ enum Slot {
   // combined distance of several bag types
   kMbPair, kMbTmpLab, kMbTmpD2, kMbCnt, kMbStart, kMbPObj, kMbPCen, kMbD2, kMbSt,
   // joint weights (Alg. 1 Step 1)
-  kJState, kJPot, kJPStart, kJEps, kJIters,
+  kJState, kJPot, kJPStart, kJEps, kJIters, kJSort, kJPObj, kJPCen, kJW, kJSt,
   kSlots
 };
 
@@ -296,6 +296,16 @@ __global__ void k_pairs_from_labels(const int* labels, long long N, long long* p
        i += (long long)gridDim.x * blockDim.x) {
     pobj[i] = i;
     pcen[i] = labels[i];
+  }
+}
+
+// pairs (i, global centroid of i) of a level: g = seg(i) * K + labels[i]
+__global__ void k_pairs_global(const int* labels, long long N, long long seg_size, const int* segof,
+                               int K, long long* pobj, long long* pcen) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    pobj[i] = i;
+    pcen[i] = (segof ? (long long)segof[i] : i / seg_size) * K + labels[i];
   }
 }
 
@@ -1024,6 +1034,93 @@ int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labe
 
 namespace {
 
+// A centroid set the joint-weights core works on: the resident set, or a
+// level's replicated sets (K = all centroids of the set).
+struct CentSet {
+  float* loc32;
+  double* loc64;
+  long long* Q;
+  double* w64;
+  const long long* off;
+  long long K;
+  long long Tc;
+};
+
+// Alg. 1 Step 1 for every centroid of `cs` (cluster g = seg(i)*K + label):
+// cutting-plane rounds of exact member solves and per-cluster master LPs
+// (d2_joint.cu); the set's weights (w64, Q) end as the best weights found.
+// eps_d / it_d: [cs.K] device outputs (may be null).  *certified: every
+// non-empty cluster closed its gap within max_iter rounds.
+int joint_core(d2_ctx* c, const ObjView& v, const double* om, const int* dl, long long seg, int K,
+               const CentSet& cs, int mmax, int max_iter, double tol, double* eps_d, int* it_d,
+               bool* certified) {
+  const long long N = v.count, KT = cs.K;
+  int rc = D2_OK;
+  const int nmax = std::max(c->nmax, 1);
+  const int itmax = max_iter;
+  const int G = d2k::joint_groups(nmax);
+  void* scr = grow(c, kJSort, d2k::update_scratch_bytes(std::max(N, 1LL), KT), &rc);
+  void* jmem = grow(c, kJState, d2k::joint_state_bytes(KT, cs.Tc, nmax, itmax, G), &rc);
+  long long* pobj = static_cast<long long*>(grow(c, kJPObj, (size_t)std::max(N, 1LL) * 8, &rc));
+  long long* pcen = static_cast<long long*>(grow(c, kJPCen, (size_t)std::max(N, 1LL) * 8, &rc));
+  double* W = static_cast<double*>(grow(c, kJW, (size_t)std::max(N, 1LL) * 8, &rc));
+  int* pst = static_cast<int*>(grow(c, kJSt, (size_t)std::max(N, KT) * 4, &rc));
+  double* pot = static_cast<double*>(grow(c, kJPot, (size_t)std::max(N, 1LL) * nmax * 8, &rc));
+  long long* pstart = static_cast<long long*>(grow(c, kJPStart, (size_t)(KT + 1) * 8, &rc));
+  if (rc != D2_OK) return rc;
+  const long long* start;
+  const int* order;
+  if (N > 0) {  // members of every cluster, increasing object index
+    FlowOut none{nullptr, nullptr, 0};
+    CK(d2k::update_locations(v, nullptr, dl, seg, K, none, KT, cs.off, c->d, c->cent_ldt,
+                             cs.loc32, cs.loc64, scr, c->stream));
+    d2k::sorted_groups(scr, N, KT, &start, &order);
+  } else {
+    long long* z = static_cast<long long*>(scr);  // no members: start = 0
+    CK(cudaMemsetAsync(z, 0, (size_t)(KT + 1) * 8, c->stream));
+    start = z;
+    order = nullptr;
+  }
+  d2k::JointView jv = d2k::joint_view(jmem, KT, cs.Tc, nmax, itmax, G, tol);
+  CK(d2k::joint_init(jv, start, cs.off, cs.w64, c->stream));
+  SolveCfg cfg = solve_cfg(c, mode_for(c, v.ldt), mmax);
+  FlowOut fo{nullptr, nullptr, 0};
+  fo.pot = pot;
+  fo.pstride = nmax;
+  CentView cv{cs.loc32, cs.loc64, cs.Q, cs.off, KT, c->d};
+  cv.tab32 = c->tab32;
+  cv.tab64 = c->tab64;
+  cv.A = c->A;
+  long long* hP = reinterpret_cast<long long*>(c->h_pin + 4);
+  for (int it = 0; it < itmax; ++it) {
+    if (it > 0)  // the weights chosen by the last master solve
+      CK(d2k::prep_centroids(cs.loc64, D2_F64, jv.wnext, D2_F64, cs.off, KT, c->d, cs.loc32,
+                             cs.loc64, cs.Q, cs.w64, c->d_err, c->stream));
+    CK(d2k::joint_list(jv, order, start, pstart, pobj, pcen, c->stream));
+    CK(cudaMemcpyAsync(hP, pstart + KT, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const long long P = *hP;
+    if (P == 0) break;
+    CK(d2k::mallows_pairs(v, cv, pobj, pcen, P, cfg, W, fo, pst, c->d_err, c->stream));
+    CK(d2k::joint_round(jv, pstart, pobj, om, W, pot, nmax, pst, cs.off, cs.w64, c->stream));
+    d2k::joint_note(1, 0);
+  }
+  int* jst = pst;  // per-cluster status, reusing the pair status room
+  CK(d2k::joint_finish(jv, cs.off, eps_d, it_d, jst, c->stream));
+  CK(d2k::prep_centroids(cs.loc64, D2_F64, jv.wnext, D2_F64, cs.off, KT, c->d, cs.loc32, cs.loc64,
+                         cs.Q, cs.w64, c->d_err, c->stream));
+  unsigned long long* hpiv = reinterpret_cast<unsigned long long*>(c->h_pin + 4);
+  CK(cudaMemcpyAsync(hpiv, jv.pivots, 8, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<int> hs((size_t)KT);
+  CK(cudaMemcpyAsync(hs.data(), jst, (size_t)KT * 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  d2k::joint_note(0, (long long)*hpiv);
+  *certified = true;
+  for (int s2 : hs)
+    if (s2 == 2 || s2 == 4) *certified = false;
+  return D2_OK;
+}
+
 // flows for pairs (i, labels[i]) re-solved in FP64 into slots
 int resolve_assigned(d2_ctx* c, const ObjView& v, const int* dl, int mmax, const CentView& cv,
                      FlowOut* fo) {
@@ -1120,76 +1217,18 @@ int d2_update_weights(d2_ctx* c, const d2_bags* objs, const double* omega, const
       (rc = stage_out(c, reinterpret_cast<int*>(iters_out), (size_t)K, kJIters, &it_d, &it_h)))
     return rc;
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-  // members of every cluster, increasing object index
-  void* scr = grow(c, kUpd, d2k::update_scratch_bytes(std::max(N, 1LL), K), &rc);
-  const int nmax = std::max(c->nmax, 1);
-  const int itmax = max_iter;
-  const int G = d2k::joint_groups(nmax);
-  void* jmem = grow(c, kJState, d2k::joint_state_bytes(K, c->Tc, nmax, itmax, G), &rc);
-  long long* pobj = static_cast<long long*>(grow(c, kPairObj, (size_t)std::max(N, 1LL) * 8, &rc));
-  long long* pcen = static_cast<long long*>(grow(c, kPairCen, (size_t)std::max(N, 1LL) * 8, &rc));
-  double* W = static_cast<double*>(grow(c, kOutD2, (size_t)std::max(N, 1LL) * 8, &rc));
-  int* pst = static_cast<int*>(grow(c, kOutStatus, (size_t)std::max(N, 1LL) * 4, &rc));
-  double* pot = static_cast<double*>(grow(c, kJPot, (size_t)std::max(N, 1LL) * nmax * 8, &rc));
-  long long* pstart = static_cast<long long*>(grow(c, kJPStart, (size_t)(K + 1) * 8, &rc));
-  if (rc != D2_OK) return rc;
-  const long long* start;
-  const int* order;
-  if (N > 0) {
-    FlowOut none{nullptr, nullptr, 0};
-    CK(d2k::update_locations(v, nullptr, dl, N, (int)K, none, K, c->c_off, c->d, c->cent_ldt,
-                             c->c_loc32, c->c_loc64, scr, c->stream));
-    d2k::sorted_groups(scr, N, K, &start, &order);
-  } else {
-    long long* z = static_cast<long long*>(scr);  // no members: start = 0
-    CK(cudaMemsetAsync(z, 0, (size_t)(K + 1) * 8, c->stream));
-    start = z;
-    order = nullptr;
-  }
-  d2k::JointView jv = d2k::joint_view(jmem, K, c->Tc, nmax, itmax, G, tol);
-  CK(d2k::joint_init(jv, start, c->c_off, c->c_w64, c->stream));
-  SolveCfg cfg = solve_cfg(c, mode_for(c, v.ldt), mmax);
-  FlowOut fo{nullptr, nullptr, 0};
-  fo.pot = pot;
-  fo.pstride = nmax;
-  const CentView cv = resident_view(c);
-  long long* hP = reinterpret_cast<long long*>(c->h_pin + 4);
-  for (int it = 0; it < itmax; ++it) {
-    if (it > 0)  // the weights chosen by the last master solve
-      CK(d2k::prep_centroids(c->c_loc64, D2_F64, jv.wnext, D2_F64, c->c_off, K, c->d, c->c_loc32,
-                             c->c_loc64, c->c_Q, c->c_w64, c->d_err, c->stream));
-    CK(d2k::joint_list(jv, order, start, pstart, pobj, pcen, c->stream));
-    CK(cudaMemcpyAsync(hP, pstart + K, 8, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    const long long P = *hP;
-    if (P == 0) break;
-    CK(d2k::mallows_pairs(v, cv, pobj, pcen, P, cfg, W, fo, pst, c->d_err, c->stream));
-    CK(d2k::joint_round(jv, pstart, pobj, om, W, pot, nmax, pst, c->c_off, c->c_w64, c->stream));
-    d2k::joint_note(1, 0);
-  }
-  int* jst = reinterpret_cast<int*>(pst);  // per-cluster status, reusing the pair status room
-  if ((size_t)std::max(N, 1LL) < (size_t)K) {
-    jst = static_cast<int*>(grow(c, kOutStatus, (size_t)K * 4, &rc));
-    if (rc != D2_OK) return rc;
-  }
-  CK(d2k::joint_finish(jv, c->c_off, eps_d, it_d, jst, c->stream));
-  unsigned long long* hpiv = reinterpret_cast<unsigned long long*>(c->h_pin + 4);
-  CK(cudaMemcpyAsync(hpiv, jv.pivots, 8, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  d2k::joint_note(0, (long long)*hpiv);
-  CK(d2k::prep_centroids(c->c_loc64, D2_F64, jv.wnext, D2_F64, c->c_off, K, c->d, c->c_loc32,
-                         c->c_loc64, c->c_Q, c->c_w64, c->d_err, c->stream));
+  CentSet cs{c->c_loc32, c->c_loc64, c->c_Q, c->c_w64, c->c_off, K, c->Tc};
+  bool certified = true;
+  if ((rc = joint_core(c, v, om, dl, std::max(N, 1LL), (int)K, cs, mmax, max_iter, tol, eps_d,
+                       it_d, &certified)))
+    return rc;
   if (eps_h) CK(cudaMemcpyAsync(eps_out, eps_d, (size_t)K * 8, cudaMemcpyDeviceToHost, c->stream));
   if (it_h) CK(cudaMemcpyAsync(iters_out, it_d, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
-  std::vector<int> hs((size_t)K);
-  CK(cudaMemcpyAsync(hs.data(), jst, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
   int bits = 0;
   if ((rc = read_err(c, &bits))) return rc;
   if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
   if (bits & d2k::kErrInvalid) return D2_EINVAL;
-  for (int s : hs)
-    if (s == 2 || s == 4) return D2_ENOTCONVERGED;
-  return D2_OK;
+  return certified ? D2_OK : D2_ENOTCONVERGED;
 }
 
 int d2_assign_multi(d2_ctx* const* ctxs, int32_t B, const d2_bags* objs, int32_t* labels,
@@ -1313,8 +1352,22 @@ int d2_segment(d2_ctx* c, const d2_bags* objs, const double* omega, int64_t tau,
 
 int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t K, int64_t seg_size,
                      int32_t iters, double* out_loc, double* out_cent_weight, int32_t* labels) {
+  return d2_cluster_level_ex(c, objs, omega, K, seg_size, iters, out_loc, nullptr, out_cent_weight,
+                             labels);
+}
+
+int d2_cluster_level_ex(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t K,
+                        int64_t seg_size, int32_t iters, double* out_loc, double* out_support_w,
+                        double* out_cent_weight, int32_t* labels) {
   if (!c || !bags_ok(objs) || K < 1 || iters < 0 || !out_loc || !out_cent_weight || !labels)
     return D2_EINVAL;
+  const bool alg1 = c->cfg.centroid_update == D2_UPDATE_ALG1;
+  if (c->cfg.centroid_update != D2_UPDATE_CONSTRAINED && !alg1) return D2_EINVAL;
+  if (alg1 && c->nmax > d2k::kMaxJointN) return D2_EUNSUPPORTED;
+  const int jmax = c->cfg.joint_max_iter > 0 ? std::min(c->cfg.joint_max_iter, D2_JOINT_MAX_ITER)
+                                             : 512;
+  const double jtol = c->cfg.joint_tol > 0.0 && c->cfg.joint_tol < 1.0 ? c->cfg.joint_tol : 1e-9;
+  bool uncertified = false;
   if (c->K == 0) return D2_ENOCENTROIDS;
   if (c->A > 0) return D2_EUNSUPPORTED;  // symbolic supports are not moved
   if (c->K != K || objs->dim != c->d || seg_size <= K) return D2_EINVAL;
@@ -1398,7 +1451,8 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     const int ns = cur_mmax + c->nmax;
     const size_t meta_bytes = (size_t)npairs * ns * 3;
     const size_t flow_bytes = (size_t)npairs * ns * 8;
-    if (cfg.mode == 1 && iters > 1 && meta_bytes + flow_bytes <= kWarmBudgetBytes) {
+    // (not with Alg. 1 updates: the weights, so every pair's supplies, change each round)
+    if (cfg.mode == 1 && iters > 1 && !alg1 && meta_bytes + flow_bytes <= kWarmBudgetBytes) {
       unsigned char* meta = static_cast<unsigned char*>(grow(c, kWarmMeta, meta_bytes, &rc));
       long long* wf = static_cast<long long*>(grow(c, kWarmFlow, flow_bytes, &rc));
       if (rc != D2_OK) return rc;
@@ -1410,8 +1464,8 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     // is captured into a CUDA graph once and replayed.
     cudaGraphExec_t gexec = nullptr;
     long long glaunches = 0;
-    const bool graphs = iters > 2 && c->stream != nullptr && c->stream != cudaStreamLegacy &&
-                        c->stream != cudaStreamPerThread;
+    const bool graphs = iters > 2 && !alg1 && c->stream != nullptr &&
+                        c->stream != cudaStreamLegacy && c->stream != cudaStreamPerThread;
     // "until epsilon converges" (eps_tol > 0): the level objective of each
     // round's assignment, summed in a fixed order, read back before the next
     double* lterms = nullptr;
@@ -1450,6 +1504,25 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
       int rc2 = run_assign(c, cur, cv, seg, K, cfg.mode, cur_mmax, om, lab, ld2, lterms, fo, cand,
                            ws.par8 ? &ws : nullptr, bins);
       cudaError_t ue = cudaSuccess;
+      if (rc2 == D2_OK && it < iters && alg1) {
+        // Alg. 1 Step 1: support weights of every cluster of the level by the
+        // joint LP, then the assigned pairs' flows at those weights
+        CentSet cs{l32, l64, lQ, lw, loff, KT, M * Tc};
+        bool cert = true;
+        rc2 = joint_core(c, cur, om, lab, seg, K, cs, cur_mmax, jmax, jtol, nullptr, nullptr, &cert);
+        if (rc2 == D2_OK) {
+          uncertified |= !cert;
+          long long* po = static_cast<long long*>(grow(c, kJPObj, (size_t)n_l * 8, &rc));
+          long long* pc = static_cast<long long*>(grow(c, kJPCen, (size_t)n_l * 8, &rc));
+          double* dd = static_cast<double*>(grow(c, kJW, (size_t)n_l * 8, &rc));
+          if (rc != D2_OK) return rc;
+          k_pairs_global<<<blocks_for(n_l), 256, 0, c->stream>>>(lab, n_l, seg, cur.segof, K, po, pc);
+          d2k::note_launches(1);
+          CK(cudaGetLastError());
+          const CentView cv2{l32, l64, lQ, loff, KT, d};
+          CK(d2k::mallows_pairs(cur, cv2, po, pc, n_l, cfg, dd, fo, nullptr, c->d_err, c->stream));
+        }
+      }
       if (rc2 == D2_OK && it < iters)
         ue = d2k::update_locations(cur, om, lab, seg, K, fo, KT, loff, d, c->cent_ldt, l32, l64, scr,
                                    c->stream, lpart, lpart_n);
@@ -1491,6 +1564,8 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
     CK(cudaGetLastError());
     if (M == 1) {
       CK(cudaMemcpyAsync(out_loc, l64, (size_t)Tc * d * 8, cudaMemcpyDefault, c->stream));
+      if (out_support_w)
+        CK(cudaMemcpyAsync(out_support_w, lw, (size_t)Tc * 8, cudaMemcpyDefault, c->stream));
       CK(cudaMemcpyAsync(out_cent_weight, wnew, (size_t)K * 8, cudaMemcpyDefault, c->stream));
       CK(cudaMemcpyAsync(labels, C, (size_t)N0 * 4, cudaMemcpyDefault, c->stream));
       break;
@@ -1526,7 +1601,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
   if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
   if (bits & d2k::kErrInvalid) return D2_EINVAL;
   if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
-  return D2_OK;
+  return uncertified ? D2_ENOTCONVERGED : D2_OK;
 }
 
 int d2_get_stats(d2_stats* out) {

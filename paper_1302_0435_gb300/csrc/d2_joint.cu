@@ -193,6 +193,9 @@ constexpr int kSig = 1 << 24;
 constexpr int kNu = -1;
 constexpr int kRefactor = 64;
 constexpr int kMT = 256;  // master block size
+// Multipliers below this are rounding noise of a zero weight: they are set
+// to 0 so that the support carries no mass (and keeps its location).
+constexpr double kPTiny = 1e-13;
 
 struct Master {
   const JointView& jv;
@@ -592,7 +595,7 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
   __shared__ double psum_s, lb_s;
   if (threadIdx.x == 0) {
     double s = 0.0, t = 0.0;
-    for (int r = 0; r < n; ++r) s += M.y[G + r] > 0.0 ? M.y[G + r] : 0.0;
+    for (int r = 0; r < n; ++r) s += M.y[G + r] > kPTiny ? M.y[G + r] : 0.0;
     for (int g = 0; g < G; ++g) t += M.y[g];
     psum_s = s;
     lb_s = t * M.S;
@@ -608,7 +611,7 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
   for (int i = threadIdx.x; i < R; i += blockDim.x) bv_g[i] = M.bvar[i];
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) bi_g[e] = M.Binv[e];
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    const double pr = M.y[G + r] > 0.0 ? M.y[G + r] : 0.0;
+    const double pr = M.y[G + r] > kPTiny ? M.y[G + r] : 0.0;
     jv.wnext[c0 + r] = status == kJActive ? pr / psum_s : jv.pbest[c0 + r];
   }
   if (threadIdx.x == 0) {

@@ -20,6 +20,7 @@ D2_PREC_AUTO, D2_PREC_FP64, D2_PREC_FP32, D2_PREC_TC = 0, 1, 2, 3
 D2_TC_AUTO, D2_TC_OFF, D2_TC_ON = 0, 1, 2
 D2_START_AUTO, D2_START_RANKED, D2_START_VOGEL = 0, 1, 2
 D2_SEG_SLICES, D2_SEG_CONSTRAINED = 0, 1
+D2_UPDATE_CONSTRAINED, D2_UPDATE_ALG1 = 0, 1
 MAX_SUPPORT = 64
 
 EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_strerror",
@@ -27,7 +28,7 @@ EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_st
            "d2_mallows_batch", "d2_assign", "d2_update_locations", "d2_cluster_level",
            "d2_get_stats", "d2_update_locations_noalloc", "d2_server_create", "d2_server_submit",
            "d2_server_poll", "d2_server_stats", "d2_server_destroy", "d2_segment",
-           "d2_set_cost_table", "d2_assign_multi", "d2_update_weights"]
+           "d2_set_cost_table", "d2_assign_multi", "d2_update_weights", "d2_cluster_level_ex"]
 
 
 class D2Bags(ctypes.Structure):
@@ -41,7 +42,8 @@ class D2Config(ctypes.Structure):
                 ("group_lanes", ctypes.c_int32), ("cost_tc", ctypes.c_int32),
                 ("tile_budget_mib", ctypes.c_int32), ("start_rule", ctypes.c_int32),
                 ("segmentation", ctypes.c_int32), ("split_iters", ctypes.c_int32),
-                ("eps_tol", ctypes.c_double)]
+                ("eps_tol", ctypes.c_double), ("centroid_update", ctypes.c_int32),
+                ("joint_max_iter", ctypes.c_int32), ("joint_tol", ctypes.c_double)]
 
 
 class D2Flows(ctypes.Structure):
@@ -97,6 +99,8 @@ def load(path=None):
     lib.d2_assign_multi.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(D2Bags), vp, vp]
     lib.d2_update_weights.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, i32, ctypes.c_double,
                                       vp, vp]
+    lib.d2_cluster_level_ex.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i32, i64, i32, vp, vp, vp,
+                                        vp]
     lib.d2_server_create.argtypes = [ctypes.POINTER(vp), vp, i32, i64]
     lib.d2_server_submit.argtypes = [vp, ctypes.POINTER(D2Bags), ctypes.POINTER(i64)]
     lib.d2_server_poll.argtypes = [vp, i64, vp, vp, ctypes.POINTER(ctypes.c_double), i32]
@@ -174,11 +178,13 @@ class Context:
 
     def __init__(self, device=0, precision=D2_PREC_AUTO, pivot_budget=0, group_lanes=0,
                  cost_tc=D2_TC_AUTO, tile_budget_mib=0, start_rule=D2_START_AUTO,
-                 segmentation=D2_SEG_SLICES, split_iters=0, eps_tol=0.0):
+                 segmentation=D2_SEG_SLICES, split_iters=0, eps_tol=0.0,
+                 centroid_update=D2_UPDATE_CONSTRAINED, joint_max_iter=0, joint_tol=0.0):
         lib = load()
         self.h = ctypes.c_void_p()
         cfg = D2Config(precision, pivot_budget, group_lanes, cost_tc, tile_budget_mib, start_rule,
-                       segmentation, split_iters, float(eps_tol))
+                       segmentation, split_iters, float(eps_tol), int(centroid_update),
+                       int(joint_max_iter), float(joint_tol))
         _check(lib.d2_ctx_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)), "d2_ctx_create")
         self._cents = None
 
@@ -287,6 +293,16 @@ def d2_cluster_level(ctx, objs, K, seg_size, iters, out_loc, out_cent_weight, la
                                  int(iters), _ptr(out_loc), _ptr(out_cent_weight), _ptr(labels))
     if rc not in (D2_OK, D2_ENOTCONVERGED):
         _check(rc, "d2_cluster_level")
+    return rc
+
+
+def d2_cluster_level_ex(ctx, objs, K, seg_size, iters, out_loc, out_support_w, out_cent_weight,
+                        labels, omega=None):
+    rc = load().d2_cluster_level_ex(ctx.h, ctypes.byref(objs.s), _ptr(omega), int(K),
+                                    int(seg_size), int(iters), _ptr(out_loc), _ptr(out_support_w),
+                                    _ptr(out_cent_weight), _ptr(labels))
+    if rc not in (D2_OK, D2_ENOTCONVERGED):
+        _check(rc, "d2_cluster_level_ex")
     return rc
 
 

@@ -64,7 +64,7 @@ def test_null_arguments_rejected(lib):
 def test_layout_of_config_structs():
     from paper_1302_0435_gb300 import d2
     assert ctypes.sizeof(d2.D2Bags) == 48
-    assert ctypes.sizeof(d2.D2Config) == 40
+    assert ctypes.sizeof(d2.D2Config) == 56
     assert ctypes.sizeof(d2.D2Flows) == 24
 
 

@@ -23,3 +23,29 @@ def test_loose_tolerance_stops_after_two_rounds(oracle_mod):
     two = oracle_mod.cluster_level(objs, None, cents, 3, 100, 2)
     loose = oracle_mod.cluster_level(objs, None, cents, 3, 100, 30, eps_tol=1.0)
     assert all(np.array_equal(a, b) for a, b in zip(two, loose))
+
+
+def test_alg1_with_one_support_equals_the_constrained_update(oracle_mod):
+    """With one support per centroid the weight LP has the single feasible
+    point p = [1]: Alg. 1 and the constrained update coincide."""
+    objs, _ = synth.image_like(N=160, K=3, seed=43)
+    rng = np.random.default_rng(5)
+    cents = synth._pack(np.ones(3, dtype=np.int64), rng.normal(0, 3, (3, objs.dim)),
+                        np.ones(3), "f64", "f64")
+    a = oracle_mod.cluster_level(objs, None, cents, 3, 80, 3, return_support_weights=True)
+    b = oracle_mod.cluster_level(objs, None, cents, 3, 80, 3, update="alg1",
+                                 return_support_weights=True)
+    assert np.array_equal(a[2], b[2])
+    assert np.allclose(a[0], b[0], rtol=1e-12, atol=1e-12) and np.allclose(a[3], b[3])
+
+
+def test_alg1_weights_are_distributions_and_help(oracle_mod):
+    """Alg. 1 moves the support weights away from the uniform start, and
+    each centroid's weights stay a distribution."""
+    objs, cents = synth.image_like(N=120, K=2, seed=44)
+    loc, w, lab, sw = oracle_mod.cluster_level(objs, None, cents, 2, 200, 1, update="alg1",
+                                               return_support_weights=True)
+    off = np.asarray(cents.off)
+    for j in range(2):
+        assert abs(sw[off[j]:off[j + 1]].sum() - 1.0) < 1e-9 and (sw >= 0).all()
+    assert not np.allclose(sw, np.asarray(cents.w, dtype=float))

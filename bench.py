@@ -514,6 +514,30 @@ def run_profile_case(args):
         ctx.close()
         print("profile case done: cluster_level rc=%d on %d bags" % (rc, objs.count))
         return 0 if rc == 0 else 1
+    if args.profile_workload == "joint_weights":
+        # Alg. 1 Step 1 on the image-like law: the bags' nearest-centroid
+        # clusters, then the cutting-plane rounds of d2_update_weights
+        import time
+        objs, cents = synth.image_like(N=args.profile_n, K=WORKLOAD["K"])
+        ctx = d2.Context(0)
+        d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
+        ob = d2.bags_from_synth(objs, device="cuda:0")
+        lab = torch.empty(objs.count, dtype=torch.int32, device="cuda:0")
+        dd = torch.empty(objs.count, dtype=torch.float64, device="cuda:0")
+        d2.d2_assign(ctx, ob, lab, dd)
+        its = torch.zeros(WORKLOAD["K"], dtype=torch.int32, device="cuda:0")
+        d2.d2_sync(ctx)
+        s0 = d2.d2_get_stats()
+        t0 = time.perf_counter()
+        rc = d2.d2_update_weights(ctx, ob, lab, max_iter=1000, tol=1e-9, iters=its)
+        d2.d2_sync(ctx)
+        dt = time.perf_counter() - t0
+        s1 = d2.d2_get_stats()
+        ctx.close()
+        print("profile case done: joint weights rc=%d on %d bags, %.3f s, %d rounds, %d master "
+              "pivots" % (rc, objs.count, dt, int(its.max()),
+                          s1["joint_master_pivots"] - s0["joint_master_pivots"]))
+        return 0 if rc == 0 else 1
     if args.profile_workload == "high_dim":
         objs, cents = synth.high_dim(N=args.profile_n, K=512)
         ctx = d2.Context(0, tile_budget_mib=1024)  # keep a capture to about 1 GB of tiles
@@ -545,7 +569,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="small k_assign case for ncu")
     ap.add_argument("--profile-n", type=int, default=20000)
     ap.add_argument("--profile-workload", default="image_like",
-                    choices=["image_like", "image_level", "high_dim"])
+                    choices=["image_like", "image_level", "high_dim", "joint_weights"])
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args)

@@ -534,9 +534,12 @@ def run_profile_case(args):
         dt = time.perf_counter() - t0
         s1 = d2.d2_get_stats()
         ctx.close()
+        pe = s1["pairs_exact"] - s0["pairs_exact"]
         print("profile case done: joint weights rc=%d on %d bags, %.3f s, %d rounds, %d master "
-              "pivots" % (rc, objs.count, dt, int(its.max()),
-                          s1["joint_master_pivots"] - s0["joint_master_pivots"]))
+              "pivots, %d member solves, %.1f pivots per solve"
+              % (rc, objs.count, dt, int(its.max()),
+                 s1["joint_master_pivots"] - s0["joint_master_pivots"], pe,
+                 (s1["pivots_exact"] - s0["pivots_exact"]) / max(pe, 1)))
         return 0 if rc == 0 else 1
     if args.profile_workload == "high_dim":
         objs, cents = synth.high_dim(N=args.profile_n, K=512)

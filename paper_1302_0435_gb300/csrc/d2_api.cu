@@ -38,6 +38,7 @@ enum Slot {
   kMbPair, kMbTmpLab, kMbTmpD2, kMbCnt, kMbStart, kMbPObj, kMbPCen, kMbD2, kMbSt,
   // joint weights (Alg. 1 Step 1)
   kJState, kJPot, kJPStart, kJEps, kJIters, kJSort, kJPObj, kJPCen, kJW, kJSt,
+  kPairTree,
   kSlots
 };
 
@@ -246,6 +247,20 @@ SolveCfg solve_cfg(const d2_ctx* c, int mode, int mmax) {
   s.sms = c->sms;
   s.start = start_default(c);
   return s;
+}
+
+// Room for the FP32 bases of a two-launch exact solve (SolveCfg::tree);
+// past 2 GiB the solve stays one fused launch.
+int attach_tree(d2_ctx* c, SolveCfg* cfg, long long npairs) {
+  if (cfg->mode != 1 || npairs <= 0) return D2_OK;
+  const size_t b = d2k::pair_tree_bytes(npairs, cfg->mmax, cfg->nmax);
+  if (b > ((size_t)2 << 30)) return D2_OK;
+  int rc = D2_OK;
+  void* p = grow(c, kPairTree, b, &rc);
+  if (rc != D2_OK) return rc;
+  cfg->tree = static_cast<unsigned char*>(p);
+  cfg->tree_bytes = b;
+  return D2_OK;
 }
 
 CentView resident_view(const d2_ctx* c) {
@@ -948,7 +963,8 @@ int d2_mallows_batch(d2_ctx* c, const d2_bags* objs, const int64_t* pair_obj, co
   }
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   if ((rc = check_bag_symbols(c, v))) return rc;
-  const SolveCfg cfg = solve_cfg(c, mode_for(c, objs->loc_dtype), mmax);
+  SolveCfg cfg = solve_cfg(c, mode_for(c, objs->loc_dtype), mmax);
+  if ((rc = attach_tree(c, &cfg, npairs))) return rc;
   CK(d2k::mallows_pairs(v, resident_view(c), po, pc, npairs, cfg, dd, fo, ds, c->d_err, c->stream));
   if (h1) CK(cudaMemcpyAsync(dist2, dd, (size_t)npairs * 8, cudaMemcpyDeviceToHost, c->stream));
   if (h2) CK(cudaMemcpyAsync(status, ds, (size_t)npairs * 4, cudaMemcpyDeviceToHost, c->stream));
@@ -1101,6 +1117,7 @@ int joint_core(d2_ctx* c, const ObjView& v, const double* om, const int* dl, lon
     CK(cudaStreamSynchronize(c->stream));
     const long long P = *hP;
     if (P == 0) break;
+    if ((rc = attach_tree(c, &cfg, P))) return rc;
     CK(d2k::mallows_pairs(v, cv, pobj, pcen, P, cfg, W, fo, pst, c->d_err, c->stream));
     CK(d2k::joint_round(jv, pstart, pobj, om, W, pot, nmax, pst, cs.off, cs.w64, c->stream));
     d2k::joint_note(1, 0);
@@ -1305,7 +1322,8 @@ int d2_assign_multi(d2_ctx* const* ctxs, int32_t B, const d2_bags* objs, int32_t
   for (int b = 0; b < B; ++b) {
     d2_ctx* cb = ctxs[b];
     CK(cudaMemsetAsync(cb->d_err, 0, sizeof(int), cb->stream));
-    const SolveCfg cfg = solve_cfg(cb, mode_for(cb, objs[b].loc_dtype), mmax[b]);
+    SolveCfg cfg = solve_cfg(cb, mode_for(cb, objs[b].loc_dtype), mmax[b]);
+    if ((rc = attach_tree(cb, &cfg, P))) return rc;
     if (P > 0)
       CK(d2k::mallows_pairs(v[b], resident_view(cb), pobj, pcen, P, cfg, dd + (size_t)b * P,
                             FlowOut{nullptr, nullptr, 0}, pst, cb->d_err, cb->stream));
@@ -1520,7 +1538,9 @@ int d2_cluster_level_ex(d2_ctx* c, const d2_bags* objs, const double* omega, int
           d2k::note_launches(1);
           CK(cudaGetLastError());
           const CentView cv2{l32, l64, lQ, loff, KT, d};
-          CK(d2k::mallows_pairs(cur, cv2, po, pc, n_l, cfg, dd, fo, nullptr, c->d_err, c->stream));
+          SolveCfg cfg2 = cfg;
+          if ((rc = attach_tree(c, &cfg2, n_l))) return rc;
+          CK(d2k::mallows_pairs(cur, cv2, po, pc, n_l, cfg2, dd, fo, nullptr, c->d_err, c->stream));
         }
       }
       if (rc2 == D2_OK && it < iters)

@@ -120,7 +120,18 @@ struct SolveCfg {
   float* pair_out = nullptr;
   bool screen_only = false;
   TileView tile;              // precomputed FP32 tiles of the screen (optional)
+  // mallows_pairs with mode 1: room (pair_tree_bytes) for the FP32 bases
+  // handed from the FP32 launch to the FP64 launch; null: one fused launch
+  unsigned char* tree = nullptr;
+  size_t tree_bytes = 0;
 };
+
+// Bases of npairs pairs of up to mmax + nmax nodes (par/pos/size bytes and
+// int64 flows per node) plus a status int per pair.
+inline size_t pair_tree_bytes(long long npairs, int mmax, int nmax) {
+  const size_t nodes = (size_t)npairs * (size_t)(mmax + nmax);
+  return (nodes * 3 + 15) / 16 * 16 + nodes * 8 + (size_t)npairs * 4;
+}
 
 // Error bits raised by kernels into a device int.
 enum : int { kErrInvalid = 1, kErrNotConverged = 2, kErrTimeout = 4 };

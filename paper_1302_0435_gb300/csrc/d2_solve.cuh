@@ -435,6 +435,114 @@ __global__ void __launch_bounds__(128) k_mallows_pairs(ObjView ob, CentView cv,
   if (g.lane == 0) add_stats(0, 0, n_pairs, n_piv);
 }
 
+// The same exact solve in two launches: the FP32 start and pivots here,
+// the FP64 continuation in k_pairs64 from the basis handed over in global
+// memory (the same tree and integer flows solve_exact hands over in
+// registers, so the results are identical).  Each kernel then carries only
+// one Simplex instantiation, which keeps its code within the instruction
+// cache.
+template <int G, int NPL, int ST>
+__global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5))
+    k_pairs32(ObjView ob, CentView cv, const long long* pobj, const long long* pcen,
+              long long npairs, SolveCfg cfg, size_t slice, WarmStore tr, int* st32) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Grp<G> g;
+  const int gpb = blockDim.x / G;
+  unsigned char* base = smem + (threadIdx.x / G) * slice;
+  int n_piv = 0;
+  for (long long t = (long long)blockIdx.x * gpb + threadIdx.x / G; t < npairs;
+       t += (long long)gridDim.x * gpb) {
+    const long long i = pobj[t], j = pcen[t];
+    int st = kStInvalid;
+    if (i >= 0 && i < ob.count && j >= 0 && j < cv.K) {
+      const long long o0 = ob.off[i];
+      const int m = (int)(ob.off[i + 1] - o0);
+      const long long c0 = cv.off[j];
+      const int n = (int)(cv.off[j + 1] - c0);
+      if (m >= 1 && m <= cfg.mmax && n >= 1 && n <= cfg.nmax && m + n <= G * NPL) {
+        const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax, cv.d);
+        if (load_obj_prefix<G>(g, ob, o0, m, s32.P)) {
+          load_cent_prefix<G>(g, cv, c0, n, s32.Q);
+          const float c32 =
+              cv.A ? build_cost_tab<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0, cv.loc32 + c0,
+                                              cv.tab32, cv.A)
+                   : build_cost<float, G, 8>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
+                                             cv.loc32 + c0 * cv.d, cv.d);
+          Simplex<float, G, NPL> S32(s32, m, n, g);
+          if constexpr (ST == 1) {
+            S32.init_vogel();
+          } else {
+            order_rows<G>(g, s32, ob, o0, m, cv.d);
+            order_cols<G>(g, s32, cv.loc32 + c0 * cv.d, n, cv.d);
+            S32.init_northwest_ranked();
+          }
+          st = S32.run(cfg.budget * (m + n), tol32(c32), &n_piv);
+          if (st != kStInvalid) {
+            const long long wt = t * tr.ns;
+            S32.store_tree(tr.par8 + wt, tr.pos8 + wt, tr.sz8 + wt, tr.flow + wt);
+          }
+        }
+      }
+    }
+    if (g.lane == 0) st32[t] = st;
+    g.sync();
+  }
+  if (g.lane == 0) add_stats(0, 0, 0, n_piv);
+}
+
+template <int G, int NPL>
+__global__ void __launch_bounds__(128) k_pairs64(ObjView ob, CentView cv, const long long* pobj,
+                                                 const long long* pcen, long long npairs,
+                                                 SolveCfg cfg, size_t slice, WarmStore tr,
+                                                 const int* st32, double* dist2, FlowOut fo,
+                                                 int* status, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Grp<G> g;
+  const int gpb = blockDim.x / G;
+  unsigned char* base = smem + (threadIdx.x / G) * slice;
+  int n_pairs = 0, n_piv = 0;
+  for (long long t = (long long)blockIdx.x * gpb + threadIdx.x / G; t < npairs;
+       t += (long long)gridDim.x * gpb) {
+    const long long i = pobj[t], j = pcen[t];
+    int st = kStInvalid;
+    double res = nan("");
+    if (st32[t] != kStInvalid && i >= 0 && i < ob.count && j >= 0 && j < cv.K) {
+      const long long o0 = ob.off[i];
+      const int m = (int)(ob.off[i + 1] - o0);
+      const long long c0 = cv.off[j];
+      const int n = (int)(cv.off[j + 1] - c0);
+      const PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax, cv.d);
+      if (load_obj_prefix<G>(g, ob, o0, m, s64.P)) {
+        load_cent_prefix<G>(g, cv, c0, n, s64.Q);
+        const double cmax =
+            cv.A ? build_cost_tab<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
+                                             cv.loc64 + c0, cv.tab64, cv.A)
+                 : build_cost<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
+                                         cv.loc64 + c0 * cv.d, cv.d);
+        Simplex<double, G, NPL> S(s64, m, n, g);
+        const long long wt = t * tr.ns;
+        S.load_tree(tr.par8 + wt, tr.pos8 + wt, tr.sz8 + wt, tr.flow + wt);
+        S.bad = false;
+        st = S.run(cfg.budget * (m + n), tol64(cmax), &n_piv);
+        res = S.template objective<double>();
+        ++n_pairs;
+        if (fo.cell && st != kStInvalid)
+          S.write_flows(fo.cell + t * fo.stride, fo.w + t * fo.stride, fo.stride);
+        if (fo.pot && st == kStOk)  // potentials of the final, freshly priced basis
+          for (int r = g.lane; r < n; r += G) fo.pot[t * fo.pstride + r] = s64.pot[m + r];
+      }
+    }
+    if (g.lane == 0) {
+      dist2[t] = res;
+      if (status) status[t] = st == kStOk ? 0 : (st == kStNotConverged ? -3 : -1);
+      if (st == kStInvalid) atomicOr(err, kErrInvalid);
+      if (st == kStNotConverged) atomicOr(err, kErrNotConverged);
+    }
+    g.sync();
+  }
+  if (g.lane == 0) add_stats(0, 0, n_pairs, n_piv);
+}
+
 // Nearest centroid, Alg. 2 Step 2, in two kernels.  Object i uses the
 // centroids [seg(i)*K, seg(i)*K + K) of the set (seg(i) = i/seg_size, or
 // the object's entry of ob.segof).
@@ -782,6 +890,25 @@ static cudaError_t mallows_pairs_g(const ObjView& ob, const CentView& cv, const 
   if (gpb == 0) return cudaErrorInvalidConfiguration;
   const size_t smem = slice * gpb;
   unsigned grid = 1;
+  if (cfg.mode == 1 && cfg.tree &&
+      cfg.tree_bytes >= pair_tree_bytes(npairs, cfg.mmax, cfg.nmax)) {
+    const int ns = cfg.mmax + cfg.nmax;
+    const size_t nodes = (size_t)npairs * ns;
+    WarmStore tr{cfg.tree, cfg.tree + nodes, cfg.tree + 2 * nodes,
+                 reinterpret_cast<long long*>(cfg.tree + (nodes * 3 + 15) / 16 * 16), ns, 0};
+    int* st32 = reinterpret_cast<int*>(tr.flow + nodes);
+    unsigned g1 = 1, g2 = 1;
+    cudaError_t e = launch_cfg(k_pairs32<G, NPL, ST>, smem, gpb * G, cfg.sms, npairs, gpb, &g1);
+    if (e != cudaSuccess) return e;
+    e = launch_cfg(k_pairs64<G, NPL>, smem, gpb * G, cfg.sms, npairs, gpb, &g2);
+    if (e != cudaSuccess) return e;
+    k_pairs32<G, NPL, ST><<<g1, gpb * G, smem, st>>>(ob, cv, pobj, pcen, npairs, cfg, slice, tr,
+                                                      st32);
+    k_pairs64<G, NPL><<<g2, gpb * G, smem, st>>>(ob, cv, pobj, pcen, npairs, cfg, slice, tr, st32,
+                                                 dist2, fo, status, d_err);
+    note_launches(2);
+    return cudaGetLastError();
+  }
   cudaError_t e = launch_cfg(k_mallows_pairs<G, NPL, ST>, smem, gpb * G, cfg.sms, npairs, gpb, &grid);
   if (e != cudaSuccess) return e;
   k_mallows_pairs<G, NPL, ST><<<grid, gpb * G, smem, st>>>(ob, cv, pobj, pcen, npairs, cfg, slice,

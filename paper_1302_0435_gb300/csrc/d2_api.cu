@@ -15,6 +15,7 @@
 
 #include "d2.h"
 #include "d2_internal.h"
+#include "d2_trace.h"
 
 using d2k::CentView;
 using d2k::FlowOut;
@@ -774,6 +775,7 @@ int d2_sync(d2_ctx* c) {
 }
 
 int d2_set_centroids(d2_ctx* c, const d2_bags* b) {
+  d2k::TraceRange trace_("d2_set_centroids");
   if (!c || !bags_ok(b) || b->count < 1) return D2_EINVAL;
   cudaSetDevice(c->device);
   ObjView v;
@@ -883,6 +885,7 @@ int d2_get_centroids(d2_ctx* c, double* loc_out, double* w_out, int64_t* off_out
 
 int d2_cost_matrix(d2_ctx* c, const d2_bags* objs, int64_t i, int64_t j, int32_t precision,
                    double* C) {
+  d2k::TraceRange trace_("d2_cost_matrix");
   if (!c || !C || !bags_ok(objs)) return D2_EINVAL;
   if (c->K == 0) return D2_ENOCENTROIDS;
   if (i < 0 || i >= objs->count || j < 0 || j >= c->K || objs->dim != c->d) return D2_EINVAL;
@@ -931,6 +934,7 @@ int d2_cost_matrix(d2_ctx* c, const d2_bags* objs, int64_t i, int64_t j, int32_t
 
 int d2_mallows_batch(d2_ctx* c, const d2_bags* objs, const int64_t* pair_obj, const int64_t* pair_cen,
                      int64_t npairs, double* dist2, d2_flows* flows, int32_t* status) {
+  d2k::TraceRange trace_("d2_mallows_batch");
   if (!c || !bags_ok(objs) || npairs < 0 || (npairs > 0 && (!pair_obj || !pair_cen || !dist2)))
     return D2_EINVAL;
   if (c->K == 0) return D2_ENOCENTROIDS;
@@ -980,6 +984,7 @@ int d2_mallows_batch(d2_ctx* c, const d2_bags* objs, const int64_t* pair_obj, co
 
 int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labels, double* dist2,
               double* eps_total, d2_flows* flows) {
+  d2k::TraceRange trace_("d2_assign");
   if (!c || !bags_ok(objs) || !labels || !dist2) return D2_EINVAL;
   if (c->K == 0) return D2_ENOCENTROIDS;
   if (objs->dim != c->d) return D2_EINVAL;
@@ -1109,6 +1114,7 @@ int joint_core(d2_ctx* c, const ObjView& v, const double* om, const int* dl, lon
   cv.A = c->A;
   long long* hP = reinterpret_cast<long long*>(c->h_pin + 4);
   for (int it = 0; it < itmax; ++it) {
+    d2k::TraceRange round_("joint round");
     if (it > 0)  // the weights chosen by the last master solve
       CK(d2k::prep_centroids(cs.loc64, D2_F64, jv.wnext, D2_F64, cs.off, KT, c->d, cs.loc32,
                              cs.loc64, cs.Q, cs.w64, c->d_err, c->stream));
@@ -1161,6 +1167,7 @@ int resolve_assigned(d2_ctx* c, const ObjView& v, const int* dl, int mmax, const
 
 int d2_update_locations(d2_ctx* c, const d2_bags* objs, const double* omega, const int32_t* labels,
                         const d2_flows* flows) {
+  d2k::TraceRange trace_("d2_update_locations");
   if (!c || !bags_ok(objs) || !labels) return D2_EINVAL;
   if (c->K == 0) return D2_ENOCENTROIDS;
   if (c->A > 0) return D2_EUNSUPPORTED;  // symbolic supports are not moved
@@ -1209,6 +1216,7 @@ int d2_update_locations(d2_ctx* c, const d2_bags* objs, const double* omega, con
 
 int d2_update_weights(d2_ctx* c, const d2_bags* objs, const double* omega, const int32_t* labels,
                       int32_t max_iter, double tol, double* eps_out, int32_t* iters_out) {
+  d2k::TraceRange trace_("d2_update_weights");
   if (!c || !bags_ok(objs) || !labels || max_iter < 1 || max_iter > D2_JOINT_MAX_ITER ||
       !(tol >= 0.0 && tol < 1.0))
     return D2_EINVAL;
@@ -1250,6 +1258,7 @@ int d2_update_weights(d2_ctx* c, const d2_bags* objs, const double* omega, const
 
 int d2_assign_multi(d2_ctx* const* ctxs, int32_t B, const d2_bags* objs, int32_t* labels,
                     double* dist2) {
+  d2k::TraceRange trace_("d2_assign_multi");
   if (!ctxs || B < 1 || B > d2k::kMaxBagTypes || !objs || !labels || !dist2) return D2_EINVAL;
   d2_ctx* c = ctxs[0];
   if (!c) return D2_EINVAL;
@@ -1345,6 +1354,7 @@ int d2_assign_multi(d2_ctx* const* ctxs, int32_t B, const d2_bags* objs, int32_t
 
 int d2_segment(d2_ctx* c, const d2_bags* objs, const double* omega, int64_t tau, int32_t iters,
                int32_t* seg_id, int64_t* n_segments) {
+  d2k::TraceRange trace_("d2_segment");
   if (!c || !bags_ok(objs) || tau < 1 || iters < 0 || !seg_id || !n_segments) return D2_EINVAL;
   const long long N = objs->count;
   if (N < 1) return D2_EINVAL;
@@ -1377,6 +1387,7 @@ int d2_cluster_level(d2_ctx* c, const d2_bags* objs, const double* omega, int32_
 int d2_cluster_level_ex(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t K,
                         int64_t seg_size, int32_t iters, double* out_loc, double* out_support_w,
                         double* out_cent_weight, int32_t* labels) {
+  d2k::TraceRange trace_("d2_cluster_level");
   if (!c || !bags_ok(objs) || K < 1 || iters < 0 || !out_loc || !out_cent_weight || !labels)
     return D2_EINVAL;
   const bool alg1 = c->cfg.centroid_update == D2_UPDATE_ALG1;
@@ -1496,6 +1507,7 @@ int d2_cluster_level_ex(d2_ctx* c, const d2_bags* objs, const double* omega, int
     }
     double eps_prev = -1.0;
     for (int it = 0; it < std::max(iters, 1); ++it) {
+      d2k::TraceRange round_("level round");
       if (lterms && it >= 1) {
         CK(d2k::sum_fixed_order(lterms, n_l, leps, c->stream));
         double* he = reinterpret_cast<double*>(c->h_pin + 6);

@@ -32,6 +32,7 @@
 
 #include "d2.h"
 #include "d2_internal.h"
+#include "d2_trace.h"
 
 namespace {
 
@@ -137,6 +138,7 @@ struct d2_server {
 
 // Stage a request into a slot and enqueue its copies and kernels.
 bool d2_server::launch(Slot& s, const std::shared_ptr<Request>& r) {
+  d2k::TraceRange trace_("serve request");
   const long long N = r->count;
   const long long T = r->off.empty() ? 0 : r->off.back();
   const size_t b_loc = (size_t)T * r->dim * esz(r->ldt);

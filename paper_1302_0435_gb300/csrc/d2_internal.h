@@ -312,6 +312,8 @@ struct JointView {
   double* scale;    // [K] master scaling
   double* pbest;    // [Tc] weights of the best F
   double* wnext;    // [Tc] weights for the next round (final: the result)
+  float* cutA32;    // [K][itmax][G][nmax] FP32 copies of the scaled cuts (pricing filter)
+  float* cutB32;    // [K][itmax][G]
   unsigned long long* pivots;  // master pivots, summed
   long long K;
   int itmax;

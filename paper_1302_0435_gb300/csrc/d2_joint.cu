@@ -203,6 +203,7 @@ struct Master {
   int n, G, R, nk;
   double S;
   double *Binv, *aug, *col, *y, *xB, *cB, *fac, *row;
+  float* y32;
   int* bvar;
   unsigned* inB;  // basic flags as bits: [nk*G] mu, then [n] sigma
 
@@ -217,13 +218,34 @@ struct Master {
     cB = d; d += R;
     fac = d; d += R;
     row = d; d += R;
-    bvar = reinterpret_cast<int*>(d);
+    y32 = reinterpret_cast<float*>(d);
+    bvar = reinterpret_cast<int*>(y32 + ((R + 1) & ~1));
     inB = reinterpret_cast<unsigned*>(bvar + R);
   }
   __device__ const double* cut(int id) const {  // id = k*G + g
     return jv.cutA + ((size_t)j * jv.itmax * G + id) * jv.nmax;
   }
   __device__ double cutb(int id) const { return jv.cutB[(size_t)j * jv.itmax * G + id]; }
+  __device__ const float* cut32(int id) const {
+    return jv.cutA32 + ((size_t)j * jv.itmax * G + id) * jv.nmax;
+  }
+  __device__ float cutb32(int id) const { return jv.cutB32[(size_t)j * jv.itmax * G + id]; }
+  // FP32 reduced cost of mu flag e (scaled units) and a bound on its
+  // distance to the FP64 value: inputs rounded to FP32 (2^-24 each), n + 2
+  // rounded terms summed in FP32; (n + 8) * 2^-23 of the sum of |terms|
+  // covers both with a factor of two to spare.
+  __device__ float reduced32(int e, float* bound) const {
+    const float* a = cut32(e);
+    const float b = cutb32(e), yg = y32[e % G];
+    float s = b - yg, t = fabsf(b) + fabsf(yg);
+    for (int r = 0; r < n; ++r) {
+      const float pr = y32[G + r] * a[r];
+      s += pr;
+      t += fabsf(pr);
+    }
+    *bound = (float)(n + 8) * 0x1p-23f * t;
+    return s;
+  }
   __device__ double cost(int v) const {
     if (v == kNu) return 1.0;
     if (v >= kSig) return 0.0;
@@ -462,6 +484,13 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
   Master M(jv, j, n, nk, sm);
   M.S = S_s;
   const int R = M.R;
+  // FP32 copies of this round's cuts, scaled (the pricing filter reads them)
+  for (int e = threadIdx.x; e < G * (n + 1); e += blockDim.x) {
+    const int g = e / (n + 1), c = e - g * (n + 1);
+    const int id = kk * G + g;
+    if (c < n) jv.cutA32[((size_t)j * jv.itmax * G + id) * jv.nmax + c] = (float)(M.cut(id)[c] / M.S);
+    else jv.cutB32[(size_t)j * jv.itmax * G + id] = (float)(M.cutb(id) / M.S);
+  }
   int* bv_g = jv.bvar + (size_t)j * (jv.G + jv.nmax);
   double* bi_g = jv.binv + (size_t)j * (jv.G + jv.nmax) * (jv.G + jv.nmax);
   if (kk == 0) {
@@ -512,10 +541,17 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
     int q = INT_MAX;
     for (int pass = bland ? 1 : 0; pass < 2 && q == INT_MAX; ++pass) {
       const int lo = pass == 0 ? fresh0 : 0, hi = nflag;
+      for (int i = threadIdx.x; i < R; i += blockDim.x) M.y32[i] = (float)M.y[i];
+      __syncthreads();
       double bd = -INFINITY;
       int bvv = INT_MAX;
       for (int e = lo + threadIdx.x; e < hi; e += blockDim.x) {
         if (M.basic(e)) continue;
+        if (e < nk * G) {  // FP32 filter: only a cut that may enter is priced in FP64
+          float eb;
+          const float d32 = M.reduced32(e, &eb);
+          if (!((double)d32 + (double)eb > tol_d)) continue;
+        }
         int v;
         const double d = M.reduced(e, &v);
         if (d > tol_d) {
@@ -650,7 +686,7 @@ unsigned blocks_for(long long n) {
 
 size_t master_smem(int nmax, int itmax, int G) {
   const int R = G + nmax;
-  return (size_t)(3 * R * R + 6 * R) * 8 + (size_t)R * 4 +
+  return (size_t)(3 * R * R + 6 * R) * 8 + (size_t)(R + 1) * 4 + (size_t)R * 4 +
          ((size_t)itmax * G + nmax + 31) / 32 * 4 + 16;
 }
 
@@ -670,6 +706,7 @@ void joint_counters(int64_t* rounds, int64_t* pivots) {
 
 size_t joint_state_bytes(long long K, long long Tc, int nmax, int itmax, int G) {
   return al((size_t)K * itmax * G * nmax * 8) + al((size_t)K * itmax * G * 8) +
+         al((size_t)K * itmax * G * nmax * 4) + al((size_t)K * itmax * G * 4) +
          al((size_t)K * (G + nmax) * 4) + al((size_t)K * (G + nmax) * (G + nmax) * 8) +
          3 * al((size_t)K * 4) + 6 * al((size_t)K * 8) + 2 * al((size_t)Tc * 8) + al(8);
 }
@@ -685,6 +722,8 @@ JointView joint_view(void* mem, long long K, long long Tc, int nmax, int itmax, 
   v.tol = tol;
   v.cutA = reinterpret_cast<double*>(p); p += al((size_t)K * itmax * G * nmax * 8);
   v.cutB = reinterpret_cast<double*>(p); p += al((size_t)K * itmax * G * 8);
+  v.cutA32 = reinterpret_cast<float*>(p); p += al((size_t)K * itmax * G * nmax * 4);
+  v.cutB32 = reinterpret_cast<float*>(p); p += al((size_t)K * itmax * G * 4);
   v.bvar = reinterpret_cast<int*>(p); p += al((size_t)K * (G + nmax) * 4);
   v.binv = reinterpret_cast<double*>(p); p += al((size_t)K * (G + nmax) * (G + nmax) * 8);
   v.since = reinterpret_cast<int*>(p); p += al((size_t)K * 4);

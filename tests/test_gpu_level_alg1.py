@@ -88,3 +88,35 @@ def test_alg1_level_invariants(d2):
     assert c[0] == d2.D2_OK
     assert np.allclose(c[2], 1.0 / 16)          # constrained: the resident uniform weights
     assert not np.allclose(sw, c[2])
+
+
+def test_alg1_with_constrained_segmentation(d2):
+    """Alg. 1 updates inside segments formed by the binary constrained D2
+    splits: the level conserves omega, weights stay distributions, runs
+    repeat bitwise."""
+    import torch
+    objs, cents = synth.image_like(N=900, K=3, seed=503)
+
+    def run():
+        ctx = d2.Context(0, centroid_update=d2.D2_UPDATE_ALG1, segmentation=d2.D2_SEG_CONSTRAINED,
+                         split_iters=4, joint_max_iter=1000)
+        d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
+        ob = d2.bags_from_synth(objs, device="cuda:0")
+        T = cents.loc.shape[0]
+        loc = torch.empty((T, objs.dim), dtype=torch.float64, device="cuda:0")
+        sw = torch.empty(T, dtype=torch.float64, device="cuda:0")
+        w = torch.empty(3, dtype=torch.float64, device="cuda:0")
+        lab = torch.empty(objs.count, dtype=torch.int32, device="cuda:0")
+        rc = d2.d2_cluster_level_ex(ctx, ob, 3, 300, 2, loc, sw, w, lab)
+        d2.d2_sync(ctx)
+        ctx.close()
+        return rc, loc.cpu().numpy(), sw.cpu().numpy(), w.cpu().numpy(), lab.cpu().numpy()
+
+    a, b = run(), run()
+    assert a[0] == d2.D2_OK
+    assert all(np.array_equal(x, y) for x, y in zip(a[1:], b[1:]))
+    off = cents.off
+    for j in range(3):
+        assert a[2][off[j]:off[j + 1]].sum() == pytest.approx(1.0, abs=1e-12)
+    assert a[3].sum() == pytest.approx(objs.count, rel=1e-12)
+    assert a[4].min() >= 0 and a[4].max() < 3

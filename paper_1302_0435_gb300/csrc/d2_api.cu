@@ -15,6 +15,7 @@
 
 #include "d2.h"
 #include "d2_internal.h"
+#include "d2_joint.h"
 #include "d2_trace.h"
 
 using d2k::CentView;

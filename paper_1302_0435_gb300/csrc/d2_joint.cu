@@ -29,6 +29,7 @@
 #include <cmath>
 
 #include "d2_internal.h"
+#include "d2_joint.h"
 
 namespace d2k {
 namespace {

@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5))
       const long long c0 = cv.off[j];
       const int n = (int)(cv.off[j + 1] - c0);
       if (m >= 1 && m <= cfg.mmax && n >= 1 && n <= cfg.nmax && m + n <= G * NPL) {
-        const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax, cv.d);
+        const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax, cv.d, 4);  // FP32 only
         if (load_obj_prefix<G>(g, ob, o0, m, s32.P)) {
           load_cent_prefix<G>(g, cv, c0, n, s32.Q);
           const float c32 =
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
   extern __shared__ __align__(16) unsigned char smem[];
   Grp<G> g;
   unsigned char* base = smem + (threadIdx.x / G) * slice;
-  const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax, cv.d);
+  const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax, cv.d, 4);  // FP32 only
   int* cand = s32.sc;                                          // [kCandCap]
   float* clo = reinterpret_cast<float*>(s32.sc + kCandCap);    // [kCandCap]
   int n_scr = 0, p_scr = 0;
@@ -897,13 +897,17 @@ static cudaError_t mallows_pairs_g(const ObjView& ob, const CentView& cv, const 
     WarmStore tr{cfg.tree, cfg.tree + nodes, cfg.tree + 2 * nodes,
                  reinterpret_cast<long long*>(cfg.tree + (nodes * 3 + 15) / 16 * 16), ns, 0};
     int* st32 = reinterpret_cast<int*>(tr.flow + nodes);
+    const size_t slice32 = pair_mem_bytes(cfg.mmax, cfg.nmax, cv.d, 4);  // FP32-only kernel
+    const int gpb32 = groups_per_block(G, slice32);
+    if (gpb32 == 0) return cudaErrorInvalidConfiguration;
+    const size_t smem32 = slice32 * gpb32;
     unsigned g1 = 1, g2 = 1;
-    cudaError_t e = launch_cfg(k_pairs32<G, NPL, ST>, smem, gpb * G, cfg.sms, npairs, gpb, &g1);
+    cudaError_t e = launch_cfg(k_pairs32<G, NPL, ST>, smem32, gpb32 * G, cfg.sms, npairs, gpb32, &g1);
     if (e != cudaSuccess) return e;
     e = launch_cfg(k_pairs64<G, NPL>, smem, gpb * G, cfg.sms, npairs, gpb, &g2);
     if (e != cudaSuccess) return e;
-    k_pairs32<G, NPL, ST><<<g1, gpb * G, smem, st>>>(ob, cv, pobj, pcen, npairs, cfg, slice, tr,
-                                                      st32);
+    k_pairs32<G, NPL, ST><<<g1, gpb32 * G, smem32, st>>>(ob, cv, pobj, pcen, npairs, cfg, slice32,
+                                                          tr, st32);
     k_pairs64<G, NPL><<<g2, gpb * G, smem, st>>>(ob, cv, pobj, pcen, npairs, cfg, slice, tr, st32,
                                                  dist2, fo, status, d_err);
     note_launches(2);
@@ -928,6 +932,11 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
   const int gpb = groups_per_block(G, slice, cfg.tpb);
   if (gpb == 0) return cudaErrorInvalidConfiguration;
   const size_t smem = slice * gpb;
+  // the screen solves in FP32 only: the tighter slice of 4-byte costs
+  const size_t slice32 = pair_mem_bytes(cfg.mmax, cfg.nmax, cv.d, 4);
+  const int gpb32 = groups_per_block(G, slice32, cfg.tpb);
+  if (gpb32 == 0) return cudaErrorInvalidConfiguration;
+  const size_t smem32 = slice32 * gpb32;
   unsigned grid = 1;
   cudaError_t e;
   const bool screen = cfg.mode == 1 && cand != nullptr;
@@ -950,17 +959,17 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
       if (e2 != cudaSuccess) return e2;
       unsigned g2 = 1;
       if (sc.tile.C) {
-        e2 = launch_cfg(k_screen<G, NPL, true, ST>, smem, gpb * G, sc.sms, cnt * (long long)NB, gpb,
-                        &g2);
+        e2 = launch_cfg(k_screen<G, NPL, true, ST>, smem32, gpb32 * G, sc.sms, cnt * (long long)NB,
+                        gpb32, &g2);
         if (e2 != cudaSuccess) return e2;
-        k_screen<G, NPL, true, ST><<<g2, gpb * G, smem, st>>>(ob, cv, seg_size, K, KB, NB, sc, slice,
-                                                              items, queue, ws, d_err);
+        k_screen<G, NPL, true, ST><<<g2, gpb32 * G, smem32, st>>>(ob, cv, seg_size, K, KB, NB, sc,
+                                                                  slice32, items, queue, ws, d_err);
       } else {
-        e2 = launch_cfg(k_screen<G, NPL, false, ST>, smem, gpb * G, sc.sms, cnt * (long long)NB, gpb,
-                        &g2);
+        e2 = launch_cfg(k_screen<G, NPL, false, ST>, smem32, gpb32 * G, sc.sms, cnt * (long long)NB,
+                        gpb32, &g2);
         if (e2 != cudaSuccess) return e2;
-        k_screen<G, NPL, false, ST><<<g2, gpb * G, smem, st>>>(ob, cv, seg_size, K, KB, NB, sc,
-                                                               slice, items, queue, ws, d_err);
+        k_screen<G, NPL, false, ST><<<g2, gpb32 * G, smem32, st>>>(ob, cv, seg_size, K, KB, NB, sc,
+                                                                   slice32, items, queue, ws, d_err);
       }
       const unsigned mb = (unsigned)std::min<long long>((cnt + 255) / 256, 4096);
       k_merge<<<mb, 256, 0, st>>>(items, cnt, NB, sc.oidx, sc.obase, merged);

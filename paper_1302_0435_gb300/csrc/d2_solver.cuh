@@ -84,8 +84,11 @@ __device__ __forceinline__ bool gany(const Grp<G>& g, bool p) {
   return (__ballot_sync(g.mask, p) & g.mask) != 0u;
 }
 
-// Shared-memory slice of one lane group (byte layout independent of the
-// cost type: cost and potential areas are sized for doubles).
+// Shared-memory slice of one lane group.  The cost and potential areas hold
+// eb bytes per entry: 8 (the default) gives the same byte layout for float
+// and double, so that one slice can hold an FP32 solve and then its FP64
+// continuation (recast); kernels that only ever solve in FP32 use eb = 4,
+// half the cost tile, so more warps fit on an SM.
 template <typename T>
 struct PairMem {
   T* cost;            // [m*n] row-major, stride n
@@ -118,15 +121,15 @@ struct PairMem {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline size_t pair_mem_bytes(int mmax, int nmax, int dmax = 256) {
+__host__ __device__ inline size_t pair_mem_bytes(int mmax, int nmax, int dmax = 256, int eb = 8) {
   const size_t N = (size_t)(mmax + nmax);
   const size_t mx = (size_t)(mmax > nmax ? mmax : nmax);
   size_t b = 0;
   b += align_up((size_t)mmax * 4, 16) * 2 + align_up((size_t)nmax * 4, 16) * 2;  // ranks
   b += align_up((size_t)mmax * 8, 16) + align_up((size_t)nmax * 8, 16);          // Pr Qr
   b += align_up((size_t)dmax * 4, 16) * 2 + align_up(mx * 4, 16);               // dir mu proj
-  b += align_up((size_t)mmax * nmax * 8, 16);  // cost
-  b += align_up(N * 8, 16);                    // pot
+  b += align_up((size_t)mmax * nmax * eb, 16);  // cost
+  b += align_up(N * eb, 16);                    // pot
   b += align_up(N * 4, 16) * 2;                // pos sz
   b += align_up(N * 4, 16) * 3;                // ppos psz pnode
   b += align_up(N * 8, 16);                    // pflow
@@ -134,13 +137,14 @@ __host__ __device__ inline size_t pair_mem_bytes(int mmax, int nmax, int dmax = 
   b += align_up((size_t)nmax * 8, 16);         // Q
   b += align_up((size_t)mmax * 4, 16);         // re
   b += align_up(N * 4, 16) * 2;                // pj0 pj1
-  b += align_up(N * 8, 16) * 2;                // acc0 acc1
+  b += align_up(N * eb, 16) * 2;               // acc0 acc1
   b += 128;                                    // sc: 32 group scalars
   return align_up(b, 128);
 }
 
 template <typename T>
-__device__ inline PairMem<T> carve(unsigned char* base, int mmax, int nmax, int dmax = 256) {
+__device__ inline PairMem<T> carve(unsigned char* base, int mmax, int nmax, int dmax = 256,
+                                   int eb = 8) {
   const size_t N = (size_t)(mmax + nmax);
   const size_t mx = (size_t)(mmax > nmax ? mmax : nmax);
   PairMem<T> s;
@@ -154,8 +158,8 @@ __device__ inline PairMem<T> carve(unsigned char* base, int mmax, int nmax, int 
   s.dir = reinterpret_cast<float*>(p); p += align_up((size_t)dmax * 4, 16);
   s.mu = reinterpret_cast<float*>(p); p += align_up((size_t)dmax * 4, 16);
   s.proj = reinterpret_cast<float*>(p); p += align_up(mx * 4, 16);
-  s.cost = reinterpret_cast<T*>(p); p += align_up((size_t)mmax * nmax * 8, 16);
-  s.pot = reinterpret_cast<T*>(p); p += align_up(N * 8, 16);
+  s.cost = reinterpret_cast<T*>(p); p += align_up((size_t)mmax * nmax * eb, 16);
+  s.pot = reinterpret_cast<T*>(p); p += align_up(N * eb, 16);
   s.pos = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
   s.sz = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
   s.ppos = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
@@ -167,8 +171,8 @@ __device__ inline PairMem<T> carve(unsigned char* base, int mmax, int nmax, int 
   s.re = reinterpret_cast<int*>(p); p += align_up((size_t)mmax * 4, 16);
   s.pj0 = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
   s.pj1 = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
-  s.acc0 = reinterpret_cast<T*>(p); p += align_up(N * 8, 16);
-  s.acc1 = reinterpret_cast<T*>(p); p += align_up(N * 8, 16);
+  s.acc0 = reinterpret_cast<T*>(p); p += align_up(N * eb, 16);
+  s.acc1 = reinterpret_cast<T*>(p); p += align_up(N * eb, 16);
   s.sc = reinterpret_cast<int*>(p);
   return s;
 }

@@ -1,6 +1,7 @@
 // d2_serve.cu -- continuous-batching server for assignment requests
 // (Alg. 2 Step 2 against a resident centroid set).  A worker thread admits
-// queued requests (smallest first) into slots as slots and device memory
+// queued requests (small ones smallest first, large ones in arrival order)
+// into slots as slots and device memory
 // free up; each slot owns two CUDA streams (high and low priority) and
 // grow-only device/pinned buffers, so requests that arrive while others are
 // on the GPU start at once and their kernels overlap with the running ones.
@@ -240,26 +241,35 @@ void d2_server::run() {
       progressed = true;
       cv_done.notify_all();
     }
-    // admissions: free slot and memory budget (staging runs unlocked);
-    // the smallest queued request goes first (ties: arrival order)
+    // admissions: free slot and memory budget (staging runs unlocked)
     const int nslots = (int)slots.size();
     const int reserved = nslots >= 2 ? std::max(1, nslots / 4) : 0;  // small requests only
     while (!queue.empty()) {
-      auto pick = queue.begin();
-      for (auto q = queue.begin(); q != queue.end(); ++q)
-        if ((*q)->count < (*pick)->count) pick = q;
-      std::shared_ptr<Request> r = *pick;
-      const bool small = r->chunks <= kSmallChunks;
+      // small requests: the smallest first; large ones: in arrival order
+      // (a large request is not overtaken again and again by smaller large
+      // ones, which bounds the tail)
       int large = 0;
       for (Slot& s : slots) large += (s.req && s.req->chunks > kSmallChunks) ? 1 : 0;
-      if (!small && large >= kMaxLarge) break;  // the rest of the queue is larger still
+      auto pick = queue.end();
+      for (auto q = queue.begin(); q != queue.end(); ++q)
+        if ((*q)->chunks <= kSmallChunks && (pick == queue.end() || (*q)->count < (*pick)->count))
+          pick = q;
       Slot* free_slot = nullptr;
-      const int limit = small ? nslots : nslots - reserved;
-      for (int k = 0; k < limit; ++k) {
-        Slot& s = slots[k];
-        if (!s.req && !s.staging) { free_slot = &s; break; }
+      if (pick != queue.end()) {
+        for (int k = 0; k < nslots && !free_slot; ++k)
+          if (!slots[k].req && !slots[k].staging) free_slot = &slots[k];
+      }
+      if (!free_slot) {  // no small request can start: the oldest large one
+        pick = queue.end();
+        if (large < kMaxLarge)
+          for (auto q = queue.begin(); q != queue.end(); ++q)
+            if ((*q)->chunks > kSmallChunks) { pick = q; break; }
+        if (pick == queue.end()) break;
+        for (int k = 0; k < nslots - reserved && !free_slot; ++k)
+          if (!slots[k].req && !slots[k].staging) free_slot = &slots[k];
       }
       if (!free_slot) break;
+      std::shared_ptr<Request> r = *pick;
       if (mem_inflight > 0 && mem_inflight + r->bytes > mem_budget) break;
       queue.erase(pick);
       free_slot->staging = true;

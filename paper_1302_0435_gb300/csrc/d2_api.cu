@@ -15,6 +15,7 @@
 
 #include "d2.h"
 #include "d2_internal.h"
+#include "d2_segment.h"
 #include "d2_joint.h"
 #include "d2_trace.h"
 
@@ -35,6 +36,7 @@ enum Slot {
   // initial data segmentation
   kSgMem, kSgOff, kSgLoc, kSgW, kSgOm, kSgCLoc, kSgCW, kSgCOff, kSgC32, kSgC64, kSgCQ, kSgCW64,
   kSgLab, kSgD2, kSgCell, kSgFw, kSgUpd, kSgCand, kSgOut, kLvSegof, kSgPart, kUpdPart, kLvPart,
+  kSgSid, kSgIdx, kSgAct, kSgULab,
   kLvTerms, kLvEps,
   // combined distance of several bag types
   kMbPair, kMbTmpLab, kMbTmpD2, kMbCnt, kMbStart, kMbPObj, kMbPCen, kMbD2, kMbSt,
@@ -559,31 +561,26 @@ int tc_work(d2_ctx* c, long long rows, int mmax, d2k::TcWork* w) {
 // are numbered by their smallest member.
 int segment_impl(d2_ctx* c, const ObjView& v, int mmax, const double* om, long long tau, int iters,
                  int* segof, long long* M_out) {
+  // Every segment above tau splits in two; a split depends only on its own
+  // members (in increasing object order), so all the splits of one
+  // generation run together: one gathered view, one centroid set of two
+  // per segment, one assignment and one update per round.  The result is
+  // the partition of largest-first splitting, one split at a time.
   const long long N = v.count;
   int rc = D2_OK;
-  const size_t lsz = esize(v.ldt), wsz = esize(v.wdt);
   const long long rows_cap = N * (long long)mmax;
   const long long stride = 2LL * mmax - 1;
   int* dmem = static_cast<int*>(grow(c, kSgMem, (size_t)N * 4, &rc));
+  int* dsid = static_cast<int*>(grow(c, kSgSid, (size_t)N * 4, &rc));
   long long* soff = static_cast<long long*>(grow(c, kSgOff, (size_t)(N + 1) * 8, &rc));
-  void* sloc = grow(c, kSgLoc, (size_t)rows_cap * v.d * lsz, &rc);
-  void* sw = grow(c, kSgW, (size_t)rows_cap * wsz, &rc);
+  void* sloc = grow(c, kSgLoc, (size_t)rows_cap * v.d * esize(v.ldt), &rc);
+  void* sw = grow(c, kSgW, (size_t)rows_cap * esize(v.wdt), &rc);
   double* som = static_cast<double*>(grow(c, kSgOm, (size_t)N * 8, &rc));
-  double* zloc = static_cast<double*>(grow(c, kSgCLoc, (size_t)2 * mmax * v.d * 8, &rc));
-  double* zw = static_cast<double*>(grow(c, kSgCW, (size_t)2 * mmax * 8, &rc));
-  long long* zoff = static_cast<long long*>(grow(c, kSgCOff, 3 * 8, &rc));
-  float* z32 = static_cast<float*>(grow(c, kSgC32, (size_t)2 * mmax * v.d * 4, &rc));
-  double* z64 = static_cast<double*>(grow(c, kSgC64, (size_t)2 * mmax * v.d * 8, &rc));
-  long long* zQ = static_cast<long long*>(grow(c, kSgCQ, (size_t)2 * mmax * 8, &rc));
-  double* zw64 = static_cast<double*>(grow(c, kSgCW64, (size_t)2 * mmax * 8, &rc));
   int* lab = static_cast<int*>(grow(c, kSgLab, (size_t)N * 4, &rc));
   double* dd = static_cast<double*>(grow(c, kSgD2, (size_t)N * 8, &rc));
   int* fcell = static_cast<int*>(grow(c, kSgCell, (size_t)(N * stride) * 4, &rc));
   double* fw = static_cast<double*>(grow(c, kSgFw, (size_t)(N * stride) * 8, &rc));
-  void* uscr = grow(c, kSgUpd, d2k::update_scratch_bytes(N, 2), &rc);
   int* cand = static_cast<int*>(grow(c, kSgCand, (size_t)d2k::assign_scratch_ints(N, 2, c->sms) * 4, &rc));
-  const size_t spart_n = d2k::update_part_bytes(N, 2, v.d);
-  double* spart = static_cast<double*>(grow(c, kSgPart, spart_n, &rc));
   if (rc != D2_OK) return rc;
   SolveCfg cfg = solve_cfg(c, mode_for(c, v.ldt), mmax);
   cfg.nmax = mmax;  // the split centroids are bags of the data
@@ -592,8 +589,6 @@ int segment_impl(d2_ctx* c, const ObjView& v, int mmax, const double* om, long l
   const FlowOut fo{fcell, fw, stride};
   std::vector<std::vector<int>> segs(1, std::vector<int>((size_t)N));
   for (long long i = 0; i < N; ++i) segs[0][(size_t)i] = (int)i;
-  std::vector<double> hd;
-  std::vector<int> hl, hl2;
   auto check = [&]() -> int {
     int bits = 0;
     int r = read_err(c, &bits);
@@ -603,15 +598,42 @@ int segment_impl(d2_ctx* c, const ObjView& v, int mmax, const double* om, long l
     if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
     return D2_OK;
   };
+  std::vector<double> hd;
+  std::vector<int> hl, hl2, list, sid, idx;
   for (;;) {
-    size_t big = 0;
-    for (size_t k = 1; k < segs.size(); ++k)
-      if (segs[k].size() > segs[big].size()) big = k;
-    if ((long long)segs[big].size() <= tau) break;
-    if ((long long)segs.size() > N) return D2_EINVAL;  // every split makes progress
-    const std::vector<int> S = segs[big];
-    const long long cnt = (long long)S.size();
-    CK(cudaMemcpyAsync(dmem, S.data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, c->stream));
+    std::vector<size_t> B;  // the segments split in this generation
+    for (size_t k = 0; k < segs.size(); ++k)
+      if ((long long)segs[k].size() > tau) B.push_back(k);
+    if (B.empty()) break;
+    if ((long long)(segs.size() + B.size()) > N) return D2_EINVAL;  // every split makes progress
+    const long long nB = (long long)B.size();
+    std::vector<long long> s0((size_t)nB + 1, 0);
+    list.clear();
+    sid.clear();
+    for (long long b = 0; b < nB; ++b) {
+      s0[(size_t)b] = (long long)list.size();
+      const std::vector<int>& S = segs[B[(size_t)b]];
+      list.insert(list.end(), S.begin(), S.end());
+      sid.insert(sid.end(), S.size(), (int)b);
+    }
+    s0[(size_t)nB] = (long long)list.size();
+    const long long cnt = (long long)list.size();
+    // room for two centroids of at most mmax supports per segment
+    const long long KT = 2 * nB;
+    double* zloc = static_cast<double*>(grow(c, kSgCLoc, (size_t)KT * mmax * v.d * 8, &rc));
+    double* zw = static_cast<double*>(grow(c, kSgCW, (size_t)KT * mmax * 8, &rc));
+    long long* zoff = static_cast<long long*>(grow(c, kSgCOff, (size_t)(KT + 1) * 8, &rc));
+    float* z32 = static_cast<float*>(grow(c, kSgC32, (size_t)KT * mmax * v.d * 4, &rc));
+    double* z64 = static_cast<double*>(grow(c, kSgC64, (size_t)KT * mmax * v.d * 8, &rc));
+    long long* zQ = static_cast<long long*>(grow(c, kSgCQ, (size_t)KT * mmax * 8, &rc));
+    double* zw64 = static_cast<double*>(grow(c, kSgCW64, (size_t)KT * mmax * 8, &rc));
+    int* didx = static_cast<int*>(grow(c, kSgIdx, (size_t)KT * 4, &rc));
+    void* uscr = grow(c, kSgUpd, d2k::update_scratch_bytes(cnt, KT), &rc);
+    const size_t spart_n = d2k::update_part_bytes(cnt, KT, v.d);
+    double* spart = static_cast<double*>(grow(c, kSgPart, spart_n, &rc));
+    if (rc != D2_OK) return rc;
+    CK(cudaMemcpyAsync(dmem, list.data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(dsid, sid.data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, c->stream));
     CK(d2k::seg_gather(v, dmem, cnt, om, soff, sloc, sw, som, c->stream));
     ObjView sub;
     sub.loc = sloc;
@@ -621,15 +643,24 @@ int segment_impl(d2_ctx* c, const ObjView& v, int mmax, const double* om, long l
     sub.d = v.d;
     sub.ldt = v.ldt;
     sub.wdt = v.wdt;
-    auto set_cents = [&](int i0, int i1, int K) -> int {
-      CK(d2k::seg_cents(sub, i0, i1, K, zloc, zw, zoff, c->stream));
-      CK(d2k::prep_centroids(zloc, D2_F64, zw, D2_F64, zoff, K, v.d, z32, z64, zQ, zw64, c->d_err,
-                             c->stream));
+    sub.segof = dsid;  // segment b of the generation uses centroids [b*K, b*K + K)
+    auto set_cents = [&](int K) -> int {  // centroids from compact bags idx[0 .. K*nB)
+      CK(cudaMemcpyAsync(didx, idx.data(), (size_t)(K * nB) * 4, cudaMemcpyHostToDevice,
+                         c->stream));
+      CK(d2k::seg_cents_list(sub, didx, K * nB, zloc, zw, zoff, c->stream));
+      CK(d2k::prep_centroids(zloc, D2_F64, zw, D2_F64, zoff, K * nB, v.d, z32, z64, zQ, zw64,
+                             c->d_err, c->stream));
       return D2_OK;
     };
+    // objects of the segments still open (nullptr: all of them)
+    const int* act_d = nullptr;
+    long long act_n = cnt;
     auto solve = [&](int K) -> int {
-      const CentView zc{z32, z64, zQ, zoff, K, v.d};
-      CK(d2k::assign(sub, zc, cnt, K, cfg, nullptr, lab, dd, nullptr, fo, cand, c->d_err,
+      const CentView zc{z32, z64, zQ, zoff, K * nB, v.d};
+      SolveCfg sc = cfg;
+      sc.oidx = act_d;
+      sc.nobj = act_d ? act_n : -1;
+      CK(d2k::assign(sub, zc, cnt, K, sc, nullptr, lab, dd, nullptr, fo, cand, c->d_err,
                      c->stream));
       return check();
     };
@@ -640,31 +671,77 @@ int segment_impl(d2_ctx* c, const ObjView& v, int mmax, const double* om, long l
       return D2_OK;
     };
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-    // start: the first member, then the member farthest from it
-    if ((rc = set_cents(0, 0, 1)) || (rc = solve(1))) return rc;
+    // start: each segment's first member, then the member farthest from it
+    idx.assign((size_t)nB, 0);
+    for (long long b = 0; b < nB; ++b) idx[(size_t)b] = (int)s0[(size_t)b];
+    if ((rc = set_cents(1)) || (rc = solve(1))) return rc;
     hd.resize((size_t)cnt);
     CK(cudaMemcpyAsync(hd.data(), dd, (size_t)cnt * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    int i2 = 0;
-    for (long long t = 1; t < cnt; ++t)
-      if (hd[(size_t)t] > hd[(size_t)i2]) i2 = (int)t;
-    if ((rc = set_cents(0, i2, 2)) || (rc = solve(2)) || (rc = labels_to(hl))) return rc;
-    for (int r = 0; r < iters; ++r) {
-      CK(d2k::update_locations(sub, som, lab, cnt, 2, fo, 2, zoff, v.d, D2_F64, z32, z64, uscr,
+    idx.assign((size_t)KT, 0);
+    for (long long b = 0; b < nB; ++b) {
+      long long i2 = s0[(size_t)b];
+      for (long long t = s0[(size_t)b] + 1; t < s0[(size_t)b + 1]; ++t)
+        if (hd[(size_t)t] > hd[(size_t)i2]) i2 = t;
+      idx[(size_t)(2 * b)] = (int)s0[(size_t)b];
+      idx[(size_t)(2 * b + 1)] = (int)i2;
+    }
+    if ((rc = set_cents(2)) || (rc = solve(2)) || (rc = labels_to(hl))) return rc;
+    // rounds: a segment whose labels repeat is done; its labels are frozen
+    // there (the serial loop stops at that round) while the others go on
+    std::vector<char> done((size_t)nB, 0);
+    long long open = nB;
+    int* dact = static_cast<int*>(grow(c, kSgAct, (size_t)cnt * 4, &rc));
+    int* ulab = static_cast<int*>(grow(c, kSgULab, (size_t)cnt * 4, &rc));
+    if (rc != D2_OK) return rc;
+    std::vector<int> act, hul;
+    for (int r = 0; r < iters && open > 0; ++r) {
+      // finished segments drop out: their objects are not re-solved and
+      // carry label -1 into the update, which leaves their centroids alone
+      const int* ul = lab;
+      if (open < nB) {
+        act.clear();
+        hul = hl;
+        for (long long b = 0; b < nB; ++b) {
+          if (done[(size_t)b]) {
+            std::fill(hul.begin() + s0[(size_t)b], hul.begin() + s0[(size_t)b + 1], -1);
+          } else {
+            for (long long t = s0[(size_t)b]; t < s0[(size_t)b + 1]; ++t) act.push_back((int)t);
+          }
+        }
+        CK(cudaMemcpyAsync(dact, act.data(), act.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(ulab, hul.data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, c->stream));
+        act_d = dact;
+        act_n = (long long)act.size();
+        ul = ulab;
+      }
+      CK(d2k::update_locations(sub, som, ul, cnt, 2, fo, KT, zoff, v.d, D2_F64, z32, z64, uscr,
                                c->stream, spart, spart_n));
       if ((rc = solve(2)) || (rc = labels_to(hl2))) return rc;
-      if (hl2 == hl) break;
-      hl.swap(hl2);
+      for (long long b = 0; b < nB; ++b) {
+        if (done[(size_t)b]) continue;
+        const auto lo = hl.begin() + s0[(size_t)b], hi = hl.begin() + s0[(size_t)b + 1];
+        if (std::equal(lo, hi, hl2.begin() + s0[(size_t)b])) {
+          done[(size_t)b] = 1;
+          --open;
+        } else {
+          std::copy(hl2.begin() + s0[(size_t)b], hl2.begin() + s0[(size_t)b + 1], lo);
+        }
+      }
     }
-    std::vector<int> a, b;
-    for (long long t = 0; t < cnt; ++t) (hl[(size_t)t] == 0 ? a : b).push_back(S[(size_t)t]);
-    if (a.empty() || b.empty()) {
-      const long long h = cnt / 2;
-      a.assign(S.begin(), S.begin() + h);
-      b.assign(S.begin() + h, S.end());
+    for (long long b = 0; b < nB; ++b) {
+      const std::vector<int>& S = segs[B[(size_t)b]];
+      std::vector<int> pa, pb;
+      for (size_t t = 0; t < S.size(); ++t)
+        (hl[(size_t)s0[(size_t)b] + t] == 0 ? pa : pb).push_back(S[t]);
+      if (pa.empty() || pb.empty()) {
+        const size_t h = S.size() / 2;
+        pa.assign(S.begin(), S.begin() + h);
+        pb.assign(S.begin() + h, S.end());
+      }
+      segs[B[(size_t)b]] = std::move(pa);
+      segs.push_back(std::move(pb));
     }
-    segs[big] = std::move(a);
-    segs.push_back(std::move(b));
   }
   std::vector<size_t> order(segs.size());
   for (size_t k = 0; k < segs.size(); ++k) order[k] = k;

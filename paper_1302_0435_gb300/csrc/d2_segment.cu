@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "d2_internal.h"
+#include "d2_segment.h"
 
 namespace d2k {
 namespace {
@@ -101,7 +102,34 @@ __global__ void k_seg_cents(const void* loc, int ldt, const long long* __restric
   if (threadIdx.x == 0) coff[K] = base;
 }
 
+// Start centroids of several splits at once: centroid t is compact bag
+// idx[t] with uniform weights 1/s, FP64 locations, at row coff[t] (the
+// prefix of the bags' sizes, k_seg_offsets).  One warp per centroid.
+__global__ void k_seg_cents_list(const void* loc, int ldt, const long long* __restrict__ off,
+                                 int d, const int* __restrict__ idx, long long KT,
+                                 const long long* __restrict__ coff, double* __restrict__ cloc,
+                                 double* __restrict__ cw) {
+  const int lane = threadIdx.x & 31;
+  for (long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; t < KT;
+       t += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const long long i = idx[t];
+    const long long r0 = off[i], n = off[i + 1] - r0, base = coff[t];
+    for (long long e = lane; e < n * d; e += 32) cloc[base * d + e] = ld_any(loc, ldt, r0 * d + e);
+    for (long long r = lane; r < n; r += 32) cw[base + r] = 1.0 / (double)n;
+  }
+}
+
 }  // namespace
+
+cudaError_t seg_cents_list(const ObjView& v, const int* idx, long long KT, double* cloc,
+                           double* cw, long long* coff, cudaStream_t st) {
+  if (KT <= 0) return cudaSuccess;
+  k_seg_offsets<<<1, 1024, 0, st>>>(v.off, idx, KT, coff);
+  const unsigned gb = (unsigned)((KT * 32 + 255) / 256 < 8192 ? (KT * 32 + 255) / 256 : 8192);
+  k_seg_cents_list<<<gb, 256, 0, st>>>(v.loc, v.ldt, v.off, v.d, idx, KT, coff, cloc, cw);
+  note_launches(2);
+  return cudaGetLastError();
+}
 
 cudaError_t seg_gather(const ObjView& v, const int* members, long long cnt, const double* om_in,
                        long long* off_out, void* loc_out, void* w_out, double* om_out,

@@ -89,3 +89,26 @@ def test_constrained_level_conserves_weight_and_labels_members(oracle_mod):
     assert abs(w.sum() - omega.sum()) <= 1e-9 * omega.sum()
     assert C.min() >= 0 and C.max() < 4
     assert np.allclose(np.bincount(C, weights=omega, minlength=4), w)
+
+
+def test_split_order_does_not_change_the_partition(oracle_mod):
+    """A split depends only on its own members, so splitting every segment
+    above tau generation by generation (as the device batches them) gives
+    the partition of largest-first splitting."""
+    objs, _ = synth.image_like(N=260, K=2, seed=37)
+    tau, iters = 40, 4
+    ref, M = oracle_mod.segment(objs, None, tau, iters)
+    segs = [np.arange(objs.count, dtype=np.int64)]
+    while any(len(s) > tau for s in segs):
+        nxt = []
+        for s in segs:
+            if len(s) > tau:
+                a, b = oracle_mod.split_binary(objs, None, s, iters)
+                nxt += [a, b]
+            else:
+                nxt.append(s)
+        segs = nxt
+    got = np.empty(objs.count, dtype=np.int64)
+    for new_id, s in enumerate(sorted(segs, key=lambda s: int(s[0]))):
+        got[s] = new_id
+    assert len(segs) == M and np.array_equal(got, ref)

@@ -119,3 +119,23 @@ def test_update_weights_per_cluster(oracle_mod):
             x, wx = oracle_mod.bag(objs, i)
             tot += oracle_mod.transport(oracle_mod.cost(z, x), pj / pj.sum(), wx / wx.sum())[0]
         assert tot == pytest.approx(eps[j], rel=1e-9)
+
+
+def test_hand_derived_optima(oracle_mod):
+    """Hand-derived values of the joint LP (tests/golden/joint_hand.json),
+    including a face of optimal weights."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "joint_hand.json")) as f:
+        g = json.load(f)
+    z = np.asarray(g["z"], dtype=float)[:, None]
+    for case in g["cases"]:
+        cs, qs = [], []
+        for xs, ws in case["bags"]:
+            cs.append(oracle_mod.cost(z, np.asarray(xs, dtype=float)[:, None]))
+            qs.append(np.asarray(ws, dtype=float) / np.sum(ws))
+        eps, p = oracle_mod.joint_lp(cs, qs, np.asarray(case["omega"], dtype=float))
+        assert eps == pytest.approx(case["eps"], rel=1e-12), case["name"]
+        lo, hi = case["p0_range"]
+        assert lo - 1e-9 <= p[0] <= hi + 1e-9, case["name"]
+        assert p.sum() == pytest.approx(1.0, abs=1e-12)

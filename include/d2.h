@@ -92,6 +92,17 @@ extern "C" {
                                     weights by the joint LP (d2_update_weights), then the
                                     locations with flows at the new weights */
 
+/* which screened pairs are certified in FP64 (d2_config.certify) */
+#define D2_CERTIFY_CANDIDATES 0  /* only the centroids the FP32 error bound cannot rule
+                                    out of the argmin (labels and dist2 stay FP64-exact) */
+#define D2_CERTIFY_ALL 1         /* every (object, centroid) pair: the FP32-optimal basis
+                                    of each pair gets an FP64 optimality certificate (FP64
+                                    costs on the basis, FP64 potentials and objective,
+                                    reduced costs checked against a rounding bound), so its
+                                    D^2 is the FP64 objective of a feasible plan within
+                                    max(2^-24 D^2, 2^-43 c_max) of the optimum; a pair that
+                                    fails the check is solved to FP64 optimality */
+
 /* segments of d2_cluster_level (d2_config.segmentation) */
 #define D2_SEG_SLICES 0       /* contiguous slices of seg_size objects */
 #define D2_SEG_CONSTRAINED 1  /* the binary constrained D2 splits of d2_segment */
@@ -139,6 +150,9 @@ typedef struct {
     int32_t joint_max_iter;     /* D2_UPDATE_ALG1: cutting-plane rounds per weight update;
                                    0 = 512 */
     double joint_tol;           /* D2_UPDATE_ALG1: relative gap of the weight LP; 0 = 1e-9 */
+    int32_t certify;            /* D2_CERTIFY_* : d2_assign and d2_cluster_level;
+                                   0 = CANDIDATES */
+    int32_t reserved;
 } d2_config;
 
 /*
@@ -236,6 +250,20 @@ int d2_mallows_batch(d2_ctx* ctx, const d2_bags* objs, const int64_t* pair_obj,
  */
 int d2_assign(d2_ctx* ctx, const d2_bags* objs, const double* omega, int32_t* labels,
               double* dist2, double* eps_total, d2_flows* flows);
+
+/*
+ * Mallows distance of every (object, resident centroid) pair, Eq. (D2opt)
+ * with z fixed for each z_j, and the argmin of Alg. 2 Step 2 over them:
+ * dist2_all [count][K] (row-major: dist2_all[i*K + j] = D^2(v_i, z_j)),
+ * labels [count] and dist2 [count] as d2_assign (either may be NULL).
+ * Every value is certified in FP64 as with D2_CERTIFY_ALL (FP32 inputs),
+ * or solved in FP64 throughout (FP64 inputs or D2_PREC_FP64): it lies
+ * within max(2^-24 D^2, 2^-43 c_max) of the LP optimum, c_max the pair's
+ * largest ground cost; values the argmin needs closer are solved to FP64
+ * optimality.  Host or device pointers.
+ */
+int d2_mallows_all(d2_ctx* ctx, const d2_bags* objs, double* dist2_all, int32_t* labels,
+                   double* dist2);
 
 /*
  * Centroid location update, Eq. (WeightedUpdate) (Eq. (UpdateZ) when omega
@@ -375,40 +403,53 @@ int d2_server_destroy(d2_server* srv);
 
 /*
  * d2_update_locations_noalloc -- the location update of d2_update_locations
- * (same kernels, same arithmetic, same results) for callers that cannot
- * call cudaMalloc during the call: for instance a framework that owns all
- * device memory through its own caching allocator and a fixed budget, so
- * an outside allocation would exceed or fragment it, or a latency-critical
- * serving loop that must not pay for the allocator's implicit device
- * synchronisation.  It allocates nothing: no cudaMalloc, cudaFree or
- * allocating library routine.  The paper has no counterpart; this is an
- * integration variant only.
+ * (the same kernels) for callers that cannot call cudaMalloc during the
+ * call: for instance a framework that owns all device memory through its
+ * own caching allocator and a fixed budget, so an outside allocation would
+ * exceed or fragment it, or a latency-critical serving loop that must not
+ * pay for the allocator's implicit device synchronisation.  It allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.  The
+ * paper has no counterpart; this is an integration variant only.
+ *
+ * Results: with at most 512*K bags, d2_update_locations sums each centroid
+ * in one block, as this call always does, and the two give identical
+ * centroids.  Beyond that d2_update_locations splits large clusters over
+ * several blocks and adds the parts, a different summation order; the two
+ * then agree to the rounding of those FP64 sums, i.e. within one unit in
+ * the last place of the centroid location type (cent_loc_dtype) after the
+ * final rounding to it.
  *
  * Scratch: a fixed array of about 3 MB in the library's own device memory
  * (a file-scope __device__ array), which every GPU that loads the library
- * holds until the process exits.  Limits: at most 262,144 bags and 1,024
- * centroids per call; larger calls return D2_EUNSUPPORTED.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress,
- * once per device, with the device current); make that first call before
- * any stream capture.  Every call shares the one array: calls whose work
+ * holds until the process exits.  With lazy module loading the first call
+ * on a device may be the one that loads the module and, with it, that
+ * array.  Limits: at most 262,144 bags and 1,024 centroids per call; larger
+ * calls return D2_EUNSUPPORTED.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress, once per device, with the
+ * device current).  Every call shares the one array: calls whose work
  * overlaps on the GPU (other streams, other host threads) race and give
- * wrong results, so serialise them.  The sort counters are cleared at the
- * start of every call.
+ * wrong results, so serialise them.  The sort counters and the offset check
+ * words are cleared at the start of every call.
  *
- * Arguments (all device pointers, caller-owned; host pointers -> D2_EINVAL):
- *   objs, omega (may be NULL = all ones), labels [N] int32 (centroid index
- *   in [0,K), others ignored), flows (required: the d2_assign flow records
- *   of the assigned pairs), cent_off [K+1] int64 (centroid j owns supports
- *   [cent_off[j], cent_off[j+1]), at most 64),
- *   cent_loc64 [T][dim] FP64 centroid locations, updated in place,
- *   cent_loc32 [T][dim] FP32 mirror, rewritten where a location changes,
- *   cent_loc_dtype: the centroid location type the FP64 result is rounded
- *   to (as d2_set_centroids' loc_dtype does for the resident set),
- *   cuda_stream: the stream to enqueue on (NULL = legacy default stream).
- * It waits once for the stream to read and check cent_off (each centroid
- * 1..D2_MAX_SUPPORT supports, else D2_EINVAL), then enqueues the update and
- * returns without waiting for it.  Flow entries that are not cells of
- * their pair are ignored.
+ * Waiting: every call waits once on cuda_stream, to read back the check of
+ * the bag offsets and the centroid offsets; it therefore cannot be
+ * captured into a CUDA graph.  After that wait it enqueues the update and
+ * returns without waiting for it.
+ *
+ * Arguments (all device pointers of the current device, caller-owned; host
+ * pointers or another device's memory -> D2_EINVAL):
+ *   objs (offsets checked on the device: off[0] = 0 and every bag
+ *   1..D2_MAX_SUPPORT supports, else D2_EINVAL), omega (may be NULL = all
+ *   ones), labels [N] int32 (centroid index in [0,K), others ignored), flows
+ *   (required: the d2_assign flow records of the assigned pairs; entries
+ *   that are not cells of their pair are ignored), cent_off [K+1] int64
+ *   (centroid j owns supports [cent_off[j], cent_off[j+1]), 1..D2_MAX_SUPPORT
+ *   of them, else D2_EINVAL), cent_loc64 [T][dim] FP64 centroid locations,
+ *   updated in place, cent_loc32 [T][dim] FP32 mirror, rewritten where a
+ *   location changes, cent_loc_dtype: the centroid location type the FP64
+ *   result is rounded to (as d2_set_centroids' loc_dtype does for the
+ *   resident set), cuda_stream: the stream to enqueue on (NULL = legacy
+ *   default stream).
  */
 int d2_update_locations_noalloc(const d2_bags* objs, const double* omega, const int32_t* labels,
                                 const d2_flows* flows, int64_t K, const int64_t* cent_off,
@@ -421,7 +462,10 @@ int d2_update_locations_noalloc(const d2_bags* objs, const double* omega, const 
  * solved on the FP32 screening path and their simplex pivots; pair LPs
  * solved to FP64 optimality and their pivots (FP32 warm start + FP64);
  * cutting-plane rounds of d2_update_weights (summed over calls) and the
- * pivots of its per-cluster master LPs.
+ * pivots of its per-cluster master LPs; screened pairs whose FP32-optimal
+ * basis passed the FP64 certificate of D2_CERTIFY_ALL (the others are
+ * solved to FP64 optimality and counted in pairs_exact), and the cells the
+ * certificate had to re-price in FP64.
  * Reading the device counters synchronises the current device.
  */
 typedef struct {
@@ -432,7 +476,8 @@ typedef struct {
     int64_t pivots_exact;
     int64_t joint_rounds;
     int64_t joint_master_pivots;
-    int64_t reserved[1];
+    int64_t pairs_certified;
+    int64_t cells_checked;
 } d2_stats;
 int d2_get_stats(d2_stats* out);
 

@@ -43,6 +43,8 @@ enum Slot {
   // joint weights (Alg. 1 Step 1)
   kJState, kJPot, kJPStart, kJEps, kJIters, kJSort, kJPObj, kJPCen, kJW, kJSt,
   kPairTree,
+  // d2_mallows_all
+  kAllLab, kAllD2, kAllPair,
   kSlots
 };
 
@@ -250,6 +252,7 @@ SolveCfg solve_cfg(const d2_ctx* c, int mode, int mmax) {
   s.budget = c->cfg.pivot_budget > 0 ? c->cfg.pivot_budget : 64;
   s.sms = c->sms;
   s.start = start_default(c);
+  s.certify = mode == 1 && c->cfg.certify == D2_CERTIFY_ALL;
   return s;
 }
 
@@ -416,9 +419,12 @@ int make_bins(d2_ctx* c, const ObjView& v, int nmax, Bins* b) {
 int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, int K, int mode,
                int mmax, const double* om, int* lab, double* d2o, double* terms, FlowOut fo,
                int* cand, const d2k::WarmStore* ws, const Bins& bins,
-               const d2k::TcWork* tw = nullptr) {
+               const d2k::TcWork* tw = nullptr, bool certify_all = false,
+               double* pair64 = nullptr) {
   const int nmax = std::max(c->nmax, 1);
   SolveCfg base = solve_cfg(c, mode, mmax);
+  if (certify_all && mode == 1) base.certify = true;
+  base.pair64 = pair64;
   if (!bins.binned) {
     CK(d2k::assign(v, cv, seg, K, base, om, lab, d2o, terms, fo, cand, c->d_err, c->stream, ws, tw));
     return D2_OK;
@@ -430,11 +436,13 @@ int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, i
     cfg.mmax = std::max(1, std::min(mmax, 32 * (b + 1) - nmax));
     cfg.oidx = bins.order + bins.hstart[b];
     cfg.nobj = cnt;
-    const auto key = std::make_tuple(b, (long long)K, cfg.mmax, nmax, v.d, mode);
+    const auto key = std::make_tuple(b, (long long)K, cfg.mmax, nmax, v.d,
+                                     mode + (cfg.certify ? 2 : 0));
     auto it = c->tuned.find(key);
     if (it == c->tuned.end() && c->cfg.group_lanes == 0 && mode == 1 && cnt >= 8192) {
       // autotune on a sample of this bin: threads per block x screening items per SM
       SolveCfg t = cfg;
+      t.pair64 = nullptr;
       // a sample of about 2^17 pairs, at least 256 objects
       t.nobj = std::min<long long>(cnt, std::max<long long>(256, (1LL << 17) / std::max(K, 1)));
       int rc = D2_OK;
@@ -1060,10 +1068,14 @@ int d2_mallows_batch(d2_ctx* c, const d2_bags* objs, const int64_t* pair_obj, co
   return D2_OK;
 }
 
-int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labels, double* dist2,
-              double* eps_total, d2_flows* flows) {
-  d2k::TraceRange trace_("d2_assign");
-  if (!c || !bags_ok(objs) || !labels || !dist2) return D2_EINVAL;
+namespace {
+
+// d2_assign, and with dist2_all (or certify_all) d2_mallows_all: every pair
+// certified in FP64, the pair values into dist2_all [N][K].
+int assign_impl(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labels,
+                double* dist2, double* eps_total, d2_flows* flows, double* dist2_all,
+                bool certify_all) {
+  if (!c || !bags_ok(objs)) return D2_EINVAL;
   if (c->K == 0) return D2_ENOCENTROIDS;
   if (objs->dim != c->d) return D2_EINVAL;
   if (objs->count == 0) {
@@ -1085,9 +1097,21 @@ int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labe
   if ((rc = stage_in(c, omega, (size_t)N, kOmega, &om))) return rc;
   int* dl;
   double* dd;
-  bool h1, h2, h3 = false, h4 = false;
-  if ((rc = stage_out(c, labels, (size_t)N, kOutLab, &dl, &h1))) return rc;
-  if ((rc = stage_out(c, dist2, (size_t)N, kOutD2, &dd, &h2))) return rc;
+  double* dall = nullptr;
+  bool h1 = false, h2 = false, h3 = false, h4 = false, h5 = false;
+  if (labels) {
+    if ((rc = stage_out(c, labels, (size_t)N, kOutLab, &dl, &h1))) return rc;
+  } else {
+    dl = static_cast<int*>(grow(c, kAllLab, (size_t)N * 4, &rc));
+  }
+  if (dist2) {
+    if ((rc = stage_out(c, dist2, (size_t)N, kOutD2, &dd, &h2))) return rc;
+  } else {
+    dd = static_cast<double*>(grow(c, kAllD2, (size_t)N * 8, &rc));
+  }
+  if (rc != D2_OK) return rc;
+  if (dist2_all && (rc = stage_out(c, dist2_all, (size_t)(N * c->K), kAllPair, &dall, &h5)))
+    return rc;
   FlowOut fo{nullptr, nullptr, 0};
   if (flows) {
     fo.stride = flows->stride;
@@ -1111,7 +1135,7 @@ int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labe
   const bool tc = tc_wanted(c, objs, v, mode);
   if (tc && (rc = tc_work(c, N * (long long)mmax, mmax, &tw))) return rc;
   if ((rc = run_assign(c, v, resident_view(c), N, (int)c->K, mode, mmax, om, dl, dd, terms, fo,
-                       cand, nullptr, bins, tc ? &tw : nullptr)))
+                       cand, nullptr, bins, tc ? &tw : nullptr, certify_all, dall)))
     return rc;
   if (eps_total) {
     double* de = static_cast<double*>(grow(c, kEpsOut, 8, &rc));
@@ -1123,12 +1147,29 @@ int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labe
   if (h2) CK(cudaMemcpyAsync(dist2, dd, (size_t)N * 8, cudaMemcpyDeviceToHost, c->stream));
   if (h3) CK(cudaMemcpyAsync(flows->cell, fo.cell, (size_t)(N * fo.stride) * 4, cudaMemcpyDeviceToHost, c->stream));
   if (h4) CK(cudaMemcpyAsync(flows->w, fo.w, (size_t)(N * fo.stride) * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (h5) CK(cudaMemcpyAsync(dist2_all, dall, (size_t)(N * c->K) * 8, cudaMemcpyDeviceToHost, c->stream));
   int bits = 0;
   if ((rc = read_err(c, &bits))) return rc;
   if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
   if (bits & d2k::kErrInvalid) return D2_EINVAL;
   if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
   return D2_OK;
+}
+
+}  // namespace
+
+int d2_assign(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* labels, double* dist2,
+              double* eps_total, d2_flows* flows) {
+  d2k::TraceRange trace_("d2_assign");
+  if (!labels || !dist2) return D2_EINVAL;
+  return assign_impl(c, objs, omega, labels, dist2, eps_total, flows, nullptr, false);
+}
+
+int d2_mallows_all(d2_ctx* c, const d2_bags* objs, double* dist2_all, int32_t* labels,
+                   double* dist2) {
+  d2k::TraceRange trace_("d2_mallows_all");
+  if (!dist2_all) return D2_EINVAL;
+  return assign_impl(c, objs, nullptr, labels, dist2, nullptr, nullptr, dist2_all, true);
 }
 
 namespace {
@@ -1719,12 +1760,14 @@ int d2_get_stats(d2_stats* out) {
   std::memset(out, 0, sizeof(*out));
   out->kernel_launches = d2k::launches();
   d2k::joint_counters(&out->joint_rounds, &out->joint_master_pivots);
-  long long v[4];
+  long long v[6];
   if (d2k::solver_stats(v) == cudaSuccess) {
     out->pairs_screened = v[0];
     out->pivots_screened = v[1];
     out->pairs_exact = v[2];
     out->pivots_exact = v[3];
+    out->pairs_certified = v[4];
+    out->cells_checked = v[5];
   } else {
     cudaGetLastError();
   }

@@ -119,6 +119,13 @@ struct SolveCfg {
   // for an invalid bag); screen_only: no FP64 certification launch
   float* pair_out = nullptr;
   bool screen_only = false;
+  // certify every screened pair in FP64 (see certify_fp64 in d2_solve.cuh):
+  // a pair whose FP32-optimal basis passes the FP64 reduced-cost check keeps
+  // its FP64 objective; one that fails is sent to the exact pass with its
+  // object's candidates.  pair64 (optional, certify only): [count][K] FP64
+  // D^2 of every pair, pair64[i*K + j] (j local to the object's segment).
+  bool certify = false;
+  double* pair64 = nullptr;
   TileView tile;              // precomputed FP32 tiles of the screen (optional)
   // mallows_pairs with mode 1: room (pair_tree_bytes) for the FP32 bases
   // handed from the FP32 launch to the FP64 launch; null: one fused launch
@@ -163,7 +170,7 @@ cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, in
                                    const long long* pobj, const long long* pcen,              \
                                    long long npairs, const SolveCfg& cfg, double* dist2,       \
                                    FlowOut fo, int* status, int* d_err, cudaStream_t st);     \
-  cudaError_t stats_npl##N(long long out[4]);
+  cudaError_t stats_npl##N(long long out[6]);
 D2_NPL_DECL(1)
 D2_NPL_DECL(2)
 D2_NPL_DECL(3)
@@ -232,9 +239,13 @@ cudaError_t tc_extract(const float* C, long long ldc, int m, long long c0, int n
 // nobj*ceil(want/nobj) <= want + count items, want <= sms*256.
 // The screen keeps up to kCandCap candidates per (object, centroid block)
 // item and per object; more means the object is certified against all K.
+// An item record also carries the FP64 value of its smallest upper end's
+// centroid when that pair was certified (two ints of double bits, NaN
+// otherwise); a merged record carries the object's.
 constexpr int kCandCap = 16;
-constexpr int kItemInts = 2 + 2 * kCandCap;  // count, centroids, lower ends, best upper end
-constexpr int kMergedInts = 1 + kCandCap;    // count, centroids
+// count, centroids, lower ends, best upper end, certified FP64 value of that centroid
+constexpr int kItemInts = 2 + 2 * kCandCap + 2;
+constexpr int kMergedInts = 1 + kCandCap + 2;  // count, centroids, certified FP64 value
 inline long long assign_scratch_ints(long long count, long long K, int sms = 160) {
   (void)K;
   return 4 + ((count * kMergedInts + 3) & ~3LL) + (count + (long long)sms * 256) * kItemInts + 4;
@@ -291,7 +302,8 @@ int device_sms(int dev);
 // kernel launches issued by this library (all contexts)
 void note_launches(long long k);
 long long launches();
-// pairs screened, their pivots, pairs solved exactly, their pivots
-cudaError_t solver_stats(long long out[4]);
+// pairs screened, their pivots, pairs solved exactly, their pivots,
+// screened pairs certified in FP64, cells the certificate checked in FP64
+cudaError_t solver_stats(long long out[6]);
 
 }  // namespace d2k

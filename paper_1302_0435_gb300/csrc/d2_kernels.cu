@@ -127,14 +127,14 @@ void note_launches(long long k) { __atomic_fetch_add(&g_launches, (unsigned long
 long long launches() { return (long long)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 // Sum of the solver counters of the units that hold the solver kernels.
-cudaError_t solver_stats(long long out[4]) {
+cudaError_t solver_stats(long long out[6]) {
   cudaError_t (*const units[4])(long long*) = {stats_npl1, stats_npl2, stats_npl3, stats_npl4};
-  for (int i = 0; i < 4; ++i) out[i] = 0;
+  for (int i = 0; i < 6; ++i) out[i] = 0;
   for (auto f : units) {
-    long long v[4];
+    long long v[6];
     const cudaError_t e = f(v);
     if (e != cudaSuccess) return e;
-    for (int i = 0; i < 4; ++i) out[i] += v[i];
+    for (int i = 0; i < 6; ++i) out[i] += v[i];
   }
   return cudaSuccess;
 }

@@ -19,9 +19,13 @@ constexpr long long kChunkBags = 1024;   // chunk size of the label sort
 
 constexpr size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 // Same layout as d2k::update_scratch_bytes(kMaxBags, kMaxCents).
-constexpr size_t kScratchBytes =
+constexpr size_t kSortBytes =
     al256((size_t)((kMaxBags + kChunkBags - 1) / kChunkBags) * kMaxCents * 4) +
     al256((size_t)(kMaxCents + 1) * 8) * 2 + al256((size_t)kMaxBags * 4) * 2;
+// After the sort area: two ints for the bag-offset check (largest support
+// count, invalid-offset flag).
+constexpr size_t kInfoBytes = 256;
+constexpr size_t kScratchBytes = kSortBytes + kInfoBytes;
 
 // The scratch: allocated with the module, so every GPU that loads this
 // library holds kScratchBytes (about 3 MB) until the process exits.
@@ -52,14 +56,17 @@ int scratch_for_current_device(void** out) {
   return D2_OK;
 }
 
-bool on_device(const void* p) {
+// Device (or managed) memory of the current device: host memory and
+// another GPU's memory are refused.
+bool on_device(const void* p, int dev) {
   if (!p) return false;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -79,25 +86,38 @@ extern "C" int d2_update_locations_noalloc(const d2_bags* objs, const double* om
       d2k::update_scratch_bytes(objs->count, K) > kScratchBytes)
     return D2_EUNSUPPORTED;
   if (objs->count == 0) return D2_OK;
-  // every buffer must already be in device memory: no staging copies
-  if (!on_device(objs->loc) || !on_device(objs->w) || !on_device(objs->off) ||
-      !on_device(labels) || !on_device(flows->cell) || !on_device(flows->w) ||
-      !on_device(cent_off) || !on_device(cent_loc64) || !on_device(cent_loc32) ||
-      (omega && !on_device(omega)))
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return D2_ECUDA;
+  }
+  // every buffer must already be in this device's memory: no staging copies
+  if (!on_device(objs->loc, dev) || !on_device(objs->w, dev) || !on_device(objs->off, dev) ||
+      !on_device(labels, dev) || !on_device(flows->cell, dev) || !on_device(flows->w, dev) ||
+      !on_device(cent_off, dev) || !on_device(cent_loc64, dev) || !on_device(cent_loc32, dev) ||
+      (omega && !on_device(omega, dev)))
     return D2_EINVAL;
   void* scratch = nullptr;
   const int rc = scratch_for_current_device(&scratch);
   if (rc != D2_OK) return rc;
-  // Check the centroid offsets (the accumulator holds at most
-  // D2_MAX_SUPPORT supports per centroid): read them into a stack array.
   const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // Check the bag offsets on the device (off[0] = 0, every bag 1..64
+  // supports) into the info words after the sort area, and read them back
+  // with the centroid offsets (the accumulator holds at most D2_MAX_SUPPORT
+  // supports per centroid) in one wait on the stream.
+  int* info_dev = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) + kSortBytes);
+  int info[2] = {0, 0};
   long long hoff[kMaxCents + 1];
-  if (cudaMemcpyAsync(hoff, cent_off, (size_t)(K + 1) * sizeof(long long), cudaMemcpyDeviceToHost,
+  if (d2k::scan_bags(reinterpret_cast<const long long*>(objs->off), objs->count, info_dev, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(info, info_dev, sizeof(info), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(hoff, cent_off, (size_t)(K + 1) * sizeof(long long), cudaMemcpyDeviceToHost,
                       st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     return D2_ECUDA;
   }
+  if (info[1] != 0 || info[0] < 1 || info[0] > D2_MAX_SUPPORT) return D2_EINVAL;
   if (hoff[0] != 0) return D2_EINVAL;
   for (long long j = 0; j < K; ++j) {
     const long long n = hoff[j + 1] - hoff[j];

@@ -19,6 +19,6 @@ cudaError_t mallows_pairs_npl3(const ObjView& ob, const CentView& cv, const long
   return mallows_pairs_st<32, 3>(ob, cv, pobj, pcen, npairs, cfg, dist2, fo, status, d_err, st);
 }
 
-cudaError_t stats_npl3(long long out[4]) { return read_unit_stats(out); }
+cudaError_t stats_npl3(long long out[6]) { return read_unit_stats(out); }
 
 }  // namespace d2k

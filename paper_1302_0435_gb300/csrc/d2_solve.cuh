@@ -20,15 +20,20 @@ namespace {
 
 
 // Solver activity counters: pairs screened, their pivots, pairs solved
-// exactly, their pivots.  Accumulated once per lane group per launch.
-__device__ unsigned long long g_solver_stats[4];
+// exactly, their pivots, screened pairs certified in FP64, cells the
+// certificate checked in FP64.  Accumulated once per lane group per launch.
+constexpr int kStatWords = 6;
+__device__ unsigned long long g_solver_stats[kStatWords];
 
 __device__ __forceinline__ void add_stats(unsigned long long a, unsigned long long b,
-                                          unsigned long long c, unsigned long long d) {
+                                          unsigned long long c, unsigned long long d,
+                                          unsigned long long e = 0, unsigned long long f = 0) {
   if (a) atomicAdd(&g_solver_stats[0], a);
   if (b) atomicAdd(&g_solver_stats[1], b);
   if (c) atomicAdd(&g_solver_stats[2], c);
   if (d) atomicAdd(&g_solver_stats[3], d);
+  if (e) atomicAdd(&g_solver_stats[4], e);
+  if (f) atomicAdd(&g_solver_stats[5], f);
 }
 
 // ---------------------------------------------------------------- loads --
@@ -606,7 +611,189 @@ __device__ __forceinline__ float tc_bound(int d, float nxm, float cn, float cd) 
   return (e1 + e2) * (1.f + 0x1p-10f);
 }
 
-template <int G, int NPL, bool TC, int ST>
+// FP64 ground cost of cell (a, r) of a pair, by explicit differences in
+// coordinate order (the arithmetic of build_cost<double>, so the same value
+// as the FP64 tile's cell); the table entry with symbol ground costs.
+__device__ __forceinline__ double cost64_cell(const ObjView& ob, long long o0, const CentView& cv,
+                                              long long c0, int a, int r) {
+  if (cv.A) {  // ids checked before the launch; the clamp only keeps reads in the table
+    int xs = (int)ldx<double>(ob.loc, ob.ldt, o0 + a);
+    int ys = (int)cv.loc64[c0 + r];
+    xs = xs < 0 ? 0 : (xs >= cv.A ? cv.A - 1 : xs);
+    ys = ys < 0 ? 0 : (ys >= cv.A ? cv.A - 1 : ys);
+    return cv.tab64[xs * cv.A + ys];
+  }
+  const int d = cv.d;
+  const double* y = cv.loc64 + (c0 + r) * d;
+  const long long x0 = (o0 + a) * d;
+  double acc = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const double df = ldx<double>(ob.loc, ob.ldt, x0 + k) - y[k];
+    acc = fma(df, df, acc);
+  }
+  return acc;
+}
+
+// FP64 certificate of the basis an FP32 solve stopped at (precision
+// pattern: FP32 pivots, FP64 optimality check and objective).
+//   1. The costs of the m+n-1 basic cells (tree edges) in FP64; the FP64
+//      objective D = sum w c of the basic flows (exact integer masses), an
+//      upper bound of the optimum since the basis is feasible; FP64
+//      potentials u_a + v_r = c_ar on every tree edge (pointer jumping).
+//   2. LP duality: for any optimal plan w*, D* = sum w* (u + v + d) =
+//      D + sum w* d >= D + min d, because sum w* = 1 and the marginals are
+//      those of the basis.  So D - D* <= max(0, -min d) over all cells.
+//   3. min d is checked in FP32 against a rounding bound: with the FP32
+//      tile c32, potentials rounded to FP32 and two FP32 subtractions,
+//      |d32 - d| <= E = ecost + 2^-24 (2 c_max + 5 p_max) (ecost bounds
+//      |c32 - c| per cell, p_max the largest |potential|), so d32 >= E - tau
+//      implies d >= -tau.  The few cells below that are re-priced in FP64.
+// Returns true when every reduced cost is >= -tau, tau = max(2^-24 D,
+// 2^-43 c_max): the pair's D^2 is then certified, D - tau <= D* <= D.  *D64:
+// the FP64 objective of the basis (valid whatever the outcome); *nchk: cells
+// re-priced in FP64.  Overwrites the basic cells of the FP32 tile and the
+// solver's pivot scratch; the tree is untouched.
+template <int G, int NPL>
+__device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long long o0,
+                             const CentView& cv, long long c0, float cmax, float ecost,
+                             double* D64, int* nchk) {
+  const Grp<G>& g = S.g;
+  const int m = S.m, n = S.n, N = S.N;
+  const PairMem<float>& s = S.s;
+  double ec[NPL];
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < NPL; ++k) {
+    const int y = S.node_of(k);
+    ec[k] = 0.0;
+    if (y < N && y != S.root) {
+      const int p = S.t.par[k];
+      const int a = y < m ? y : p;
+      const int r = y < m ? p - m : y - m;
+      ec[k] = cost64_cell(ob, o0, cv, c0, a, r);
+      acc += ((double)S.t.flow[k] * kInvMass) * ec[k];
+    }
+  }
+  const double D = gsum<G>(g, acc);
+  *D64 = D;
+  // FP64 potentials: pot(root) = 0, pot(y) = c(y, par y) - pot(par y)
+  double* P64 = reinterpret_cast<double*>(s.pflow);  // [N] final potentials
+  double pot[NPL];
+  bool bad = false;
+  if constexpr (NPL == 1 && G == 32) {
+    const int y = g.lane;
+    int code = y;
+    double a = 0.0;
+    if (y < N && y != S.root) {
+      const int p = S.t.par[0];
+      if (p < 0 || p >= N || (y < m) == (p < m)) { bad = true; code = S.root; }
+      else { code = p | (1 << 16); a = ec[0]; }
+    }
+    for (int round = 0;; ++round) {
+      if (round > 9) { bad = true; break; }
+      const int an = code & 0xffff;
+      const int c2 = __shfl_sync(g.mask, code, an);
+      const double v = __shfl_sync(g.mask, a, an);
+      const bool mv = y < N && an != S.root;
+      if (mv) {
+        const int par1 = code >> 16;
+        a = par1 ? a - v : a + v;
+        code = (c2 & 0xffff) | ((par1 ^ (c2 >> 16)) << 16);
+      }
+      if (!gany<G>(g, mv)) break;
+    }
+    pot[0] = a;
+  } else {
+    int* pa = s.pj0;
+    int* pb = s.pj1;
+    double* aa = P64;
+    double* ab = reinterpret_cast<double*>(s.acc0);  // acc0 and acc1 together: N doubles
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = S.node_of(k);
+      if (y == S.root) { pa[y] = y; aa[y] = 0.0; }
+      else if (y < N) {
+        const int p = S.t.par[k];
+        if (p < 0 || p >= N || (y < m) == (p < m)) { bad = true; pa[y] = S.root; aa[y] = 0.0; }
+        else { pa[y] = p | (1 << 16); aa[y] = ec[k]; }
+      }
+    }
+    g.sync();
+    for (int round = 0;; ++round) {
+      if (round > 9) { bad = true; break; }
+      bool moved = false;
+#pragma unroll
+      for (int k = 0; k < NPL; ++k) {
+        const int y = S.node_of(k);
+        if (y < N) {
+          const int code = pa[y];
+          const int an = code & 0xffff;
+          if (an != S.root) {
+            const int c2 = pa[an];
+            const double v = aa[an];
+            const int par1 = code >> 16;
+            ab[y] = par1 ? aa[y] - v : aa[y] + v;
+            pb[y] = (c2 & 0xffff) | ((par1 ^ (c2 >> 16)) << 16);
+            moved = true;
+          } else {
+            ab[y] = aa[y];
+            pb[y] = code;
+          }
+        }
+      }
+      g.sync();
+      int* tp = pa; pa = pb; pb = tp;
+      double* ta = aa; aa = ab; ab = ta;
+      if (!gany<G>(g, moved)) break;
+    }
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = S.node_of(k);
+      pot[k] = y < N ? aa[y] : 0.0;
+    }
+    g.sync();
+  }
+  // potentials to shared memory (FP64 for re-pricing, FP32 for the scan);
+  // the basic cells leave the scan (+inf in the FP32 tile)
+  float pmax = 0.f;
+#pragma unroll
+  for (int k = 0; k < NPL; ++k) {
+    const int y = S.node_of(k);
+    if (y < N) {
+      const float p32 = (float)pot[k];
+      P64[y] = pot[k];
+      s.pot[y] = p32;
+      pmax = fmaxf(pmax, fabsf(p32));
+      if (y != S.root) s.cost[S.edge_idx(y, S.t.par[k])] = INFINITY;
+    }
+  }
+  pmax = gmax<G>(g, pmax);
+  g.sync();
+  if (gany<G>(g, bad)) { *D64 = NAN; return false; }
+  if (!isfinite(D) || !isfinite(pmax)) return false;
+  const double tau = fmax(0x1p-24 * D, 0x1p-43 * (double)cmax);
+  const double E = ((double)ecost + 0x1p-24 * (2.0 * (double)cmax + 5.0 * (double)pmax)) *
+                   (1.0 + 0x1p-10);
+  const float thr = __double2float_ru(E - tau);
+  const int mn = m * n;
+  int a = S.a0, r = S.r0;
+  bool fail = false;
+  int cnt = 0;
+  for (int i = g.lane; i < mn; i += G) {
+    const float d32 = s.cost[i] - s.pot[a] - s.pot[m + r];
+    if (d32 < thr) {  // +inf (basic) cells never are
+      ++cnt;
+      const double d64 = cost64_cell(ob, o0, cv, c0, a, r) - P64[a] - P64[m + r];
+      fail |= !(d64 >= -tau);
+    }
+    r += S.sr; a += S.sq;
+    if (r >= n) { r -= n; ++a; }
+  }
+  *nchk += cnt;
+  return !gany<G>(g, fail);
+}
+
+template <int G, int NPL, bool TC, int ST, bool CERT>
 __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, CentView cv, long long seg_size, int K,
                                                 int KB, int NB, SolveCfg cfg, size_t slice,
                                                 int* items_out, unsigned long long* queue,
@@ -617,7 +804,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
   const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax, cv.d, 4);  // FP32 only
   int* cand = s32.sc;                                          // [kCandCap]
   float* clo = reinterpret_cast<float*>(s32.sc + kCandCap);    // [kCandCap]
-  int n_scr = 0, p_scr = 0;
+  int n_scr = 0, p_scr = 0, n_cert = 0, n_chk = 0;
   const float rel = (float)(cv.d + 3) * 0x1p-24f + 0x1p-17f;
   const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
   const unsigned long long total = (unsigned long long)nobj * NB;
@@ -650,6 +837,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
     int ncand = 0;
     bool all = false;
     float best_hi = FLT_MAX;
+    double best_d64 = NAN;  // certified FP64 value of the smallest upper end's centroid
     for (int j = j0; ok && j < j1; ++j) {
       const long long c0 = cv.off[cb + j];
       const int n = (int)(cv.off[cb + j + 1] - c0);
@@ -688,16 +876,44 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
         S.store_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
       }
       ++n_scr;
-      if (st != kStOk) all = true;  // no bound: let the exact pass decide
-      const float D = S.template objective<float>();
-      float e = D * rel + cmax * 0x1p-14f;
-      if constexpr (TC) e += tc_bound(cv.d, nxm, cfg.tile.cn[cb + j], cfg.tile.cd[cb + j]);
-      if (cfg.pair_out && g.lane == 0) {
-        float* po = cfg.pair_out + 2 * (i * (long long)K + j);
-        po[0] = D;
-        po[1] = st != kStOk ? INFINITY : e;
+      float lo, hi;
+      double pair_d64 = NAN;
+      if constexpr (CERT) {
+        // every pair certified in FP64 (certify_fp64); one that fails is
+        // always a candidate, so the exact pass solves it
+        double D64 = NAN;
+        bool cert = false;
+        if (st == kStOk) {
+          float ecost;
+          if constexpr (TC) ecost = tc_bound(cv.d, nxm, cfg.tile.cn[cb + j], cfg.tile.cd[cb + j]);
+          else ecost = (cv.A ? 0x1p-23f : (float)(cv.d + 3) * 0x1p-24f) * cmax;
+          cert = certify_fp64<G, NPL>(S, ob, o0, cv, c0, cmax, ecost, &D64, &n_chk);
+        }
+        const double up = D64 * (1.0 + 0x1p-40);  // covers the FP64 rounding of D64
+        if (cert) {
+          ++n_cert;
+          const double tau = fmax(0x1p-24 * D64, 0x1p-43 * (double)cmax);
+          lo = __double2float_rd(D64 - tau);
+          hi = __double2float_ru(up);
+          pair_d64 = D64;
+        } else {
+          lo = -FLT_MAX;
+          hi = isfinite(D64) ? __double2float_ru(up) : FLT_MAX;
+        }
+        if (cfg.pair64 && g.lane == 0) cfg.pair64[i * (long long)K + j] = pair_d64;
+      } else {
+        if (st != kStOk) all = true;  // no bound: let the exact pass decide
+        const float D = S.template objective<float>();
+        float e = D * rel + cmax * 0x1p-14f;
+        if constexpr (TC) e += tc_bound(cv.d, nxm, cfg.tile.cn[cb + j], cfg.tile.cd[cb + j]);
+        if (cfg.pair_out && g.lane == 0) {
+          float* po = cfg.pair_out + 2 * (i * (long long)K + j);
+          po[0] = D;
+          po[1] = st != kStOk ? INFINITY : e;
+        }
+        lo = D - e;
+        hi = D + e;
       }
-      const float lo = D - e, hi = D + e;
       if (lo <= best_hi) {
         if (ncand < kCandCap) {
           if (g.lane == 0) { cand[ncand] = j; clo[ncand] = lo; }
@@ -709,6 +925,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       g.sync();
       if (hi < best_hi) {
         best_hi = hi;
+        best_d64 = pair_d64;
         int k2 = 0;
         for (int c = 0; c < ncand; ++c) {
           const int cj = cand[c];
@@ -725,10 +942,15 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
     }
     if (!ok && cfg.pair_out && g.lane == 0)
       for (int j = j0; j < j1; ++j) cfg.pair_out[2 * (i * (long long)K + j)] = NAN;
+    if (!ok && cfg.pair64 && g.lane == 0)
+      for (int j = j0; j < j1; ++j) cfg.pair64[i * (long long)K + j] = NAN;
     int* out = items_out + item * kItemInts;
     if (g.lane == 0) {
       out[0] = !ok ? -2 : (all ? -1 : ncand);
       out[2 * kCandCap + 1] = __float_as_int(best_hi);
+      const long long bits = __double_as_longlong(best_d64);
+      out[2 * kCandCap + 2] = (int)(unsigned)(bits & 0xffffffffLL);
+      out[2 * kCandCap + 3] = (int)(bits >> 32);
     }
     if (g.lane >= 1 && g.lane <= kCandCap) {
       out[g.lane] = (g.lane <= ncand) ? cand[g.lane - 1] : -1;
@@ -736,7 +958,8 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
     }
     g.sync();
   }
-  if (g.lane == 0) add_stats(n_scr, p_scr, 0, 0);
+  n_chk = gsum<G>(g, n_chk);
+  if (g.lane == 0) add_stats(n_scr, p_scr, 0, 0, n_cert, n_chk);
 }
 
 // Per object: merge its NB block lists into one candidate list (count,
@@ -750,11 +973,13 @@ __global__ void k_merge(const int* items, long long N, int NB, const int* oidx, 
     const int* it = items + tt * NB * kItemInts;
     float best_hi = FLT_MAX;
     int state = 0;  // 0 ok, -1 all, -2 invalid
+    int bbest = 0;  // first block holding the smallest upper end
     for (int b = 0; b < NB; ++b) {
       const int c = it[b * kItemInts];
       if (c == -2) state = -2;
       else if (c == -1 && state == 0) state = -1;
-      best_hi = fminf(best_hi, __int_as_float(it[b * kItemInts + 2 * kCandCap + 1]));
+      const float h = __int_as_float(it[b * kItemInts + 2 * kCandCap + 1]);
+      if (h < best_hi) { best_hi = h; bbest = b; }
     }
     int cnt = 0;
     int* out = cand + i * kMergedInts;
@@ -771,6 +996,10 @@ __global__ void k_merge(const int* items, long long N, int NB, const int* oidx, 
       if (cnt > kCandCap) state = -1;
     }
     out[0] = state == 0 ? cnt : state;
+    // the certified FP64 value of the smallest upper end's centroid (the
+    // only candidate when cnt == 1)
+    out[1 + kCandCap] = it[bbest * kItemInts + 2 * kCandCap + 2];
+    out[2 + kCandCap] = it[bbest * kItemInts + 2 * kCandCap + 3];
   }
 }
 
@@ -802,8 +1031,40 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
     int st = kStOk;
     const int cnt = cand_in ? cand_in[i * kMergedInts] : -1;
     const bool okm = m >= 1 && m <= cfg.mmax && cb + K <= cv.K && cnt != -2;
+    double d64c = NAN;  // certified FP64 value of the single candidate, if any
+    if (cfg.certify && cnt == 1) {
+      const int* mr = cand_in + i * kMergedInts;
+      d64c = __longlong_as_double(((long long)mr[2 + kCandCap] << 32) |
+                                  (long long)(unsigned)mr[1 + kCandCap]);
+    }
     if (!okm || !load_obj_prefix<G>(g, ob, o0, m, s64.P)) {
       st = kStInvalid;
+    } else if (!isnan(d64c)) {
+      // one candidate, certified by the screen: its FP64 value stands; its
+      // flows come from the basis the screen saved (or a re-solve)
+      const int j = cand_in[i * kMergedInts + 1];
+      const long long c0 = cv.off[cb + j];
+      const int n = (int)(cv.off[cb + j + 1] - c0);
+      if (j < 0 || j >= K || n < 1 || n > cfg.nmax || m + n > G * NPL) {
+        st = kStInvalid;
+      } else {
+        best_j = j;
+        best = d64c;
+        if (fo.cell) {
+          Simplex<double, G, NPL> S(s64, m, n, g);
+          if (ws.par8) {
+            const long long wt = (i * (long long)K + j) * ws.ns;
+            S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+          } else {
+            double D;
+            const int s2 = solve_exact<G, NPL, ST>(g, s64, S, ob, o0, m, cv, c0, n, cfg.budget,
+                                                   true, &D, &p_ex);
+            ++n_ex;
+            if (s2 != kStOk) st = s2;
+          }
+          if (st != kStInvalid) S.write_flows(fo.cell + i * fo.stride, fo.w + i * fo.stride, fo.stride);
+        }
+      }
     } else {
       const bool all = cnt < 0;
       const int count = all ? K : cnt;
@@ -832,6 +1093,7 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
                                        &D, &p_ex);
         }
         ++n_ex;
+        if (cfg.pair64 && g.lane == 0) cfg.pair64[i * (long long)K + j] = s2 == kStInvalid ? NAN : D;
         if (s2 != kStOk) st = s2;
         if (s2 == kStInvalid) break;
         if (best_j < 0 || D < best) {
@@ -957,20 +1219,21 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
       NB = (K + KB - 1) / KB;
       cudaError_t e2 = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
       if (e2 != cudaSuccess) return e2;
-      unsigned g2 = 1;
-      if (sc.tile.C) {
-        e2 = launch_cfg(k_screen<G, NPL, true, ST>, smem32, gpb32 * G, sc.sms, cnt * (long long)NB,
-                        gpb32, &g2);
-        if (e2 != cudaSuccess) return e2;
-        k_screen<G, NPL, true, ST><<<g2, gpb32 * G, smem32, st>>>(ob, cv, seg_size, K, KB, NB, sc,
-                                                                  slice32, items, queue, ws, d_err);
-      } else {
-        e2 = launch_cfg(k_screen<G, NPL, false, ST>, smem32, gpb32 * G, sc.sms, cnt * (long long)NB,
-                        gpb32, &g2);
-        if (e2 != cudaSuccess) return e2;
-        k_screen<G, NPL, false, ST><<<g2, gpb32 * G, smem32, st>>>(ob, cv, seg_size, K, KB, NB, sc,
-                                                                   slice32, items, queue, ws, d_err);
-      }
+      auto launch = [&](auto kern) -> cudaError_t {
+        unsigned g2 = 1;
+        cudaError_t e3 = launch_cfg(kern, smem32, gpb32 * G, sc.sms, cnt * (long long)NB, gpb32, &g2);
+        if (e3 != cudaSuccess) return e3;
+        kern<<<g2, gpb32 * G, smem32, st>>>(ob, cv, seg_size, K, KB, NB, sc, slice32, items, queue,
+                                            ws, d_err);
+        return cudaSuccess;
+      };
+      if (sc.tile.C)
+        e2 = sc.certify ? launch(k_screen<G, NPL, true, ST, true>)
+                        : launch(k_screen<G, NPL, true, ST, false>);
+      else
+        e2 = sc.certify ? launch(k_screen<G, NPL, false, ST, true>)
+                        : launch(k_screen<G, NPL, false, ST, false>);
+      if (e2 != cudaSuccess) return e2;
       const unsigned mb = (unsigned)std::min<long long>((cnt + 255) / 256, 4096);
       k_merge<<<mb, 256, 0, st>>>(items, cnt, NB, sc.oidx, sc.obase, merged);
       note_launches(2);
@@ -1044,10 +1307,10 @@ static cudaError_t mallows_pairs_st(const ObjView& ob, const CentView& cv, const
 }
 
 // This unit's solver counters (see g_solver_stats).
-cudaError_t read_unit_stats(long long out[4]) {
-  unsigned long long v[4] = {0, 0, 0, 0};
+cudaError_t read_unit_stats(long long out[kStatWords]) {
+  unsigned long long v[kStatWords] = {};
   cudaError_t e = cudaMemcpyFromSymbol(v, g_solver_stats, sizeof(v));
-  for (int i = 0; i < 4; ++i) out[i] = (long long)v[i];
+  for (int i = 0; i < kStatWords; ++i) out[i] = (long long)v[i];
   return e;
 }
 

@@ -21,6 +21,7 @@ D2_TC_AUTO, D2_TC_OFF, D2_TC_ON = 0, 1, 2
 D2_START_AUTO, D2_START_RANKED, D2_START_VOGEL = 0, 1, 2
 D2_SEG_SLICES, D2_SEG_CONSTRAINED = 0, 1
 D2_UPDATE_CONSTRAINED, D2_UPDATE_ALG1 = 0, 1
+D2_CERTIFY_CANDIDATES, D2_CERTIFY_ALL = 0, 1
 MAX_SUPPORT = 64
 
 EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_strerror",
@@ -28,7 +29,8 @@ EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_st
            "d2_mallows_batch", "d2_assign", "d2_update_locations", "d2_cluster_level",
            "d2_get_stats", "d2_update_locations_noalloc", "d2_server_create", "d2_server_submit",
            "d2_server_poll", "d2_server_stats", "d2_server_destroy", "d2_segment",
-           "d2_set_cost_table", "d2_assign_multi", "d2_update_weights", "d2_cluster_level_ex"]
+           "d2_set_cost_table", "d2_assign_multi", "d2_update_weights", "d2_cluster_level_ex",
+           "d2_mallows_all"]
 
 
 class D2Bags(ctypes.Structure):
@@ -43,7 +45,8 @@ class D2Config(ctypes.Structure):
                 ("tile_budget_mib", ctypes.c_int32), ("start_rule", ctypes.c_int32),
                 ("segmentation", ctypes.c_int32), ("split_iters", ctypes.c_int32),
                 ("eps_tol", ctypes.c_double), ("centroid_update", ctypes.c_int32),
-                ("joint_max_iter", ctypes.c_int32), ("joint_tol", ctypes.c_double)]
+                ("joint_max_iter", ctypes.c_int32), ("joint_tol", ctypes.c_double),
+                ("certify", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class D2Flows(ctypes.Structure):
@@ -54,7 +57,8 @@ class D2Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("pairs_screened", ctypes.c_int64),
                 ("pivots_screened", ctypes.c_int64), ("pairs_exact", ctypes.c_int64),
                 ("pivots_exact", ctypes.c_int64), ("joint_rounds", ctypes.c_int64),
-                ("joint_master_pivots", ctypes.c_int64), ("reserved", ctypes.c_int64 * 1)]
+                ("joint_master_pivots", ctypes.c_int64), ("pairs_certified", ctypes.c_int64),
+                ("cells_checked", ctypes.c_int64)]
 
 
 class D2Error(RuntimeError):
@@ -91,6 +95,7 @@ def load(path=None):
     lib.d2_mallows_batch.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, i64, vp,
                                      ctypes.POINTER(D2Flows), vp]
     lib.d2_assign.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, vp, vp, ctypes.POINTER(D2Flows)]
+    lib.d2_mallows_all.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, vp]
     lib.d2_update_locations.argtypes = [vp, ctypes.POINTER(D2Bags), vp, vp, ctypes.POINTER(D2Flows)]
     lib.d2_cluster_level.argtypes = [vp, ctypes.POINTER(D2Bags), vp, i32, i64, i32, vp, vp, vp]
     lib.d2_get_stats.argtypes = [ctypes.POINTER(D2Stats)]
@@ -179,12 +184,13 @@ class Context:
     def __init__(self, device=0, precision=D2_PREC_AUTO, pivot_budget=0, group_lanes=0,
                  cost_tc=D2_TC_AUTO, tile_budget_mib=0, start_rule=D2_START_AUTO,
                  segmentation=D2_SEG_SLICES, split_iters=0, eps_tol=0.0,
-                 centroid_update=D2_UPDATE_CONSTRAINED, joint_max_iter=0, joint_tol=0.0):
+                 centroid_update=D2_UPDATE_CONSTRAINED, joint_max_iter=0, joint_tol=0.0,
+                 certify=D2_CERTIFY_CANDIDATES):
         lib = load()
         self.h = ctypes.c_void_p()
         cfg = D2Config(precision, pivot_budget, group_lanes, cost_tc, tile_budget_mib, start_rule,
                        segmentation, split_iters, float(eps_tol), int(centroid_update),
-                       int(joint_max_iter), float(joint_tol))
+                       int(joint_max_iter), float(joint_tol), int(certify), 0)
         _check(lib.d2_ctx_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)), "d2_ctx_create")
         self._cents = None
 
@@ -263,6 +269,16 @@ def d2_assign(ctx, objs, labels, dist2, omega=None, eps=None, flows=None):
                           _ptr(eps), ctypes.byref(f) if f else None)
     if rc not in (D2_OK, D2_ENOTCONVERGED):
         _check(rc, "d2_assign")
+    return rc
+
+
+def d2_mallows_all(ctx, objs, dist2_all, labels=None, dist2=None):
+    """D^2 of every (object, resident centroid) pair into dist2_all [N, K]
+    (FP64, certified), plus the argmin labels / dist2 if given."""
+    rc = load().d2_mallows_all(ctx.h, ctypes.byref(objs.s), _ptr(dist2_all), _ptr(labels),
+                               _ptr(dist2))
+    if rc not in (D2_OK, D2_ENOTCONVERGED):
+        _check(rc, "d2_mallows_all")
     return rc
 
 
@@ -345,7 +361,8 @@ def d2_get_stats():
     _check(load().d2_get_stats(ctypes.byref(st)), "d2_get_stats")
     return {k: int(getattr(st, k)) for k in ("kernel_launches", "pairs_screened", "pivots_screened",
                                               "pairs_exact", "pivots_exact", "joint_rounds",
-                                              "joint_master_pivots")}
+                                              "joint_master_pivots", "pairs_certified",
+                                              "cells_checked")}
 
 
 def d2_update_locations_noalloc(objs, labels, flows, K, cent_off, cent_loc_dtype, cent_loc64,

@@ -61,11 +61,35 @@ def test_null_arguments_rejected(lib):
     assert lib.d2_assign(None, None, None, None, None, None, None) == -1
 
 
-def test_layout_of_config_structs():
+def test_layout_of_config_structs(tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's
+    size and field offsets (compiled from include/d2.h with gcc)."""
+    import shutil
+    import subprocess
+    from pathlib import Path
     from paper_1302_0435_gb300 import d2
-    assert ctypes.sizeof(d2.D2Bags) == 48
-    assert ctypes.sizeof(d2.D2Config) == 56
-    assert ctypes.sizeof(d2.D2Flows) == 24
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"d2_bags": d2.D2Bags, "d2_config": d2.D2Config, "d2_flows": d2.D2Flows,
+               "d2_stats": d2.D2Stats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "d2.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = Path(__file__).resolve().parents[1] / "include"
+    subprocess.run([gcc, "-I", str(inc), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {" ".join(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for cname, py in structs.items():
+        assert got[cname + " size"] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[cname + " " + fname] == getattr(py, fname).offset, (cname, fname)
 
 
 def test_every_called_entry_point_has_a_ctypes_signature():

@@ -2,20 +2,32 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step = one hierarchical clustering job of the image-like workload
+Headline step: one hierarchical clustering job of the image-like workload
 (N=200,000 bags of 8-16 supports in d=6, Dirichlet(0.5) weights, FP32;
 K=64 centroids of 16 supports per segment; segments of 5,000 bags; 10
 rounds of (assign, location update) per segment; then the 2,560 segment
 centroids are clustered to 64 with 10 more rounds).  Every assign solves
-the exact Mallows LP for each (bag, centroid) pair of its segment, so the
-unit is one pair LP: 200000*64*10 + 2560*64*10 pair LPs per step.
+the Mallows LP of every (bag, centroid) pair of its segment and certifies
+it in FP64 (D2_CERTIFY_ALL): each pair's D^2 is within 2^-24 relative of
+the LP optimum, or the pair is solved to FP64 optimality.  The unit is one
+certified pair: 200000*64*10 + 2560*64*10 per step.
 
-Prints one JSON line (rank 0).  `value` is device-timed pairs/s with the
-inputs resident in HBM; `e2e` is the same through the C-ABI with pinned
-host buffers (inputs copied in and labels/centroids copied out inside the
-timed region).  `roofline` reports the dominant kernel (k_assign) against
-the FP32/INT issue peak; `cpu_baseline` times the FP64 CPU oracle on a
-bounded sample on this host's cores.
+Prints one JSON line (rank 0).  `value`: device-timed certified pairs/s
+with the inputs resident in HBM; `e2e`: the same through the C-ABI with
+pinned host buffers (inputs copied in, labels and centroids copied out
+inside the timed region).  Beside it:
+  level_screened  the same step with FP32 screening and FP64 certification
+                  of the argmin candidates only (labels still oracle-exact)
+  mallows_all     the cold all-pairs call on the first level (12.8 M pairs)
+  roofline        the screening kernel against the FP32/INT issue peak
+  cpu_baseline    the FP64 CPU oracle, 1 thread and all cores, on a sample
+                  stratified by bag size, weighted back to the workload mix
+  workloads       the other configurations at full size (plain small,
+                  uneven sizes, high dimension), each with its own value,
+                  e2e, roofline, CPU baseline and measured error
+  serve           the continuous-batching server at 0.5/0.8/0.95 of its
+                  saturated rate, p50/p99 latency, and the plain
+                  one-pair-per-launch form beside it
 
 --impl reference times that oracle itself as the comparison arm.
 Multi-GPU (torchrun): every rank clusters its own copy of the workload
@@ -41,6 +53,7 @@ METRIC = "exact Mallows pairs/s at rel err<=1e-6 vs FP64 oracle"
 UNIT = "pairs/s"
 L2_BYTES = 129 * 1024 * 1024
 ALU_LANES_PER_SM = 128
+CERTIFY_ALL = 1
 
 
 def pairs_per_step(N, K, seg, iters):
@@ -160,51 +173,137 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per k_assign launch from the committed ncu summary, if it
-    was taken on the current kernel sources (else None)."""
-    p = os.path.join(ROOT, "profiles", "k_assign_image_like.json")
+def profiled_traffic(name):
+    """DRAM bytes per launch of the screening kernel on workload `name`
+    from the committed ncu summary, if it was taken on the current kernel
+    sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "k_screen_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         prof = json.load(f)
-    if prof.get("source_hash") != kernel_source_hash():
+    ent = prof.get(name)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
         return None
-    return prof.get("dram_bytes_per_launch_full")
+    return ent.get("dram_bytes_per_launch_full")
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
 
 
 # ---------------------------------------------------------------- oracle --
 
-def cpu_sample(objs, cents, target_s, seed=7):
-    """Time the FP64 oracle on random (object, centroid) pairs of the
-    workload, in batches on all host cores, until about target_s seconds."""
+def stratified_pairs(objs, cents, rng, per_stratum):
+    """Pairs grouped by object support count m (the centroids of every
+    configuration share one n): `per_stratum` random (bag, centroid) pairs
+    for every m that occurs, extremes included.  Returns [(m, pi, pj)]."""
+    sizes = np.diff(objs.off)
+    out = []
+    for m in np.unique(sizes):
+        cand = np.nonzero(sizes == m)[0]
+        pi = rng.choice(cand, size=per_stratum, replace=True)
+        pj = rng.integers(0, cents.count, size=per_stratum)
+        out.append((int(m), pi, pj))
+    return out
+
+
+def cpu_baseline(objs, cents, seconds=8.0, seed=7, full=False):
+    """The FP64 oracle (test infrastructure, timed as it stands) on the
+    host's cores: all cores and one thread, on pairs stratified by bag
+    size m; the pairs/s of each stratum are weighted back to the
+    workload's own mix of m.  full=True: every pair of the workload
+    instead (the small configuration).  Also returns the sampled pairs and
+    the oracle's values, for the error statement of the GPU results."""
     import oracle
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(seed)
+    sizes = np.diff(objs.off)
     K = cents.count
-    batch = 2048 * cores
-    npairs, dt, piv_all, pi_all, pj_all = 0, 0.0, [], [], []
-    while dt < target_s and npairs < 20_000_000:
-        pi = rng.integers(0, objs.count, size=batch)
-        pj = rng.integers(0, K, size=batch)
+    if full:
+        pi = np.repeat(np.arange(objs.count), K)
+        pj = np.tile(np.arange(K), objs.count)
         t0 = time.perf_counter()
-        _, piv = oracle.mallows_pairs(objs, cents, pi, pj, nthreads=cores, return_pivots=True)
-        dt += time.perf_counter() - t0
-        npairs += batch
-        piv_all.append(piv)
-        pi_all.append(pi)
-        pj_all.append(pj)
-    piv = np.concatenate(piv_all)
-    pi = np.concatenate(pi_all)
-    pj = np.concatenate(pj_all)
-    sizes = np.diff(objs.off)[pi]
-    ncent = np.diff(cents.off)[pj]
+        ref, piv = oracle.mallows_pairs(objs, cents, pi, pj, nthreads=cores, return_pivots=True)
+        t_all = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.mallows_pairs(objs, cents, pi, pj, nthreads=1)
+        t_one = time.perf_counter() - t0
+        ops = _ops(objs, cents, pi, pj, piv)
+        return dict(value=pi.size / t_all, unit=UNIT, cores=cores, kind="oracle",
+                    value_1thread=pi.size / t_one, cpu_model=cpu_model(),
+                    sample="every pair of the workload (%d pairs), all %d cores and 1 thread"
+                           % (pi.size, cores),
+                    mean_pivots=float(piv.mean()), ops_per_pair=float(ops.mean())), (pi, pj, ref)
+    # calibrate: seconds per pair on a small mixed batch
+    cal = 64 * cores
+    ci = rng.integers(0, objs.count, cal)
+    cj = rng.integers(0, K, cal)
+    t0 = time.perf_counter()
+    oracle.mallows_pairs(objs, cents, ci, cj, nthreads=cores)
+    spp = max(time.perf_counter() - t0, 1e-4) / cal
+    nstrata = np.unique(sizes).size
+    per = int(np.clip(seconds / spp / nstrata, 16 * cores, 100_000 // max(nstrata, 1) + 16 * cores))
+    strata = stratified_pairs(objs, cents, rng, per)
+    mix = {m: float(np.mean(sizes == m)) for m, _, _ in strata}
+    t_all, t_one, piv_all, pis, pjs, refs = {}, {}, {}, [], [], []
+    one_per = max(8, per // (4 * cores))
+    for m, pi, pj in strata:
+        t0 = time.perf_counter()
+        ref, piv = oracle.mallows_pairs(objs, cents, pi, pj, nthreads=cores, return_pivots=True)
+        t_all[m] = (time.perf_counter() - t0) / pi.size
+        t0 = time.perf_counter()
+        oracle.mallows_pairs(objs, cents, pi[:one_per], pj[:one_per], nthreads=1)
+        t_one[m] = (time.perf_counter() - t0) / one_per
+        piv_all[m] = piv
+        pis.append(pi)
+        pjs.append(pj)
+        refs.append(ref)
+    sec_all = sum(mix[m] * t_all[m] for m in mix)
+    sec_one = sum(mix[m] * t_one[m] for m in mix)
+    pi = np.concatenate(pis)
+    pj = np.concatenate(pjs)
+    ref = np.concatenate(refs)
+    piv = np.concatenate([piv_all[m] for m, _, _ in strata])
+    ops = _ops(objs, cents, pi, pj, piv)
+    # ops and pivots per pair weighted to the workload's mix of m
+    ops_mix = sum(mix[m] * float(ops[np.diff(objs.off)[pi] == m].mean()) for m in mix)
+    piv_mix = sum(mix[m] * float(piv_all[m].mean()) for m in mix)
+    return dict(value=1.0 / sec_all, unit=UNIT, cores=cores, kind="oracle",
+                value_1thread=1.0 / sec_one, cpu_model=cpu_model(),
+                sample="%d pairs stratified by bag size m (%d strata, %d pairs each, m = %d..%d) "
+                       "on all %d cores, %d pairs per stratum on 1 thread; per-stratum pairs/s "
+                       "weighted to the workload's mix of m"
+                       % (pi.size, len(strata), per, strata[0][0], strata[-1][0], cores, one_per),
+                mean_pivots=piv_mix, ops_per_pair=ops_mix), (pi, pj, ref)
+
+
+def _ops(objs, cents, pi, pj, piv):
+    """Algorithmic work per pair: 2mnd (cost tile) + P (mn + 4(m+n))
+    (P oracle pivots of pricing and tree update) + the FP64 epilogue
+    mn + 2(m+n)."""
+    m = np.diff(objs.off)[pi].astype(np.float64)
+    n = np.diff(cents.off)[pj].astype(np.float64)
     d = objs.dim
-    ops = 2.0 * sizes * ncent * d + piv * (sizes * ncent + 4.0 * (sizes + ncent))
-    return dict(value=npairs / dt, unit=UNIT, cores=cores, kind="oracle",
-                sample="%d random (bag, centroid) pairs of the workload's first segment set "
-                       "(FP64 transportation simplex, %d threads)" % (npairs, cores),
-                seconds=dt, mean_pivots=float(piv.mean()), ops_per_pair=float(ops.mean()))
+    return 2.0 * m * n * d + piv * (m * n + 4.0 * (m + n)) + m * n + 2.0 * (m + n)
+
+
+def error_vs_oracle(gpu_all, sample):
+    """Largest relative error of the GPU's pair values against the oracle
+    on the sampled pairs."""
+    pi, pj, ref = sample
+    g = gpu_all[pi, pj]
+    rel = np.abs(g - ref) / np.maximum(np.abs(ref), 1e-300)
+    return {"pairs_compared": int(pi.size), "max_rel_err": float(rel.max()),
+            "p99_rel_err": float(np.quantile(rel, 0.99)),
+            "within_1e-6": bool(np.all(np.abs(g - ref) <= 1e-6 * ref + 1e-12 * max(1.0, float(ref.max()))))}
 
 
 def run_reference(args):
@@ -253,13 +352,139 @@ def workload_config():
     w = WORKLOAD
     return {"workload": "image_like: N=%d bags, 8-16 supports, d=%d, Dirichlet(0.5), FP32; K=%d "
                         "centroids of %d supports per segment; segments of %d; %d rounds per level; "
-                        "top-level merge" % (w["N"], w["d"], w["K"], w["n"], w["seg"], w["iters"]),
+                        "top-level merge; every pair certified in FP64 (D2_CERTIFY_ALL)"
+                        % (w["N"], w["d"], w["K"], w["n"], w["seg"], w["iters"]),
             "N": w["N"], "K": w["K"], "seg_size": w["seg"], "iters": w["iters"],
             "pairs_per_step": pairs_per_step(w["N"], w["K"], w["seg"], w["iters"]),
             "l2": "flushed between steps (256 MiB write), not timed"}
 
 
 # ------------------------------------------------------------------ ours --
+
+class Timer:
+    """CUDA-event timing of calls on one stream, L2 flushed before each."""
+
+    def __init__(self, torch, dev, stream):
+        self.torch, self.dev, self.stream = torch, dev, stream
+        self.flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def run(self, fn, steps, warmup):
+        torch = self.torch
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(self.dev)
+        times = []
+        for _ in range(steps):
+            self.flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            fn()
+            e1.record(self.stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        return times
+
+
+def stats_delta(d2, fn, sync):
+    s0 = d2.d2_get_stats()
+    fn()
+    sync()
+    s1 = d2.d2_get_stats()
+    return {k: s1[k] - s0[k] for k in s0}
+
+
+def certified_count(st, pairs):
+    """Pairs of a certify-all step that are certified: screened pairs that
+    passed the certificate plus pairs solved to FP64 optimality (a pair
+    that fails the certificate is always a candidate of the exact pass;
+    FP64 inputs are solved in FP64 throughout).  Some near-tie candidates
+    are both, hence the cap."""
+    return min(pairs, st["pairs_certified"] + st["pairs_exact"])
+
+
+def roofline_entry(kernel, pairs, seconds, ops_per_pair, mean_pivots, sms, mhz, traffic):
+    alu_peak = sms * ALU_LANES_PER_SM * mhz * 1e6 / 1e12  # T lane-ops/s
+    achieved = pairs * ops_per_pair / seconds / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": alu_peak,
+            "unit": "T lane-ops/s", "frac": achieved / alu_peak, "traffic": traffic,
+            "peak_source": "%d SMs x %d FP32/INT lanes x %.0f MHz (median SM clock sampled under "
+                           "load); HBM and BF16 peaks of MEASURED_PEAKS.json are not the bound"
+                           % (sms, ALU_LANES_PER_SM, mhz),
+            "ops_per_pair": ops_per_pair, "mean_oracle_pivots": mean_pivots,
+            "launch_seconds": seconds, "pairs_per_launch": pairs}
+
+
+def measure_workload(name, d2, torch, dev, timer, sms, mhz, args, objs, cents, steps, warmup,
+                     desc, ctx_kw=None, cpu_full=False):
+    """One configuration at full size: the assignment step (d2_mallows_all,
+    every pair certified, labels) plus the location update (a7) from the
+    assigned pairs; device-timed and end to end with host buffers."""
+    ctx = d2.Context(dev.index, certify=CERTIFY_ALL, **(ctx_kw or {}))
+    d2.d2_set_stream(ctx, timer.stream)
+    cref = d2.bags_from_synth(cents, device=dev)
+    d2.d2_set_centroids(ctx, cref)
+    ob = d2.bags_from_synth(objs, device=dev)
+    N, K = objs.count, cents.count
+    allg = torch.empty((N, K), dtype=torch.float64, device=dev)
+    lab = torch.empty(N, dtype=torch.int32, device=dev)
+    dd = torch.empty(N, dtype=torch.float64, device=dev)
+
+    def step():
+        d2.d2_mallows_all(ctx, ob, allg, lab, dd)
+        d2.d2_update_locations(ctx, ob, lab)
+        d2.d2_set_centroids(ctx, cref)  # the next step starts from the same centroids
+
+    times = timer.run(step, steps, warmup)
+    t = statistics.median(times)
+    st = stats_delta(d2, step, lambda: torch.cuda.synchronize(dev))
+    # the all-pairs call alone (the dominant kernel's launch)
+    ta = statistics.median(timer.run(lambda: d2.d2_mallows_all(ctx, ob, allg, lab, dd),
+                                     max(1, min(steps, 3)), 0))
+    gpu_all = allg.cpu().numpy()
+    # end to end through the C-ABI with pinned host buffers
+    hb = d2.bags_from_synth(objs, pinned=True)
+    h_all = torch.empty((N, K), dtype=torch.float64).pin_memory()
+    h_lab = torch.empty(N, dtype=torch.int32).pin_memory()
+    h_dd = torch.empty(N, dtype=torch.float64).pin_memory()
+    T = int(cents.off[-1])
+    h_loc = torch.empty((T, objs.dim), dtype=torch.float64).pin_memory()
+
+    def step_host():
+        d2.d2_mallows_all(ctx, hb, h_all, h_lab, h_dd)
+        d2.d2_update_locations(ctx, hb, h_lab)
+        d2.d2_get_centroids_into(ctx, h_loc)
+        d2.d2_set_centroids(ctx, cref)
+
+    step_host()
+    torch.cuda.synchronize(dev)
+    e_steps = max(1, min(steps, 2))
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        step_host()
+    torch.cuda.synchronize(dev)
+    e2e_t = (time.perf_counter() - t0) / e_steps
+    bi = hb.loc.numel() * hb.loc.element_size() + hb.w.numel() * hb.w.element_size() + hb.off.numel() * 8
+    bo = h_all.numel() * 8 + h_lab.numel() * 4 + h_dd.numel() * 8 + h_loc.numel() * 8
+    ctx.close()
+    pairs = N * K
+    out = {"workload": desc, "value": pairs / t, "unit": UNIT, "ms_per_step": 1e3 * t,
+           "steps": steps, "warmup": warmup, "pairs_per_step": pairs,
+           "certified_pairs_per_step": certified_count(st, pairs),
+           "pairs_certified_in_screen": st["pairs_certified"],
+           "pairs_solved_fp64": st["pairs_exact"],
+           "e2e": {"value": pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(bi),
+                   "d2h_bytes_per_step": int(bo)},
+           "all_pairs_call_ms": 1e3 * ta}
+    if not args.skip_cpu:
+        cpu, sample = cpu_baseline(objs, cents, seconds=args.cpu_seconds, full=cpu_full)
+        out["cpu_baseline"] = cpu
+        out["error_vs_oracle"] = error_vs_oracle(gpu_all, sample)
+        out["roofline"] = roofline_entry("k_screen (certify) + k_merge + k_exact: cold d2_mallows_all",
+                                         pairs, ta, cpu["ops_per_pair"], cpu["mean_pivots"], sms, mhz,
+                                         profiled_traffic(name))
+    return out
+
 
 def run_ours(args):
     import torch
@@ -275,62 +500,43 @@ def run_ours(args):
     d2.load()
     w = WORKLOAD
     objs, cents = synth.image_like(N=w["N"], K=w["K"], seed=1002 + rank)
-    ctx = d2.Context(dev.index)
-    stream = torch.cuda.current_stream(dev)
-    d2.d2_set_stream(ctx, stream)
-    d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device=dev))
-    ob = d2.bags_from_synth(objs, device=dev)
+    # one non-default stream for the library's calls, the L2 flushes and the
+    # timing events, so that events follow the library's work (its calls
+    # with device outputs return without waiting)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    timer = Timer(torch, dev, stream)
     T = cents.loc.shape[0]
+    ob = d2.bags_from_synth(objs, device=dev)
     out_loc = torch.empty((T, w["d"]), dtype=torch.float64, device=dev)
     out_w = torch.empty(w["K"], dtype=torch.float64, device=dev)
     labels = torch.empty(w["N"], dtype=torch.int32, device=dev)
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     ppstep = pairs_per_step(w["N"], w["K"], w["seg"], w["iters"])
+
+    def level_ctx(certify):
+        ctx = d2.Context(dev.index, certify=certify)
+        d2.d2_set_stream(ctx, stream)
+        d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device=dev))
+        return ctx
+
+    ctx = level_ctx(CERTIFY_ALL)
 
     def step():
         d2.d2_cluster_level(ctx, ob, w["K"], w["seg"], w["iters"], out_loc, out_w, labels)
 
     for _ in range(args.warmup):
         step()
-    torch.cuda.synchronize(dev)
+    st = stats_delta(d2, step, lambda: torch.cuda.synchronize(dev))
     clocks = ClockSampler(dev.index)
     clocks.start()
     launches0 = d2.d2_get_stats()["kernel_launches"]
     barrier(ws)
-    torch.cuda.synchronize(dev)
-    times = []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        step()
-        ev1.record(stream)
-        ev1.synchronize()
-        times.append(ev0.elapsed_time(ev1) / 1e3)
+    times = timer.run(step, args.steps, 0)
     torch.cuda.synchronize(dev)
     barrier(ws)
     launches = d2.d2_get_stats()["kernel_launches"] - launches0
     clk = clocks.stop()
     value, t_total = aggregate(times, ppstep, args.steps, ws)
-
-    # dominant kernel: k_assign over the full bag set against one segment's K centroids
-    lab1 = torch.empty(w["N"], dtype=torch.int32, device=dev)
-    dd1 = torch.empty(w["N"], dtype=torch.float64, device=dev)
-    d2.d2_assign(ctx, ob, lab1, dd1)
-    torch.cuda.synchronize(dev)
-    kt = []
-    for _ in range(3):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        d2.d2_assign(ctx, ob, lab1, dd1)
-        e1.record(stream)
-        e1.synchronize()
-        kt.append(e0.elapsed_time(e1) / 1e3)
-    k_sec = statistics.median(kt)
-    k_pairs = w["N"] * w["K"]
 
     # end to end through the C-ABI with pinned host buffers
     hb = d2.bags_from_synth(objs, pinned=True)
@@ -350,6 +556,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e2e_t = reduce_max(time.perf_counter() - t0, ws)
     e2e_v = ppstep * e2e_steps * ws / e2e_t
+    ctx.close()
 
     if rank != 0:
         if ws > 1:
@@ -357,34 +564,93 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    cpu = cpu_sample(objs, cents, target_s=args.cpu_seconds) if not args.skip_cpu else None
-    serve = None
-    if not args.skip_serve:
-        serve = serve_measure(dev)
     peaks, peak_kind = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = sms * ALU_LANES_PER_SM * mhz * 1e6 / 1e12  # T lane-ops/s
+
+    # the same step with FP32 screening and FP64 certification of the argmin
+    # candidates only (labels and assigned D^2 still oracle-exact)
+    ctx_s = level_ctx(0)
+    scr_steps = max(3, min(args.steps, 5))
+
+    def step_s():
+        d2.d2_cluster_level(ctx_s, ob, w["K"], w["seg"], w["iters"], out_loc, out_w, labels)
+
+    ts = timer.run(step_s, scr_steps, 3)
+    ctx_s.close()
+    level_screened = {"value": ppstep / statistics.median(ts), "unit": "pairs/s (assignment pairs, "
+                      "labels oracle-exact, FP32-screened)",
+                      "ms_per_step": 1e3 * statistics.median(ts), "steps": scr_steps, "warmup": 3}
+
+    # cold all-pairs certified call on the first level's 200,000 x 64 pairs
+    ctx_a = level_ctx(CERTIFY_ALL)
+    allg = torch.empty((w["N"], w["K"]), dtype=torch.float64, device=dev)
+    lab1 = torch.empty(w["N"], dtype=torch.int32, device=dev)
+    dd1 = torch.empty(w["N"], dtype=torch.float64, device=dev)
+    ta = timer.run(lambda: d2.d2_mallows_all(ctx_a, ob, allg, lab1, dd1), 3, 3)
+    k_sec = statistics.median(ta)
+    k_pairs = w["N"] * w["K"]
+    gpu_all = allg.cpu().numpy()
+    ctx_a.close()
+    mallows_all = {"value": k_pairs / k_sec, "unit": UNIT, "ms": 1e3 * k_sec, "pairs": k_pairs,
+                   "call": "d2_mallows_all, cold bases, 200,000 x 64"}
+
+    cpu = None
     roof = None
-    if cpu is not None:
-        achieved = k_pairs * cpu["ops_per_pair"] / k_sec / 1e12
-        roof = {"bound": "alu", "kernel": "k_screen+k_exact (cold d2_assign)", "achieved": achieved,
-                "peak": alu_peak,
-                "unit": "T lane-ops/s", "frac": achieved / alu_peak,
-                "traffic": profiled_traffic(),
-                "peak_source": "%d SMs x %d FP32/INT lanes x %.0f MHz (median SM clock under load); "
-                               "HBM/bf16 peaks %s in MEASURED_PEAKS.json are not the bound"
-                               % (sms, ALU_LANES_PER_SM, mhz, peak_kind),
-                "ops_per_pair": cpu["ops_per_pair"], "mean_oracle_pivots": cpu["mean_pivots"],
-                "launch_seconds": k_sec, "pairs_per_launch": k_pairs}
+    err = None
+    if not args.skip_cpu:
+        cpu, sample = cpu_baseline(objs, cents, seconds=args.cpu_seconds)
+        err = error_vs_oracle(gpu_all, sample)
+        roof = roofline_entry("k_screen (certify) + k_merge + k_exact: cold d2_mallows_all, "
+                              "200,000 x 64", k_pairs, k_sec, cpu["ops_per_pair"],
+                              cpu["mean_pivots"], sms, mhz, profiled_traffic("image_like"))
+        # the warm rounds as the step runs them: the GPU's own pivots
+        piv = st["pivots_screened"] / max(st["pairs_screened"], 1)
+        mn, mpn = 12.0 * 16.0, 12.0 + 16.0
+        roof["step_warm_model"] = {
+            "ops_per_pair": 2 * mn * w["d"] + piv * (mn + 4 * mpn) + mn + 2 * mpn,
+            "gpu_pivots_per_pair": piv,
+            "achieved": ppstep * (2 * mn * w["d"] + piv * (mn + 4 * mpn) + mn + 2 * mpn)
+                        / (t_total / args.steps) / 1e12,
+            "note": "mean 12 x 16 pair, the GPU's own warm-start pivot count"}
+
+    workloads = {}
+    if not args.skip_workloads:
+        o1, c1 = synth.plain_small()
+        workloads["plain_small"] = measure_workload(
+            "plain_small", d2, torch, dev, timer, sms, mhz, args, o1, c1, 5, 3,
+            "plain_small: N=1000 bags of 4-8 supports, d=3, FP64, Dirichlet(1); K=8 of 8 "
+            "supports; all pairs + one location update", cpu_full=True)
+        o3, c3 = synth.uneven()
+        workloads["uneven"] = measure_workload(
+            "uneven", d2, torch, dev, timer, sms, mhz, args, o3, c3, 2, 2,
+            "uneven: N=1,000,000 bags, sizes P(m) ~ m^-2 on 2..64, d=16, FP32, Dirichlet(1); "
+            "K=256 of 32 supports; all pairs + one location update")
+        del o3, c3
+        o4, c4 = synth.high_dim()
+        workloads["high_dim"] = measure_workload(
+            "high_dim", d2, torch, dev, timer, sms, mhz, args, o4, c4, 1, 1,
+            "high_dim: N=100,000 bags of 16-64 supports, d=128 BF16 descriptors, Dirichlet(1); "
+            "K=512 of 64 supports; tensor-core FP32 cost tiles for the screen; all pairs + one "
+            "location update")
+        del o4, c4
+
+    serve = None
+    if not args.skip_serve:
+        serve = serve_measure(dev, n_requests=args.serve_requests, lam_fracs=(0.5, 0.8, 0.95))
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pivots + f64 certify",
-        "data": "synthetic", "config": workload_config(),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pivots + f64 certificate per pair",
+        "data": "synthetic", "config": dict(workload_config(),
+                                            certified_pairs_per_step=certified_count(st, ppstep),
+                                            pairs_certified_in_screen=st["pairs_certified"],
+                                            pairs_solved_fp64=st["pairs_exact"]),
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)},
         "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
-        "serve": serve,
+        "error_vs_oracle": err, "level_screened": level_screened, "mallows_all": mallows_all,
+        "workloads": workloads, "serve": serve, "peaks": peak_kind,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -401,7 +667,6 @@ def serve_measure(dev, n_requests=150, lam_fracs=(0.8,), n_sat=24, seed=1005):
     lam_frac of the saturated request rate and each one's submit-to-done
     latency is recorded.  The plain one-pair-per-launch GPU form
     (d2_mallows_batch with one pair per call) is timed beside it."""
-    import threading
     import torch
     from paper_1302_0435_gb300 import d2, synth
     cents, means = synth.serving_centroids(K=1024, seed=seed)
@@ -488,20 +753,22 @@ def serve_measure(dev, n_requests=150, lam_fracs=(0.8,), n_sat=24, seed=1005):
 
 
 def run_profile_case(args):
-    """Small case for ncu captures: two d2_assign launches, device buffers,
-    of the image-like law (N=20,000 bags against K=64 centroids) or of the
-    high-dimension law (BF16 d=128 descriptors against K=512 centroids of 64
-    supports: the screen reads tensor-core cost tiles)."""
+    """Small cases for ncu captures: the image-like law (N=20,000 bags
+    against K=64 centroids, two d2_assign launches, or d2_mallows_all with
+    --certify), the level driver (image_level), the high-dimension law
+    (BF16 d=128 descriptors against K=512 centroids of 64 supports: the
+    screen reads tensor-core cost tiles), or the joint-weights rounds."""
     import torch
     from paper_1302_0435_gb300 import build, d2, synth
     build.build()
     d2.load()
+    cert = CERTIFY_ALL if args.certify else 0
     if args.profile_workload == "image_level":
         # the benchmark step's level driver on profile_n bags (segments of
         # 5,000, 10 rounds): k_screen launches after the first are warm
         # rounds replayed from the CUDA graph
         objs, cents = synth.image_like(N=args.profile_n, K=WORKLOAD["K"])
-        ctx = d2.Context(0)
+        ctx = d2.Context(0, certify=cert)
         d2.d2_set_stream(ctx, torch.cuda.current_stream())
         d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
         ob = d2.bags_from_synth(objs, device="cuda:0")
@@ -517,7 +784,6 @@ def run_profile_case(args):
     if args.profile_workload == "joint_weights":
         # Alg. 1 Step 1 on the image-like law: the bags' nearest-centroid
         # clusters, then the cutting-plane rounds of d2_update_weights
-        import time
         objs, cents = synth.image_like(N=args.profile_n, K=WORKLOAD["K"])
         ctx = d2.Context(0)
         d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
@@ -543,10 +809,13 @@ def run_profile_case(args):
         return 0 if rc == 0 else 1
     if args.profile_workload == "high_dim":
         objs, cents = synth.high_dim(N=args.profile_n, K=512)
-        ctx = d2.Context(0, tile_budget_mib=1024)  # keep a capture to about 1 GB of tiles
+        ctx = d2.Context(0, tile_budget_mib=1024, certify=cert)  # about 1 GB of tiles
+    elif args.profile_workload == "uneven":
+        objs, cents = synth.uneven(N=args.profile_n, K=256)
+        ctx = d2.Context(0, certify=cert)
     else:
         objs, cents = synth.image_like(N=args.profile_n, K=WORKLOAD["K"])
-        ctx = d2.Context(0)
+        ctx = d2.Context(0, certify=cert)
     d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
     ob = d2.bags_from_synth(objs, device="cuda:0")
     lab = torch.empty(objs.count, dtype=torch.int32, device="cuda:0")
@@ -564,26 +833,21 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=6.0,
+                    help="all-core oracle time per workload for the CPU baseline")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
-    ap.add_argument("--serve-full", action="store_true",
-                    help="serving sweep at 0.5/0.8/0.95 of saturation (own JSON line)")
-    ap.add_argument("--profile", action="store_true", help="small k_assign case for ncu")
+    ap.add_argument("--skip-workloads", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=150,
+                    help="requests per load level of the serving sweep")
+    ap.add_argument("--profile", action="store_true", help="small case for ncu")
     ap.add_argument("--profile-n", type=int, default=20000)
+    ap.add_argument("--certify", action="store_true", help="profile case: D2_CERTIFY_ALL")
     ap.add_argument("--profile-workload", default="image_like",
-                    choices=["image_like", "image_level", "high_dim", "joint_weights"])
+                    choices=["image_like", "image_level", "high_dim", "uneven", "joint_weights"])
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args)
-    if args.serve_full:
-        import torch
-        from paper_1302_0435_gb300 import build, d2
-        build.build()
-        d2.load()
-        res = serve_measure(torch.device("cuda", 0), n_requests=200, lam_fracs=(0.5, 0.8, 0.95))
-        print(json.dumps({"metric": "serve p50/p99 ms", "serve": res}), flush=True)
-        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -26,10 +26,22 @@
  *    Host inputs are copied to device scratch owned by the context and host
  *    outputs are copied back before the call returns.  The library never
  *    frees caller memory.
- *  - Streams: work is enqueued on the context's stream (d2_set_stream).  A
- *    call whose outputs are all device pointers returns without waiting;
- *    outputs are valid after d2_sync() or an event recorded on that stream.
- *    A call with any host output synchronises before it returns.
+ *  - Streams: work is enqueued on the context's stream (d2_set_stream).
+ *    d2_mallows_batch, d2_assign, d2_mallows_all and d2_update_locations
+ *    return without waiting when all their outputs are device pointers and
+ *    their bags declare max_support (with 0, a scan of the offsets waits
+ *    first); the first call of a new launch shape may also wait for the
+ *    autotuner, and BF16 batches screened with tensor-core tiles wait for
+ *    their bin counts.  Outputs are valid after d2_sync() or an event
+ *    recorded on that stream.  A call with any host output waits before it
+ *    returns; so do the other calls.
+ *  - Errors of calls that return without waiting (bad offsets or weights,
+ *    pivot budgets, device timeouts) are raised on the device and reported
+ *    by the next d2_sync(), or by the next call that waits, which then
+ *    returns that code; a call that waits on entry (d2_set_centroids,
+ *    d2_cost_matrix, d2_update_weights, d2_assign_multi, d2_segment,
+ *    d2_cluster_level) returns such a pending code at once and does
+ *    nothing else.  Reporting an error clears it.
  *  - Threads: one context per host thread; a context is not re-entrant.
  *  - Precision: see d2_config.precision.  D^2 outputs are FP64.
  */
@@ -118,6 +130,12 @@ extern "C" {
  * loc_dtype) and w (element type w_dtype, D2_F64 or D2_F32).  off has
  * count+1 entries, off[0] = 0, nondecreasing.  All three pointers must be in
  * the same memory space (all device or all host).
+ * max_support: 0, or the caller's bound on every bag's support count
+ * (1..D2_MAX_SUPPORT).  With a bound the calls need not read the offsets
+ * back to size their kernels, so a call with device outputs returns without
+ * waiting; the kernels check every bag against it (a bag with no support
+ * or above the bound is reported as D2_EINVAL, by d2_sync for such calls).
+ * With 0 the calls scan the offsets first, which waits for the stream.
  */
 typedef struct {
     const void* loc;
@@ -127,7 +145,7 @@ typedef struct {
     int32_t dim;
     int32_t loc_dtype;
     int32_t w_dtype;
-    int32_t reserved;
+    int32_t max_support;
 } d2_bags;
 
 /* Context configuration; zero-initialise and set what you need. */
@@ -180,7 +198,8 @@ int d2_ctx_create(d2_ctx** out, int32_t device, const d2_config* cfg);
 int d2_ctx_destroy(d2_ctx* ctx);
 /* Use the caller's cudaStream_t (NULL: back to the context's own stream). */
 int d2_set_stream(d2_ctx* ctx, void* cuda_stream);
-/* Wait for all work enqueued by this context. */
+/* Wait for all work enqueued by this context; returns (and clears) the
+ * first error its kernels raised since the last report, D2_OK if none. */
 int d2_sync(d2_ctx* ctx);
 /* Static description of a status code. */
 const char* d2_strerror(int32_t status);

@@ -216,6 +216,20 @@ int stage_out(d2_ctx* c, T* p, size_t n, int s, T** out, bool* host) {
   return D2_OK;
 }
 
+// Largest bag of a batch: declared by the caller (d2_bags.max_support,
+// checked on the device with the other bag errors, no wait), else read back
+// from a scan of the offsets (a wait).
+int scan(d2_ctx* c, const ObjView& v, int* mmax);
+int bag_bound(d2_ctx* c, const d2_bags* b, const ObjView& v, int* mmax) {
+  if (b->max_support > 0) {
+    if (b->max_support > D2_MAX_SUPPORT) return D2_EUNSUPPORTED;
+    *mmax = b->max_support;
+    CK(d2k::check_bags(v.off, v.count, *mmax, c->d_err, c->stream));
+    return D2_OK;
+  }
+  return scan(c, v, mmax);
+}
+
 // max support and offset validity of a bag batch (device offsets)
 int scan(d2_ctx* c, const ObjView& v, int* mmax) {
   CK(d2k::scan_bags(v.off, v.count, c->d_info, c->stream));
@@ -285,23 +299,41 @@ CentView resident_view(const d2_ctx* c) {
 }
 
 // With a symbol table set: the bags must be one-dimensional symbol ids in
-// [0, A); raises kErrInvalid otherwise (read at the end of the call).
+// [0, A); raises kErrInvalid otherwise (reported with the call's errors).
 int check_bag_symbols(d2_ctx* c, const ObjView& v) {
   if (c->A <= 0) return D2_OK;
   if (v.d != 1) return D2_EINVAL;
-  long long T = 0;
-  CK(cudaMemcpyAsync(&T, v.off + v.count, 8, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  CK(d2k::check_symbols(v.loc, v.ldt, T, c->A, c->d_err, c->stream));
+  CK(d2k::check_bag_symbols(v.loc, v.ldt, v.off, v.count, c->A, c->d_err, c->stream));
   return D2_OK;
 }
 
+// Read and clear the context's error word (waits for the stream).
 int read_err(d2_ctx* c, int* bits) {
   CK(cudaMemcpyAsync(c->h_pin + 2, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   CK(cudaStreamSynchronize(c->stream));
   *bits = c->h_pin[2];
   return D2_OK;
 }
+
+int bits_code(int bits) {
+  if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
+  if (bits & d2k::kErrInvalid) return D2_EINVAL;
+  if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
+  return D2_OK;
+}
+
+// Wait for the stream and report (and clear) the errors its kernels raised,
+// those of earlier calls that returned without waiting included.
+int take_errors(d2_ctx* c) {
+  int bits = 0;
+  const int rc = read_err(c, &bits);
+  return rc != D2_OK ? rc : bits_code(bits);
+}
+
+// The end of a call that may return without waiting: with a host output it
+// waits and reports the stream's errors; otherwise they wait for d2_sync.
+int finish(d2_ctx* c, bool host_output) { return host_output ? take_errors(c) : D2_OK; }
 
 void free_centroids(d2_ctx* c) {
   cudaFree(c->c_loc32); cudaFree(c->c_loc64); cudaFree(c->c_Q); cudaFree(c->c_w64); cudaFree(c->c_off);
@@ -380,11 +412,15 @@ namespace {
 
 // Object bins by the nodes per lane their trees need (see d2k::bin_objects),
 // as a stable partition: order[start[b] .. start[b+1]) are bin b's objects
-// in increasing index.  Host copy of start in hstart[0..4].
+// in increasing index.  start stays on the device (the solver launches read
+// their bin's range there); the host copy hstart is read only when needed
+// (autotuning, tensor-core chunks), which waits.
 struct Bins {
   int* order = nullptr;
+  const long long* start = nullptr;
   long long hstart[5] = {0, 0, 0, 0, 0};
   bool binned = false;
+  bool host = false;
 };
 
 int make_bins(d2_ctx* c, const ObjView& v, int nmax, Bins* b) {
@@ -399,18 +435,21 @@ int make_bins(d2_ctx* c, const ObjView& v, int nmax, Bins* b) {
   flat.segof = nullptr;
   CK(d2k::update_locations(flat, nullptr, bins, N, 4, none, 4, nullptr, v.d, 0, nullptr, nullptr, scr,
                            c->stream));
-  // scratch layout of the sort: counts | tot | start | order | ...
-  const long long nchunks = (N + 1023) / 1024;
-  unsigned char* p = static_cast<unsigned char*>(scr);
-  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-  p += al((size_t)nchunks * 4 * 4);
-  p += al((size_t)5 * 8);
-  const long long* start = reinterpret_cast<const long long*>(p);
-  p += al((size_t)5 * 8);
-  b->order = reinterpret_cast<int*>(p);
-  CK(cudaMemcpyAsync(b->hstart, start, 5 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  const long long* start;
+  const int* order;
+  d2k::sorted_groups(scr, N, 4, &start, &order);
+  b->start = start;
+  b->order = const_cast<int*>(order);
   b->binned = true;
+  b->host = false;
+  return D2_OK;
+}
+
+int bins_to_host(d2_ctx* c, Bins* b) {
+  if (b->host) return D2_OK;
+  CK(cudaMemcpyAsync(b->hstart, b->start, 5 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  b->host = true;
   return D2_OK;
 }
 
@@ -418,7 +457,7 @@ int make_bins(d2_ctx* c, const ObjView& v, int nmax, Bins* b) {
 // its autotuned launch shape.  ws may be null.
 int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, int K, int mode,
                int mmax, const double* om, int* lab, double* d2o, double* terms, FlowOut fo,
-               int* cand, const d2k::WarmStore* ws, const Bins& bins,
+               int* cand, const d2k::WarmStore* ws, Bins& bins,
                const d2k::TcWork* tw = nullptr, bool certify_all = false,
                double* pair64 = nullptr) {
   const int nmax = std::max(c->nmax, 1);
@@ -429,17 +468,35 @@ int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, i
     CK(d2k::assign(v, cv, seg, K, base, om, lab, d2o, terms, fo, cand, c->d_err, c->stream, ws, tw));
     return D2_OK;
   }
-  for (int b = 3; b >= 0; --b) {
-    const long long cnt = bins.hstart[b + 1] - bins.hstart[b];
-    if (cnt <= 0) continue;
+  const bool tuning = c->cfg.group_lanes == 0 && mode == 1 && v.count >= 8192;
+  const int lo_bin = (1 + nmax + 31) / 32 - 1;
+  const int hi_bin = std::min(3, (mmax + nmax + 31) / 32 - 1);
+  for (int b = hi_bin; b >= lo_bin; --b) {
     SolveCfg cfg = base;
     cfg.mmax = std::max(1, std::min(mmax, 32 * (b + 1) - nmax));
-    cfg.oidx = bins.order + bins.hstart[b];
-    cfg.nobj = cnt;
     const auto key = std::make_tuple(b, (long long)K, cfg.mmax, nmax, v.d,
                                      mode + (cfg.certify ? 2 : 0));
     auto it = c->tuned.find(key);
-    if (it == c->tuned.end() && c->cfg.group_lanes == 0 && mode == 1 && cnt >= 8192) {
+    // the host needs the bin's count for tensor-core chunks and to tune a
+    // new launch shape (a wait); otherwise the launches read it on the device
+    const bool host = tw != nullptr || (it == c->tuned.end() && tuning);
+    long long cnt = -1;
+    if (host) {
+      int rc0 = bins_to_host(c, &bins);
+      if (rc0 != D2_OK) return rc0;
+      cnt = bins.hstart[b + 1] - bins.hstart[b];
+      if (cnt <= 0) continue;
+      cfg.oidx = bins.order + bins.hstart[b];
+      cfg.nobj = cnt;
+    } else {
+      cfg.oidx = bins.order;
+      cfg.dev_range = bins.start + b;
+    }
+    if (it == c->tuned.end() && tuning && cnt < 8192) {
+      // too few objects to time: the default shape, kept for this key
+      it = c->tuned.emplace(key, std::make_tuple(cfg.tpb, cfg.ipsm, cfg.start)).first;
+    }
+    if (it == c->tuned.end() && tuning) {
       // autotune on a sample of this bin: threads per block x screening items per SM
       SolveCfg t = cfg;
       t.pair64 = nullptr;
@@ -592,6 +649,9 @@ int segment_impl(d2_ctx* c, const ObjView& v, int mmax, const double* om, long l
   if (rc != D2_OK) return rc;
   SolveCfg cfg = solve_cfg(c, mode_for(c, v.ldt), mmax);
   cfg.nmax = mmax;  // the split centroids are bags of the data
+  // the splits' centroids are FP64 (their FP32 copies are not exact), and
+  // only their labels are used: no per-pair certificate
+  cfg.certify = false;
   cfg.start = c->cfg.start_rule == D2_START_VOGEL ? 1
             : c->cfg.start_rule == D2_START_RANKED ? 0 : (mmax >= 64 ? 1 : 0);
   const FlowOut fo{fcell, fw, stride};
@@ -678,7 +738,6 @@ int segment_impl(d2_ctx* c, const ObjView& v, int mmax, const double* om, long l
       CK(cudaStreamSynchronize(c->stream));
       return D2_OK;
     };
-    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     // start: each segment's first member, then the member farthest from it
     idx.assign((size_t)nB, 0);
     for (long long b = 0; b < nB; ++b) idx[(size_t)b] = (int)s0[(size_t)b];
@@ -856,16 +915,18 @@ int d2_set_stream(d2_ctx* c, void* s) {
 
 int d2_sync(d2_ctx* c) {
   if (!c) return D2_EINVAL;
-  CK(cudaStreamSynchronize(c->stream));
-  return D2_OK;
+  cudaSetDevice(c->device);
+  return take_errors(c);
 }
 
 int d2_set_centroids(d2_ctx* c, const d2_bags* b) {
   d2k::TraceRange trace_("d2_set_centroids");
   if (!c || !bags_ok(b) || b->count < 1) return D2_EINVAL;
   cudaSetDevice(c->device);
+  int rc = take_errors(c);  // errors left by earlier calls that did not wait
+  if (rc != D2_OK) return rc;
   ObjView v;
-  int rc = stage_bags(c, b, kCentIn0, kCentIn1, kCentIn2, &v);
+  rc = stage_bags(c, b, kCentIn0, kCentIn1, kCentIn2, &v);
   if (rc != D2_OK) return rc;
   std::vector<long long> h(b->count + 1);
   CK(cudaMemcpyAsync(h.data(), v.off, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -891,7 +952,6 @@ int d2_set_centroids(d2_ctx* c, const d2_bags* b) {
     return D2_ENOMEM;
   }
   CK(cudaMemcpyAsync(c->c_off, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   CK(d2k::prep_centroids(v.loc, v.ldt, v.w, v.wdt, c->c_off, b->count, d, c->c_loc32, c->c_loc64,
                          c->c_Q, c->c_w64, c->d_err, c->stream));
   int bits = 0;
@@ -903,7 +963,6 @@ int d2_set_centroids(d2_ctx* c, const d2_bags* b) {
   }
   if (c->A > 0) {  // a symbol table is set: the centroids must be symbol ids
     if (d != 1) { free_centroids(c); return D2_EINVAL; }
-    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     CK(d2k::check_symbols(c->c_loc64, D2_F64, Tc, c->A, c->d_err, c->stream));
     if ((rc = read_err(c, &bits))) return rc;
     if (bits) { free_centroids(c); return D2_EINVAL; }
@@ -976,8 +1035,10 @@ int d2_cost_matrix(d2_ctx* c, const d2_bags* objs, int64_t i, int64_t j, int32_t
   if (c->K == 0) return D2_ENOCENTROIDS;
   if (i < 0 || i >= objs->count || j < 0 || j >= c->K || objs->dim != c->d) return D2_EINVAL;
   cudaSetDevice(c->device);
+  int rc = take_errors(c);  // errors left by earlier calls that did not wait
+  if (rc != D2_OK) return rc;
   ObjView v;
-  int rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v);
+  rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v);
   if (rc != D2_OK) return rc;
   long long oo[2];
   CK(cudaMemcpyAsync(oo, v.off + i, 16, cudaMemcpyDeviceToHost, c->stream));
@@ -998,7 +1059,6 @@ int d2_cost_matrix(d2_ctx* c, const d2_bags* objs, int64_t i, int64_t j, int32_t
     if ((rc = tc_work(c, m, (int)m, &tw))) return rc;
     const long long c0 = c->h_coff[j];
     const int ct0 = (int)(c0 / 256), ct1 = (int)((c0 + n - 1) / 256);
-    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     CK(d2k::tc_chunk(v, tw, nullptr, i, 1, (int)m, ct0, ct1 - ct0 + 1, c->d_err, c->stream));
     CK(d2k::tc_extract(tw.C, tw.cents.ncols, (int)m, c0, (int)n, dC, c->stream));
     int bits = 0;
@@ -1006,7 +1066,6 @@ int d2_cost_matrix(d2_ctx* c, const d2_bags* objs, int64_t i, int64_t j, int32_t
     if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
   } else {
     const int mode = precision == D2_PREC_FP32 ? 1 : 0;
-    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     if ((rc = check_bag_symbols(c, v))) return rc;
     CK(d2k::cost_matrix(v, resident_view(c), i, j, mode, dC, c->stream));
     int bits = 0;
@@ -1031,7 +1090,7 @@ int d2_mallows_batch(d2_ctx* c, const d2_bags* objs, const int64_t* pair_obj, co
   int rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v);
   if (rc != D2_OK) return rc;
   int mmax = 0;
-  rc = scan(c, v, &mmax);
+  rc = bag_bound(c, objs, v, &mmax);
   if (rc != D2_OK) return rc;
   if (flows && flows->stride < (long long)mmax + c->nmax - 1) return D2_EINVAL;
   const long long* po;
@@ -1051,7 +1110,6 @@ int d2_mallows_batch(d2_ctx* c, const d2_bags* objs, const int64_t* pair_obj, co
         (rc = stage_out(c, flows->w, (size_t)(npairs * flows->stride), kFlowW, &fo.w, &h4)))
       return rc;
   }
-  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   if ((rc = check_bag_symbols(c, v))) return rc;
   SolveCfg cfg = solve_cfg(c, mode_for(c, objs->loc_dtype), mmax);
   if ((rc = attach_tree(c, &cfg, npairs))) return rc;
@@ -1060,12 +1118,7 @@ int d2_mallows_batch(d2_ctx* c, const d2_bags* objs, const int64_t* pair_obj, co
   if (h2) CK(cudaMemcpyAsync(status, ds, (size_t)npairs * 4, cudaMemcpyDeviceToHost, c->stream));
   if (h3) CK(cudaMemcpyAsync(flows->cell, fo.cell, (size_t)(npairs * fo.stride) * 4, cudaMemcpyDeviceToHost, c->stream));
   if (h4) CK(cudaMemcpyAsync(flows->w, fo.w, (size_t)(npairs * fo.stride) * 8, cudaMemcpyDeviceToHost, c->stream));
-  int bits = 0;
-  if ((rc = read_err(c, &bits))) return rc;
-  if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
-  if (bits & d2k::kErrInvalid) return D2_EINVAL;
-  if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
-  return D2_OK;
+  return finish(c, h1 || h2 || h3 || h4);
 }
 
 namespace {
@@ -1091,7 +1144,7 @@ int assign_impl(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* la
   int rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v);
   if (rc != D2_OK) return rc;
   int mmax = 0;
-  if ((rc = scan(c, v, &mmax))) return rc;
+  if ((rc = bag_bound(c, objs, v, &mmax))) return rc;
   if (flows && flows->stride < (long long)mmax + c->nmax - 1) return D2_EINVAL;
   const double* om;
   if ((rc = stage_in(c, omega, (size_t)N, kOmega, &om))) return rc;
@@ -1126,7 +1179,6 @@ int assign_impl(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* la
   }
   int* cand = static_cast<int*>(grow(c, kCand, (size_t)d2k::assign_scratch_ints(N, c->K, c->sms) * 4, &rc));
   if (rc != D2_OK) return rc;
-  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   if ((rc = check_bag_symbols(c, v))) return rc;
   Bins bins;
   if (want_bins(c, N, mmax) && (rc = make_bins(c, v, c->nmax, &bins))) return rc;
@@ -1148,12 +1200,8 @@ int assign_impl(d2_ctx* c, const d2_bags* objs, const double* omega, int32_t* la
   if (h3) CK(cudaMemcpyAsync(flows->cell, fo.cell, (size_t)(N * fo.stride) * 4, cudaMemcpyDeviceToHost, c->stream));
   if (h4) CK(cudaMemcpyAsync(flows->w, fo.w, (size_t)(N * fo.stride) * 8, cudaMemcpyDeviceToHost, c->stream));
   if (h5) CK(cudaMemcpyAsync(dist2_all, dall, (size_t)(N * c->K) * 8, cudaMemcpyDeviceToHost, c->stream));
-  int bits = 0;
-  if ((rc = read_err(c, &bits))) return rc;
-  if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
-  if (bits & d2k::kErrInvalid) return D2_EINVAL;
-  if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
-  return D2_OK;
+  const bool eps_host = eps_total && where(eps_total) != 1;
+  return finish(c, h1 || h2 || h3 || h4 || h5 || eps_host);
 }
 
 }  // namespace
@@ -1298,12 +1346,11 @@ int d2_update_locations(d2_ctx* c, const d2_bags* objs, const double* omega, con
   int rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v);
   if (rc != D2_OK) return rc;
   int mmax = 0;
-  if ((rc = scan(c, v, &mmax))) return rc;
+  if ((rc = bag_bound(c, objs, v, &mmax))) return rc;
   const double* om;
   const int* dl;
   if ((rc = stage_in(c, omega, (size_t)N, kOmega, &om))) return rc;
   if ((rc = stage_in(c, labels, (size_t)N, kLabelsIn, &dl))) return rc;
-  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   FlowOut fo{nullptr, nullptr, 0};
   if (flows) {
     if (!flows->cell || !flows->w || flows->stride < 1) return D2_EINVAL;
@@ -1325,12 +1372,7 @@ int d2_update_locations(d2_ctx* c, const d2_bags* objs, const double* omega, con
   c->tc_stale = true;
   CK(d2k::update_locations(v, om, dl, N, (int)c->K, fo, c->K, c->c_off, c->d, c->cent_ldt,
                            c->c_loc32, c->c_loc64, scr, c->stream, upart, upart_n));
-  int bits = 0;
-  if ((rc = read_err(c, &bits))) return rc;
-  if (bits & d2k::kErrTimeout) return D2_ETIMEOUT;
-  if (bits & d2k::kErrInvalid) return D2_EINVAL;
-  if (bits & d2k::kErrNotConverged) return D2_ENOTCONVERGED;
-  return D2_OK;
+  return D2_OK;  // device work only: errors are reported by d2_sync
 }
 
 int d2_update_weights(d2_ctx* c, const d2_bags* objs, const double* omega, const int32_t* labels,
@@ -1344,11 +1386,12 @@ int d2_update_weights(d2_ctx* c, const d2_bags* objs, const double* omega, const
   if (c->nmax > d2k::kMaxJointN) return D2_EUNSUPPORTED;
   cudaSetDevice(c->device);
   const long long N = objs->count, K = c->K;
-  int rc = D2_OK;
+  int rc = take_errors(c);  // errors left by earlier calls that did not wait
+  if (rc != D2_OK) return rc;
   ObjView v;
   if ((rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v))) return rc;
   int mmax = 0;
-  if ((rc = scan(c, v, &mmax))) return rc;
+  if ((rc = bag_bound(c, objs, v, &mmax))) return rc;
   if ((rc = check_bag_symbols(c, v))) return rc;
   const double* om;
   const int* dl;
@@ -1360,7 +1403,6 @@ int d2_update_weights(d2_ctx* c, const d2_bags* objs, const double* omega, const
   if ((rc = stage_out(c, eps_out, (size_t)K, kJEps, &eps_d, &eps_h)) ||
       (rc = stage_out(c, reinterpret_cast<int*>(iters_out), (size_t)K, kJIters, &it_d, &it_h)))
     return rc;
-  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   CentSet cs{c->c_loc32, c->c_loc64, c->c_Q, c->c_w64, c->c_off, K, c->Tc};
   bool certified = true;
   if ((rc = joint_core(c, v, om, dl, std::max(N, 1LL), (int)K, cs, mmax, max_iter, tol, eps_d,
@@ -1395,6 +1437,8 @@ int d2_assign_multi(d2_ctx* const* ctxs, int32_t B, const d2_bags* objs, int32_t
   cudaSetDevice(c->device);
   const int K = (int)c->K;
   int rc = D2_OK;
+  for (int b = 0; b < B; ++b)  // errors left by earlier calls that did not wait
+    if ((rc = take_errors(ctxs[b]))) return rc;
   ObjView v[d2k::kMaxBagTypes];
   int mmax[d2k::kMaxBagTypes];
   d2k::MultiScreen ms{};
@@ -1412,15 +1456,15 @@ int d2_assign_multi(d2_ctx* const* ctxs, int32_t B, const d2_bags* objs, int32_t
   for (int b = 0; b < B; ++b) {
     d2_ctx* cb = ctxs[b];
     if ((rc = stage_bags(cb, &objs[b], kObjOff, kObjLoc, kObjW, &v[b]))) return rc;
-    if ((rc = scan(cb, v[b], &mmax[b]))) return rc;
+    if ((rc = bag_bound(cb, &objs[b], v[b], &mmax[b]))) return rc;
     float* pair = static_cast<float*>(grow(cb, kMbPair, (size_t)N * K * 2 * 4, &rc));
     int* cand = static_cast<int*>(grow(cb, kCand, (size_t)d2k::assign_scratch_ints(N, K, cb->sms) * 4, &rc));
     int* tl = static_cast<int*>(grow(cb, kMbTmpLab, (size_t)N * 4, &rc));
     double* td = static_cast<double*>(grow(cb, kMbTmpD2, (size_t)N * 8, &rc));
     if (rc != D2_OK) return rc;
-    CK(cudaMemsetAsync(cb->d_err, 0, sizeof(int), cb->stream));
     if ((rc = check_bag_symbols(cb, v[b]))) return rc;
     SolveCfg cfg = solve_cfg(cb, 1, mmax[b]);  // the FP32 screen, whatever the data type
+    cfg.certify = false;  // the summed bounds decide; candidates are solved exactly below
     cfg.pair_out = pair;
     cfg.screen_only = true;
     CK(d2k::assign(v[b], resident_view(cb), N, K, cfg, nullptr, tl, td, nullptr,
@@ -1432,7 +1476,6 @@ int d2_assign_multi(d2_ctx* const* ctxs, int32_t B, const d2_bags* objs, int32_t
   long long* cnt = static_cast<long long*>(grow(c, kMbCnt, (size_t)N * 8, &rc));
   long long* start = static_cast<long long*>(grow(c, kMbStart, (size_t)(N + 1) * 8, &rc));
   if (rc != D2_OK) return rc;
-  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   CK(d2k::multi_candidates(ms, N, K, cnt, start, c->d_err, c->stream));
   long long P = 0;
   CK(cudaMemcpyAsync(&P, start + N, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -1449,7 +1492,6 @@ int d2_assign_multi(d2_ctx* const* ctxs, int32_t B, const d2_bags* objs, int32_t
   mx.B = B;
   for (int b = 0; b < B; ++b) {
     d2_ctx* cb = ctxs[b];
-    CK(cudaMemsetAsync(cb->d_err, 0, sizeof(int), cb->stream));
     SolveCfg cfg = solve_cfg(cb, mode_for(cb, objs[b].loc_dtype), mmax[b]);
     if ((rc = attach_tree(cb, &cfg, P))) return rc;
     if (P > 0)
@@ -1478,17 +1520,17 @@ int d2_segment(d2_ctx* c, const d2_bags* objs, const double* omega, int64_t tau,
   const long long N = objs->count;
   if (N < 1) return D2_EINVAL;
   cudaSetDevice(c->device);
-  int rc = D2_OK;
+  int rc = take_errors(c);  // errors left by earlier calls that did not wait
+  if (rc != D2_OK) return rc;
   ObjView v;
   if ((rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v))) return rc;
   int mmax = 0;
-  if ((rc = scan(c, v, &mmax))) return rc;
+  if ((rc = bag_bound(c, objs, v, &mmax))) return rc;
   const double* om;
   if ((rc = stage_in(c, omega, (size_t)N, kOmega, &om))) return rc;
   int* ds;
   bool host = false;
   if ((rc = stage_out(c, seg_id, (size_t)N, kSgOut, &ds, &host))) return rc;
-  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   long long M = 0;
   if ((rc = segment_impl(c, v, mmax, om, tau, iters, ds, &M))) return rc;
   if (host) CK(cudaMemcpyAsync(seg_id, ds, (size_t)N * 4, cudaMemcpyDeviceToHost, c->stream));
@@ -1522,11 +1564,12 @@ int d2_cluster_level_ex(d2_ctx* c, const d2_bags* objs, const double* omega, int
   const long long N0 = objs->count;
   if (N0 < 1) return D2_EINVAL;
   cudaSetDevice(c->device);
-  int rc = D2_OK;
+  int rc = take_errors(c);  // errors left by earlier calls that did not wait
+  if (rc != D2_OK) return rc;
   ObjView v;
   if ((rc = stage_bags(c, objs, kObjOff, kObjLoc, kObjW, &v))) return rc;
   int mmax = 0;
-  if ((rc = scan(c, v, &mmax))) return rc;
+  if ((rc = bag_bound(c, objs, v, &mmax))) return rc;
   const double* om0;
   if ((rc = stage_in(c, omega, (size_t)N0, kOmega, &om0))) return rc;
   const int d = c->d;
@@ -1546,7 +1589,6 @@ int d2_cluster_level_ex(d2_ctx* c, const d2_bags* objs, const double* omega, int
     }
     CK(cudaStreamSynchronize(c->stream));
   }
-  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   ObjView cur = v;
   int cur_mmax = mmax;
   for (int level = 0;; ++level) {
@@ -1560,7 +1602,6 @@ int d2_cluster_level_ex(d2_ctx* c, const d2_bags* objs, const double* omega, int
       const int si = c->cfg.split_iters > 0 ? c->cfg.split_iters : 10;
       if ((rc = segment_impl(c, cur, cur_mmax, om, seg_size, si, segof, &M))) return rc;
       cur.segof = segof;
-      CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     }
     const long long seg = M == 1 ? n_l : seg_size;
     const long long KT = M * K;

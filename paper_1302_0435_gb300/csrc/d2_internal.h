@@ -113,6 +113,9 @@ struct SolveCfg {
   const int* oidx = nullptr;  // objects of this launch (nullptr: obase..obase+nobj-1)
   long long nobj = -1;        // entries of oidx (-1: all ob.count objects)
   long long obase = 0;        // first object when oidx is nullptr
+  // device-side object range (bins whose counts stay on the device): the
+  // launch takes oidx[dev_range[0] .. dev_range[1]); overrides nobj
+  const long long* dev_range = nullptr;
   int start = 0;              // cold start basis: 0 ranked northwest staircase, 1 Vogel
   // per-pair screen output (optional): pair_out[2*(i*K + j)] = FP32 value,
   // [..+1] = its error bound (+inf when the screen could not bound it, NaN
@@ -144,6 +147,10 @@ inline size_t pair_tree_bytes(long long npairs, int mmax, int nmax) {
 enum : int { kErrInvalid = 1, kErrNotConverged = 2, kErrTimeout = 4 };
 
 cudaError_t scan_bags(const long long* off, long long count, int* d_info, cudaStream_t st);
+// Raise kErrInvalid into d_err unless off[0] = 0 and every bag has 1..maxm
+// supports (no host wait: callers that declare their largest bag).
+cudaError_t check_bags(const long long* off, long long count, int maxm, int* d_err,
+                       cudaStream_t st);
 cudaError_t prep_centroids(const void* loc, int ldt, const void* w, int wdt, const long long* off,
                            long long K, int d, float* loc32, double* loc64, long long* Qpre,
                            double* w64, int* d_err, cudaStream_t st);
@@ -179,6 +186,9 @@ D2_NPL_DECL(4)
 
 // Raise kErrInvalid into d_err unless every location of the T supports is
 // an integer symbol id in [0, A) (d = 1).
+// The same for the supports of a bag batch (their count read on the device).
+cudaError_t check_bag_symbols(const void* loc, int ldt, const long long* off, long long count,
+                              int A, int* d_err, cudaStream_t st);
 cudaError_t check_symbols(const void* loc, int ldt, long long T, int A, int* d_err,
                           cudaStream_t st);
 

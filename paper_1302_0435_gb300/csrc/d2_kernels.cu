@@ -28,6 +28,14 @@ __global__ void k_scan_bags(const long long* off, long long count, int* info) {
   }
 }
 
+__global__ void k_check_bags(const long long* off, long long count, int maxm, int* err) {
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < count;
+       b += (long long)gridDim.x * blockDim.x) {
+    const long long m = off[b + 1] - off[b];
+    if (m < 1 || m > maxm || (b == 0 && off[0] != 0)) atomicOr(err, kErrInvalid);
+  }
+}
+
 template <int G>
 __global__ void k_prep_centroids(const void* loc, int ldt, const void* w, int wdt,
                                  const long long* off, long long K, int d, float* loc32,
@@ -106,6 +114,16 @@ __global__ void k_check_symbols(const void* loc, int ldt, long long T, int A, in
   }
 }
 
+__global__ void k_check_bag_symbols(const void* loc, int ldt, const long long* off, long long count,
+                                    int A, int* err) {
+  const long long T = off[count];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double v = ldx<double>(loc, ldt, t);
+    if (!(v >= 0.0 && v < (double)A && v == floor(v))) atomicOr(err, kErrInvalid);
+  }
+}
+
 // Fixed-order sum (one block, strided partials then a tree): deterministic.
 __global__ void k_sum_fixed(const double* v, long long n, double* out) {
   __shared__ double sh[256];
@@ -151,6 +169,15 @@ cudaError_t scan_bags(const long long* off, long long count, int* d_info, cudaSt
   if (count <= 0) return cudaSuccess;
   const long long blocks = (count + 255) / 256;
   k_scan_bags<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(off, count, d_info);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t check_bags(const long long* off, long long count, int maxm, int* d_err,
+                       cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const long long blocks = (count + 255) / 256;
+  k_check_bags<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(off, count, maxm, d_err);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -231,6 +258,14 @@ cudaError_t check_symbols(const void* loc, int ldt, long long T, int A, int* d_e
   if (T <= 0) return cudaSuccess;
   const unsigned b = (unsigned)std::min<long long>((T + 255) / 256, 4096);
   k_check_symbols<<<b, 256, 0, st>>>(loc, ldt, T, A, d_err);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t check_bag_symbols(const void* loc, int ldt, const long long* off, long long count,
+                              int A, int* d_err, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_check_bag_symbols<<<(unsigned)(152 * 4), 256, 0, st>>>(loc, ldt, off, count, A, d_err);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -568,6 +568,33 @@ __global__ void __launch_bounds__(128) k_pairs64(ObjView ob, CentView cv, const 
 // kCandCap candidate indices in increasing order, their lower ends (float
 // bits), and the block's smallest upper end (float bits).
 
+// Objects of a launch: their count and list (oidx, or obase.. when null);
+// with a device-side range the count is read here (SolveCfg::dev_range).
+__device__ __forceinline__ long long launch_objects(const SolveCfg& cfg, long long count,
+                                                    const int** oidx) {
+  if (cfg.dev_range) {
+    const long long lo = cfg.dev_range[0];
+    *oidx = cfg.oidx + lo;
+    return cfg.dev_range[1] - lo;
+  }
+  *oidx = cfg.oidx;
+  return cfg.nobj >= 0 ? cfg.nobj : count;
+}
+
+// Centroid blocks of the screen: enough (object, block) items to fill the
+// GPU (sms x items per SM), blocks of at least 8 centroids.
+__host__ __device__ inline void centroid_blocks(const SolveCfg& cfg, long long cnt, int K, int* NB,
+                                                int* KB) {
+  const int ip = cfg.ipsm < 8 ? 8 : (cfg.ipsm > 256 ? 256 : cfg.ipsm);
+  const long long want = (long long)cfg.sms * ip;
+  long long nb = cnt > 0 ? (want + cnt - 1) / cnt : 1;
+  const long long cap = K / 8 > 1 ? K / 8 : 1;
+  nb = nb < 1 ? 1 : (nb > cap ? cap : nb);
+  const int kb = (int)((K + nb - 1) / nb);
+  *KB = kb;
+  *NB = (K + kb - 1) / kb;
+}
+
 // FP32 cost tile of one pair from a chunk's precomputed tile rows (see
 // TileView): row a of the pair is row a of src, columns 0..n-1.  Returns
 // the tile maximum (group-uniform).
@@ -634,66 +661,189 @@ __device__ __forceinline__ double cost64_cell(const ObjView& ob, long long o0, c
   return acc;
 }
 
-// FP64 certificate of the basis an FP32 solve stopped at (precision
-// pattern: FP32 pivots, FP64 optimality check and objective).
-//   1. The costs of the m+n-1 basic cells (tree edges) in FP64; the FP64
-//      objective D = sum w c of the basic flows (exact integer masses), an
-//      upper bound of the optimum since the basis is feasible; FP64
-//      potentials u_a + v_r = c_ar on every tree edge (pointer jumping).
-//   2. LP duality: for any optimal plan w*, D* = sum w* (u + v + d) =
+// ---- double-float arithmetic (an unevaluated sum hi + lo of two floats,
+// about 48 significant bits) on the FP32 pipes, which run 64 times the FP64
+// rate on this GPU.  The intrinsics keep every product and sum rounded on
+// its own (no contraction into FMA), which the error-free steps rely on.
+
+// s + e = a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) + (bh, bl) -> normalised (hi, lo): relative error <= 4 u^2 of the
+// magnitudes involved (u = 2^-24).
+__device__ __forceinline__ void dd_add(float& hi, float& lo, float bh, float bl) {
+  float s, e;
+  two_sum(hi, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(lo, bl));
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// Ground cost of cell (a, r) as hi + lo, for FP32 or BF16 object data (X)
+// and a centroid set whose FP32 copy is exact (loc32 == loc64: the screen's
+// precondition).  Per coordinate: x - y exactly by two-sum (s + e), s^2
+// exactly as p + q (q = fma(s, s, -p)), the cross term 2se + q rounded once
+// (e^2 <= u^2 s^2 dropped), and the running sum kept as hi + lo.  Error:
+// |hi + lo - c| <= (6d + 4) u^2 c.
+// One coordinate's term added to the running sum H + L.
+__device__ __forceinline__ void dd_sq_acc(float xv, float yv, float& H, float& L) {
+  float s, e;
+  two_sum(xv, -yv, s, e);
+  const float p = __fmul_rn(s, s);
+  const float q = fmaf(s, s, -p);
+  const float rr = fmaf(__fadd_rn(s, s), e, q);
+  float t, z;
+  two_sum(H, p, t, z);
+  L = __fadd_rn(L, __fadd_rn(z, rr));
+  H = t;
+}
+
+// Two independent running sums (even and odd coordinates) shorten the
+// dependent chain; they are added exactly at the end (two-sum).
+template <typename X>
+__device__ __forceinline__ void cost_dd_x(const X* __restrict__ x, const float* __restrict__ y,
+                                          int d, float& hi, float& lo) {
+  float H0 = 0.f, L0 = 0.f, H1 = 0.f, L1 = 0.f;
+  int k = 0;
+  for (; k + 1 < d; k += 2) {
+    dd_sq_acc(cvt<float>(x[k]), y[k], H0, L0);
+    dd_sq_acc(cvt<float>(x[k + 1]), y[k + 1], H1, L1);
+  }
+  if (k < d) dd_sq_acc(cvt<float>(x[k]), y[k], H0, L0);
+  float t, z;
+  two_sum(H0, H1, t, z);
+  const float L = __fadd_rn(__fadd_rn(L0, L1), z);
+  hi = __fadd_rn(t, L);
+  lo = __fsub_rn(L, __fsub_rn(hi, t));
+}
+
+// The cell cost of FP64 data or of a symbol table: the FP64 cost (the
+// arithmetic of cost64_cell) split into hi + lo.  Out of line, with scalar
+// arguments: only those rare inputs take it.
+__device__ __noinline__ float2 cost_dd_slow(const void* xloc, int ldt, long long xrow, int d,
+                                            const double* y64, const double* tab64, int A) {
+  double c;
+  if (A) {
+    int xs = (int)ldx<double>(xloc, ldt, xrow);
+    int ys = (int)y64[0];
+    xs = xs < 0 ? 0 : (xs >= A ? A - 1 : xs);
+    ys = ys < 0 ? 0 : (ys >= A ? A - 1 : ys);
+    c = tab64[xs * A + ys];
+  } else {
+    c = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const double df = ldx<double>(xloc, ldt, xrow * d + k) - y64[k];
+      c = fma(df, df, c);
+    }
+  }
+  const float hi = __double2float_rn(c);
+  return make_float2(hi, __double2float_rn(c - (double)hi));
+}
+
+// Cost of cell (a, r) as hi + lo (cost_dd_x, or cost_dd_slow when `fast`
+// does not hold).
+template <typename X>
+__device__ __forceinline__ void cost_dd(bool fast, const ObjView& ob, long long o0,
+                                        const CentView& cv, long long c0, int a, int r,
+                                        float& hi, float& lo) {
+  if (fast) {
+    cost_dd_x(static_cast<const X*>(ob.loc) + (o0 + a) * cv.d, cv.loc32 + (c0 + r) * cv.d, cv.d,
+              hi, lo);
+  } else {
+    const float2 c = cost_dd_slow(ob.loc, ob.ldt, o0 + a, cv.d,
+                                  cv.A ? cv.loc64 + c0 + r : cv.loc64 + (c0 + r) * cv.d, cv.tab64,
+                                  cv.A);
+    hi = c.x;
+    lo = c.y;
+  }
+}
+
+// Optimality certificate of the basis an FP32 solve stopped at (precision
+// pattern: FP32 pivots, then a check and objective of FP64 accuracy).
+//   1. Costs of the m+n-1 basic cells (tree edges) in double-float; the
+//      objective D = sum w c of the basic flows (exact integer masses) in
+//      FP64 -- an upper bound of the optimum, the basis being feasible.
+//   2. Potentials u_a + v_r = c_ar on every tree edge: the FP32 solve's own
+//      potentials plus a correction delta, from the residuals
+//      c_ar - pot_a - pot_r of the tree edges (double-float costs, so the
+//      small residuals are exact to about 2^-48 c) propagated down the tree
+//      by pointer jumping in FP32 (delta is small, its own rounding
+//      negligible).
+//   3. LP duality: for an optimal plan w*, D* = sum w* (u + v + d) =
 //      D + sum w* d >= D + min d, because sum w* = 1 and the marginals are
-//      those of the basis.  So D - D* <= max(0, -min d) over all cells.
-//   3. min d is checked in FP32 against a rounding bound: with the FP32
-//      tile c32, potentials rounded to FP32 and two FP32 subtractions,
-//      |d32 - d| <= E = ecost + 2^-24 (2 c_max + 5 p_max) (ecost bounds
-//      |c32 - c| per cell, p_max the largest |potential|), so d32 >= E - tau
-//      implies d >= -tau.  The few cells below that are re-priced in FP64.
+//      the basis's.  So D - D* <= max(0, -min d) over all cells.
+//   4. min d is checked in FP32 against a rounding bound: with the FP32
+//      tile c32, the potentials rounded to FP32 and two FP32 subtractions,
+//      |d32 - d~| <= E = ecost + 2^-24 (2 c_max + 5 p_max) (ecost bounds
+//      |c32 - c| per cell, p_max the largest |potential|, d~ the reduced
+//      cost of the computed potentials), and |d~ - d| <= err = (N + 1)
+//      ((6d + 32) 2^-48 c_max + 2^-24 delta_max) covers the double-float
+//      costs and the corrections; so d32 >= E + err - tau implies
+//      d >= -tau.  The few cells below that are re-priced in double-float
+//      and must reach err - tau.
 // Returns true when every reduced cost is >= -tau, tau = max(2^-24 D,
-// 2^-43 c_max): the pair's D^2 is then certified, D - tau <= D* <= D.  *D64:
-// the FP64 objective of the basis (valid whatever the outcome); *nchk: cells
-// re-priced in FP64.  Overwrites the basic cells of the FP32 tile and the
-// solver's pivot scratch; the tree is untouched.
-template <int G, int NPL>
+// 2^-43 c_max) (*tau_out, FP32 rounded down): the pair's D^2 is then
+// certified, D - tau <= D* <= D (up to (6d + 4) 2^-48 relative for the
+// double-float costs in D).  *D64: the FP64 objective of the basis (NaN if
+// the tree was inconsistent); *nchk: cells re-priced.  Overwrites the
+// basic cells of the FP32 tile and the solver's pivot scratch; the tree
+// and the solver's potentials are kept.
+template <int G, int NPL, typename X>
 __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long long o0,
                              const CentView& cv, long long c0, float cmax, float ecost,
-                             double* D64, int* nchk) {
+                             double* D64, float* tau_out, int* nchk) {
   const Grp<G>& g = S.g;
   const int m = S.m, n = S.n, N = S.N;
   const PairMem<float>& s = S.s;
-  double ec[NPL];
+  const bool fast = cv.A == 0 && ob.ldt != 0;  // cost_dd_x applies
+  float rres[NPL];
   double acc = 0.0;
 #pragma unroll
   for (int k = 0; k < NPL; ++k) {
     const int y = S.node_of(k);
-    ec[k] = 0.0;
+    rres[k] = 0.f;
     if (y < N && y != S.root) {
       const int p = S.t.par[k];
       const int a = y < m ? y : p;
       const int r = y < m ? p - m : y - m;
-      ec[k] = cost64_cell(ob, o0, cv, c0, a, r);
-      acc += ((double)S.t.flow[k] * kInvMass) * ec[k];
+      float ch, cl;
+      cost_dd<X>(fast, ob, o0, cv, c0, a, r, ch, cl);
+      const double w = (double)S.t.flow[k] * kInvMass;
+      acc = fma(w, (double)ch, acc);
+      acc = fma(w, (double)cl, acc);
+      // residual of the FP32 potentials on this edge: c - pot_y - pot_p
+      float s1, e1;
+      two_sum(ch, -S.pot[k], s1, e1);
+      e1 = __fadd_rn(e1, cl);
+      float s2, e2;
+      two_sum(s1, -s.pot[p], s2, e2);
+      rres[k] = __fadd_rn(s2, __fadd_rn(e2, e1));
     }
   }
   const double D = gsum<G>(g, acc);
   *D64 = D;
-  // FP64 potentials: pot(root) = 0, pot(y) = c(y, par y) - pot(par y)
-  double* P64 = reinterpret_cast<double*>(s.pflow);  // [N] final potentials
-  double pot[NPL];
+  // corrections: delta(root) = 0, delta(y) = residual(y) - delta(par y)
+  float2* PD = reinterpret_cast<float2*>(s.pflow);  // [N] (solver potential, correction)
+  float dl[NPL];
   bool bad = false;
   if constexpr (NPL == 1 && G == 32) {
     const int y = g.lane;
     int code = y;
-    double a = 0.0;
+    float a = 0.f;
     if (y < N && y != S.root) {
       const int p = S.t.par[0];
       if (p < 0 || p >= N || (y < m) == (p < m)) { bad = true; code = S.root; }
-      else { code = p | (1 << 16); a = ec[0]; }
+      else { code = p | (1 << 16); a = rres[0]; }
     }
     for (int round = 0;; ++round) {
       if (round > 9) { bad = true; break; }
       const int an = code & 0xffff;
       const int c2 = __shfl_sync(g.mask, code, an);
-      const double v = __shfl_sync(g.mask, a, an);
+      const float v = __shfl_sync(g.mask, a, an);
       const bool mv = y < N && an != S.root;
       if (mv) {
         const int par1 = code >> 16;
@@ -702,20 +852,20 @@ __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long 
       }
       if (!gany<G>(g, mv)) break;
     }
-    pot[0] = a;
+    dl[0] = a;
   } else {
     int* pa = s.pj0;
     int* pb = s.pj1;
-    double* aa = P64;
-    double* ab = reinterpret_cast<double*>(s.acc0);  // acc0 and acc1 together: N doubles
+    float* aa = s.acc0;
+    float* ab = s.acc1;
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
       const int y = S.node_of(k);
-      if (y == S.root) { pa[y] = y; aa[y] = 0.0; }
+      if (y == S.root) { pa[y] = y; aa[y] = 0.f; }
       else if (y < N) {
         const int p = S.t.par[k];
-        if (p < 0 || p >= N || (y < m) == (p < m)) { bad = true; pa[y] = S.root; aa[y] = 0.0; }
-        else { pa[y] = p | (1 << 16); aa[y] = ec[k]; }
+        if (p < 0 || p >= N || (y < m) == (p < m)) { bad = true; pa[y] = S.root; aa[y] = 0.f; }
+        else { pa[y] = p | (1 << 16); aa[y] = rres[k]; }
       }
     }
     g.sync();
@@ -730,7 +880,7 @@ __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long 
           const int an = code & 0xffff;
           if (an != S.root) {
             const int c2 = pa[an];
-            const double v = aa[an];
+            const float v = aa[an];
             const int par1 = code >> 16;
             ab[y] = par1 ? aa[y] - v : aa[y] + v;
             pb[y] = (c2 & 0xffff) | ((par1 ^ (c2 >> 16)) << 16);
@@ -743,49 +893,66 @@ __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long 
       }
       g.sync();
       int* tp = pa; pa = pb; pb = tp;
-      double* ta = aa; aa = ab; ab = ta;
+      float* ta = aa; aa = ab; ab = ta;
       if (!gany<G>(g, moved)) break;
     }
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
       const int y = S.node_of(k);
-      pot[k] = y < N ? aa[y] : 0.0;
+      dl[k] = y < N ? aa[y] : 0.f;
     }
     g.sync();
   }
-  // potentials to shared memory (FP64 for re-pricing, FP32 for the scan);
-  // the basic cells leave the scan (+inf in the FP32 tile)
-  float pmax = 0.f;
+  // potentials to shared memory ((base, correction) for re-pricing, their
+  // FP32 sum for the scan); the basic cells leave the scan (+inf in the tile)
+  float pmax = 0.f, dmax = 0.f;
 #pragma unroll
   for (int k = 0; k < NPL; ++k) {
     const int y = S.node_of(k);
     if (y < N) {
-      const float p32 = (float)pot[k];
-      P64[y] = pot[k];
-      s.pot[y] = p32;
-      pmax = fmaxf(pmax, fabsf(p32));
+      PD[y] = make_float2(S.pot[k], dl[k]);
+      const float u = S.pot[k] + dl[k];
+      s.pot[y] = u;
+      pmax = fmaxf(pmax, fabsf(u));
+      dmax = fmaxf(dmax, fabsf(dl[k]));
       if (y != S.root) s.cost[S.edge_idx(y, S.t.par[k])] = INFINITY;
     }
   }
   pmax = gmax<G>(g, pmax);
+  dmax = gmax<G>(g, dmax);
   g.sync();
   if (gany<G>(g, bad)) { *D64 = NAN; return false; }
-  if (!isfinite(D) || !isfinite(pmax)) return false;
-  const double tau = fmax(0x1p-24 * D, 0x1p-43 * (double)cmax);
-  const double E = ((double)ecost + 0x1p-24 * (2.0 * (double)cmax + 5.0 * (double)pmax)) *
-                   (1.0 + 0x1p-10);
-  const float thr = __double2float_ru(E - tau);
+  if (!isfinite(D) || !isfinite(pmax) || !isfinite(dmax) || !(cmax < FLT_MAX)) return false;
+  // tau and the bounds in FP32, rounded toward the safe side
+  const float tau = fmaxf(__fmul_rd(__double2float_rd(D), 0x1p-24f), __fmul_rd(cmax, 0x1p-43f));
+  *tau_out = tau;
+  const float err = __fmul_ru((float)(N + 1),
+                              __fmaf_ru((float)(6 * cv.d + 32) * 0x1p-48f, cmax,
+                                        __fmul_ru(dmax, 0x1p-24f)));
+  const float E = __fmul_ru(__fadd_ru(ecost, __fmul_ru(__fmaf_ru(5.f, pmax, 2.f * cmax), 0x1p-24f)),
+                            1.f + 0x1p-10f);
+  const float thr = __fsub_ru(__fadd_ru(E, err), tau);  // d32 >= thr    =>  d >= -tau
+  const float thr_dd = __fsub_ru(err, tau);              // d~ >= thr_dd  =>  d >= -tau
   const int mn = m * n;
-  int a = S.a0, r = S.r0;
   bool fail = false;
   int cnt = 0;
+  // a cell below thr (+inf basic cells never are) is re-priced in double-float
+  auto reprice = [&](int a, int r) {
+    ++cnt;
+    float ch, cl;
+    cost_dd<X>(fast, ob, o0, cv, c0, a, r, ch, cl);
+    const float2 u = PD[a], v = PD[m + r];
+    dd_add(ch, cl, -u.x, -u.y);
+    dd_add(ch, cl, -v.x, -v.y);
+    fail |= !((double)ch + (double)cl >= (double)thr_dd);
+  };
+  // when n divides the group (sr == 0) the lane's cells share column r0:
+  // its potential stays in a register
+  const bool colfix = S.sr == 0;
+  const float vfix = s.pot[m + S.r0];
+  int a = S.a0, r = S.r0;
   for (int i = g.lane; i < mn; i += G) {
-    const float d32 = s.cost[i] - s.pot[a] - s.pot[m + r];
-    if (d32 < thr) {  // +inf (basic) cells never are
-      ++cnt;
-      const double d64 = cost64_cell(ob, o0, cv, c0, a, r) - P64[a] - P64[m + r];
-      fail |= !(d64 >= -tau);
-    }
+    if (s.cost[i] - s.pot[a] - (colfix ? vfix : s.pot[m + r]) < thr) reprice(a, r);
     r += S.sr; a += S.sq;
     if (r >= n) { r -= n; ++a; }
   }
@@ -795,7 +962,7 @@ __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long 
 
 template <int G, int NPL, bool TC, int ST, bool CERT>
 __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, CentView cv, long long seg_size, int K,
-                                                int KB, int NB, SolveCfg cfg, size_t slice,
+                                                SolveCfg cfg, size_t slice,
                                                 int* items_out, unsigned long long* queue,
                                                 WarmStore ws, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -806,15 +973,18 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
   float* clo = reinterpret_cast<float*>(s32.sc + kCandCap);    // [kCandCap]
   int n_scr = 0, p_scr = 0, n_cert = 0, n_chk = 0;
   const float rel = (float)(cv.d + 3) * 0x1p-24f + 0x1p-17f;
-  const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
-  const unsigned long long total = (unsigned long long)nobj * NB;
+  const int* oidx;
+  const long long nobj = launch_objects(cfg, ob.count, &oidx);
+  int NB, KB;
+  centroid_blocks(cfg, nobj, K, &NB, &KB);
+  const unsigned long long total = nobj > 0 ? (unsigned long long)nobj * NB : 0ull;
   for (;;) {
     unsigned long long item = 0;
     if (g.lane == 0) item = atomicAdd(queue, 1ull);
     item = __shfl_sync(g.mask, item, 0, G);
     if (item >= total) break;
     const long long tt = (long long)(item / NB);
-    const long long i = cfg.oidx ? (long long)cfg.oidx[tt] : cfg.obase + tt;
+    const long long i = oidx ? (long long)oidx[tt] : cfg.obase + tt;
     const int jb = (int)(item - (unsigned long long)tt * NB);
     const int j0 = jb * KB, j1 = min(K, j0 + KB);
     const long long o0 = ob.off[i];
@@ -882,23 +1052,30 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
         // every pair certified in FP64 (certify_fp64); one that fails is
         // always a candidate, so the exact pass solves it
         double D64 = NAN;
+        float tau = 0.f;
         bool cert = false;
         if (st == kStOk) {
           float ecost;
           if constexpr (TC) ecost = tc_bound(cv.d, nxm, cfg.tile.cn[cb + j], cfg.tile.cd[cb + j]);
           else ecost = (cv.A ? 0x1p-23f : (float)(cv.d + 3) * 0x1p-24f) * cmax;
-          cert = certify_fp64<G, NPL>(S, ob, o0, cv, c0, cmax, ecost, &D64, &n_chk);
+          cert = ob.ldt == 2
+                     ? certify_fp64<G, NPL, __nv_bfloat16>(S, ob, o0, cv, c0, cmax, ecost, &D64,
+                                                           &tau, &n_chk)
+                     : certify_fp64<G, NPL, float>(S, ob, o0, cv, c0, cmax, ecost, &D64, &tau,
+                                                   &n_chk);
         }
-        const double up = D64 * (1.0 + 0x1p-40);  // covers the FP64 rounding of D64
+        // D64 is within (6d + 4) 2^-48 relative of the basis's objective
+        // (double-float costs, FP64 sum); the FP32 interval ends, widened by
+        // 2^-22 relative, cover it
+        const float dhi = __double2float_ru(D64);
         if (cert) {
           ++n_cert;
-          const double tau = fmax(0x1p-24 * D64, 0x1p-43 * (double)cmax);
-          lo = __double2float_rd(D64 - tau);
-          hi = __double2float_ru(up);
+          lo = __fsub_rd(__fmul_rd(__double2float_rd(D64), 1.f - 0x1p-22f), tau);
+          hi = __fmul_ru(dhi, 1.f + 0x1p-22f);
           pair_d64 = D64;
         } else {
           lo = -FLT_MAX;
-          hi = isfinite(D64) ? __double2float_ru(up) : FLT_MAX;
+          hi = isfinite(D64) ? __fmul_ru(dhi, 1.f + 0x1p-22f) : FLT_MAX;
         }
         if (cfg.pair64 && g.lane == 0) cfg.pair64[i * (long long)K + j] = pair_d64;
       } else {
@@ -965,11 +1142,14 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
 // Per object: merge its NB block lists into one candidate list (count,
 // kCandCap indices increasing) at cand[i*kMergedInts]: keep the block
 // candidates whose lower end reaches the smallest upper end over all blocks.
-__global__ void k_merge(const int* items, long long N, int NB, const int* oidx, long long obase,
-                        int* cand) {
+__global__ void k_merge(const int* items, long long count, int K, SolveCfg cfg, int* cand) {
+  const int* oidx;
+  const long long N = launch_objects(cfg, count, &oidx);
+  int NB, KB;
+  centroid_blocks(cfg, N, K, &NB, &KB);
   for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < N;
        tt += (long long)gridDim.x * blockDim.x) {
-    const long long i = oidx ? (long long)oidx[tt] : obase + tt;
+    const long long i = oidx ? (long long)oidx[tt] : cfg.obase + tt;
     const int* it = items + tt * NB * kItemInts;
     float best_hi = FLT_MAX;
     int state = 0;  // 0 ok, -1 all, -2 invalid
@@ -1019,10 +1199,11 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
   unsigned char* base = smem + (threadIdx.x / G) * slice;
   const PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax, cv.d);
   int n_ex = 0, p_ex = 0;
-  const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
+  const int* oidx;
+  const long long nobj = launch_objects(cfg, ob.count, &oidx);
   for (long long tt = (long long)blockIdx.x * gpb + threadIdx.x / G; tt < nobj;
        tt += (long long)gridDim.x * gpb) {
-    const long long i = cfg.oidx ? (long long)cfg.oidx[tt] : cfg.obase + tt;
+    const long long i = oidx ? (long long)oidx[tt] : cfg.obase + tt;
     const long long o0 = ob.off[i];
     const int m = (int)(ob.off[i + 1] - o0);
     const long long cb = seg_of(ob, i, seg_size) * (long long)K;
@@ -1202,7 +1383,9 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
   unsigned grid = 1;
   cudaError_t e;
   const bool screen = cfg.mode == 1 && cand != nullptr;
-  const long long nobj = cfg.nobj >= 0 ? cfg.nobj : ob.count;
+  // with a device-side range the count is not known here: persistent
+  // grids, sized by the batch
+  const long long nobj = cfg.dev_range ? ob.count : (cfg.nobj >= 0 ? cfg.nobj : ob.count);
   if (nobj <= 0) return cudaSuccess;
   if (screen) {
     // scratch layout: [queue counter: 4 ints][merged lists: count*kMergedInts][items]
@@ -1211,20 +1394,19 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
     int* items = merged + ((ob.count * kMergedInts + 3) & ~3LL);  // merged is indexed by object
     // one screening launch over objects [t0, t0+cnt) of this launch
     auto screen_part = [&](const SolveCfg& sc, long long cnt) -> cudaError_t {
-      // centroid blocks: enough (object, block) items to fill the GPU
-      const long long want = (long long)sc.sms * std::min(std::max(sc.ipsm, 8), 256);
-      int NB = (int)std::min<long long>(std::max<long long>(1, (want + cnt - 1) / cnt),
-                                        std::max(1, K / 8));
-      const int KB = (K + NB - 1) / NB;
-      NB = (K + KB - 1) / KB;
+      // items: (object, centroid block), the blocks chosen on the device
+      // (centroid_blocks) from the launch's object count
+      int NB, KB;
+      centroid_blocks(sc, cnt, K, &NB, &KB);
+      const long long work = sc.dev_range ? (1LL << 40) : cnt * (long long)NB;
       cudaError_t e2 = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
       if (e2 != cudaSuccess) return e2;
       auto launch = [&](auto kern) -> cudaError_t {
         unsigned g2 = 1;
-        cudaError_t e3 = launch_cfg(kern, smem32, gpb32 * G, sc.sms, cnt * (long long)NB, gpb32, &g2);
+        cudaError_t e3 = launch_cfg(kern, smem32, gpb32 * G, sc.sms, work, gpb32, &g2);
         if (e3 != cudaSuccess) return e3;
-        kern<<<g2, gpb32 * G, smem32, st>>>(ob, cv, seg_size, K, KB, NB, sc, slice32, items, queue,
-                                            ws, d_err);
+        kern<<<g2, gpb32 * G, smem32, st>>>(ob, cv, seg_size, K, sc, slice32, items, queue, ws,
+                                            d_err);
         return cudaSuccess;
       };
       if (sc.tile.C)
@@ -1234,8 +1416,8 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
         e2 = sc.certify ? launch(k_screen<G, NPL, false, ST, true>)
                         : launch(k_screen<G, NPL, false, ST, false>);
       if (e2 != cudaSuccess) return e2;
-      const unsigned mb = (unsigned)std::min<long long>((cnt + 255) / 256, 4096);
-      k_merge<<<mb, 256, 0, st>>>(items, cnt, NB, sc.oidx, sc.obase, merged);
+      const unsigned mb = (unsigned)std::max<long long>(1, std::min<long long>((cnt + 255) / 256, 4096));
+      k_merge<<<mb, 256, 0, st>>>(items, ob.count, K, sc, merged);
       note_launches(2);
       return cudaGetLastError();
     };
@@ -1266,7 +1448,8 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
     }
   }
   if (screen && cfg.screen_only) return cudaGetLastError();
-  e = launch_cfg(k_exact<G, NPL, ST>, smem, gpb * G, cfg.sms, nobj, gpb, &grid);
+  e = launch_cfg(k_exact<G, NPL, ST>, smem, gpb * G, cfg.sms,
+                 cfg.dev_range ? (1LL << 40) : nobj, gpb, &grid);
   if (e != cudaSuccess) return e;
   WarmStore wx = ws;
   if (!screen) wx.par8 = nullptr;

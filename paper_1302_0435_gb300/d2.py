@@ -36,7 +36,7 @@ EXPORTS = ["d2_ctx_create", "d2_ctx_destroy", "d2_set_stream", "d2_sync", "d2_st
 class D2Bags(ctypes.Structure):
     _fields_ = [("loc", ctypes.c_void_p), ("w", ctypes.c_void_p), ("off", ctypes.c_void_p),
                 ("count", ctypes.c_int64), ("dim", ctypes.c_int32), ("loc_dtype", ctypes.c_int32),
-                ("w_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("w_dtype", ctypes.c_int32), ("max_support", ctypes.c_int32)]
 
 
 class D2Config(ctypes.Structure):
@@ -143,12 +143,14 @@ _DT = {"f64": D2_F64, "f32": D2_F32, "bf16": D2_BF16}
 
 
 class BagsRef:
-    """A bag batch as the C ABI sees it, holding references to its arrays."""
+    """A bag batch as the C ABI sees it, holding references to its arrays.
+    max_support: the largest bag's support count if known (0: the library
+    scans the offsets, which waits for the stream)."""
 
-    def __init__(self, loc, w, off, count, dim, loc_dtype, w_dtype):
+    def __init__(self, loc, w, off, count, dim, loc_dtype, w_dtype, max_support=0):
         self.loc, self.w, self.off = loc, w, off
         self.s = D2Bags(_ptr(loc), _ptr(w), _ptr(off), int(count), int(dim), int(loc_dtype),
-                        int(w_dtype), 0)
+                        int(w_dtype), int(max_support))
 
     @property
     def count(self):
@@ -164,8 +166,13 @@ def bags_from_synth(b, device=None, pinned=False):
         loc_np = np.ascontiguousarray(b.loc)
     w_np = np.ascontiguousarray(b.w)
     off_np = np.ascontiguousarray(b.off.astype(np.int64))
+    # the largest bag, declared so that calls need not scan the offsets (only
+    # when every bag fits the kernels; otherwise the library's scan reports it)
+    sizes = np.diff(off_np)
+    mx = int(sizes.max()) if sizes.size else 0
+    ms = mx if 1 <= mx <= MAX_SUPPORT and sizes.min() >= 1 else 0
     if device is None and not pinned:
-        return BagsRef(loc_np, w_np, off_np, b.count, b.dim, _DT[b.loc_dtype], _DT[b.w_dtype])
+        return BagsRef(loc_np, w_np, off_np, b.count, b.dim, _DT[b.loc_dtype], _DT[b.w_dtype], ms)
     import torch
     tl = torch.from_numpy(loc_np)
     if b.loc_dtype == "bf16":
@@ -175,7 +182,7 @@ def bags_from_synth(b, device=None, pinned=False):
         tl, tw, to = tl.pin_memory(), tw.pin_memory(), to.pin_memory()
     else:
         tl, tw, to = tl.to(device), tw.to(device), to.to(device)
-    return BagsRef(tl, tw, to, b.count, b.dim, _DT[b.loc_dtype], _DT[b.w_dtype])
+    return BagsRef(tl, tw, to, b.count, b.dim, _DT[b.loc_dtype], _DT[b.w_dtype], ms)
 
 
 class Context:
@@ -233,6 +240,13 @@ def d2_get_centroids(ctx, dim):
     off = np.empty(k.value + 1, dtype=np.int64)
     _check(lib.d2_get_centroids(ctx.h, _ptr(loc), _ptr(w), _ptr(off), None, None), "d2_get_centroids")
     return loc, w, off
+
+
+def d2_get_centroids_into(ctx, loc_out):
+    """Resident centroid locations into a caller buffer ([T, dim] float64,
+    host or device)."""
+    _check(load().d2_get_centroids(ctx.h, _ptr(loc_out), None, None, None, None),
+           "d2_get_centroids")
 
 
 def d2_cost_matrix(ctx, objs, i, j, precision, m, n):

@@ -60,6 +60,7 @@ def test_table_plans_and_cost_matrix(d2, oracle_mod):
           torch.empty((len(pi), 63), dtype=torch.float64, device="cuda:0"))
     rc = d2.d2_mallows_batch(ctx, ob, torch.as_tensor(pi, device="cuda:0"),
                              torch.as_tensor(pj, device="cuda:0"), dist, flows=fl, status=st)
+    d2.d2_sync(ctx)  # device outputs: the call returned without waiting
     assert rc == d2.D2_OK and (st.cpu().numpy() == 0).all()
     cell, w = fl[0].cpu().numpy(), fl[1].cpu().numpy()
     got = dist.cpu().numpy()
@@ -121,8 +122,15 @@ def test_table_errors(d2):
     bad = synth._pack(np.diff(objs.off).astype(np.int64), objs.loc + np.float32(0.5), objs.w,
                       "f32", "f32")                # not integer symbol ids
     dist = torch.empty(objs.count, dtype=torch.float64, device="cuda:0")
+    # device outputs: the call returns without waiting, d2_sync reports
+    d2.d2_assign(ctx2, d2.bags_from_synth(bad, device="cuda:0"), lab, dist)
     with pytest.raises(d2.D2Error) as e:
-        d2.d2_assign(ctx2, d2.bags_from_synth(bad, device="cuda:0"), lab, dist)
+        d2.d2_sync(ctx2)
+    assert e.value.code == d2.D2_EINVAL
+    # host outputs: the call waits and reports it itself
+    with pytest.raises(d2.D2Error) as e:
+        d2.d2_assign(ctx2, d2.bags_from_synth(bad), np.empty(objs.count, np.int32),
+                     np.empty(objs.count))
     assert e.value.code == d2.D2_EINVAL
     ctx.close()
     ctx2.close()

@@ -416,10 +416,13 @@ def roofline_entry(kernel, pairs, seconds, ops_per_pair, mean_pivots, sms, mhz, 
 
 
 def measure_workload(name, d2, torch, dev, timer, sms, mhz, args, objs, cents, steps, warmup,
-                     desc, ctx_kw=None, cpu_full=False):
+                     desc, ctx_kw=None, cpu_full=False, e2e_warm=True):
     """One configuration at full size: the assignment step (d2_mallows_all,
     every pair certified, labels) plus the location update (a7) from the
-    assigned pairs; device-timed and end to end with host buffers."""
+    assigned pairs; device-timed (L2 flushed before each step) and end to
+    end with host buffers (e2e_warm: one untimed host step first; the
+    seconds-long steps skip it, their staging buffers' allocation being
+    negligible next to the step)."""
     ctx = d2.Context(dev.index, certify=CERTIFY_ALL, **(ctx_kw or {}))
     d2.d2_set_stream(ctx, timer.stream)
     cref = d2.bags_from_synth(cents, device=dev)
@@ -430,17 +433,36 @@ def measure_workload(name, d2, torch, dev, timer, sms, mhz, args, objs, cents, s
     lab = torch.empty(N, dtype=torch.int32, device=dev)
     dd = torch.empty(N, dtype=torch.float64, device=dev)
 
+    marks = []
+
     def step():
         d2.d2_mallows_all(ctx, ob, allg, lab, dd)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(timer.stream)  # the all-pairs call ends here (the dominant kernel's launches)
+        marks.append(ev)
         d2.d2_update_locations(ctx, ob, lab)
         d2.d2_set_centroids(ctx, cref)  # the next step starts from the same centroids
 
-    times = timer.run(step, steps, warmup)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    s0 = d2.d2_get_stats()
+    marks.clear()
+    times, ta_all = [], []
+    for _ in range(steps):
+        timer.flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(timer.stream)
+        step()
+        e1.record(timer.stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        ta_all.append(e0.elapsed_time(marks[-1]) / 1e3)
+    s1 = d2.d2_get_stats()
+    st = {k: (s1[k] - s0[k]) // steps for k in s0}
     t = statistics.median(times)
-    st = stats_delta(d2, step, lambda: torch.cuda.synchronize(dev))
-    # the all-pairs call alone (the dominant kernel's launch)
-    ta = statistics.median(timer.run(lambda: d2.d2_mallows_all(ctx, ob, allg, lab, dd),
-                                     max(1, min(steps, 3)), 0))
+    ta = statistics.median(ta_all)
     gpu_all = allg.cpu().numpy()
     # end to end through the C-ABI with pinned host buffers
     hb = d2.bags_from_synth(objs, pinned=True)
@@ -456,7 +478,8 @@ def measure_workload(name, d2, torch, dev, timer, sms, mhz, args, objs, cents, s
         d2.d2_get_centroids_into(ctx, h_loc)
         d2.d2_set_centroids(ctx, cref)
 
-    step_host()
+    if e2e_warm:
+        step_host()
     torch.cuda.synchronize(dev)
     e_steps = max(1, min(steps, 2))
     t0 = time.perf_counter()
@@ -623,16 +646,16 @@ def run_ours(args):
             "supports; all pairs + one location update", cpu_full=True)
         o3, c3 = synth.uneven()
         workloads["uneven"] = measure_workload(
-            "uneven", d2, torch, dev, timer, sms, mhz, args, o3, c3, 2, 2,
+            "uneven", d2, torch, dev, timer, sms, mhz, args, o3, c3, 2, 1,
             "uneven: N=1,000,000 bags, sizes P(m) ~ m^-2 on 2..64, d=16, FP32, Dirichlet(1); "
-            "K=256 of 32 supports; all pairs + one location update")
+            "K=256 of 32 supports; all pairs + one location update", e2e_warm=False)
         del o3, c3
         o4, c4 = synth.high_dim()
         workloads["high_dim"] = measure_workload(
             "high_dim", d2, torch, dev, timer, sms, mhz, args, o4, c4, 1, 1,
             "high_dim: N=100,000 bags of 16-64 supports, d=128 BF16 descriptors, Dirichlet(1); "
             "K=512 of 64 supports; tensor-core FP32 cost tiles for the screen; all pairs + one "
-            "location update")
+            "location update", e2e_warm=False)
         del o4, c4
 
     serve = None
@@ -763,6 +786,7 @@ def run_profile_case(args):
     build.build()
     d2.load()
     cert = CERTIFY_ALL if args.certify else 0
+    lanes = 32 if args.no_tune else 0  # a fixed launch shape: no autotuning launches
     if args.profile_workload == "image_level":
         # the benchmark step's level driver on profile_n bags (segments of
         # 5,000, 10 rounds): k_screen launches after the first are warm
@@ -809,13 +833,14 @@ def run_profile_case(args):
         return 0 if rc == 0 else 1
     if args.profile_workload == "high_dim":
         objs, cents = synth.high_dim(N=args.profile_n, K=512)
-        ctx = d2.Context(0, tile_budget_mib=1024, certify=cert)  # about 1 GB of tiles
+        # about 1 GB of tiles
+        ctx = d2.Context(0, tile_budget_mib=1024, certify=cert, group_lanes=lanes)
     elif args.profile_workload == "uneven":
         objs, cents = synth.uneven(N=args.profile_n, K=256)
-        ctx = d2.Context(0, certify=cert)
+        ctx = d2.Context(0, certify=cert, group_lanes=lanes)
     else:
         objs, cents = synth.image_like(N=args.profile_n, K=WORKLOAD["K"])
-        ctx = d2.Context(0, certify=cert)
+        ctx = d2.Context(0, certify=cert, group_lanes=lanes)
     d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
     ob = d2.bags_from_synth(objs, device="cuda:0")
     lab = torch.empty(objs.count, dtype=torch.int32, device="cuda:0")
@@ -843,6 +868,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="small case for ncu")
     ap.add_argument("--profile-n", type=int, default=20000)
     ap.add_argument("--certify", action="store_true", help="profile case: D2_CERTIFY_ALL")
+    ap.add_argument("--no-tune", action="store_true", help="profile case: no autotuning")
     ap.add_argument("--profile-workload", default="image_like",
                     choices=["image_like", "image_level", "high_dim", "uneven", "joint_weights"])
     args = ap.parse_args()

@@ -595,27 +595,21 @@ __host__ __device__ inline void centroid_blocks(const SolveCfg& cfg, long long c
   *NB = (K + kb - 1) / kb;
 }
 
-// FP32 cost tile of one pair from a chunk's precomputed tile rows (see
-// TileView): row a of the pair is row a of src, columns 0..n-1.  Returns
-// the tile maximum (group-uniform).
+// Largest cost of a pair's block of a chunk's tile (read in place).
 template <int G>
-__device__ __forceinline__ float load_tile(const Grp<G>& g, float* C, int m, int n,
-                                           const float* __restrict__ src, long long ldc) {
+__device__ __forceinline__ float tile_max(const Grp<G>& g, const float* __restrict__ src, int m,
+                                          int n, long long ldc) {
   const int mn = m * n;
   const int q = G / n, rem = G - (G / n) * n;
   int a = g.lane / n, r = g.lane - (g.lane / n) * n;
   float cmax = 0.f;
 #pragma unroll 4
   for (int t = g.lane; t < mn; t += G) {
-    const float v = __ldg(src + (long long)a * ldc + r);
-    C[t] = v;
-    cmax = fmaxf(cmax, v);
+    cmax = fmaxf(cmax, __ldg(src + (long long)a * ldc + r));
     r += rem; a += q;
     if (r >= n) { r -= n; ++a; }
   }
-  cmax = gmax<G>(g, cmax);
-  g.sync();
-  return cmax;
+  return gmax<G>(g, cmax);
 }
 
 // Bound on |C^ - C| for every cell of a tensor-core tile (C^ = the FP32
@@ -915,7 +909,7 @@ __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long 
       s.pot[y] = u;
       pmax = fmaxf(pmax, fabsf(u));
       dmax = fmaxf(dmax, fabsf(dl[k]));
-      if (y != S.root) s.cost[S.edge_idx(y, S.t.par[k])] = INFINITY;
+      if (y != S.root) S.cost[S.edge_idx(y, S.t.par[k])] = INFINITY;
     }
   }
   pmax = gmax<G>(g, pmax);
@@ -951,10 +945,12 @@ __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long 
   const bool colfix = S.sr == 0;
   const float vfix = s.pot[m + S.r0];
   int a = S.a0, r = S.r0;
+  int o = S.a0 * S.cs + S.r0;  // offset of cell (a, r) in the tile
+  const int ostep = S.sq * S.cs + S.sr, owrap = S.cs - n;
   for (int i = g.lane; i < mn; i += G) {
-    if (s.cost[i] - s.pot[a] - (colfix ? vfix : s.pot[m + r]) < thr) reprice(a, r);
-    r += S.sr; a += S.sq;
-    if (r >= n) { r -= n; ++a; }
+    if (S.cost[o] - s.pot[a] - (colfix ? vfix : s.pot[m + r]) < thr) reprice(a, r);
+    r += S.sr; a += S.sq; o += ostep;
+    if (r >= n) { r -= n; ++a; o += owrap; }
   }
   *nchk += cnt;
   return !gany<G>(g, fail);
@@ -968,7 +964,8 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
   extern __shared__ __align__(16) unsigned char smem[];
   Grp<G> g;
   unsigned char* base = smem + (threadIdx.x / G) * slice;
-  const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax, cv.d, 4);  // FP32 only
+  // FP32 only; with tensor-core tiles the solver reads them in place
+  const PairMem<float> s32 = carve<float>(base, cfg.mmax, cfg.nmax, cv.d, 4, !TC);
   int* cand = s32.sc;                                          // [kCandCap]
   float* clo = reinterpret_cast<float*>(s32.sc + kCandCap);    // [kCandCap]
   int n_scr = 0, p_scr = 0, n_cert = 0, n_chk = 0;
@@ -1016,16 +1013,18 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       // regardless: fewer live values across the solve)
       if (cold || NPL > 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
       float cmax;
-      if constexpr (TC)
-        cmax = load_tile<G>(g, s32.cost, m, n,
-                            cfg.tile.C + trow0 * cfg.tile.ldc + (c0 - cfg.tile.col0), cfg.tile.ldc);
-      else if (cv.A)
+      float* tile_g = nullptr;  // the pair's block of the chunk's tile (TC)
+      if constexpr (TC) {
+        tile_g = const_cast<float*>(cfg.tile.C) + trow0 * cfg.tile.ldc + (c0 - cfg.tile.col0);
+        cmax = tile_max<G>(g, tile_g, m, n, cfg.tile.ldc);
+      } else if (cv.A)
         cmax = build_cost_tab<float, G>(g, s32.cost, m, n, ob.loc, ob.ldt, o0, cv.loc32 + c0,
                                         cv.tab32, cv.A);
       else
         cmax = build_cost<float, G, (NPL <= 1 ? 8 : 32)>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
                                                          cv.loc32 + c0 * cv.d, cv.d);
       Simplex<float, G, NPL> S(s32, m, n, g);
+      if constexpr (TC) S.set_cost(tile_g, (int)cfg.tile.ldc);
       const long long wt = (i * (long long)K + j) * ws.ns;
       int st;
       if (!cold) {
@@ -1393,6 +1392,9 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
     int* merged = cand + 4;
     int* items = merged + ((ob.count * kMergedInts + 3) & ~3LL);  // merged is indexed by object
     // one screening launch over objects [t0, t0+cnt) of this launch
+    // with tensor-core tiles the screen reads them in place: no tile slice
+    const size_t slice_tc = pair_mem_bytes(cfg.mmax, cfg.nmax, cv.d, 4, false);
+    const int gpb_tc = groups_per_block(G, slice_tc, cfg.tpb);
     auto screen_part = [&](const SolveCfg& sc, long long cnt) -> cudaError_t {
       // items: (object, centroid block), the blocks chosen on the device
       // (centroid_blocks) from the launch's object count
@@ -1401,12 +1403,13 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
       const long long work = sc.dev_range ? (1LL << 40) : cnt * (long long)NB;
       cudaError_t e2 = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
       if (e2 != cudaSuccess) return e2;
+      const size_t sl = sc.tile.C ? slice_tc : slice32;
+      const int gp = sc.tile.C ? gpb_tc : gpb32;
       auto launch = [&](auto kern) -> cudaError_t {
         unsigned g2 = 1;
-        cudaError_t e3 = launch_cfg(kern, smem32, gpb32 * G, sc.sms, work, gpb32, &g2);
+        cudaError_t e3 = launch_cfg(kern, sl * gp, gp * G, sc.sms, work, gp, &g2);
         if (e3 != cudaSuccess) return e3;
-        kern<<<g2, gpb32 * G, smem32, st>>>(ob, cv, seg_size, K, sc, slice32, items, queue, ws,
-                                            d_err);
+        kern<<<g2, gp * G, sl * gp, st>>>(ob, cv, seg_size, K, sc, sl, items, queue, ws, d_err);
         return cudaSuccess;
       };
       if (sc.tile.C)
@@ -1422,6 +1425,7 @@ static cudaError_t assign_g(const ObjView& ob, const CentView& cv, long long seg
       return cudaGetLastError();
     };
     if (tw && tw->C && cfg.mmax <= 64) {
+      if (cfg.dev_range) return cudaErrorInvalidValue;  // chunks are cut on the host
       // tensor-core tiles, chunk by chunk within the tile buffer
       const long long per = std::max<long long>(1, tw->rows_cap / cfg.mmax);
       for (long long t0 = 0; t0 < nobj; t0 += per) {

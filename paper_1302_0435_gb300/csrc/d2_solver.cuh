@@ -121,14 +121,17 @@ struct PairMem {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline size_t pair_mem_bytes(int mmax, int nmax, int dmax = 256, int eb = 8) {
+// tile = false: no cost tile in shared memory (the solver reads a tile that
+// already sits in global memory, see Simplex::set_cost).
+__host__ __device__ inline size_t pair_mem_bytes(int mmax, int nmax, int dmax = 256, int eb = 8,
+                                                 bool tile = true) {
   const size_t N = (size_t)(mmax + nmax);
   const size_t mx = (size_t)(mmax > nmax ? mmax : nmax);
   size_t b = 0;
   b += align_up((size_t)mmax * 4, 16) * 2 + align_up((size_t)nmax * 4, 16) * 2;  // ranks
   b += align_up((size_t)mmax * 8, 16) + align_up((size_t)nmax * 8, 16);          // Pr Qr
   b += align_up((size_t)dmax * 4, 16) * 2 + align_up(mx * 4, 16);               // dir mu proj
-  b += align_up((size_t)mmax * nmax * eb, 16);  // cost
+  if (tile) b += align_up((size_t)mmax * nmax * eb, 16);  // cost
   b += align_up(N * eb, 16);                    // pot
   b += align_up(N * 4, 16) * 2;                // pos sz
   b += align_up(N * 4, 16) * 3;                // ppos psz pnode
@@ -144,7 +147,7 @@ __host__ __device__ inline size_t pair_mem_bytes(int mmax, int nmax, int dmax = 
 
 template <typename T>
 __device__ inline PairMem<T> carve(unsigned char* base, int mmax, int nmax, int dmax = 256,
-                                   int eb = 8) {
+                                   int eb = 8, bool tile = true) {
   const size_t N = (size_t)(mmax + nmax);
   const size_t mx = (size_t)(mmax > nmax ? mmax : nmax);
   PairMem<T> s;
@@ -158,7 +161,8 @@ __device__ inline PairMem<T> carve(unsigned char* base, int mmax, int nmax, int 
   s.dir = reinterpret_cast<float*>(p); p += align_up((size_t)dmax * 4, 16);
   s.mu = reinterpret_cast<float*>(p); p += align_up((size_t)dmax * 4, 16);
   s.proj = reinterpret_cast<float*>(p); p += align_up(mx * 4, 16);
-  s.cost = reinterpret_cast<T*>(p); p += align_up((size_t)mmax * nmax * eb, 16);
+  s.cost = nullptr;
+  if (tile) { s.cost = reinterpret_cast<T*>(p); p += align_up((size_t)mmax * nmax * eb, 16); }
   s.pot = reinterpret_cast<T*>(p); p += align_up(N * eb, 16);
   s.pos = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
   s.sz = reinterpret_cast<int*>(p); p += align_up(N * 4, 16);
@@ -272,27 +276,41 @@ struct Simplex {
   // cell stepping of this lane: cells i = lane, lane+G, ... are (a, r) with
   // a += sq, r += sr per step (wrapping r at n)
   int a0, r0, sq, sr;
-  int cand = -1;     // this lane's candidate cell from the last full pricing
+  // the cost tile: cell (a, r) at cost[a * cs + r] -- the shared-memory tile
+  // (cs = n) or a tile row block in global memory (set_cost)
+  T* cost;
+  int cs;
+  bool own_tile = true;
+  int cand = -1;     // this lane's candidate cell (offset a * cs + r) from the last full pricing
   int cand_a = 0, cand_r = 0;
   int root = 0;      // the tree root: the node at preorder position 0
 
   __device__ __forceinline__ Simplex(const PairMem<T>& s_, int m_, int n_, const Grp<G>& g_)
-      : s(s_), m(m_), n(n_), N(m_ + n_), g(g_) {
+      : s(s_), m(m_), n(n_), N(m_ + n_), g(g_), cost(s_.cost), cs(n_) {
     set_dims(m_, n_);
   }
   __device__ __forceinline__ void set_dims(int m_, int n_) {
     m = m_; n = n_; N = m_ + n_;
     a0 = g.lane / n; r0 = g.lane - a0 * n;
     sq = G / n; sr = G - sq * n;
+    if (own_tile) cs = n;
     cand = -1;
   }
+  // Price from a tile in global memory: cell (a, r) at c[a * stride + r].
+  __device__ __forceinline__ void set_cost(T* c, int stride) {
+    cost = c;
+    cs = stride;
+    own_tile = false;
+    cand = -1;
+  }
+  __device__ __forceinline__ T cost_at(int a, int r) const { return cost[a * cs + r]; }
 
   __device__ __forceinline__ int node_of(int k) const { return g.lane + G * k; }
   // cell key of an edge: (row << 8) | col -- orders cells like row*n+col
   __device__ __forceinline__ static int key_rc(int a, int r) { return (a << 8) | r; }
-  // tile index of the edge (y, p)
+  // tile offset of the edge (y, p)
   __device__ __forceinline__ int edge_idx(int y, int p) const {
-    return y < m ? y * n + (p - m) : p * n + (y - m);
+    return y < m ? y * cs + (p - m) : p * cs + (y - m);
   }
   __device__ __forceinline__ int edge_key(int y, int p) const {
     return y < m ? key_rc(y, p - m) : key_rc(p, y - m);
@@ -307,7 +325,7 @@ struct Simplex {
     i1 = i2 = -1;
     for (unsigned long long b = ra; b; b &= b - 1) {
       const int a = __ffsll((long long)b) - 1;
-      const T c = s.cost[a * n + r];
+      const T c = cost_at(a, r);
       if (c < v1) { v2 = v1; i2 = i1; v1 = c; i1 = a; }
       else if (c < v2) { v2 = c; i2 = a; }
     }
@@ -322,7 +340,7 @@ struct Simplex {
     for (int h = 0; h < 2; ++h) {
       const int r = g.lane + 32 * h;
       if (r < n && ((ca >> r) & 1ull)) {
-        const T c = s.cost[a * n + r];
+        const T c = cost_at(a, r);
         if (c < b1) { b2 = b1; j2 = j1; b1 = c; j1 = r; }
         else if (c < b2) { b2 = c; j2 = r; }
       }
@@ -674,7 +692,7 @@ struct Simplex {
       if (y < N && y != root) {
         const int p = t.par[0];
         if (p < 0 || p >= N || (y < m) == (p < m)) { lbad = true; code = root; }
-        else { code = p | (1 << 16); acc = s.cost[edge_idx(y, p)]; }
+        else { code = p | (1 << 16); acc = cost[edge_idx(y, p)]; }
       }
       if (gany<G>(g, lbad)) bad = true;
       for (int round = 0;; ++round) {
@@ -705,7 +723,7 @@ struct Simplex {
       else if (y < N) {
         const int p = t.par[k];
         if (p < 0 || p >= N || (y < m) == (p < m)) { lbad = true; pa[y] = root; aa[y] = T(0); }
-        else { pa[y] = p | (1 << 16); aa[y] = s.cost[edge_idx(y, p)]; }
+        else { pa[y] = p | (1 << 16); aa[y] = cost[edge_idx(y, p)]; }
       }
     }
     if (gany<G>(g, lbad)) bad = true;
@@ -784,11 +802,12 @@ struct Simplex {
       const T vr = s.pot[m + r0];
       best = T(0);
       int bi = -1, ba = 0;
-      for (int a = a0, i = g.lane; a < m; a += sq, i += G) {
-        const T d = s.cost[i] - s.pot[a] - vr;
+      const int step = sq * cs;
+      for (int a = a0, o = a0 * cs + r0; a < m; a += sq, o += step) {
+        const T d = cost[o] - s.pot[a] - vr;
         const bool better = d < best;
         best = better ? d : best;
-        bi = better ? i : bi;
+        bi = better ? o : bi;
         ba = better ? a : ba;
       }
       cell = bi >= 0 ? key_rc(ba, r0) : INT_MAX;
@@ -799,22 +818,25 @@ struct Simplex {
     }
     const int mn = m * n;
     int a = a0, r = r0;
+    int o = a0 * cs + r0;  // offset of cell (a, r)
+    const int ostep = sq * cs + sr, owrap = cs - n;
     best = T(0);
     cell = INT_MAX;
     int bi = -1, ba = 0, br = 0;
     const T* pv = s.pot + m;
     for (int i = g.lane; i < mn; i += G) {
-      const T d = s.cost[i] - s.pot[a] - pv[r];
+      const T d = cost[o] - s.pot[a] - pv[r];
       const bool better = d < best;
       best = better ? d : best;
       cell = better ? key_rc(a, r) : cell;
-      bi = better ? i : bi;
+      bi = better ? o : bi;
       ba = better ? a : ba;
       br = better ? r : br;
-      r += sr; a += sq;
+      r += sr; a += sq; o += ostep;
       const bool wrap = r >= n;
       r = wrap ? r - n : r;
       a = wrap ? a + 1 : a;
+      o = wrap ? o + owrap : o;
     }
     cand = bi;
     cand_a = ba;
@@ -829,7 +851,7 @@ struct Simplex {
     int cell = INT_MAX;
     const T* pv = s.pot + m;
     for (int i = g.lane; i < mn && cell == INT_MAX; i += G) {
-      const T d = s.cost[i] - s.pot[a] - pv[r];
+      const T d = cost_at(a, r) - s.pot[a] - pv[r];
       if (d < -tol) { best = d; cell = key_rc(a, r); }
       r += sr; a += sq;
       if (r >= n) { r -= n; ++a; }
@@ -861,7 +883,7 @@ struct Simplex {
       return (best < -tol && cell != INT_MAX) ? cell : -1;
     }
     if (cand >= 0) {
-      best = s.cost[cand] - s.pot[cand_a] - s.pot[m + cand_r];
+      best = cost[cand] - s.pot[cand_a] - s.pot[m + cand_r];
       cell = key_rc(cand_a, cand_r);
     }
     if (!(best < -tol)) { best = T(0); cell = INT_MAX; }
@@ -1121,7 +1143,7 @@ struct Simplex {
     for (int k = 0; k < NPL; ++k) {
       const int y = node_of(k);
       if (y < N && y != root)
-        acc += ((A)t.flow[k] * (A)kInvMass) * (A)s.cost[edge_idx(y, t.par[k])];
+        acc += ((A)t.flow[k] * (A)kInvMass) * (A)cost[edge_idx(y, t.par[k])];
     }
     return gsum<G>(g, acc);
   }

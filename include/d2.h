@@ -170,7 +170,12 @@ typedef struct {
     double joint_tol;           /* D2_UPDATE_ALG1: relative gap of the weight LP; 0 = 1e-9 */
     int32_t certify;            /* D2_CERTIFY_* : d2_assign and d2_cluster_level;
                                    0 = CANDIDATES */
-    int32_t reserved;
+    int32_t tc_wait_probe;      /* diagnostic, 0 = off: > 0 makes the tensor-core kernel's
+                                   first completion wait poll a barrier nothing arrives on
+                                   (at most this many non-blocking polls), so it runs out
+                                   and the call reports D2_ETIMEOUT after the kernel has
+                                   waited for its issued MMAs and freed its tensor memory;
+                                   tests of the timeout path use it */
 } d2_config;
 
 /*

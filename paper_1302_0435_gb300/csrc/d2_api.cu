@@ -615,6 +615,7 @@ int tc_work(d2_ctx* c, long long rows, int mmax, d2k::TcWork* w) {
   w->nx = static_cast<float*>(grow(c, kTcNx, (size_t)cap * 4, &rc));
   if (rc != D2_OK) return rc;
   w->rows_cap = cap;
+  w->probe_polls = c->cfg.tc_wait_probe;
   return D2_OK;
 }
 

@@ -99,6 +99,9 @@ struct TcWork {
   long long* rowsrc = nullptr;  // [rows_cap]
   float* nx = nullptr;          // [rows_cap]
   long long rows_cap = 0;       // tile rows the buffers hold (C: rows_cap*ncols floats)
+  // diagnostic: > 0 makes the contraction's first completion wait poll a
+  // barrier nothing arrives on, at most this many times (timeout path tests)
+  long long probe_polls = 0;
 };
 
 // Launch-wide solver settings.

@@ -78,6 +78,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 
+// Non-blocking polls of a barrier, at most `polls` of them.
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity, long long polls) {
+  uint32_t done = 0;
+  for (long long it = 0; it < polls && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
@@ -95,9 +109,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     k_cost_tc(const __nv_bfloat16* __restrict__ X, const long long* __restrict__ rowsrc,
               const float* __restrict__ nx, const long long* __restrict__ total_p,
               const __nv_bfloat16* __restrict__ Y, const float* __restrict__ yn, int d,
-              long long ldc, int ct0, float* __restrict__ C, int* err) {
+              long long ldc, int ct0, float* __restrict__ C, int* err, long long probe_polls) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) unsigned long long mbar;
+  // diagnostic (probe_polls > 0): the first completion wait polls this
+  // barrier instead, which nothing ever arrives on, so it runs out and the
+  // kernel takes its timeout path with MMAs really in flight
+  __shared__ __align__(8) unsigned long long mbar_probe;
   __shared__ uint32_t tmem_slot;
   unsigned char* sA = sm;                                                   // 128 x d BF16
   unsigned char* sB = sm + (size_t)kTcBM * d * 2;                          // 256 x d BF16
@@ -124,6 +142,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar_probe)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -169,7 +188,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           : "memory");
     }
     issued = true;
-    const bool ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
+    const bool got = probe_polls > 0 ? mbar_test(smem_u32(&mbar_probe), 0u, probe_polls)
+                                     : mbar_wait(bar, phase);
+    const bool ok = __syncthreads_and(got ? 1 : 0) != 0;
     if (!ok) {
       if (tid == 0) atomicOr(err, kErrTimeout);
       alive = false;
@@ -356,6 +377,7 @@ cudaError_t tc_prep_centroids(const double* loc64, const long long* off, long lo
 
 cudaError_t tc_chunk(const ObjView& ob, const TcWork& w, const int* oidx, long long obase,
                      long long cnt, int mmax, int ct0, int nct, int* d_err, cudaStream_t st) {
+  if (w.probe_polls < 0) return cudaErrorInvalidValue;
   if (cnt <= 0) return cudaSuccess;
   if (ob.ldt != 2 || !tc_dim_ok(ob.d) || mmax < 1 || mmax > 64) return cudaErrorInvalidValue;
   const int d = ob.d;
@@ -377,7 +399,7 @@ cudaError_t tc_chunk(const ObjView& ob, const TcWork& w, const int* oidx, long l
   dim3 grid((unsigned)nct, (unsigned)gy);
   k_cost_tc<<<grid, kTcThreads, smem, st>>>(X, w.rowsrc, w.nx, w.trow + cnt,
                                             static_cast<const __nv_bfloat16*>(w.cents.yb),
-                                            w.cents.yn, d, ncols, ct0, w.C, d_err);
+                                            w.cents.yn, d, ncols, ct0, w.C, d_err, w.probe_polls);
   note_launches(3);
   return cudaGetLastError();
 }

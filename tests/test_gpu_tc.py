@@ -176,3 +176,33 @@ def test_tc_assign_after_update_uses_new_centroids(d2, oracle_mod):
     assert not np.array_equal(_bf16(moved.loc), moved.loc)  # not BF16-exact any more
     _check_vs(oracle_mod, objs, moved, lab.cpu().numpy(), dist.cpu().numpy(),
               np.arange(objs.count))
+
+
+def test_tc_completion_wait_runs_out_and_is_reported(d2, oracle_mod):
+    """The contraction's bounded wait on its MMA-completion barrier: the
+    diagnostic probe makes the first wait poll a barrier that nothing
+    arrives on, so it runs out with MMAs in flight.  The kernel must then
+    raise the timeout (D2_ETIMEOUT), wait (bounded) for its issued MMAs, free
+    its tensor memory and return; the context and the GPU stay usable."""
+    objs, cents = synth.high_dim(N=6, K=4, seed=131)
+    ob = d2.bags_from_synth(objs, device="cuda:0")
+    m = int(objs.off[1] - objs.off[0])
+    n = int(cents.off[1] - cents.off[0])
+    ctx = d2.Context(0, tc_wait_probe=256)
+    d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
+    for _ in range(2):  # twice: the first expiry left nothing behind
+        with pytest.raises(d2.D2Error) as e:
+            d2.d2_cost_matrix(ctx, ob, 0, 0, d2.D2_PREC_TC, m, n)
+        assert e.value.code == d2.D2_ETIMEOUT
+    # the same context still computes: FP64 tile against the oracle's cost
+    x, _ = oracle_mod.bag(objs, 0)
+    y, _ = oracle_mod.bag(cents, 0)
+    c64 = d2.d2_cost_matrix(ctx, ob, 0, 0, d2.D2_PREC_FP64, m, n)
+    assert np.allclose(c64, oracle_mod.cost(x, y), rtol=1e-12, atol=1e-12)
+    ctx.close()
+    # and a context without the probe gets its tensor-core tile within the bound
+    ctx2 = d2.Context(0)
+    d2.d2_set_centroids(ctx2, d2.bags_from_synth(cents, device="cuda:0"))
+    ctc = d2.d2_cost_matrix(ctx2, ob, 0, 0, d2.D2_PREC_TC, m, n)
+    assert np.abs(ctc - oracle_mod.cost(x, y)).max() <= tc_bound(x, y)
+    ctx2.close()

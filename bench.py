@@ -416,7 +416,7 @@ def roofline_entry(kernel, pairs, seconds, ops_per_pair, mean_pivots, sms, mhz, 
 
 
 def measure_workload(name, d2, torch, dev, timer, sms, mhz, args, objs, cents, steps, warmup,
-                     desc, ctx_kw=None, cpu_full=False, e2e_warm=True):
+                     desc, ctx_kw=None, cpu_full=False, e2e_warm=True, graph=False):
     """One configuration at full size: the assignment step (d2_mallows_all,
     every pair certified, labels) plus the location update (a7) from the
     assigned pairs; device-timed (L2 flushed before each step) and end to
@@ -446,6 +446,21 @@ def measure_workload(name, d2, torch, dev, timer, sms, mhz, args, objs, cents, s
     for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
+    run = step
+    if graph:
+        # the pairs at the initial centroids, for the error statement
+        gpu_all = allg.cpu().numpy()
+        # once the bins' launch shapes are tuned, one assignment step (the
+        # certified all-pairs call, then the update) only enqueues kernels:
+        # capture it into a CUDA graph and time its replays (each replay is a
+        # clustering iteration from the centroids the previous one left)
+        cgraph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cgraph, stream=timer.stream, capture_error_mode="relaxed"):
+            d2.d2_mallows_all(ctx, ob, allg, lab, dd)
+            d2.d2_update_locations(ctx, ob, lab)
+        run = cgraph.replay
+        cgraph.replay()  # untimed first replay
+        torch.cuda.synchronize(dev)
     s0 = d2.d2_get_stats()
     marks.clear()
     times, ta_all = [], []
@@ -454,16 +469,18 @@ def measure_workload(name, d2, torch, dev, timer, sms, mhz, args, objs, cents, s
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(timer.stream)
-        step()
+        run()
         e1.record(timer.stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
-        ta_all.append(e0.elapsed_time(marks[-1]) / 1e3)
+        ta_all.append(e0.elapsed_time(marks[-1]) / 1e3 if marks else times[-1])
     s1 = d2.d2_get_stats()
     st = {k: (s1[k] - s0[k]) // steps for k in s0}
     t = statistics.median(times)
     ta = statistics.median(ta_all)
-    gpu_all = allg.cpu().numpy()
+    if not graph:
+        gpu_all = allg.cpu().numpy()
+    d2.d2_set_centroids(ctx, cref)
     # end to end through the C-ABI with pinned host buffers
     hb = d2.bags_from_synth(objs, pinned=True)
     h_all = torch.empty((N, K), dtype=torch.float64).pin_memory()
@@ -498,14 +515,16 @@ def measure_workload(name, d2, torch, dev, timer, sms, mhz, args, objs, cents, s
            "pairs_solved_fp64": st["pairs_exact"],
            "e2e": {"value": pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(bi),
                    "d2h_bytes_per_step": int(bo)},
-           "all_pairs_call_ms": 1e3 * ta}
+           "all_pairs_call_ms" if not graph else "step_ms_graph_replay": 1e3 * ta,
+           "cuda_graph": bool(graph)}
     if not args.skip_cpu:
         cpu, sample = cpu_baseline(objs, cents, seconds=args.cpu_seconds, full=cpu_full)
         out["cpu_baseline"] = cpu
         out["error_vs_oracle"] = error_vs_oracle(gpu_all, sample)
-        out["roofline"] = roofline_entry("k_screen (certify) + k_merge + k_exact: cold d2_mallows_all",
-                                         pairs, ta, cpu["ops_per_pair"], cpu["mean_pivots"], sms, mhz,
-                                         profiled_traffic(name))
+        kname = ("k_screen (certify) + k_merge + k_exact: cold d2_mallows_all" if not graph else
+                 "k_screen (certify) + k_merge + k_exact + update: the graph-replayed step")
+        out["roofline"] = roofline_entry(kname, pairs, ta, cpu["ops_per_pair"], cpu["mean_pivots"],
+                                         sms, mhz, profiled_traffic(name))
     return out
 
 
@@ -648,7 +667,8 @@ def run_ours(args):
         workloads["uneven"] = measure_workload(
             "uneven", d2, torch, dev, timer, sms, mhz, args, o3, c3, 2, 1,
             "uneven: N=1,000,000 bags, sizes P(m) ~ m^-2 on 2..64, d=16, FP32, Dirichlet(1); "
-            "K=256 of 32 supports; all pairs + one location update", e2e_warm=False)
+            "K=256 of 32 supports; all pairs + one location update, replayed from a CUDA graph "
+            "(autotuned tree-size bins, device-side bin ranges)", e2e_warm=False, graph=True)
         del o3, c3
         o4, c4 = synth.high_dim()
         workloads["high_dim"] = measure_workload(
@@ -694,6 +714,8 @@ def serve_measure(dev, n_requests=150, lam_fracs=(0.8,), n_sat=24, seed=1005):
     from paper_1302_0435_gb300 import d2, synth
     cents, means = synth.serving_centroids(K=1024, seed=seed)
     ctx = d2.Context(dev.index)
+    # the caller's stream: the device inputs below are written there
+    d2.d2_set_stream(ctx, torch.cuda.current_stream(dev))
     d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device=dev))
     rng = np.random.default_rng(seed + 1)
     K = cents.count

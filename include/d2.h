@@ -196,8 +196,12 @@ typedef struct {
 typedef struct d2_ctx d2_ctx;
 
 /* Create a context on CUDA device `device`.  cfg may be NULL (defaults).
- * Creates its own non-blocking stream.  Returns D2_ECUDA if the device
- * cannot be used (no GPU, or the library was not built for it). */
+ * Creates its own stream, a blocking one: it is ordered with the legacy
+ * default stream, so device inputs written there (for instance by a
+ * framework's default stream) are complete before the context's kernels
+ * read them.  Work on other streams must be ordered by the caller (events,
+ * or d2_set_stream).  Returns D2_ECUDA if the device cannot be used (no
+ * GPU, or the library was not built for it). */
 int d2_ctx_create(d2_ctx** out, int32_t device, const d2_config* cfg);
 /* Destroy a context and free everything it owns (not caller buffers). */
 int d2_ctx_destroy(d2_ctx* ctx);

@@ -879,7 +879,7 @@ int d2_ctx_create(d2_ctx** out, int32_t device, const d2_config* cfg) {
   c->device = device;
   if (cfg) c->cfg = *cfg;
   if (cudaSetDevice(device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->own, cudaStreamDefault) != cudaSuccess ||
       cudaMalloc(&c->d_err, 4 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->d_info, 4 * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&c->h_pin, 8 * sizeof(int)) != cudaSuccess) {

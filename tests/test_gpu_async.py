@@ -38,6 +38,7 @@ def test_device_calls_return_before_their_kernels(d2):
     stream = torch.cuda.Stream()  # the context's stream, so that the event follows its work
     ctx = _ctx(d2, torch, cents, stream=stream)
     ob = d2.bags_from_synth(objs, device="cuda:0")
+    torch.cuda.synchronize()  # inputs written on the default stream, read on `stream`
     assert ob.s.max_support == 16
     lab = torch.empty(objs.count, dtype=torch.int32, device="cuda:0")
     dist = torch.empty(objs.count, dtype=torch.float64, device="cuda:0")
@@ -138,3 +139,40 @@ def test_binned_assign_without_host_counts_matches(d2):
     # the tuned shape may pick another cold start: same optima
     assert np.array_equal(out[0][0], out[1][0])
     assert np.allclose(out[0][1], out[1][1], rtol=1e-12, atol=0)
+
+
+def test_all_pairs_step_replays_from_a_cuda_graph(d2):
+    """Once its launch shapes are tuned, the certified all-pairs call and
+    the location update only enqueue kernels, so a caller can capture them
+    into a CUDA graph: bins, screen, merge, exact pass and update replay
+    with the eager results."""
+    import torch
+    objs, cents = synth.uneven(N=40000, K=64, seed=906)
+    stream = torch.cuda.Stream()
+    ctx = _ctx(d2, torch, cents, stream=stream, certify=d2.D2_CERTIFY_ALL)
+    ob = d2.bags_from_synth(objs, device="cuda:0")
+    torch.cuda.synchronize()  # inputs written on the default stream, read on `stream`
+    N, K = objs.count, cents.count
+    allg = torch.empty((N, K), dtype=torch.float64, device="cuda:0")
+    lab = torch.empty(N, dtype=torch.int32, device="cuda:0")
+    dd = torch.empty(N, dtype=torch.float64, device="cuda:0")
+    d2.d2_mallows_all(ctx, ob, allg, lab, dd)  # tunes the bins' launch shapes
+    d2.d2_update_locations(ctx, ob, lab)
+    d2.d2_sync(ctx)
+    d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
+    d2.d2_mallows_all(ctx, ob, allg, lab, dd)  # eager reference at the initial centroids
+    d2.d2_sync(ctx)
+    ref = (allg.clone(), lab.clone(), dd.clone())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
+        d2.d2_mallows_all(ctx, ob, allg, lab, dd)
+    d2.d2_sync(ctx)
+    allg.zero_()
+    lab.fill_(-1)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        g.replay()
+    stream.synchronize()
+    d2.d2_sync(ctx)
+    assert torch.equal(allg, ref[0]) and torch.equal(lab, ref[1]) and torch.equal(dd, ref[2])
+    ctx.close()

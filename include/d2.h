@@ -176,6 +176,14 @@ typedef struct {
                                    and the call reports D2_ETIMEOUT after the kernel has
                                    waited for its issued MMAs and freed its tensor memory;
                                    tests of the timeout path use it */
+    int32_t no_prune;           /* 0: d2_assign, d2_cluster_level and serving (without
+                                   D2_CERTIFY_ALL) skip the pairs that cannot be an
+                                   object's argmin: D^2 >= ||mean_P - mean_Q||^2 (Jensen),
+                                   and the product plan bounds D^2 from above by that plus
+                                   both bags' spreads, so a centroid whose lower bound
+                                   exceeds the object's best upper bound is never solved
+                                   (labels and distances unchanged); 1: every pair solved */
+    int32_t reserved;
 } d2_config;
 
 /*

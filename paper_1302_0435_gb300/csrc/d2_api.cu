@@ -45,6 +45,8 @@ enum Slot {
   kPairTree,
   // d2_mallows_all
   kAllLab, kAllD2, kAllPair,
+  // pruning of pairs that cannot be the argmin
+  kPrMuO, kPrVarO, kPrMuC, kPrVarC, kPrKeep,
   kSlots
 };
 
@@ -464,6 +466,23 @@ int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, i
   SolveCfg base = solve_cfg(c, mode, mmax);
   if (certify_all && mode == 1) base.certify = true;
   base.pair64 = pair64;
+  if (base.mode == 1 && !base.certify && !pair64 && cv.A == 0 && !c->cfg.no_prune) {
+    // pairs whose lower bound is above their object's upper bound cannot be
+    // the argmin: bounds from the bags' means and spreads, keep bits per object
+    int rc = D2_OK;
+    const int kw = (K + 31) / 32;
+    double* mu_o = static_cast<double*>(grow(c, kPrMuO, (size_t)v.count * v.d * 8, &rc));
+    double* var_o = static_cast<double*>(grow(c, kPrVarO, (size_t)v.count * 8, &rc));
+    double* mu_c = static_cast<double*>(grow(c, kPrMuC, (size_t)cv.K * cv.d * 8, &rc));
+    double* var_c = static_cast<double*>(grow(c, kPrVarC, (size_t)cv.K * 8, &rc));
+    unsigned* keep = static_cast<unsigned*>(grow(c, kPrKeep, (size_t)v.count * kw * 4, &rc));
+    if (rc != D2_OK) return rc;
+    CK(d2k::bag_moments(v, mu_o, var_o, c->stream));
+    CK(d2k::cent_moments(cv, mu_c, var_c, c->stream));
+    CK(d2k::prune_keep(v, seg, K, cv.K, v.d, mu_o, var_o, mu_c, var_c, keep, kw, c->stream));
+    base.keep = keep;
+    base.keep_words = kw;
+  }
   if (!bins.binned) {
     CK(d2k::assign(v, cv, seg, K, base, om, lab, d2o, terms, fo, cand, c->d_err, c->stream, ws, tw));
     return D2_OK;
@@ -834,6 +853,7 @@ bool want_bins(const d2_ctx* c, long long count, int mmax) {
 }  // namespace
 
 namespace d2k {
+bool ctx_prune(const d2_ctx* c) { return c->cfg.no_prune == 0; }
 CentView ctx_centroids(const d2_ctx* c, int* nmax, int* d, int* device, int* mode, int* budget,
                        int* sms, long long* K, int* start) {
   *nmax = c->nmax;

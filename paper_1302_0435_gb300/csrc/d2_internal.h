@@ -132,6 +132,12 @@ struct SolveCfg {
   // D^2 of every pair, pair64[i*K + j] (j local to the object's segment).
   bool certify = false;
   double* pair64 = nullptr;
+  // pairs that cannot be the argmin are skipped (see prune_keep): bit j of
+  // keep[i*keep_words + j/32] set = centroid j (local to the object's
+  // segment) kept for object i.  Null: every pair is solved.  Only for
+  // screens that pick argmin candidates (not certify, not pair_out).
+  const unsigned* keep = nullptr;
+  int keep_words = 0;
   TileView tile;              // precomputed FP32 tiles of the screen (optional)
   // mallows_pairs with mode 1: room (pair_tree_bytes) for the FP32 bases
   // handed from the FP32 launch to the FP64 launch; null: one fused launch
@@ -186,6 +192,24 @@ D2_NPL_DECL(2)
 D2_NPL_DECL(3)
 D2_NPL_DECL(4)
 #undef D2_NPL_DECL
+
+// ---- pairs that cannot be the argmin (Alg. 2 Step 2 needs only it) ----
+// Under a pair's own marginals (the quantised masses the solver uses), for
+// every transport plan: D^2(P, Q) >= ||mu_P - mu_Q||^2 (Jensen, the plan's
+// masses summing to one), and the product plan p_a q_r costs
+// ||mu_P - mu_Q||^2 + var_P + var_Q (var: the mass-weighted squared spread
+// about the mean), an upper bound of D^2.  So centroid j cannot be object
+// i's argmin when ||mu_i - mu_j||^2 > UB_i = var_i + min_j' (||mu_i -
+// mu_j'||^2 + var_j').  All in FP64, compared with 2^-40 relative margins.
+// Means [count][d] and spreads [count] of a batch (FP64; NaN for a bag the
+// solver rejects, which keeps all its pairs).
+cudaError_t bag_moments(const ObjView& ob, double* mu, double* var, cudaStream_t st);
+// The same for the centroids of a set (masses from Qpre, locations loc64).
+cudaError_t cent_moments(const CentView& cv, double* mu, double* var, cudaStream_t st);
+// Keep bits of every object: kw = ceil(K / 32) words per object.
+cudaError_t prune_keep(const ObjView& ob, long long seg_size, int K, long long KT, int d,
+                       const double* mu_o, const double* var_o, const double* mu_c,
+                       const double* var_c, unsigned* keep, int kw, cudaStream_t st);
 
 // Raise kErrInvalid into d_err unless every location of the T supports is
 // an integer symbol id in [0, A) (d = 1).

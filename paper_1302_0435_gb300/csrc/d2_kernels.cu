@@ -124,6 +124,111 @@ __global__ void k_check_bag_symbols(const void* loc, int ldt, const long long* o
   }
 }
 
+// Mean and spread of one bag from its masses (inclusive int64 prefix, units
+// of 2^-62) in FP64: lanes over coordinates for the mean, over supports for
+// the spread.
+template <typename GetX>
+__device__ __forceinline__ void bag_mean_var(const Grp<32>& g, const long long* pre, int m, int d,
+                                             GetX x, double* mu, double* var) {
+  for (int k = g.lane; k < d; k += 32) {
+    double acc = 0.0;
+    for (int a = 0; a < m; ++a) {
+      const double w = (double)(pre[a] - (a > 0 ? pre[a - 1] : 0LL)) * kInvMass;
+      acc = fma(w, x(a, k), acc);
+    }
+    mu[k] = acc;
+  }
+  __syncwarp();
+  double v = 0.0;
+  for (int a = g.lane; a < m; a += 32) {
+    const double w = (double)(pre[a] - (a > 0 ? pre[a - 1] : 0LL)) * kInvMass;
+    double s2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const double df = x(a, k) - mu[k];
+      s2 = fma(df, df, s2);
+    }
+    v = fma(w, s2, v);
+  }
+  v = gsum<32>(g, v);
+  if (g.lane == 0) *var = v;
+}
+
+// One warp per object: the masses the solver will use (load_prefix), then
+// the mean and spread.
+__global__ void k_bag_moments(ObjView ob, double* mu, double* var) {
+  __shared__ long long pre[4][64];
+  Grp<32> g;
+  const int wb = threadIdx.x >> 5;
+  for (long long i = (long long)blockIdx.x * 4 + wb; i < ob.count; i += (long long)gridDim.x * 4) {
+    const long long o0 = ob.off[i];
+    const int m = (int)(ob.off[i + 1] - o0);
+    const int d = ob.d;
+    bool ok = m >= 1 && m <= 64;
+    if (ok) ok = ob.wdt == 0 ? load_prefix<32>(g, static_cast<const double*>(ob.w) + o0, m, pre[wb])
+                             : load_prefix<32>(g, static_cast<const float*>(ob.w) + o0, m, pre[wb]);
+    if (!ok) {
+      if (g.lane == 0) var[i] = NAN;
+      continue;
+    }
+    const void* loc = ob.loc;
+    const int ldt = ob.ldt;
+    bag_mean_var(g, pre[wb], m, d,
+                 [&](int a, int k) { return ldx<double>(loc, ldt, (o0 + a) * d + k); },
+                 mu + i * d, var + i);
+    __syncwarp();
+  }
+}
+
+__global__ void k_cent_moments(CentView cv, double* mu, double* var) {
+  Grp<32> g;
+  const int wb = threadIdx.x >> 5;
+  for (long long j = (long long)blockIdx.x * 4 + wb; j < cv.K; j += (long long)gridDim.x * 4) {
+    const long long c0 = cv.off[j];
+    const int n = (int)(cv.off[j + 1] - c0);
+    const int d = cv.d;
+    const double* y = cv.loc64 + c0 * d;
+    bag_mean_var(g, cv.Qpre + c0, n, d, [&](int r, int k) { return y[r * d + k]; }, mu + j * d,
+                 var + j);
+    __syncwarp();
+  }
+}
+
+// One warp per object: UB over its segment's K centroids, then the keep bits.
+__global__ void k_prune_keep(ObjView ob, long long seg_size, int K, long long KT, int d,
+                             const double* mu_o, const double* var_o, const double* mu_c,
+                             const double* var_c, unsigned* keep, int kw) {
+  Grp<32> g;
+  const int wb = threadIdx.x >> 5;
+  for (long long i = (long long)blockIdx.x * 4 + wb; i < ob.count; i += (long long)gridDim.x * 4) {
+    const long long cb = seg_of(ob, i, seg_size) * (long long)K;
+    const double vi = var_o[i];
+    const double* xi = mu_o + i * d;
+    const bool valid = !isnan(vi) && cb + K <= KT;
+    auto lb = [&](int j) {
+      const double* yj = mu_c + (cb + j) * d;
+      double s2 = 0.0;
+      for (int k = 0; k < d; ++k) {
+        const double df = xi[k] - yj[k];
+        s2 = fma(df, df, s2);
+      }
+      return s2;
+    };
+    double best = INFINITY;
+    if (valid)
+      for (int j = g.lane; j < K; j += 32) best = fmin(best, lb(j) + var_c[cb + j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+    const double ub = (vi + best) * (1.0 + 0x1p-40);
+    for (int w = 0; w < kw; ++w) {
+      const int j = w * 32 + g.lane;
+      // keep unless the lower bound is above the upper bound (NaN keeps)
+      const bool k = j < K && (!valid || !(lb(j) * (1.0 - 0x1p-40) > ub));
+      const unsigned bits = __ballot_sync(0xffffffffu, k);
+      if (g.lane == 0) keep[i * kw + w] = bits;
+    }
+  }
+}
+
 // Fixed-order sum (one block, strided partials then a tree): deterministic.
 __global__ void k_sum_fixed(const double* v, long long n, double* out) {
   __shared__ double sh[256];
@@ -266,6 +371,34 @@ cudaError_t check_bag_symbols(const void* loc, int ldt, const long long* off, lo
                               int A, int* d_err, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   k_check_bag_symbols<<<(unsigned)(152 * 4), 256, 0, st>>>(loc, ldt, off, count, A, d_err);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t bag_moments(const ObjView& ob, double* mu, double* var, cudaStream_t st) {
+  if (ob.count <= 0) return cudaSuccess;
+  const long long blocks = (ob.count + 3) / 4;
+  k_bag_moments<<<(unsigned)(blocks < 8192 ? blocks : 8192), 128, 0, st>>>(ob, mu, var);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t cent_moments(const CentView& cv, double* mu, double* var, cudaStream_t st) {
+  if (cv.K <= 0) return cudaSuccess;
+  const long long blocks = (cv.K + 3) / 4;
+  k_cent_moments<<<(unsigned)(blocks < 8192 ? blocks : 8192), 128, 0, st>>>(cv, mu, var);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t prune_keep(const ObjView& ob, long long seg_size, int K, long long KT, int d,
+                       const double* mu_o, const double* var_o, const double* mu_c,
+                       const double* var_c, unsigned* keep, int kw, cudaStream_t st) {
+  if (ob.count <= 0) return cudaSuccess;
+  if (kw < (K + 31) / 32) return cudaErrorInvalidValue;
+  const long long blocks = (ob.count + 3) / 4;
+  k_prune_keep<<<(unsigned)(blocks < 8192 ? blocks : 8192), 128, 0, st>>>(
+      ob, seg_size, K, KT, d, mu_o, var_o, mu_c, var_c, keep, kw);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -78,6 +78,10 @@ struct Slot {
   int* d_lab = nullptr; size_t n_lab = 0;
   double* d_d2 = nullptr; size_t n_d2 = 0;
   int* d_cand = nullptr; size_t n_cand = 0;
+  // bounds of the pairs that cannot be an object's argmin
+  double* d_mu = nullptr; size_t n_mu = 0;
+  double* d_var = nullptr; size_t n_var = 0;
+  unsigned* d_keep = nullptr; size_t n_keep = 0;
   int* d_err = nullptr;
   // pinned host
   unsigned char* h_in = nullptr; size_t n_in = 0;
@@ -122,6 +126,9 @@ struct d2_server {
   d2k::CentView cv{};
   int nmax = 0, d = 0, mode = 1, budget_pivots = 64, sms = 1, start = 0;
   long long K = 0;
+  // means and spreads of the resident centroids (pruning; null: off)
+  double* d_cmu = nullptr;
+  double* d_cvar = nullptr;
   size_t mem_budget = 0, mem_inflight = 0;
   std::vector<Slot> slots;
   std::deque<std::shared_ptr<Request>> queue;
@@ -154,6 +161,9 @@ bool d2_server::launch(Slot& s, const std::shared_ptr<Request>& r) {
       !grow_dev(&s.d_lab, &s.n_lab, (size_t)N * 4 + 16) ||
       !grow_dev(&s.d_d2, &s.n_d2, (size_t)N * 8 + 16) ||
       !grow_dev(&s.d_cand, &s.n_cand, (size_t)d2k::assign_scratch_ints(N, K, sms) * 4 + 16) ||
+      (d_cmu && (!grow_dev(&s.d_mu, &s.n_mu, (size_t)N * r->dim * 8 + 16) ||
+                 !grow_dev(&s.d_var, &s.n_var, (size_t)N * 8 + 16) ||
+                 !grow_dev(&s.d_keep, &s.n_keep, (size_t)N * ((K + 31) / 32) * 4 + 16))) ||
       !grow_host(&s.h_in, &s.n_in, b_in) ||
       !grow_host(&s.h_out, &s.n_out, b_out))
     return false;
@@ -184,6 +194,18 @@ bool d2_server::launch(Slot& s, const std::shared_ptr<Request>& r) {
   cfg.sms = sms;
   cfg.start = start;
   d2k::FlowOut fo{nullptr, nullptr, 0};
+  if (d_cmu && cfg.mode == 1) {
+    // skip the pairs that cannot be an object's argmin (d2k::prune_keep)
+    const int kw = (int)((K + 31) / 32);
+    if (d2k::bag_moments(ob, s.d_mu, s.d_var, st) != cudaSuccess ||
+        d2k::prune_keep(ob, N, (int)K, K, ob.d, s.d_mu, s.d_var, d_cmu, d_cvar, s.d_keep, kw, st) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cfg.keep = s.d_keep;
+    cfg.keep_words = kw;
+  }
   // bounded chunks, bin by bin (largest trees first); one stream, so the
   // chunks of a request run in order and share its scratch
   const long long per = std::max<long long>(1, kChunkPairs / std::max<long long>(K, 1));
@@ -308,6 +330,7 @@ void d2_server::run() {
 namespace d2k {
 CentView ctx_centroids(const d2_ctx* c, int* nmax, int* d, int* device, int* mode, int* budget,
                        int* sms, long long* K, int* start);
+bool ctx_prune(const d2_ctx* c);
 }
 
 extern "C" int d2_server_create(d2_server** out, d2_ctx* ctx, int32_t nslots, int64_t mem_budget) {
@@ -349,6 +372,19 @@ extern "C" int d2_server_create(d2_server** out, d2_ctx* ctx, int32_t nslots, in
       }
       delete sv;
       return D2_ECUDA;
+    }
+  }
+  if (d2k::ctx_prune(ctx) && sv->cv.A == 0) {
+    // the resident centroids' means and spreads, once
+    if (cudaMalloc(&sv->d_cmu, (size_t)sv->K * sv->d * 8) != cudaSuccess ||
+        cudaMalloc(&sv->d_cvar, (size_t)sv->K * 8) != cudaSuccess ||
+        d2k::cent_moments(sv->cv, sv->d_cmu, sv->d_cvar, sv->slots[0].stream) != cudaSuccess ||
+        cudaStreamSynchronize(sv->slots[0].stream) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(sv->d_cmu);
+      cudaFree(sv->d_cvar);
+      sv->d_cmu = nullptr;
+      sv->d_cvar = nullptr;
     }
   }
   sv->worker = std::thread([sv] { sv->run(); });
@@ -477,10 +513,13 @@ extern "C" int d2_server_destroy(d2_server* sv) {
     cudaFree(s.d_loc); cudaFree(s.d_w); cudaFree(s.d_off); cudaFree(s.d_order); cudaFree(s.d_lab);
     cudaFree(s.d_d2);
     cudaFree(s.d_cand); cudaFree(s.d_err);
+    cudaFree(s.d_mu); cudaFree(s.d_var); cudaFree(s.d_keep);
     if (s.h_in) cudaFreeHost(s.h_in);
     if (s.h_out) cudaFreeHost(s.h_out);
     if (s.h_err) cudaFreeHost(s.h_err);
   }
+  cudaFree(sv->d_cmu);
+  cudaFree(sv->d_cvar);
   delete sv;
   return D2_OK;
 }

@@ -1009,9 +1009,21 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       const long long c0 = cv.off[cb + j];
       const int n = (int)(cv.off[cb + j + 1] - c0);
       if (n < 1 || n > cfg.nmax || m + n > G * NPL) { ok = false; break; }
+      const long long wt = (i * (long long)K + j) * ws.ns;
+      if constexpr (!CERT) {
+        // a centroid whose lower bound is above the object's upper bound
+        // cannot be its argmin: no solve (and no saved basis: a later warm
+        // round starts that pair cold)
+        if (cfg.keep && !((cfg.keep[i * cfg.keep_words + (j >> 5)] >> (j & 31)) & 1u)) {
+          if (ws.par8 && g.lane == 0) ws.sz8[wt] = 0;
+          continue;
+        }
+      }
+      // a warm round restarts the pairs whose basis was not saved
+      const bool fresh = cold || ws.sz8[wt] == 0;
       // warm bases carry their flows (the larger instantiations load Q
       // regardless: fewer live values across the solve)
-      if (cold || NPL > 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
+      if (fresh || NPL > 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
       float cmax;
       float* tile_g = nullptr;  // the pair's block of the chunk's tile (TC)
       if constexpr (TC) {
@@ -1025,10 +1037,11 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
                                                          cv.loc32 + c0 * cv.d, cv.d);
       Simplex<float, G, NPL> S(s32, m, n, g);
       if constexpr (TC) S.set_cost(tile_g, (int)cfg.tile.ldc);
-      const long long wt = (i * (long long)K + j) * ws.ns;
       int st;
-      if (!cold) {
+      if (!fresh) {
         S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+      } else if (!cold) {
+        S.init_northwest();  // warm round, no saved basis (the object's order was not built)
       } else if constexpr (vogel) {
         S.init_vogel();
       } else {
@@ -1039,7 +1052,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       if (ws.par8) {
         // always leave a valid basis for the next round
         if (st == kStInvalid) {
-          if (!cold && NPL == 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
+          if (!fresh && NPL == 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
           S.init_northwest();
         }
         S.store_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);

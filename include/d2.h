@@ -152,7 +152,12 @@ typedef struct {
 typedef struct {
     int32_t precision;          /* D2_PREC_* ; 0 = AUTO */
     int32_t pivot_budget;       /* pivots per pair = pivot_budget*(m+n); 0 = 64 */
-    int32_t group_lanes;        /* lanes per pair: 0 = autotune, or 1/2/4/8/16/32 */
+    int32_t group_lanes;        /* lanes per pair: every pair is solved by one warp
+                                   (32 lanes, one tree node per lane and bin).
+                                   0 = the launch shape (threads per block, screening
+                                   items per SM, cold-start rule) is autotuned per
+                                   support bin on large batches; 32 = the default shape,
+                                   no tuning; other values are rejected (D2_EINVAL) */
     int32_t cost_tc;            /* D2_TC_* ; 0 = AUTO */
     int32_t tile_budget_mib;    /* device memory for tensor-core cost tiles;
                                    0 = min(32 GiB, 40% of free memory) */
@@ -204,6 +209,8 @@ typedef struct {
 typedef struct d2_ctx d2_ctx;
 
 /* Create a context on CUDA device `device`.  cfg may be NULL (defaults).
+ * A field outside its documented values (an unknown mode, a negative count
+ * or budget) is rejected with D2_EINVAL before any device work.
  * Creates its own stream, a blocking one: it is ordered with the legacy
  * default stream, so device inputs written there (for instance by a
  * framework's default stream) are complete before the context's kernels

@@ -886,9 +886,23 @@ const char* d2_strerror(int32_t s) {
 
 const char* d2_version(void) { return "d2-gb300 0.1 (sm_103a)"; }
 
+// Every field of the configuration within its documented values.
+static bool config_ok(const d2_config& f) {
+  auto in = [](int32_t v, int32_t lo, int32_t hi) { return v >= lo && v <= hi; };
+  return in(f.precision, D2_PREC_AUTO, D2_PREC_FP32) && f.pivot_budget >= 0 &&
+         (f.group_lanes == 0 || f.group_lanes == 32) && in(f.cost_tc, D2_TC_AUTO, D2_TC_ON) &&
+         f.tile_budget_mib >= 0 && in(f.start_rule, D2_START_AUTO, D2_START_VOGEL) &&
+         in(f.segmentation, D2_SEG_SLICES, D2_SEG_CONSTRAINED) && f.split_iters >= 0 &&
+         f.eps_tol >= 0.0 && in(f.centroid_update, D2_UPDATE_CONSTRAINED, D2_UPDATE_ALG1) &&
+         f.joint_max_iter >= 0 && f.joint_tol >= 0.0 &&
+         in(f.certify, D2_CERTIFY_CANDIDATES, D2_CERTIFY_ALL) && f.tc_wait_probe >= 0 &&
+         in(f.no_prune, 0, 1);
+}
+
 int d2_ctx_create(d2_ctx** out, int32_t device, const d2_config* cfg) {
   if (!out) return D2_EINVAL;
   *out = nullptr;
+  if (cfg && !config_ok(*cfg)) return D2_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();

@@ -738,15 +738,18 @@ __device__ __noinline__ float2 cost_dd_slow(const void* xloc, int ldt, long long
   return make_float2(hi, __double2float_rn(c - (double)hi));
 }
 
-// Cost of cell (a, r) as hi + lo (cost_dd_x, or cost_dd_slow when `fast`
-// does not hold).
-template <typename X>
-__device__ __forceinline__ void cost_dd(bool fast, const ObjView& ob, long long o0,
+// Cost of cell (a, r) as hi + lo: cost_dd_x for FP32 (xt == 1) or BF16
+// (xt == 2) object data, cost_dd_slow otherwise (xt == 0).  Only the load
+// loop depends on the type, so the certificate around it exists once.
+__device__ __forceinline__ void cost_dd(int xt, const ObjView& ob, long long o0,
                                         const CentView& cv, long long c0, int a, int r,
                                         float& hi, float& lo) {
-  if (fast) {
-    cost_dd_x(static_cast<const X*>(ob.loc) + (o0 + a) * cv.d, cv.loc32 + (c0 + r) * cv.d, cv.d,
-              hi, lo);
+  if (xt == 1) {
+    cost_dd_x(static_cast<const float*>(ob.loc) + (o0 + a) * cv.d, cv.loc32 + (c0 + r) * cv.d,
+              cv.d, hi, lo);
+  } else if (xt == 2) {
+    cost_dd_x(static_cast<const __nv_bfloat16*>(ob.loc) + (o0 + a) * cv.d,
+              cv.loc32 + (c0 + r) * cv.d, cv.d, hi, lo);
   } else {
     const float2 c = cost_dd_slow(ob.loc, ob.ldt, o0 + a, cv.d,
                                   cv.A ? cv.loc64 + c0 + r : cv.loc64 + (c0 + r) * cv.d, cv.tab64,
@@ -754,6 +757,14 @@ __device__ __forceinline__ void cost_dd(bool fast, const ObjView& ob, long long 
     hi = c.x;
     lo = c.y;
   }
+}
+
+// Group maximum of non-negative floats (or NaN) by the integer reduction
+// unit: their bit patterns order like the values, and a NaN (above +inf as
+// an unsigned pattern) survives, where fmaxf would drop it.
+template <int G>
+__device__ __forceinline__ float gmax_nonneg(const Grp<G>& g, float v) {
+  return __uint_as_float(__reduce_max_sync(g.mask, __float_as_uint(v)));
 }
 
 // Optimality certificate of the basis an FP32 solve stopped at (precision
@@ -786,14 +797,14 @@ __device__ __forceinline__ void cost_dd(bool fast, const ObjView& ob, long long 
 // the tree was inconsistent); *nchk: cells re-priced.  Overwrites the
 // basic cells of the FP32 tile and the solver's pivot scratch; the tree
 // and the solver's potentials are kept.
-template <int G, int NPL, typename X>
+template <int G, int NPL>
 __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long long o0,
                              const CentView& cv, long long c0, float cmax, float ecost,
                              double* D64, float* tau_out, int* nchk) {
   const Grp<G>& g = S.g;
   const int m = S.m, n = S.n, N = S.N;
   const PairMem<float>& s = S.s;
-  const bool fast = cv.A == 0 && ob.ldt != 0;  // cost_dd_x applies
+  const int xt = (cv.A == 0 && ob.ldt != 0) ? ob.ldt : 0;  // cost_dd's path
   float rres[NPL];
   double acc = 0.0;
 #pragma unroll
@@ -805,7 +816,7 @@ __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long 
       const int a = y < m ? y : p;
       const int r = y < m ? p - m : y - m;
       float ch, cl;
-      cost_dd<X>(fast, ob, o0, cv, c0, a, r, ch, cl);
+      cost_dd(xt, ob, o0, cv, c0, a, r, ch, cl);
       const double w = (double)S.t.flow[k] * kInvMass;
       acc = fma(w, (double)ch, acc);
       acc = fma(w, (double)cl, acc);
@@ -899,7 +910,9 @@ __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long 
   }
   // potentials to shared memory ((base, correction) for re-pricing, their
   // FP32 sum for the scan); the basic cells leave the scan (+inf in the tile)
-  float pmax = 0.f, dmax = 0.f;
+  // (|u| and |delta| maxima as unsigned patterns: a NaN potential wins the
+  // maximum and fails the finiteness test below)
+  unsigned pm = 0u, dm = 0u;
 #pragma unroll
   for (int k = 0; k < NPL; ++k) {
     const int y = S.node_of(k);
@@ -907,13 +920,13 @@ __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long 
       PD[y] = make_float2(S.pot[k], dl[k]);
       const float u = S.pot[k] + dl[k];
       s.pot[y] = u;
-      pmax = fmaxf(pmax, fabsf(u));
-      dmax = fmaxf(dmax, fabsf(dl[k]));
+      pm = max(pm, __float_as_uint(fabsf(u)));
+      dm = max(dm, __float_as_uint(fabsf(dl[k])));
       if (y != S.root) S.cost[S.edge_idx(y, S.t.par[k])] = INFINITY;
     }
   }
-  pmax = gmax<G>(g, pmax);
-  dmax = gmax<G>(g, dmax);
+  const float pmax = gmax_nonneg<G>(g, __uint_as_float(pm));
+  const float dmax = gmax_nonneg<G>(g, __uint_as_float(dm));
   g.sync();
   if (gany<G>(g, bad)) { *D64 = NAN; return false; }
   if (!isfinite(D) || !isfinite(pmax) || !isfinite(dmax) || !(cmax < FLT_MAX)) return false;
@@ -928,29 +941,47 @@ __device__ bool certify_fp64(Simplex<float, G, NPL>& S, const ObjView& ob, long 
   const float thr = __fsub_ru(__fadd_ru(E, err), tau);  // d32 >= thr    =>  d >= -tau
   const float thr_dd = __fsub_ru(err, tau);              // d~ >= thr_dd  =>  d >= -tau
   const int mn = m * n;
+  // pass 1: the FP32 test of every cell (a NaN reduced cost is flagged)
+  bool flagged = false;
+  if (S.sr == 0) {
+    // n divides the group: the lane's cells share column r0, whose
+    // potential stays in a register
+    const float vr = s.pot[m + S.r0];
+    const int step = S.sq * S.cs;
+    for (int a = S.a0, o = S.a0 * S.cs + S.r0; a < m; a += S.sq, o += step)
+      flagged |= !(S.cost[o] - s.pot[a] - vr >= thr);
+  } else {
+    int a = S.a0, r = S.r0;
+    int o = S.a0 * S.cs + S.r0;  // offset of cell (a, r) in the tile
+    const int ostep = S.sq * S.cs + S.sr, owrap = S.cs - n;
+    for (int i = g.lane; i < mn; i += G) {
+      flagged |= !(S.cost[o] - s.pot[a] - s.pot[m + r] >= thr);
+      r += S.sr; a += S.sq; o += ostep;
+      if (r >= n) { r -= n; ++a; o += owrap; }
+    }
+  }
+  if (!gany<G>(g, flagged)) return true;
+  // pass 2 (few pairs): the flagged cells re-priced in double-float, where
+  // they must reach thr_dd
   bool fail = false;
   int cnt = 0;
-  // a cell below thr (+inf basic cells never are) is re-priced in double-float
-  auto reprice = [&](int a, int r) {
-    ++cnt;
-    float ch, cl;
-    cost_dd<X>(fast, ob, o0, cv, c0, a, r, ch, cl);
-    const float2 u = PD[a], v = PD[m + r];
-    dd_add(ch, cl, -u.x, -u.y);
-    dd_add(ch, cl, -v.x, -v.y);
-    fail |= !((double)ch + (double)cl >= (double)thr_dd);
-  };
-  // when n divides the group (sr == 0) the lane's cells share column r0:
-  // its potential stays in a register
-  const bool colfix = S.sr == 0;
-  const float vfix = s.pot[m + S.r0];
-  int a = S.a0, r = S.r0;
-  int o = S.a0 * S.cs + S.r0;  // offset of cell (a, r) in the tile
-  const int ostep = S.sq * S.cs + S.sr, owrap = S.cs - n;
-  for (int i = g.lane; i < mn; i += G) {
-    if (S.cost[o] - s.pot[a] - (colfix ? vfix : s.pot[m + r]) < thr) reprice(a, r);
-    r += S.sr; a += S.sq; o += ostep;
-    if (r >= n) { r -= n; ++a; o += owrap; }
+  if (flagged) {
+    int a = S.a0, r = S.r0;
+    int o = S.a0 * S.cs + S.r0;
+    const int ostep = S.sq * S.cs + S.sr, owrap = S.cs - n;
+    for (int i = g.lane; i < mn; i += G) {
+      if (!(S.cost[o] - s.pot[a] - s.pot[m + r] >= thr)) {
+        ++cnt;
+        float ch, cl;
+        cost_dd(xt, ob, o0, cv, c0, a, r, ch, cl);
+        const float2 u = PD[a], v = PD[m + r];
+        dd_add(ch, cl, -u.x, -u.y);
+        dd_add(ch, cl, -v.x, -v.y);
+        fail |= !((double)ch + (double)cl >= (double)thr_dd);
+      }
+      r += S.sr; a += S.sq; o += ostep;
+      if (r >= n) { r -= n; ++a; o += owrap; }
+    }
   }
   *nchk += cnt;
   return !gany<G>(g, fail);
@@ -1019,8 +1050,10 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
           continue;
         }
       }
-      // a warm round restarts the pairs whose basis was not saved
-      const bool fresh = cold || ws.sz8[wt] == 0;
+      // a warm round restarts the pairs whose basis was not saved (a
+      // certify-all level never skips a pair, so its warm rounds always
+      // find one)
+      const bool fresh = cold || (!CERT && ws.sz8[wt] == 0);
       // warm bases carry their flows (the larger instantiations load Q
       // regardless: fewer live values across the solve)
       if (fresh || NPL > 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
@@ -1040,7 +1073,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       int st;
       if (!fresh) {
         S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
-      } else if (!cold) {
+      } else if (!CERT && !cold) {
         S.init_northwest();  // warm round, no saved basis (the object's order was not built)
       } else if constexpr (vogel) {
         S.init_vogel();
@@ -1070,11 +1103,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
           float ecost;
           if constexpr (TC) ecost = tc_bound(cv.d, nxm, cfg.tile.cn[cb + j], cfg.tile.cd[cb + j]);
           else ecost = (cv.A ? 0x1p-23f : (float)(cv.d + 3) * 0x1p-24f) * cmax;
-          cert = ob.ldt == 2
-                     ? certify_fp64<G, NPL, __nv_bfloat16>(S, ob, o0, cv, c0, cmax, ecost, &D64,
-                                                           &tau, &n_chk)
-                     : certify_fp64<G, NPL, float>(S, ob, o0, cv, c0, cmax, ecost, &D64, &tau,
-                                                   &n_chk);
+          cert = certify_fp64<G, NPL>(S, ob, o0, cv, c0, cmax, ecost, &D64, &tau, &n_chk);
         }
         // D64 is within (6d + 4) 2^-48 relative of the basis's objective
         // (double-float costs, FP64 sum); the FP32 interval ends, widened by

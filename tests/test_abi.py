@@ -55,6 +55,21 @@ def test_ctx_create_without_gpu_returns_status(lib):
     assert rc == -5 and not h.value  # D2_ECUDA
 
 
+@pytest.mark.parametrize("field,value", [
+    ("group_lanes", 16), ("group_lanes", 8), ("precision", 7), ("precision", -1),
+    ("certify", 2), ("start_rule", 3), ("cost_tc", 5), ("segmentation", 2),
+    ("centroid_update", 2), ("pivot_budget", -1), ("tile_budget_mib", -4),
+    ("no_prune", 2), ("eps_tol", -1.0), ("eps_tol", float("nan")), ("joint_tol", -1e-9)])
+def test_ctx_create_rejects_config_outside_documented_values(lib, field, value):
+    """A field outside its documented values is rejected (D2_EINVAL) before
+    the device is touched, so this holds on a machine without a GPU."""
+    from paper_1302_0435_gb300 import d2
+    cfg = d2.D2Config()
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    assert lib.d2_ctx_create(ctypes.byref(h), 0, ctypes.byref(cfg)) == -1 and not h.value
+
+
 def test_null_arguments_rejected(lib):
     assert lib.d2_sync(None) == -1
     assert lib.d2_ctx_destroy(None) == -1

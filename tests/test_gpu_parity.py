@@ -83,9 +83,9 @@ def all_pairs(N, K):
 
 
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("group", [32, 16, 8])
-def test_mallows_random_sizes(d2, oracle_mod, precision, group):
-    rng = np.random.default_rng(1000 + precision + group)
+@pytest.mark.parametrize("seed", [32, 16, 8])
+def test_mallows_random_sizes(d2, oracle_mod, precision, seed):
+    rng = np.random.default_rng(1000 + precision + seed)
     objs_l = rand_pairs(rng, 40, (1, 65), 5, alpha=0.5)
     cents_l = rand_pairs(rng, 9, (1, 65), 5)
     cents_l.append((cents_l[0][0], np.full(len(cents_l[0][1]), 1.0 / len(cents_l[0][1]))))
@@ -93,7 +93,7 @@ def test_mallows_random_sizes(d2, oracle_mod, precision, group):
     objs = make_bags(objs_l, dt, dt)
     cents = make_bags(cents_l, dt, dt)
     pi, pj = all_pairs(objs.count, cents.count)
-    got, st, rc = gpu_pairs(d2, objs, cents, pi, pj, precision=precision, group=group)
+    got, st, rc = gpu_pairs(d2, objs, cents, pi, pj, precision=precision)
     assert rc == 0 and (st == 0).all()
     ref = oracle_mod.mallows_pairs(objs, cents, pi, pj, nthreads=8)
     assert_d2_close(got, ref)

@@ -188,7 +188,12 @@ typedef struct {
                                    both bags' spreads, so a centroid whose lower bound
                                    exceeds the object's best upper bound is never solved
                                    (labels and distances unchanged); 1: every pair solved */
-    int32_t reserved;
+    int32_t joint_cold_start;   /* 0: each cutting-plane round of d2_update_weights (and of
+                                   D2_UPDATE_ALG1 levels) restarts every member's LP from its
+                                   optimal basis of the round before: only the centroid
+                                   weights changed, so that basis stays dual feasible, and
+                                   dual simplex pivots restore its flows (same optima); 1:
+                                   every round solves every member from a cold start */
 } d2_config;
 
 /*

@@ -41,7 +41,7 @@ enum Slot {
   // combined distance of several bag types
   kMbPair, kMbTmpLab, kMbTmpD2, kMbCnt, kMbStart, kMbPObj, kMbPCen, kMbD2, kMbSt,
   // joint weights (Alg. 1 Step 1)
-  kJState, kJPot, kJPStart, kJEps, kJIters, kJSort, kJPObj, kJPCen, kJW, kJSt,
+  kJState, kJPot, kJPStart, kJEps, kJIters, kJSort, kJPObj, kJPCen, kJW, kJSt, kJTree,
   kPairTree,
   // d2_mallows_all
   kAllLab, kAllD2, kAllPair,
@@ -261,8 +261,7 @@ int start_default(const d2_ctx* c) {
 SolveCfg solve_cfg(const d2_ctx* c, int mode, int mmax) {
   SolveCfg s;
   s.mode = mode;
-  s.group = c->cfg.group_lanes > 0 ? c->cfg.group_lanes : 32;
-  if (s.group != 8 && s.group != 16 && s.group != 32) s.group = 32;
+  s.group = 32;  // one warp per pair
   s.mmax = std::max(mmax, 1);
   s.nmax = std::max(c->nmax, 1);
   s.budget = c->cfg.pivot_budget > 0 ? c->cfg.pivot_budget : 64;
@@ -896,7 +895,7 @@ static bool config_ok(const d2_config& f) {
          f.eps_tol >= 0.0 && in(f.centroid_update, D2_UPDATE_CONSTRAINED, D2_UPDATE_ALG1) &&
          f.joint_max_iter >= 0 && f.joint_tol >= 0.0 &&
          in(f.certify, D2_CERTIFY_CANDIDATES, D2_CERTIFY_ALL) && f.tc_wait_probe >= 0 &&
-         in(f.no_prune, 0, 1);
+         in(f.no_prune, 0, 1) && in(f.joint_cold_start, 0, 1);
 }
 
 int d2_ctx_create(d2_ctx** out, int32_t device, const d2_config* cfg) {
@@ -1314,6 +1313,18 @@ int joint_core(d2_ctx* c, const ObjView& v, const double* om, const int* dl, lon
   cv.tab32 = c->tab32;
   cv.tab64 = c->tab64;
   cv.A = c->A;
+  // each object's optimal basis from the previous round (the solves of a
+  // round restart from it); none saved yet
+  if (N > 0 && c->cfg.joint_cold_start == 0 && cfg.mode == 1) {
+    const int ns = cfg.mmax + cfg.nmax;
+    const size_t nodes = (size_t)N * ns;
+    const size_t b3 = (nodes * 3 + 15) / 16 * 16;
+    unsigned char* jt = static_cast<unsigned char*>(grow(c, kJTree, b3 + nodes * 8, &rc));
+    if (rc != D2_OK) return rc;
+    cfg.jw = d2k::WarmStore{jt, jt + nodes, jt + 2 * nodes, reinterpret_cast<long long*>(jt + b3),
+                            ns, 1};
+    CK(cudaMemsetAsync(cfg.jw.sz8, 0, nodes, c->stream));
+  }
   long long* hP = reinterpret_cast<long long*>(c->h_pin + 4);
   for (int it = 0; it < itmax; ++it) {
     d2k::TraceRange round_("joint round");

@@ -107,7 +107,7 @@ struct TcWork {
 // Launch-wide solver settings.
 struct SolveCfg {
   int mode;        // 0: FP64 throughout; 1: FP32 screen/pivots + FP64 certify
-  int group;       // lanes per pair (1,2,4,8,16,32)
+  int group;       // lanes per pair (32: one warp)
   int mmax, nmax;  // support bounds of the launch
   int budget;      // pivots per pair = budget*(m+n)
   int sms;         // SM count
@@ -143,6 +143,14 @@ struct SolveCfg {
   // handed from the FP32 launch to the FP64 launch; null: one fused launch
   unsigned char* tree = nullptr;
   size_t tree_bytes = 0;
+  // joint-weights rounds (mallows_pairs with the hand-over above): the
+  // optimal basis of each object's pair from the previous round, indexed by
+  // OBJECT (node y of object i at [i*jw.ns + y]; sz8 of node 0 == 0: none
+  // saved).  Only the centroid weights change between rounds, so that basis
+  // stays dual feasible: the FP32 launch restarts from it (flows recomputed
+  // for the new weights, dual pivots until they are feasible, then primal
+  // pivots), and the FP64 launch saves its final basis there.
+  WarmStore jw{};
 };
 
 // Bases of npairs pairs of up to mmax + nmax nodes (par/pos/size bytes and

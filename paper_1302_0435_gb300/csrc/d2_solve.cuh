@@ -474,14 +474,32 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5))
                    : build_cost<float, G, 8>(g, s32.cost, m, n, ob.loc, ob.ldt, o0,
                                              cv.loc32 + c0 * cv.d, cv.d);
           Simplex<float, G, NPL> S32(s32, m, n, g);
-          if constexpr (ST == 1) {
-            S32.init_vogel();
-          } else {
-            order_rows<G>(g, s32, ob, o0, m, cv.d);
-            order_cols<G>(g, s32, cv.loc32 + c0 * cv.d, n, cv.d);
-            S32.init_northwest_ranked();
+          // restart from the object's basis of the previous joint round:
+          // same tree, flows for the new centroid weights, dual pivots to
+          // feasibility, then the primal run
+          const long long wi = i * (long long)cfg.jw.ns;
+          if (cfg.jw.par8 && m + n <= cfg.jw.ns && cfg.jw.sz8[wi] != 0) {
+            S32.load_tree(cfg.jw.par8 + wi, cfg.jw.pos8 + wi, cfg.jw.sz8 + wi, cfg.jw.flow + wi);
+            if (S32.tree_sane()) {
+              S32.recompute_flows();
+              st = S32.run_dual(cfg.budget * (m + n), &n_piv);
+              if (st == kStOk) st = S32.run(cfg.budget * (m + n), tol32(c32), &n_piv);
+            }
+            if (st != kStOk) {  // start over cold
+              S32.bad = false;
+              S32.set_dims(m, n);
+            }
           }
-          st = S32.run(cfg.budget * (m + n), tol32(c32), &n_piv);
+          if (st != kStOk) {
+            if constexpr (ST == 1) {
+              S32.init_vogel();
+            } else {
+              order_rows<G>(g, s32, ob, o0, m, cv.d);
+              order_cols<G>(g, s32, cv.loc32 + c0 * cv.d, n, cv.d);
+              S32.init_northwest_ranked();
+            }
+            st = S32.run(cfg.budget * (m + n), tol32(c32), &n_piv);
+          }
           if (st != kStInvalid) {
             const long long wt = t * tr.ns;
             S32.store_tree(tr.par8 + wt, tr.pos8 + wt, tr.sz8 + wt, tr.flow + wt);
@@ -535,6 +553,10 @@ __global__ void __launch_bounds__(128) k_pairs64(ObjView ob, CentView cv, const 
           S.write_flows(fo.cell + t * fo.stride, fo.w + t * fo.stride, fo.stride);
         if (fo.pot && st == kStOk)  // potentials of the final, freshly priced basis
           for (int r = g.lane; r < n; r += G) fo.pot[t * fo.pstride + r] = s64.pot[m + r];
+        if (cfg.jw.par8 && st == kStOk && m + n <= cfg.jw.ns) {  // the next joint round's start
+          const long long wi = i * (long long)cfg.jw.ns;
+          S.store_tree(cfg.jw.par8 + wi, cfg.jw.pos8 + wi, cfg.jw.sz8 + wi, cfg.jw.flow + wi);
+        }
       }
     }
     if (g.lane == 0) {

@@ -910,7 +910,17 @@ struct Simplex {
 
   // One pivot on entering cell key `cell` with reduced cost dE < 0.
   // Returns true when the pivot moved flow (theta > 0).
-  __device__ __forceinline__ bool pivot(int cell, T dE) {
+  __device__ __forceinline__ bool pivot(int cell, T dE) { return pivot_impl<false>(cell, dE, 0, 0); }
+
+  // The pivot proper.  Primal (DUAL false): the leaving edge and theta come
+  // from the ratio test over the cycle's decreasing edges.  Dual: the
+  // leaving edge (the one above node zd, flow -thd < 0) was chosen first and
+  // the entering cell crosses its cut so that the edge is an increasing one
+  // of the cycle; theta = thd brings its flow to zero.  The cycle update,
+  // the re-hanging of the leaving side and the potential shift by dE are
+  // the same in both.
+  template <bool DUAL>
+  __device__ __forceinline__ bool pivot_impl(int cell, T dE, int zd, long long thd) {
     const int ea = cell >> 8;
     const int eB = m + (cell & 0xff);
     const int pa = s.pos[ea];
@@ -931,13 +941,16 @@ struct Simplex {
         side[k] = (isA != isB) ? (isA ? 1 : 2) : 0;
         // "-" edges: row children on the row side, column children on the
         // column side
-        if (side[k] == (y < m ? 1 : 2)) {
+        if (!DUAL && side[k] == (y < m ? 1 : 2)) {
           const int key = (edge_key(y, t.par[k]) << 7) | y;
           if (t.flow[k] < th || (t.flow[k] == th && key < tkey)) { th = t.flow[k]; tkey = key; }
         }
       }
     }
-    {  // group minimum of (flow, key) with the integer reduction unit
+    if constexpr (DUAL) {
+      th = thd;
+      tkey = zd;
+    } else {  // group minimum of (flow, key) with the integer reduction unit
       if (th < 0) bad = true;  // flows are never negative
       const unsigned long long uf = (unsigned long long)th;
       const unsigned hi = (unsigned)(uf >> 32), lo = (unsigned)uf;
@@ -1096,6 +1109,157 @@ struct Simplex {
   __device__ __forceinline__ int solve(int max_pivots, T tol, int* pivots, bool fresh_stop = true) {
     init_northwest();
     return run(max_pivots, tol, pivots, fresh_stop);
+  }
+
+  // ---- restart from a basis saved for other marginals -----------------
+  // A loaded tree (load_tree) is usable when every node's preorder range
+  // lies inside [0, N) and the root spans all N nodes.
+  __device__ __forceinline__ bool tree_sane() const {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y < N) {
+        ok &= t.sz[k] >= 1 && t.pos[k] + t.sz[k] <= N;
+        if (y == root) ok &= t.pos[k] == 0 && t.sz[k] == N;
+        else ok &= t.par[k] >= 0 && t.par[k] < N && (y < m) != (t.par[k] < m);
+      }
+    }
+    return !gany<G>(g, !ok);
+  }
+
+  // Flows of the current tree for the current marginals (prefix masses
+  // s.P, s.Q): the edge above node y carries the net supply of y's subtree
+  // (rows supply their mass, columns demand theirs), read off a prefix sum
+  // of the supplies laid out in preorder, where a subtree is a contiguous
+  // range.  Returns true (group-uniform) when no flow is negative.
+  __device__ __forceinline__ bool recompute_flows() {
+    long long* B = s.pflow;  // [N]: supplies by preorder position, then prefix sums
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y < N) {
+        long long b;
+        if (y < m) b = s.P[y] - (y > 0 ? s.P[y - 1] : 0LL);
+        else {
+          const int r = y - m;
+          b = -(s.Q[r] - (r > 0 ? s.Q[r - 1] : 0LL));
+        }
+        B[t.pos[k]] = b;
+      }
+    }
+    g.sync();
+    // inclusive prefix: lane l sums positions [l*NPL, l*NPL + NPL), then an
+    // exclusive scan of the lanes' totals
+    long long loc[NPL];
+    long long run = 0;
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int p = g.lane * NPL + k;
+      run += p < N ? B[p] : 0LL;
+      loc[k] = run;
+    }
+    long long incl = run;
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      const long long v = __shfl_up_sync(g.mask, incl, o, G);
+      if (g.lane >= o) incl += v;
+    }
+    const long long excl = incl - run;
+    g.sync();
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int p = g.lane * NPL + k;
+      if (p < N) B[p] = excl + loc[k];
+    }
+    g.sync();
+    bool neg = false;
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int y = node_of(k);
+      if (y < N) {
+        if (y == root) {
+          t.flow[k] = 0;
+        } else {
+          const int p0 = t.pos[k], p1 = p0 + t.sz[k] - 1;
+          const long long net = B[p1] - (p0 > 0 ? B[p0 - 1] : 0LL);
+          t.flow[k] = y < m ? net : -net;
+          neg |= t.flow[k] < 0;
+        }
+      }
+    }
+    g.sync();
+    return !gany<G>(g, neg);
+  }
+
+  // Dual simplex from a tree whose reduced costs are (about) non-negative
+  // but whose flows may not be: while an edge carries negative flow, the
+  // most negative one leaves (ties to the smallest cell); the entering cell
+  // is the cell of least reduced cost among those crossing the leaving
+  // edge's cut in the direction that can carry its deficit (into the
+  // subtree below a row node, out of the subtree below a column node), so
+  // every other reduced cost stays non-negative.  The potentials are
+  // recomputed first and then shifted incrementally; a primal run() after
+  // this refreshes them.  Returns kStOk once every flow is non-negative,
+  // kStNotConverged at max_pivots, kStInvalid on an inconsistent tree.
+  __device__ int run_dual(int max_pivots, int* pivots) {
+    refresh_potentials();
+    if (bad) return kStInvalid;
+    int done = 0;
+    int st = kStOk;
+    const int mn = m * n;
+    for (;;) {
+      // leaving edge: the most negative flow (signed order on the unsigned
+      // reduction unit: flip the sign bit), ties to the smallest edge key
+      long long fmin = 0;
+      int lkey = INT_MAX;
+#pragma unroll
+      for (int k = 0; k < NPL; ++k) {
+        const int y = node_of(k);
+        if (y < N && y != root) {
+          const int key = (edge_key(y, t.par[k]) << 7) | y;
+          if (t.flow[k] < fmin || (t.flow[k] < 0 && t.flow[k] == fmin && key < lkey)) {
+            fmin = t.flow[k];
+            lkey = key;
+          }
+        }
+      }
+      const unsigned long long uf = (unsigned long long)fmin ^ 0x8000000000000000ull;
+      const unsigned hi = (unsigned)(uf >> 32), lo = (unsigned)uf;
+      const unsigned mh = __reduce_min_sync(g.mask, hi);
+      const unsigned ml = __reduce_min_sync(g.mask, hi == mh ? lo : 0xffffffffu);
+      lkey = (int)__reduce_min_sync(g.mask, (hi == mh && lo == ml) ? (unsigned)lkey : 0xffffffffu);
+      fmin = (long long)((((unsigned long long)mh << 32) | ml) ^ 0x8000000000000000ull);
+      if (fmin >= 0) break;  // feasible
+      if (done >= max_pivots) { st = kStNotConverged; break; }
+      if (lkey == INT_MAX) { bad = true; st = kStInvalid; break; }
+      const int zL = lkey & 0x7f;
+      const int P0 = s.pos[zL], P1 = P0 + s.sz[zL];
+      const bool zrow = zL < m;
+      // entering cell: least reduced cost over the eligible cells
+      T best = T(INFINITY);
+      int cell = INT_MAX;
+      int a = a0, r = r0;
+      int o = a0 * cs + r0;
+      const int ostep = sq * cs + sr, owrap = cs - n;
+      for (int i = g.lane; i < mn; i += G) {
+        const int qa = s.pos[a], qb = s.pos[m + r];
+        const bool inA = P0 <= qa && qa < P1, inB = P0 <= qb && qb < P1;
+        if (zrow ? (!inA && inB) : (inA && !inB)) {
+          const T d = cost[o] - s.pot[a] - s.pot[m + r];
+          if (d < best) { best = d; cell = key_rc(a, r); }
+        }
+        r += sr; a += sq; o += ostep;
+        if (r >= n) { r -= n; ++a; o += owrap; }
+      }
+      gmin_val_key(best, cell);
+      if (cell == INT_MAX || !(best < T(INFINITY))) { bad = true; st = kStInvalid; break; }
+      pivot_impl<true>(cell, best, zL, -fmin);
+      if (bad) { st = kStInvalid; break; }
+      ++done;
+    }
+    if (pivots) *pivots += done;
+    return st;
   }
 
   // Saved basis of one pair: per node parent, preorder position, subtree

@@ -25,8 +25,8 @@ def d2():
     return mod
 
 
-def _weights(d2, objs, cents, lab, omega=None, max_iter=1500, tol=1e-11, table=None):
-    ctx = d2.Context(0)
+def _weights(d2, objs, cents, lab, omega=None, max_iter=1500, tol=1e-11, table=None, cold=False):
+    ctx = d2.Context(0, joint_cold_start=cold)
     if table is not None:
         d2.d2_set_cost_table(ctx, table)
     d2.d2_set_centroids(ctx, d2.bags_from_synth(cents))
@@ -192,3 +192,28 @@ def test_joint_weights_image_like_full_size(d2, oracle_mod):
     labn = lab.cpu().numpy()
     for j in (0, 37):                                   # sampled clusters, re-evaluated
         assert _F(oracle_mod, objs, cents, labn, None, w, j) == pytest.approx(e[j], rel=1e-9)
+
+
+@pytest.mark.parametrize("law", ["image_like", "uneven"])
+def test_warm_rounds_match_cold_rounds(d2, oracle_mod, law):
+    """Rounds that restart every member from its previous optimal basis
+    (dual pivots after the weights moved) reach the same optimum as rounds
+    that solve every member cold, with fewer member pivots; the warm weights
+    attain eps and eps is the LP optimum (oracle)."""
+    if law == "image_like":
+        objs, cents = synth.image_like(N=600, K=6, seed=93)
+    else:
+        objs, cents = synth.uneven(N=500, K=5, seed=94)
+    lab, _ = oracle_mod.assign(objs, cents, nthreads=8)
+    out = {}
+    for cold in (True, False):
+        s0 = d2.d2_get_stats()
+        rc, w, eps, its = _weights(d2, objs, cents, lab, cold=cold)
+        s1 = d2.d2_get_stats()
+        out[cold] = (rc, w, eps, its, s1["pivots_exact"] - s0["pivots_exact"],
+                     s1["pairs_exact"] - s0["pairs_exact"])
+    rc, w, eps, its, piv_w, pairs_w = out[False]
+    _check(d2, oracle_mod, objs, cents, lab, None, rc, w, eps, its)
+    np.testing.assert_allclose(eps, out[True][2], rtol=1e-9)
+    # pivots per member solve: the warm restarts need fewer
+    assert piv_w / pairs_w < out[True][4] / out[True][5]

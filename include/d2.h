@@ -194,6 +194,12 @@ typedef struct {
                                    weights changed, so that basis stays dual feasible, and
                                    dual simplex pivots restore its flows (same optima); 1:
                                    every round solves every member from a cold start */
+    int32_t warm_budget_mib;    /* device memory d2_cluster_level may take for the bases it
+                                   keeps between rounds; 0 = 40% of the free memory.  The
+                                   full store is 11 B per tree node and pair; when only its
+                                   trees fit (3 B per node) the flows are recomputed on
+                                   reload (same results, slower; not with
+                                   D2_CERTIFY_ALL); below that the rounds start cold */
 } d2_config;
 
 /*

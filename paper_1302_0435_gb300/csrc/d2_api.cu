@@ -399,8 +399,17 @@ __global__ void k_compose(int* C, long long N, const int* ct) {
     C[i] = C[i] < 0 ? -1 : ct[C[i]];
 }
 
-// Device memory the level driver may use for saved bases (warm starts).
-constexpr size_t kWarmBudgetBytes = (size_t)32 << 30;
+// Device memory the level driver may use for saved bases (warm starts):
+// d2_config.warm_budget_mib, else 40 % of what is free when the level starts.
+size_t warm_budget_bytes(const d2_ctx* c) {
+  if (c->cfg.warm_budget_mib > 0) return (size_t)c->cfg.warm_budget_mib << 20;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return fr / 5 * 2;
+}
 
 unsigned blocks_for(long long n) {
   long long b = (n + 255) / 256;
@@ -895,7 +904,7 @@ static bool config_ok(const d2_config& f) {
          f.eps_tol >= 0.0 && in(f.centroid_update, D2_UPDATE_CONSTRAINED, D2_UPDATE_ALG1) &&
          f.joint_max_iter >= 0 && f.joint_tol >= 0.0 &&
          in(f.certify, D2_CERTIFY_CANDIDATES, D2_CERTIFY_ALL) && f.tc_wait_probe >= 0 &&
-         in(f.no_prune, 0, 1) && in(f.joint_cold_start, 0, 1);
+         in(f.no_prune, 0, 1) && in(f.joint_cold_start, 0, 1) && f.warm_budget_mib >= 0;
 }
 
 int d2_ctx_create(d2_ctx** out, int32_t device, const d2_config* cfg) {
@@ -1681,17 +1690,28 @@ int d2_cluster_level_ex(d2_ctx* c, const d2_bags* objs, const double* omega, int
     // Saved bases of all (object, centroid) pairs of this level: the rounds
     // re-solve the same pairs with the same marginals and moved centroid
     // locations, so each solve starts from its previous optimal basis.
+    // A basis is its tree (parent, preorder position and subtree size
+    // bytes per node: 3 B) plus its int64 flows (8 B per node).  The flows
+    // are the tree's basic solution for the pair's marginals, which the
+    // rounds do not change, so when the whole store does not fit only the
+    // trees are kept and a reload recomputes the flows exactly (slower per
+    // pair than reading them back, so only then).
     d2k::WarmStore ws{nullptr, nullptr, nullptr, nullptr, 0, 0};
     const long long npairs = n_l * (long long)K;
     const int ns = cur_mmax + c->nmax;
     const size_t meta_bytes = (size_t)npairs * ns * 3;
     const size_t flow_bytes = (size_t)npairs * ns * 8;
     // (not with Alg. 1 updates: the weights, so every pair's supplies, change each round)
-    if (cfg.mode == 1 && iters > 1 && !alg1 && meta_bytes + flow_bytes <= kWarmBudgetBytes) {
+    const size_t budget = (cfg.mode == 1 && iters > 1 && !alg1) ? warm_budget_bytes(c) : 0;
+    // (a certify-all level keeps full bases or none: its screening kernel
+    // carries no flow recomputation)
+    const bool flows = meta_bytes + flow_bytes <= budget;
+    if (flows || (meta_bytes <= budget && !cfg.certify)) {
       unsigned char* meta = static_cast<unsigned char*>(grow(c, kWarmMeta, meta_bytes, &rc));
-      long long* wf = static_cast<long long*>(grow(c, kWarmFlow, flow_bytes, &rc));
+      long long* wf = flows ? static_cast<long long*>(grow(c, kWarmFlow, flow_bytes, &rc)) : nullptr;
       if (rc != D2_OK) return rc;
-      ws = d2k::WarmStore{meta, meta + (size_t)npairs * ns, meta + (size_t)npairs * ns * 2, wf, ns, 0};
+      ws = d2k::WarmStore{meta, meta + (size_t)npairs * ns, meta + (size_t)npairs * ns * 2, wf, ns,
+                          0};
     }
     Bins bins;
     if (want_bins(c, n_l, cur_mmax) && (rc = make_bins(c, cur, c->nmax, &bins))) return rc;

@@ -51,8 +51,9 @@ struct FlowOut {
 
 // Saved optimal bases of every (object, centroid) pair of an assign call,
 // pair t = i*K + j, node y at [t*ns + y]: parent / position / size bytes and
-// int64 flow.  `warm`: the arrays hold bases saved by a previous call on the
-// same pairs (same marginals), so solves start from them.
+// int64 flow (flow == nullptr: trees only, the flows recomputed from the
+// marginals on reload).  `warm`: the arrays hold bases saved by a previous
+// call on the same pairs (same marginals), so solves start from them.
 struct WarmStore {
   unsigned char* par8;
   unsigned char* pos8;

@@ -1076,9 +1076,13 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       // certify-all level never skips a pair, so its warm rounds always
       // find one)
       const bool fresh = cold || (!CERT && ws.sz8[wt] == 0);
-      // warm bases carry their flows (the larger instantiations load Q
-      // regardless: fewer live values across the solve)
-      if (fresh || NPL > 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
+      // warm bases saved with their flows need no Q (the larger
+      // instantiations load it regardless: fewer live values across the
+      // solve); bases saved as trees only (never in certify-all levels,
+      // whose kernel carries no code for them) recompute their flows from it
+      constexpr bool kTreeOnly = !CERT;
+      const bool tree_only = kTreeOnly && !ws.flow;
+      if (fresh || NPL > 1 || tree_only) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
       float cmax;
       float* tile_g = nullptr;  // the pair's block of the chunk's tile (TC)
       if constexpr (TC) {
@@ -1094,7 +1098,12 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       if constexpr (TC) S.set_cost(tile_g, (int)cfg.tile.ldc);
       int st;
       if (!fresh) {
-        S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+        if (kTreeOnly && tree_only) {
+          S.template load_tree<false>(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, nullptr);
+          S.recompute_flows();  // the same marginals: the saved flows, exactly
+        } else {
+          S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+        }
       } else if (!CERT && !cold) {
         S.init_northwest();  // warm round, no saved basis (the object's order was not built)
       } else if constexpr (vogel) {
@@ -1107,10 +1116,11 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5)) k_screen(ObjView ob, 
       if (ws.par8) {
         // always leave a valid basis for the next round
         if (st == kStInvalid) {
-          if (!fresh && NPL == 1) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
+          if (!fresh && NPL == 1 && !tree_only) load_cent_prefix<G>(g, cv, c0, n, s32.Q);
           S.init_northwest();
         }
-        S.store_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+        if (kTreeOnly && tree_only) S.template store_tree<false>(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, nullptr);
+        else S.store_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
       }
       ++n_scr;
       float lo, hi;
@@ -1298,7 +1308,13 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
           Simplex<double, G, NPL> S(s64, m, n, g);
           if (ws.par8) {
             const long long wt = (i * (long long)K + j) * ws.ns;
-            S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+            if (ws.flow) {
+              S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+            } else {
+              load_cent_prefix<G>(g, cv, c0, n, s64.Q);
+              S.template load_tree<false>(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, nullptr);
+              S.recompute_flows();
+            }
           } else {
             double D;
             const int s2 = solve_exact<G, NPL, ST>(g, s64, S, ob, o0, m, cv, c0, n, cfg.budget,
@@ -1329,7 +1345,12 @@ __global__ void __launch_bounds__(128) k_exact(ObjView ob, CentView cv, long lon
                                                cv.loc64 + c0, cv.tab64, cv.A)
                    : build_cost<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
                                            cv.loc64 + c0 * cv.d, cv.d);
-          S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+          if (ws.flow) {
+            S.load_tree(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, ws.flow + wt);
+          } else {
+            S.template load_tree<false>(ws.par8 + wt, ws.pos8 + wt, ws.sz8 + wt, nullptr);
+            S.recompute_flows();
+          }
           s2 = S.run(cfg.budget * (m + n), tol64(cmax), &p_ex);
           D = S.template objective<double>();
         } else {

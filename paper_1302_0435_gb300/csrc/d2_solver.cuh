@@ -1263,7 +1263,9 @@ struct Simplex {
   }
 
   // Saved basis of one pair: per node parent, preorder position, subtree
-  // size (bytes) and edge flow, at [y] of arrays with room for N nodes.
+  // size (bytes) and edge flow (WITH_FLOW false: the tree only), at [y] of
+  // arrays with room for N nodes.
+  template <bool WITH_FLOW = true>
   __device__ __forceinline__ void store_tree(unsigned char* par8, unsigned char* pos8,
                                              unsigned char* sz8, long long* flow) const {
 #pragma unroll
@@ -1273,12 +1275,14 @@ struct Simplex {
         par8[y] = (unsigned char)(t.par[k] & 0xff);  // root: 255, recognised by pos 0
         pos8[y] = (unsigned char)t.pos[k];
         sz8[y] = (unsigned char)t.sz[k];
-        flow[y] = t.flow[k];
+        if constexpr (WITH_FLOW) flow[y] = t.flow[k];
       }
     }
   }
   // Restore a saved basis (the marginals must be those it was saved with,
-  // so its flows are still the basic solution).
+  // so its flows are still the basic solution).  WITH_FLOW false: the tree
+  // only; the caller recomputes the flows (recompute_flows).
+  template <bool WITH_FLOW = true>
   __device__ __forceinline__ void load_tree(const unsigned char* par8, const unsigned char* pos8,
                                             const unsigned char* sz8, const long long* flow) {
     int r0 = INT_MAX;
@@ -1289,7 +1293,8 @@ struct Simplex {
         t.pos[k] = pos8[y];
         t.par[k] = t.pos[k] == 0 ? -1 : (int)par8[y];
         t.sz[k] = sz8[y];
-        t.flow[k] = flow[y];
+        if constexpr (WITH_FLOW) t.flow[k] = flow[y];
+        else t.flow[k] = 0LL;
         s.pos[y] = t.pos[k];
         s.sz[y] = t.sz[k];
         if (t.pos[k] == 0) r0 = y;

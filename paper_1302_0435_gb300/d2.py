@@ -47,7 +47,8 @@ class D2Config(ctypes.Structure):
                 ("eps_tol", ctypes.c_double), ("centroid_update", ctypes.c_int32),
                 ("joint_max_iter", ctypes.c_int32), ("joint_tol", ctypes.c_double),
                 ("certify", ctypes.c_int32), ("tc_wait_probe", ctypes.c_int32),
-                ("no_prune", ctypes.c_int32), ("joint_cold_start", ctypes.c_int32)]
+                ("no_prune", ctypes.c_int32), ("joint_cold_start", ctypes.c_int32),
+                ("warm_budget_mib", ctypes.c_int32)]
 
 
 class D2Flows(ctypes.Structure):
@@ -194,13 +195,13 @@ class Context:
                  segmentation=D2_SEG_SLICES, split_iters=0, eps_tol=0.0,
                  centroid_update=D2_UPDATE_CONSTRAINED, joint_max_iter=0, joint_tol=0.0,
                  certify=D2_CERTIFY_CANDIDATES, tc_wait_probe=0, no_prune=False,
-                 joint_cold_start=False):
+                 joint_cold_start=False, warm_budget_mib=0):
         lib = load()
         self.h = ctypes.c_void_p()
         cfg = D2Config(precision, pivot_budget, group_lanes, cost_tc, tile_budget_mib, start_rule,
                        segmentation, split_iters, float(eps_tol), int(centroid_update),
                        int(joint_max_iter), float(joint_tol), int(certify), int(tc_wait_probe),
-                       int(bool(no_prune)), int(bool(joint_cold_start)))
+                       int(bool(no_prune)), int(bool(joint_cold_start)), int(warm_budget_mib))
         _check(lib.d2_ctx_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)), "d2_ctx_create")
         self._cents = None
 

@@ -153,3 +153,20 @@ def test_ten_rounds_invariants_and_repeatability(d2, segment):
     assert np.isfinite(loc).all()
     for x, y in zip(a, b):  # the graph-replayed warm rounds are deterministic
         assert np.array_equal(x, y)
+
+
+def test_tree_only_warm_store_is_bitwise_the_full_one(d2, segment):
+    """A warm-store budget that holds the bases' trees but not their flows
+    (3 of 11 bytes per node) recomputes the flows from the marginals on
+    reload: the level's centroids, weights and labels are bitwise those of
+    the full store."""
+    objs, cents = segment
+    out = {}
+    # full store: 5,000 x 64 pairs x 32 nodes x 11 B = 113 MB; trees 31 MB
+    for mib in (0, 64):
+        ctx = d2.Context(0, warm_budget_mib=mib, no_prune=True)
+        d2.d2_set_centroids(ctx, d2.bags_from_synth(cents, device="cuda:0"))
+        out[mib] = _level(d2, ctx, objs, 6)
+        ctx.close()
+    for a, b in zip(out[0], out[64]):
+        assert np.array_equal(a, b)

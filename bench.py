@@ -686,7 +686,8 @@ def run_ours(args):
 
     serve = None
     if not args.skip_serve:
-        serve = serve_measure(dev, n_requests=args.serve_requests, lam_fracs=(0.5, 0.8, 0.95))
+        serve = serve_measure(dev, n_requests=args.serve_requests, lam_fracs=(0.5, 0.8, 0.95),
+                              n_warm=args.serve_warmup)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -708,14 +709,16 @@ def run_ours(args):
     return 0
 
 
-def serve_measure(dev, n_requests=150, lam_fracs=(0.8,), n_sat=24, seed=1005):
+def serve_measure(dev, n_requests=150, lam_fracs=(0.8,), n_sat=24, seed=1005, n_warm=0):
     """Serving workload: Poisson arrivals of assignment requests (log-uniform
     1-4096 bags of 4-64 supports, d=32) against K=1024 resident centroids of
     32 supports, through the continuous-batching server.  Saturated
-    throughput comes from a burst of n_sat requests; then requests arrive at
-    lam_frac of the saturated request rate and each one's submit-to-done
-    latency is recorded.  The plain one-pair-per-launch GPU form
-    (d2_mallows_batch with one pair per call) is timed beside it."""
+    throughput comes from a burst of n_sat requests; then, per load level,
+    n_warm + n_requests requests arrive at lam_frac of the saturated request
+    rate and the submit-to-done latency of the last n_requests is recorded
+    (the first n_warm bring the queue to its steady state).  The plain
+    one-pair-per-launch GPU form (d2_mallows_batch with one pair per call)
+    is timed beside it."""
     import torch
     from paper_1302_0435_gb300 import d2, synth
     cents, means = synth.serving_centroids(K=1024, seed=seed)
@@ -746,40 +749,45 @@ def serve_measure(dev, n_requests=150, lam_fracs=(0.8,), n_sat=24, seed=1005):
            "saturated_pairs_per_s": sat_pairs, "saturated_requests_per_s": sat_rps, "levels": []}
     for frac in lam_fracs:
         lam = frac * sat_rps
-        reqs = [d2.bags_from_synth(synth.serving_request(rng, means)) for _ in range(n_requests)]
-        offered = sum(b.count for b in reqs) * K
-        gaps = rng.exponential(1.0 / lam, size=n_requests)
+        n_all = n_warm + n_requests
+        reqs = [d2.bags_from_synth(synth.serving_request(rng, means)) for _ in range(n_all)]
+        offered = sum(b.count for b in reqs[n_warm:]) * K
+        gaps = rng.exponential(1.0 / lam, size=n_all)
         lat = []
         tickets = []
         done = threading.Event()
+        t_meas = [None, None]  # submit time of the first measured request, last completion
 
         def poller():
             i = 0
-            while i < n_requests:
+            while i < n_all:
                 while len(tickets) <= i:
                     time.sleep(0.0002)
                 rc, _, _, ms = srv.poll(tickets[i])
                 lat.append(ms)
                 i += 1
+            t_meas[1] = time.perf_counter()
             done.set()
         th = threading.Thread(target=poller, daemon=True)
         th.start()
-        t_start = time.perf_counter()
-        nxt = t_start
-        for b, gap in zip(reqs, gaps):
+        nxt = time.perf_counter()
+        for q, (b, gap) in enumerate(zip(reqs, gaps)):
             nxt += gap
             wait = nxt - time.perf_counter()
             if wait > 0:
                 time.sleep(wait)
+            if q == n_warm:
+                t_meas[0] = time.perf_counter()
             tickets.append(srv.submit(b))
         done.wait()
-        wall = time.perf_counter() - t_start
-        lat = np.array(lat)
-        out["levels"].append({"lambda_frac": frac, "requests": n_requests,
+        wall = t_meas[1] - t_meas[0]
+        lat = np.array(lat[n_warm:])
+        out["levels"].append({"lambda_frac": frac, "warmup_requests": n_warm,
+                              "requests": n_requests,
                               "offered_pairs": int(offered), "lambda_per_s": lam,
                               "p50_ms": float(np.percentile(lat, 50)),
                               "p99_ms": float(np.percentile(lat, 99)),
-                              "pairs_per_s": sum(b.count for b in reqs) * K / wall})
+                              "pairs_per_s": offered / wall})
     srv.close()
     # plain form: one pair per launch
     one = synth.serving_request(rng, means, size=64)
@@ -891,8 +899,10 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-workloads", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=1000,
-                    help="requests per load level of the serving sweep")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="measured requests per load level of the serving sweep")
+    ap.add_argument("--serve-warmup", type=int, default=200,
+                    help="requests per load level before the measured ones (same arrival law)")
     ap.add_argument("--profile", action="store_true", help="small case for ncu")
     ap.add_argument("--profile-n", type=int, default=20000)
     ap.add_argument("--certify", action="store_true", help="profile case: D2_CERTIFY_ALL")

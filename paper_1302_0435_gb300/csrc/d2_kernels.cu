@@ -297,16 +297,15 @@ cudaError_t prep_centroids(const void* loc, int ldt, const void* w, int wdt, con
   return cudaGetLastError();
 }
 
-// Lane-group shape for supports up to (mmax, nmax): G lanes per pair, each
-// owning NPL tree nodes (m+n <= G*NPL).
+// Tree shape for supports up to (mmax, nmax): one warp (G = 32 lanes) per
+// pair, each lane owning NPL tree nodes (m+n <= 32*NPL).
 #define D2_BINS(X) \
   X(32, 1)         \
   X(32, 2)         \
   X(32, 3)         \
   X(32, 4)
 
-static bool pick_shape(int mmax, int nmax, int want, int* G, int* npl) {
-  (void)want;
+static bool pick_shape(int mmax, int nmax, int* G, int* npl) {
   const int N = mmax + nmax;
   if (N > 128) return false;
   *G = 32;
@@ -319,7 +318,7 @@ cudaError_t mallows_pairs(const ObjView& ob, const CentView& cv, const long long
                           double* dist2, FlowOut fo, int* status, int* d_err, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   int G, NP;
-  if (!pick_shape(cfg.mmax, cfg.nmax, cfg.group, &G, &NP)) return cudaErrorInvalidValue;
+  if (!pick_shape(cfg.mmax, cfg.nmax, &G, &NP)) return cudaErrorInvalidValue;
 #define X(g_, n_)                                                                          \
   if (G == g_ && NP == n_)                                                                \
     return mallows_pairs_npl##n_(ob, cv, pobj, pcen, npairs, cfg, dist2, fo, status, d_err, st);
@@ -334,7 +333,7 @@ cudaError_t assign(const ObjView& ob, const CentView& cv, long long seg_size, in
                    const WarmStore* ws, const TcWork* tw) {
   if (ob.count <= 0) return cudaSuccess;
   int G, NP;
-  if (!pick_shape(cfg.mmax, cfg.nmax, cfg.group, &G, &NP)) return cudaErrorInvalidValue;
+  if (!pick_shape(cfg.mmax, cfg.nmax, &G, &NP)) return cudaErrorInvalidValue;
 #define X(g_, n_)                                                                            \
   if (G == g_ && NP == n_)                                                                  \
     return assign_npl##n_(ob, cv, seg_size, K, cfg, omega, labels, dist2, eps_terms, fo, cand, d_err, st, ws, tw);

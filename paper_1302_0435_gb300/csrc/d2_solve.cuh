@@ -393,6 +393,29 @@ __device__ __forceinline__ int solve_exact(const Grp<G>& g, const PairMem<double
   return st;
 }
 
+// FP64 ground cost of cell (a, r) of a pair, by explicit differences in
+// coordinate order (the arithmetic of build_cost<double>, so the same value
+// as the FP64 tile's cell); the table entry with symbol ground costs.
+__device__ __forceinline__ double cost64_cell(const ObjView& ob, long long o0, const CentView& cv,
+                                              long long c0, int a, int r) {
+  if (cv.A) {  // ids checked before the launch; the clamp only keeps reads in the table
+    int xs = (int)ldx<double>(ob.loc, ob.ldt, o0 + a);
+    int ys = (int)cv.loc64[c0 + r];
+    xs = xs < 0 ? 0 : (xs >= cv.A ? cv.A - 1 : xs);
+    ys = ys < 0 ? 0 : (ys >= cv.A ? cv.A - 1 : ys);
+    return cv.tab64[xs * cv.A + ys];
+  }
+  const int d = cv.d;
+  const double* y = cv.loc64 + (c0 + r) * d;
+  const long long x0 = (o0 + a) * d;
+  double acc = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const double df = ldx<double>(ob.loc, ob.ldt, x0 + k) - y[k];
+    acc = fma(df, df, acc);
+  }
+  return acc;
+}
+
 // -------------------------------------------------------------- kernels --
 
 template <int G, int NPL, int ST>
@@ -478,12 +501,16 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5))
           // same tree, flows for the new centroid weights, dual pivots to
           // feasibility, then the primal run
           const long long wi = i * (long long)cfg.jw.ns;
+          bool same = false;  // restarted, and no pivot moved the saved tree
           if (cfg.jw.par8 && m + n <= cfg.jw.ns && cfg.jw.sz8[wi] != 0) {
             S32.load_tree(cfg.jw.par8 + wi, cfg.jw.pos8 + wi, cfg.jw.sz8 + wi, cfg.jw.flow + wi);
             if (S32.tree_sane()) {
               S32.recompute_flows();
-              st = S32.run_dual(cfg.budget * (m + n), &n_piv);
-              if (st == kStOk) st = S32.run(cfg.budget * (m + n), tol32(c32), &n_piv);
+              int pw = 0;
+              st = S32.run_dual(cfg.budget * (m + n), &pw);
+              if (st == kStOk) st = S32.run(cfg.budget * (m + n), tol32(c32), &pw);
+              n_piv += pw;
+              same = st == kStOk && pw == 0;
             }
             if (st != kStOk) {  // start over cold
               S32.bad = false;
@@ -504,6 +531,7 @@ __global__ void __launch_bounds__(128, (NPL <= 1 ? 8 : 5))
             const long long wt = t * tr.ns;
             S32.store_tree(tr.par8 + wt, tr.pos8 + wt, tr.sz8 + wt, tr.flow + wt);
           }
+          if (same) st = kStSameBasis;
         }
       }
     }
@@ -537,16 +565,37 @@ __global__ void __launch_bounds__(128) k_pairs64(ObjView ob, CentView cv, const 
       const PairMem<double> s64 = carve<double>(base, cfg.mmax, cfg.nmax, cv.d);
       if (load_obj_prefix<G>(g, ob, o0, m, s64.P)) {
         load_cent_prefix<G>(g, cv, c0, n, s64.Q);
-        const double cmax =
-            cv.A ? build_cost_tab<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
-                                             cv.loc64 + c0, cv.tab64, cv.A)
-                 : build_cost<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
-                                         cv.loc64 + c0 * cv.d, cv.d);
         Simplex<double, G, NPL> S(s64, m, n, g);
         const long long wt = t * tr.ns;
-        S.load_tree(tr.par8 + wt, tr.pos8 + wt, tr.sz8 + wt, tr.flow + wt);
-        S.bad = false;
-        st = S.run(cfg.budget * (m + n), tol64(cmax), &n_piv);
+        if (st32[t] == kStSameBasis) {
+          // the tree the previous round proved FP64-optimal, unchanged (same
+          // costs, so the same reduced costs): only its basic cells' costs
+          // are needed, for the potentials and the objective
+          S.load_tree(tr.par8 + wt, tr.pos8 + wt, tr.sz8 + wt, tr.flow + wt);
+#pragma unroll
+          for (int k = 0; k < NPL; ++k) {
+            const int y = S.node_of(k);
+            if (y < S.N && y != S.root) {
+              const int p = S.t.par[k];
+              if (p >= 0 && p < S.N && (y < m) != (p < m)) {
+                const int a = y < m ? y : p, r = y < m ? p - m : y - m;
+                s64.cost[S.edge_idx(y, p)] = cost64_cell(ob, o0, cv, c0, a, r);
+              }
+            }
+          }
+          g.sync();
+          S.refresh_potentials();
+          st = S.bad ? kStInvalid : kStOk;
+        } else {
+          const double cmax =
+              cv.A ? build_cost_tab<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
+                                               cv.loc64 + c0, cv.tab64, cv.A)
+                   : build_cost<double, G>(g, s64.cost, m, n, ob.loc, ob.ldt, o0,
+                                           cv.loc64 + c0 * cv.d, cv.d);
+          S.load_tree(tr.par8 + wt, tr.pos8 + wt, tr.sz8 + wt, tr.flow + wt);
+          S.bad = false;
+          st = S.run(cfg.budget * (m + n), tol64(cmax), &n_piv);
+        }
         res = S.template objective<double>();
         ++n_pairs;
         if (fo.cell && st != kStInvalid)
@@ -652,29 +701,6 @@ __device__ __forceinline__ float tc_bound(int d, float nxm, float cn, float cd) 
   const float e1 = rel * (nxm + cn);
   const float e2 = (2.f * (sqrtf(nxm) + sqrtf(cn)) + 2.f * cd) * cd;
   return (e1 + e2) * (1.f + 0x1p-10f);
-}
-
-// FP64 ground cost of cell (a, r) of a pair, by explicit differences in
-// coordinate order (the arithmetic of build_cost<double>, so the same value
-// as the FP64 tile's cell); the table entry with symbol ground costs.
-__device__ __forceinline__ double cost64_cell(const ObjView& ob, long long o0, const CentView& cv,
-                                              long long c0, int a, int r) {
-  if (cv.A) {  // ids checked before the launch; the clamp only keeps reads in the table
-    int xs = (int)ldx<double>(ob.loc, ob.ldt, o0 + a);
-    int ys = (int)cv.loc64[c0 + r];
-    xs = xs < 0 ? 0 : (xs >= cv.A ? cv.A - 1 : xs);
-    ys = ys < 0 ? 0 : (ys >= cv.A ? cv.A - 1 : ys);
-    return cv.tab64[xs * cv.A + ys];
-  }
-  const int d = cv.d;
-  const double* y = cv.loc64 + (c0 + r) * d;
-  const long long x0 = (o0 + a) * d;
-  double acc = 0.0;
-  for (int k = 0; k < d; ++k) {
-    const double df = ldx<double>(ob.loc, ob.ldt, x0 + k) - y[k];
-    acc = fma(df, df, acc);
-  }
-  return acc;
 }
 
 // ---- double-float arithmetic (an unevaluated sum hi + lo of two floats,

@@ -40,6 +40,10 @@ constexpr long long kMass = 1LL << 62;       // fixed-point unit of one bag's ma
 constexpr double kInvMass = 1.0 / 4611686018427387904.0;  // 2^-62
 
 enum : int { kStOk = 0, kStNotConverged = 1, kStInvalid = 2 };
+// Hand-over code of the two-launch exact solve: the FP32 launch restarted a
+// pair from the basis the FP64 launch proved optimal in the previous joint
+// round and needed no pivot, so that tree is still FP64-optimal.
+enum : int { kStSameBasis = 3 };
 
 template <int G>
 struct Grp {

@@ -202,7 +202,7 @@ struct Master {
   const JointView& jv;
   long long j;
   int n, G, R, nk;
-  double S;
+  double S, iS;  // the scale (a power of two) and its exact reciprocal
   double *Binv, *aug, *col, *y, *xB, *cB, *fac, *row;
   float* y32;
   int* bvar;
@@ -250,7 +250,7 @@ struct Master {
   __device__ double cost(int v) const {
     if (v == kNu) return 1.0;
     if (v >= kSig) return 0.0;
-    return cutb(v) / S;
+    return cutb(v) * iS;
   }
   __device__ int flag(int v) const { return v >= kSig ? nk * G + (v - kSig) : v; }
   __device__ bool basic(int f) const { return (inB[f >> 5] >> (f & 31)) & 1u; }
@@ -263,7 +263,7 @@ struct Master {
     if (v == kNu) return i >= G ? 1.0 : 0.0;
     if (v >= kSig) return i == G + (v - kSig) ? 1.0 : 0.0;
     if (i < G) return i == v % G ? 1.0 : 0.0;
-    return -cut(v)[i - G] / S;
+    return -cut(v)[i - G] * iS;
   }
   // reduced cost of nonbasic flag e (mu or sigma) and its variable id
   __device__ double reduced(int e, int* v) const {
@@ -279,7 +279,7 @@ struct Master {
       }
       for (; r < n; ++r) s0 += y[G + r] * a[r];
       *v = e;
-      return (cutb(e) + ((s0 + s1) + (s2 + s3))) / S - y[e % G];
+      return (cutb(e) + ((s0 + s1) + (s2 + s3))) * iS - y[e % G];
     }
     *v = kSig + (e - nk * G);
     return -y[G + (e - nk * G)];
@@ -293,15 +293,30 @@ struct Master {
       cB[i] = cost(bvar[i]);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < R; i += blockDim.x) {
-      double s0 = 0.0, s1 = 0.0;
-      int l = 0;
-      for (; l + 2 <= R; l += 2) {
-        s0 += cB[l] * Binv[l * R + i];
-        s1 += cB[l + 1] * Binv[(l + 1) * R + i];
-      }
-      if (l < R) s0 += cB[l] * Binv[l * R + i];
-      y[i] = s0 + s1;
+    matvec<true>(cB, y);
+  }
+  // out = Binv * v (TRANS false) or out = v * Binv (TRANS true), R x R in
+  // FP64: P = blockDim/R threads per output entry each sum a slice of the
+  // products (so every warp, on every SM sub-partition, shares the FP64
+  // work), then one thread per entry adds the P partial sums in order.  The
+  // partials use aug, which only refactor needs.  Ends synchronised.
+  template <bool TRANS>
+  __device__ void matvec(const double* v, double* out) {
+    // >= 3 (R <= kMaxJointR); at most 2R, so the P*R partials fit in aug (2 R^2)
+    const int P = min((int)blockDim.x / R, 2 * R);
+    const int t = threadIdx.x;
+    if (t < P * R) {
+      const int i = t / P, pp = t - i * P;
+      const int l0 = pp * R / P, l1 = (pp + 1) * R / P;
+      double s0 = 0.0;
+      for (int l = l0; l < l1; ++l) s0 += (TRANS ? Binv[l * R + i] : Binv[i * R + l]) * v[l];
+      aug[t] = s0;
+    }
+    __syncthreads();
+    for (int i = t; i < R; i += blockDim.x) {
+      double s = 0.0;
+      for (int pp = 0; pp < P; ++pp) s += aug[i * P + pp];
+      out[i] = s;
     }
     __syncthreads();
   }
@@ -309,14 +324,16 @@ struct Master {
   // a zero factor are skipped: B is mostly unit and 0/1 columns).
   __device__ bool refactor() {
     const int W2 = 2 * R;
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-      const int i = e / R, l = e - i * R;
-      aug[i * W2 + l] = entry(bvar[l], i);
-      aug[i * W2 + R + l] = i == l ? 1.0 : 0.0;
-    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < R; i += nw)
+      for (int l = lane; l < R; l += 32) {
+        aug[i * W2 + l] = entry(bvar[l], i);
+        aug[i * W2 + R + l] = i == l ? 1.0 : 0.0;
+      }
     __syncthreads();
     __shared__ int piv_s;
     __shared__ int ok_s;
+    __shared__ double inv_s;
     __shared__ double pv_s[kMT / 32];
     __shared__ int pi_s[kMT / 32];
     if (threadIdx.x == 0) ok_s = 1;
@@ -353,22 +370,23 @@ struct Master {
           aug[pr * W2 + e] = t;
         }
       __syncthreads();
-      const double inv = 1.0 / aug[c * W2 + c];
+      if (threadIdx.x == 0) inv_s = 1.0 / aug[c * W2 + c];  // one division, shared
       for (int i = threadIdx.x; i < R; i += blockDim.x) fac[i] = aug[i * W2 + c];
       __syncthreads();
+      const double inv = inv_s;
       for (int e = threadIdx.x; e < W2; e += blockDim.x) aug[c * W2 + e] *= inv;
       __syncthreads();
-      for (int e = threadIdx.x; e < R * W2; e += blockDim.x) {
-        const int i = e / W2, k = e - i * W2;
+      // a warp per row; rows with a zero factor (most: B is mostly unit
+      // and 0/1 columns) are skipped whole
+      for (int i = warp; i < R; i += nw) {
         const double f = fac[i];
-        if (i != c && f != 0.0) aug[e] -= f * aug[c * W2 + k];
+        if (i == c || f == 0.0) continue;
+        for (int k = lane; k < W2; k += 32) aug[i * W2 + k] -= f * aug[c * W2 + k];
       }
       __syncthreads();
     }
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-      const int i = e / R, k = e - i * R;
-      Binv[e] = aug[i * W2 + R + k];
-    }
+    for (int i = warp; i < R; i += nw)
+      for (int k = lane; k < R; k += 32) Binv[i * R + k] = aug[i * W2 + R + k];
     __syncthreads();
     basics();
     return true;
@@ -461,6 +479,7 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
   const int nk = kk + 1;
   __shared__ double S_s, sd[kMT / 32], dq_s;
   __shared__ int sv[kMT / 32], enter_s, leave_s, state_s;
+  __shared__ double inva_s;
   // incumbent
   const double F = jv.F[j];
   const bool better = F < jv.ub[j];
@@ -476,7 +495,10 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
         const double* a0 = jv.cutA + ((size_t)j * jv.itmax * G + g) * jv.nmax;
         for (int r = 0; r < n; ++r) S = fmax(S, fabs(a0[r]));
       }
-      jv.scale[j] = S > 0.0 ? S : 1.0;
+      // a power of two >= the largest magnitude: scaling by it is exact
+      int ex = 0;
+      frexp(S, &ex);
+      jv.scale[j] = S > 0.0 ? ldexp(1.0, ex) : 1.0;
     }
     S_s = jv.scale[j];
     jv.nk[j] = nk;
@@ -484,13 +506,14 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
   __syncthreads();
   Master M(jv, j, n, nk, sm);
   M.S = S_s;
+  M.iS = 1.0 / S_s;  // exact: S is a power of two
   const int R = M.R;
   // FP32 copies of this round's cuts, scaled (the pricing filter reads them)
   for (int e = threadIdx.x; e < G * (n + 1); e += blockDim.x) {
     const int g = e / (n + 1), c = e - g * (n + 1);
     const int id = kk * G + g;
-    if (c < n) jv.cutA32[((size_t)j * jv.itmax * G + id) * jv.nmax + c] = (float)(M.cut(id)[c] / M.S);
-    else jv.cutB32[(size_t)j * jv.itmax * G + id] = (float)(M.cutb(id) / M.S);
+    if (c < n) jv.cutA32[((size_t)j * jv.itmax * G + id) * jv.nmax + c] = (float)(M.cut(id)[c] * M.iS);
+    else jv.cutB32[(size_t)j * jv.itmax * G + id] = (float)(M.cutb(id) * M.iS);
   }
   int* bv_g = jv.bvar + (size_t)j * (jv.G + jv.nmax);
   double* bi_g = jv.binv + (size_t)j * (jv.G + jv.nmax) * (jv.G + jv.nmax);
@@ -569,17 +592,7 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
     const double dq = dq_s;
     for (int i = threadIdx.x; i < R; i += blockDim.x) M.col[i] = M.entry(q, i);
     __syncthreads();
-    for (int i = threadIdx.x; i < R; i += blockDim.x) {  // alpha = Binv * col
-      double s0 = 0.0, s1 = 0.0;
-      int l = 0;
-      for (; l + 2 <= R; l += 2) {
-        s0 += M.Binv[i * R + l] * M.col[l];
-        s1 += M.Binv[i * R + l + 1] * M.col[l + 1];
-      }
-      if (l < R) s0 += M.Binv[i * R + l] * M.col[l];
-      M.fac[i] = s0 + s1;
-    }
-    __syncthreads();
+    M.matvec<false>(M.col, M.fac);  // alpha = Binv * col
     {  // ratio test over the basic rows (nu never leaves), block-wide
       double rt = INFINITY, al_ = 0.0;
       int lv = INT_MAX, vid = INT_MAX;
@@ -592,21 +605,31 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
         }
       }
       block_ratio(rt, al_, lv, vid, bland, sd, sv, &leave_s);
-      if (threadIdx.x == 0) state_s = leave_s == INT_MAX ? kJFail : kJActive;
+      if (threadIdx.x == 0) {
+        state_s = leave_s == INT_MAX ? kJFail : kJActive;
+        if (leave_s != INT_MAX) inva_s = 1.0 / M.fac[leave_s];  // one division, shared
+      }
       __syncthreads();
     }
     if (state_s != kJActive) { status = kJFail; break; }
     const int l = leave_s;
-    const double apiv = M.fac[l];
-    const double theta = (M.xB[l] > 0.0 ? M.xB[l] : 0.0) / apiv;
+    const double inva = inva_s;
+    const double theta = (M.xB[l] > 0.0 ? M.xB[l] : 0.0) * inva;
     for (int i = threadIdx.x; i < R; i += blockDim.x) {
       if (i != l) M.xB[i] -= theta * M.fac[i];
-      M.row[i] = M.Binv[l * R + i] / apiv;  // new row l of Binv
+      M.row[i] = M.Binv[l * R + i] * inva;  // new row l of Binv
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-      const int i = e / R, k = e - i * R;
-      M.Binv[e] = i == l ? M.row[k] : M.Binv[e] - M.fac[i] * M.row[k];
+    {  // a warp per row of Binv; a row with a zero factor keeps its values
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int i = warp; i < R; i += nw) {
+        const double f = M.fac[i];
+        if (i == l) {
+          for (int k = lane; k < R; k += 32) M.Binv[i * R + k] = M.row[k];
+        } else if (f != 0.0) {
+          for (int k = lane; k < R; k += 32) M.Binv[i * R + k] -= f * M.row[k];
+        }
+      }
     }
     for (int i = threadIdx.x; i < R; i += blockDim.x) M.y[i] += dq * M.row[i];
     __syncthreads();

@@ -465,16 +465,32 @@ int bins_to_host(d2_ctx* c, Bins* b) {
 
 // One assign over a batch, bin by bin (largest trees first), each bin with
 // its autotuned launch shape.  ws may be null.
+// Whether run_assign screens with pruning bits for these arguments.
+bool prunes(const d2_ctx* c, const SolveCfg& base, const CentView& cv) {
+  return base.mode == 1 && !base.certify && !base.pair64 && cv.A == 0 && !c->cfg.no_prune;
+}
+
+// The bags' means and spreads into the slots run_assign reads (the rounds
+// of a level reuse them: the bags do not change).
+int prune_moments(d2_ctx* c, const ObjView& v) {
+  int rc = D2_OK;
+  double* mu_o = static_cast<double*>(grow(c, kPrMuO, (size_t)v.count * v.d * 8, &rc));
+  double* var_o = static_cast<double*>(grow(c, kPrVarO, (size_t)v.count * 8, &rc));
+  if (rc != D2_OK) return rc;
+  CK(d2k::bag_moments(v, mu_o, var_o, c->stream));
+  return D2_OK;
+}
+
 int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, int K, int mode,
                int mmax, const double* om, int* lab, double* d2o, double* terms, FlowOut fo,
                int* cand, const d2k::WarmStore* ws, Bins& bins,
                const d2k::TcWork* tw = nullptr, bool certify_all = false,
-               double* pair64 = nullptr) {
+               double* pair64 = nullptr, bool obj_moments_ready = false) {
   const int nmax = std::max(c->nmax, 1);
   SolveCfg base = solve_cfg(c, mode, mmax);
   if (certify_all && mode == 1) base.certify = true;
   base.pair64 = pair64;
-  if (base.mode == 1 && !base.certify && !pair64 && cv.A == 0 && !c->cfg.no_prune) {
+  if (prunes(c, base, cv)) {
     // pairs whose lower bound is above their object's upper bound cannot be
     // the argmin: bounds from the bags' means and spreads, keep bits per object
     int rc = D2_OK;
@@ -485,7 +501,8 @@ int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, i
     double* var_c = static_cast<double*>(grow(c, kPrVarC, (size_t)cv.K * 8, &rc));
     unsigned* keep = static_cast<unsigned*>(grow(c, kPrKeep, (size_t)v.count * kw * 4, &rc));
     if (rc != D2_OK) return rc;
-    CK(d2k::bag_moments(v, mu_o, var_o, c->stream));
+    // (a level computes its bags' moments once: prune_moments)
+    if (!obj_moments_ready) CK(d2k::bag_moments(v, mu_o, var_o, c->stream));
     CK(d2k::cent_moments(cv, mu_c, var_c, c->stream));
     CK(d2k::prune_keep(v, seg, K, cv.K, v.d, mu_o, var_o, mu_c, var_c, keep, kw, c->stream));
     base.keep = keep;
@@ -1715,6 +1732,9 @@ int d2_cluster_level_ex(d2_ctx* c, const d2_bags* objs, const double* omega, int
     }
     Bins bins;
     if (want_bins(c, n_l, cur_mmax) && (rc = make_bins(c, cur, c->nmax, &bins))) return rc;
+    // the pruning moments of this level's bags, once for all its rounds
+    const bool moments = prunes(c, cfg, cv);
+    if (moments && (rc = prune_moments(c, cur))) return rc;
     // Rounds 2.. repeat the same launches (same pairs, warm bases): round 1
     // is captured into a CUDA graph once and replayed.
     cudaGraphExec_t gexec = nullptr;
@@ -1758,7 +1778,7 @@ int d2_cluster_level_ex(d2_ctx* c, const d2_bags* objs, const double* omega, int
       cudaStreamIsCapturing(c->stream, &cst);
       const bool capturing = cst == cudaStreamCaptureStatusActive;
       int rc2 = run_assign(c, cur, cv, seg, K, cfg.mode, cur_mmax, om, lab, ld2, lterms, fo, cand,
-                           ws.par8 ? &ws : nullptr, bins);
+                           ws.par8 ? &ws : nullptr, bins, nullptr, false, nullptr, moments);
       cudaError_t ue = cudaSuccess;
       if (rc2 == D2_OK && it < iters && alg1) {
         // Alg. 1 Step 1: support weights of every cluster of the level by the
@@ -1797,7 +1817,8 @@ int d2_cluster_level_ex(d2_ctx* c, const d2_bags* objs, const double* omega, int
           gexec = nullptr;
           // run the round directly instead
           if ((rc = run_assign(c, cur, cv, seg, K, cfg.mode, cur_mmax, om, lab, ld2, lterms, fo,
-                               cand, ws.par8 ? &ws : nullptr, bins)))
+                               cand, ws.par8 ? &ws : nullptr, bins, nullptr, false, nullptr,
+                               moments)))
             return rc;
           if (it < iters)
             CK(d2k::update_locations(cur, om, lab, seg, K, fo, KT, loff, d, c->cent_ldt, l32, l64,

@@ -42,7 +42,7 @@ enum Slot {
   kMbPair, kMbTmpLab, kMbTmpD2, kMbCnt, kMbStart, kMbPObj, kMbPCen, kMbD2, kMbSt,
   // joint weights (Alg. 1 Step 1)
   kJState, kJPot, kJPStart, kJEps, kJIters, kJSort, kJPObj, kJPCen, kJW, kJSt, kJTree,
-  kPairTree,
+  kPairTree, kPairTree2,
   // d2_mallows_all
   kAllLab, kAllD2, kAllPair,
   // pruning of pairs that cannot be the argmin
@@ -273,12 +273,12 @@ SolveCfg solve_cfg(const d2_ctx* c, int mode, int mmax) {
 
 // Room for the FP32 bases of a two-launch exact solve (SolveCfg::tree);
 // past 2 GiB the solve stays one fused launch.
-int attach_tree(d2_ctx* c, SolveCfg* cfg, long long npairs) {
+int attach_tree(d2_ctx* c, SolveCfg* cfg, long long npairs, int slot = kPairTree) {
   if (cfg->mode != 1 || npairs <= 0) return D2_OK;
   const size_t b = d2k::pair_tree_bytes(npairs, cfg->mmax, cfg->nmax);
   if (b > ((size_t)2 << 30)) return D2_OK;
   int rc = D2_OK;
-  void* p = grow(c, kPairTree, b, &rc);
+  void* p = grow(c, slot, b, &rc);
   if (rc != D2_OK) return rc;
   cfg->tree = static_cast<unsigned char*>(p);
   cfg->tree_bytes = b;
@@ -941,7 +941,7 @@ int d2_ctx_create(d2_ctx** out, int32_t device, const d2_config* cfg) {
       cudaStreamCreateWithFlags(&c->own, cudaStreamDefault) != cudaSuccess ||
       cudaMalloc(&c->d_err, 4 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->d_info, 4 * sizeof(int)) != cudaSuccess ||
-      cudaMallocHost(&c->h_pin, 8 * sizeof(int)) != cudaSuccess) {
+      cudaMallocHost(&c->h_pin, 16 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     d2_ctx_destroy(c);
     return D2_ECUDA;
@@ -1307,14 +1307,19 @@ int joint_core(d2_ctx* c, const ObjView& v, const double* om, const int* dl, lon
   const int nmax = std::max(c->nmax, 1);
   const int itmax = max_iter;
   const int G = d2k::joint_groups(nmax);
+  // the clusters in two halves, each with its own pair lists and stream: a
+  // half's member solves run while the other half's masters (one block per
+  // cluster) hold only some of the SMs
+  const int H = KT >= 2 ? 2 : 1;
+  const long long NB = std::max(N, 1LL);  // pair room per half
   void* scr = grow(c, kJSort, d2k::update_scratch_bytes(std::max(N, 1LL), KT), &rc);
   void* jmem = grow(c, kJState, d2k::joint_state_bytes(KT, cs.Tc, nmax, itmax, G), &rc);
-  long long* pobj = static_cast<long long*>(grow(c, kJPObj, (size_t)std::max(N, 1LL) * 8, &rc));
-  long long* pcen = static_cast<long long*>(grow(c, kJPCen, (size_t)std::max(N, 1LL) * 8, &rc));
-  double* W = static_cast<double*>(grow(c, kJW, (size_t)std::max(N, 1LL) * 8, &rc));
-  int* pst = static_cast<int*>(grow(c, kJSt, (size_t)std::max(N, KT) * 4, &rc));
-  double* pot = static_cast<double*>(grow(c, kJPot, (size_t)std::max(N, 1LL) * nmax * 8, &rc));
-  long long* pstart = static_cast<long long*>(grow(c, kJPStart, (size_t)(KT + 1) * 8, &rc));
+  long long* pobj = static_cast<long long*>(grow(c, kJPObj, (size_t)(H * NB) * 8, &rc));
+  long long* pcen = static_cast<long long*>(grow(c, kJPCen, (size_t)(H * NB) * 8, &rc));
+  double* W = static_cast<double*>(grow(c, kJW, (size_t)(H * NB) * 8, &rc));
+  int* pst = static_cast<int*>(grow(c, kJSt, (size_t)std::max(H * NB, KT) * 4, &rc));
+  double* pot = static_cast<double*>(grow(c, kJPot, (size_t)(H * NB) * nmax * 8, &rc));
+  long long* pstart = static_cast<long long*>(grow(c, kJPStart, (size_t)(KT + H) * 8, &rc));
   if (rc != D2_OK) return rc;
   const long long* start;
   const int* order;
@@ -1351,21 +1356,93 @@ int joint_core(d2_ctx* c, const ObjView& v, const double* om, const int* dl, lon
                             ns, 1};
     CK(cudaMemsetAsync(cfg.jw.sz8, 0, nodes, c->stream));
   }
-  long long* hP = reinterpret_cast<long long*>(c->h_pin + 4);
+  struct Half {
+    long long k0, k1;
+    d2k::JointView jv;
+    long long *pobj, *pcen, *pstart, *hP;
+    double *W, *pot;
+    int* pst;
+    SolveCfg cfg;
+    CentView cv;
+    FlowOut fo;
+    cudaStream_t s;
+    cudaEvent_t ev;
+    bool done;
+  };
+  // the second stream and the events live for this call only
+  struct Owned {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    ~Owned() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+      if (s) cudaStreamDestroy(s);
+    }
+  } own;
+  for (int h = 0; h < 3; ++h) CK(cudaEventCreateWithFlags(&own.e[h], cudaEventDisableTiming));
+  if (H > 1) {
+    CK(cudaStreamCreateWithFlags(&own.s, cudaStreamNonBlocking));
+    CK(cudaEventRecord(own.e[2], c->stream));  // the set-up above, then both halves
+    CK(cudaStreamWaitEvent(own.s, own.e[2], 0));
+  }
+  Half hf[2];
+  const long long kmid = H > 1 ? KT / 2 : KT;
+  for (int h = 0; h < H; ++h) {
+    Half& x = hf[h];
+    x.k0 = h == 0 ? 0 : kmid;
+    x.k1 = h == 0 ? kmid : KT;
+    x.jv = d2k::joint_sub(jv, x.k0, x.k1);
+    x.pobj = pobj + h * NB;
+    x.pcen = pcen + h * NB;
+    x.W = W + h * NB;
+    x.pot = pot + (size_t)(h * NB) * nmax;
+    x.pst = pst + h * NB;
+    x.pstart = pstart + (h == 0 ? 0 : kmid + 1);
+    x.hP = reinterpret_cast<long long*>(c->h_pin + 4 + 4 * h);
+    x.cfg = cfg;
+    x.cv = cv;
+    x.cv.off = cs.off + x.k0;  // the half's clusters as centroids 0 .. k1-k0-1
+    x.cv.K = x.k1 - x.k0;
+    x.fo = fo;
+    x.fo.pot = x.pot;
+    x.s = h == 0 ? c->stream : own.s;
+    x.ev = own.e[h];
+    x.done = false;
+  }
   for (int it = 0; it < itmax; ++it) {
     d2k::TraceRange round_("joint round");
-    if (it > 0)  // the weights chosen by the last master solve
-      CK(d2k::prep_centroids(cs.loc64, D2_F64, jv.wnext, D2_F64, cs.off, KT, c->d, cs.loc32,
-                             cs.loc64, cs.Q, cs.w64, c->d_err, c->stream));
-    CK(d2k::joint_list(jv, order, start, pstart, pobj, pcen, c->stream));
-    CK(cudaMemcpyAsync(hP, pstart + KT, 8, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    const long long P = *hP;
-    if (P == 0) break;
-    if ((rc = attach_tree(c, &cfg, P))) return rc;
-    CK(d2k::mallows_pairs(v, cv, pobj, pcen, P, cfg, W, fo, pst, c->d_err, c->stream));
-    CK(d2k::joint_round(jv, pstart, pobj, om, W, pot, nmax, pst, cs.off, cs.w64, c->stream));
+    for (int h = 0; h < H; ++h) {
+      Half& x = hf[h];
+      if (x.done) continue;
+      if (it > 0)  // the weights chosen by the half's last master solves
+        CK(d2k::prep_centroids(cs.loc64, D2_F64, jv.wnext, D2_F64, cs.off + x.k0, x.k1 - x.k0, c->d,
+                               cs.loc32, cs.loc64, cs.Q, cs.w64, c->d_err, x.s));
+      CK(d2k::joint_list(x.jv, order, start + x.k0, x.pstart, x.pobj, x.pcen, x.s));
+      CK(cudaMemcpyAsync(x.hP, x.pstart + (x.k1 - x.k0), 8, cudaMemcpyDeviceToHost, x.s));
+      CK(cudaEventRecord(x.ev, x.s));
+    }
+    bool any = false;
+    for (int h = 0; h < H; ++h) {
+      Half& x = hf[h];
+      if (x.done) continue;
+      CK(cudaEventSynchronize(x.ev));  // the other half keeps running meanwhile
+      const long long P = *x.hP;
+      if (P == 0) {
+        x.done = true;
+        continue;
+      }
+      any = true;
+      if ((rc = attach_tree(c, &x.cfg, P, h == 0 ? kPairTree : kPairTree2))) return rc;
+      CK(d2k::mallows_pairs(v, x.cv, x.pobj, x.pcen, P, x.cfg, x.W, x.fo, x.pst, c->d_err, x.s));
+      CK(d2k::joint_round(x.jv, x.pstart, x.pobj, om, x.W, x.pot, nmax, x.pst, cs.off + x.k0,
+                          cs.w64, x.s));
+    }
+    if (!any) break;
     d2k::joint_note(1, 0);
+  }
+  if (H > 1) {  // both halves done before the results are read
+    CK(cudaEventRecord(own.e[2], own.s));
+    CK(cudaStreamWaitEvent(c->stream, own.e[2], 0));
   }
   int* jst = pst;  // per-cluster status, reusing the pair status room
   CK(d2k::joint_finish(jv, cs.off, eps_d, it_d, jst, c->stream));

@@ -765,6 +765,31 @@ JointView joint_view(void* mem, long long K, long long Tc, int nmax, int itmax, 
   return v;
 }
 
+// The clusters [k0, k1) of a joint state as a state of their own: every
+// per-cluster array shifted by k0 (the per-support arrays keep their global
+// offsets, which the callers' coff + k0 supplies).
+JointView joint_sub(const JointView& v, long long k0, long long k1) {
+  JointView s = v;
+  const size_t G = (size_t)v.G, nm = (size_t)v.nmax, it = (size_t)v.itmax, R = G + nm;
+  const size_t k = (size_t)k0;
+  s.cutA += k * it * G * nm;
+  s.cutB += k * it * G;
+  s.cutA32 += k * it * G * nm;
+  s.cutB32 += k * it * G;
+  s.bvar += k * R;
+  s.binv += k * R * R;
+  s.since += k;
+  s.nk += k;
+  s.status += k;
+  s.F += k;
+  s.ub += k;
+  s.lb += k;
+  s.omsum += k;
+  s.scale += k;
+  s.K = k1 - k0;
+  return s;
+}
+
 cudaError_t joint_init(const JointView& jv, const long long* start, const long long* coff,
                        const double* w64, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(jv.pivots, 0, 8, st);

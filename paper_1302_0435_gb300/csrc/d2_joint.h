@@ -59,6 +59,7 @@ struct JointView {
 size_t joint_state_bytes(long long K, long long Tc, int nmax, int itmax, int G);
 JointView joint_view(void* mem, long long K, long long Tc, int nmax, int itmax, int G,
                      double tol);
+JointView joint_sub(const JointView& v, long long k0, long long k1);
 cudaError_t joint_init(const JointView& jv, const long long* start, const long long* coff,
                        const double* w64, cudaStream_t st);
 // pair list (object, cluster) of the active clusters; pstart [K+1]

@@ -294,6 +294,8 @@ struct Master {
     }
     __syncthreads();
     matvec<true>(cB, y);
+    for (int i = threadIdx.x; i < R; i += blockDim.x) y32[i] = (float)y[i];
+    __syncthreads();
   }
   // out = Binv * v (TRANS false) or out = v * Binv (TRANS true), R x R in
   // FP64: P = blockDim/R threads per output entry each sum a slice of the
@@ -395,74 +397,45 @@ struct Master {
 
 // Entering candidate of the block from each thread's (d, v): the largest d
 // (Dantzig; ties to the smaller id), or with bland the smallest id.
-// v == INT_MAX: no candidate.
+// v == INT_MAX: no candidate.  Candidates have d > 0, whose IEEE patterns
+// order like their values, so the warps reduce integer keys (the FP64
+// compares of a shuffle tree would each take the FP64 pipe).
 __device__ void block_pick(double d, int v, bool bland, double* sd, int* sv, int* out_v,
                            double* out_d) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    const double d2 = __shfl_down_sync(0xffffffffu, d, o);
-    const int v2 = __shfl_down_sync(0xffffffffu, v, o);
-    bool take;
-    if (v2 == INT_MAX) take = false;
-    else if (v == INT_MAX) take = true;
-    else if (bland) take = v2 < v;
-    else take = d2 > d || (d2 == d && v2 < v);
-    if (take) { d = d2; v = v2; }
+  const bool has = v != INT_MAX;
+  const unsigned long long key = has ? (unsigned long long)__double_as_longlong(d) : 0ull;
+  const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+  int vw;
+  unsigned long long kw;
+  if (bland) {
+    vw = __reduce_min_sync(0xffffffffu, has ? v : INT_MAX);
+    const unsigned owner = __ballot_sync(0xffffffffu, has && v == vw);
+    const long long k2 = __shfl_sync(0xffffffffu, (long long)key, owner ? __ffs(owner) - 1 : 0);
+    kw = owner ? (unsigned long long)k2 : 0ull;
+  } else {
+    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    vw = __reduce_min_sync(0xffffffffu, (has && hi == mh && lo == ml) ? v : INT_MAX);
+    kw = ((unsigned long long)mh << 32) | ml;
   }
-  if (lane == 0) { sd[warp] = d; sv[warp] = v; }
+  if (lane == 0) { sd[warp] = __longlong_as_double((long long)kw); sv[warp] = vw; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double bd = sd[0];
+    unsigned long long bk = (unsigned long long)__double_as_longlong(sd[0]);
     int bv = sv[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      const double d2 = sd[w];
+      const unsigned long long k2 = (unsigned long long)__double_as_longlong(sd[w]);
       const int v2 = sv[w];
       bool take;
       if (v2 == INT_MAX) take = false;
       else if (bv == INT_MAX) take = true;
       else if (bland) take = v2 < bv;
-      else take = d2 > bd || (d2 == bd && v2 < bv);
-      if (take) { bd = d2; bv = v2; }
+      else take = k2 > bk || (k2 == bk && v2 < bv);
+      if (take) { bk = k2; bv = v2; }
     }
     *out_v = bv;
-    *out_d = bd;
-  }
-  __syncthreads();
-}
-
-// Leaving-row order of the ratio test: the smaller ratio (within a relative
-// 1e-12), then the larger pivot element, or with bland the smaller
-// variable id.  vid == INT_MAX: no candidate yet.
-__device__ __forceinline__ bool ratio_better(double rt, double al, int vid, double r2, double a2,
-                                             int v2, bool bland) {
-  if (v2 == INT_MAX) return false;
-  if (vid == INT_MAX) return true;
-  const double eps = 1e-12 * (1.0 + rt);
-  if (r2 < rt - eps) return true;
-  if (r2 > rt + eps) return false;
-  return bland ? v2 < vid : a2 > al;
-}
-
-__device__ void block_ratio(double rt, double al, int lv, int vid, bool bland, double* sd,
-                            int* sv, int* out_l) {
-  __shared__ double sa[kMT / 32];
-  __shared__ int sl[kMT / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    const double r2 = __shfl_down_sync(0xffffffffu, rt, o);
-    const double a2 = __shfl_down_sync(0xffffffffu, al, o);
-    const int l2 = __shfl_down_sync(0xffffffffu, lv, o);
-    const int v2 = __shfl_down_sync(0xffffffffu, vid, o);
-    if (ratio_better(rt, al, vid, r2, a2, v2, bland)) { rt = r2; al = a2; lv = l2; vid = v2; }
-  }
-  if (lane == 0) { sd[warp] = rt; sa[warp] = al; sl[warp] = lv; sv[warp] = vid; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-      if (ratio_better(sd[0], sa[0], sv[0], sd[w], sa[w], sv[w], bland)) {
-        sd[0] = sd[w]; sa[0] = sa[w]; sl[0] = sl[w]; sv[0] = sv[w];
-      }
-    *out_l = sv[0] == INT_MAX ? INT_MAX : sl[0];
+    *out_d = __longlong_as_double((long long)bk);
   }
   __syncthreads();
 }
@@ -564,9 +537,7 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
     // columns when that finds nothing or under Bland's rule
     int q = INT_MAX;
     for (int pass = bland ? 1 : 0; pass < 2 && q == INT_MAX; ++pass) {
-      const int lo = pass == 0 ? fresh0 : 0, hi = nflag;
-      for (int i = threadIdx.x; i < R; i += blockDim.x) M.y32[i] = (float)M.y[i];
-      __syncthreads();
+      const int lo = pass == 0 ? fresh0 : 0, hi = nflag;  // (M.y32 follows M.y)
       double bd = -INFINITY;
       int bvv = INT_MAX;
       for (int e = lo + threadIdx.x; e < hi; e += blockDim.x) {
@@ -593,21 +564,65 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
     for (int i = threadIdx.x; i < R; i += blockDim.x) M.col[i] = M.entry(q, i);
     __syncthreads();
     M.matvec<false>(M.col, M.fac);  // alpha = Binv * col
-    {  // ratio test over the basic rows (nu never leaves), block-wide
-      double rt = INFINITY, al_ = 0.0;
-      int lv = INT_MAX, vid = INT_MAX;
+    {  // ratio test over the basic rows (nu never leaves), in two passes
+       // (Harris): the smallest ratio x_B / alpha over the rows with
+       // alpha > tol_p, then among the rows within 1e-12 (1 + r*) of it the
+       // largest alpha (Bland: the smallest variable).  The ratios go to
+       // shared memory (aug is free here); one warp reduces integer keys
+       // (non-negative doubles order like their bit patterns).
       for (int i = threadIdx.x; i < R; i += blockDim.x) {
         const double a = M.fac[i];
-        if (M.bvar[i] == kNu || !(a > tol_p)) continue;
-        const double r2 = (M.xB[i] > 0.0 ? M.xB[i] : 0.0) / a;
-        if (ratio_better(rt, al_, vid, r2, a, M.bvar[i], bland)) {
-          rt = r2; al_ = a; lv = i; vid = M.bvar[i];
-        }
+        const bool cand = M.bvar[i] != kNu && a > tol_p;
+        M.aug[i] = cand ? (M.xB[i] > 0.0 ? M.xB[i] : 0.0) / a : -1.0;  // -1: no candidate
       }
-      block_ratio(rt, al_, lv, vid, bland, sd, sv, &leave_s);
-      if (threadIdx.x == 0) {
-        state_s = leave_s == INT_MAX ? kJFail : kJActive;
-        if (leave_s != INT_MAX) inva_s = 1.0 / M.fac[leave_s];  // one division, shared
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        unsigned long long kmin = ~0ull;
+        for (int i = lane; i < R; i += 32) {
+          const double r = M.aug[i];
+          if (r >= 0.0) {
+            const unsigned long long k = (unsigned long long)__double_as_longlong(r);
+            kmin = k < kmin ? k : kmin;
+          }
+        }
+        const unsigned mh = __reduce_min_sync(0xffffffffu, (unsigned)(kmin >> 32));
+        const unsigned ml = __reduce_min_sync(0xffffffffu, (unsigned)(kmin >> 32) == mh ? (unsigned)kmin : ~0u);
+        const unsigned long long kbest = ((unsigned long long)mh << 32) | ml;
+        int row = INT_MAX;
+        if (kbest != ~0ull) {
+          const double rs = __longlong_as_double((long long)kbest);
+          const double thr = rs + 1e-12 * (1.0 + rs);
+          // this lane's best row within the threshold
+          unsigned long long ak = 0ull;
+          int av = INT_MAX, ar = INT_MAX;
+          for (int i = lane; i < R; i += 32) {
+            const double r = M.aug[i];
+            if (r >= 0.0 && r <= thr) {
+              const unsigned long long k = (unsigned long long)__double_as_longlong(M.fac[i]);
+              const int vid = M.bvar[i];
+              const bool take = ar == INT_MAX ||
+                                (bland ? vid < av : (k > ak || (k == ak && vid < av)));
+              if (take) { ak = k; av = vid; ar = i; }
+            }
+          }
+          int vw;
+          if (bland) {
+            vw = __reduce_min_sync(0xffffffffu, av);
+          } else {
+            const unsigned h2 = __reduce_max_sync(0xffffffffu, (unsigned)(ak >> 32));
+            const unsigned l2 = __reduce_max_sync(0xffffffffu, (unsigned)(ak >> 32) == h2 ? (unsigned)ak : 0u);
+            const unsigned long long kw = ((unsigned long long)h2 << 32) | l2;
+            vw = __reduce_min_sync(0xffffffffu, (ar != INT_MAX && ak == kw) ? av : INT_MAX);
+          }
+          const unsigned own = __ballot_sync(0xffffffffu, ar != INT_MAX && av == vw);
+          row = own ? __shfl_sync(0xffffffffu, ar, __ffs(own) - 1) : INT_MAX;
+        }
+        if (lane == 0) {
+          leave_s = row;
+          state_s = row == INT_MAX ? kJFail : kJActive;
+          if (row != INT_MAX) inva_s = 1.0 / M.fac[row];  // one division, shared
+        }
       }
       __syncthreads();
     }
@@ -631,7 +646,10 @@ __global__ void __launch_bounds__(kMT) k_joint_master(JointView jv, const long l
         }
       }
     }
-    for (int i = threadIdx.x; i < R; i += blockDim.x) M.y[i] += dq * M.row[i];
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+      M.y[i] += dq * M.row[i];
+      M.y32[i] = (float)M.y[i];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       const int old = M.bvar[l];

@@ -108,9 +108,11 @@ extern "C" {
 #define D2_CERTIFY_CANDIDATES 0  /* only the centroids the FP32 error bound cannot rule
                                     out of the argmin (labels and dist2 stay FP64-exact) */
 #define D2_CERTIFY_ALL 1         /* every (object, centroid) pair: the FP32-optimal basis
-                                    of each pair gets an FP64 optimality certificate (FP64
-                                    costs on the basis, FP64 potentials and objective,
-                                    reduced costs checked against a rounding bound), so its
+                                    of each pair gets an optimality certificate of FP64
+                                    accuracy (the basic cells' costs in double-float,
+                                    potentials corrected to them, the objective summed in
+                                    FP64, reduced costs checked against a rounding bound
+                                    and the few near the bound re-priced), so its
                                     D^2 is the FP64 objective of a feasible plan within
                                     max(2^-24 D^2, 2^-43 c_max) of the optimum; a pair that
                                     fails the check is solved to FP64 optimality */

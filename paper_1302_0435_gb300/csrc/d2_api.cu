@@ -544,8 +544,11 @@ int run_assign(d2_ctx* c, const ObjView& v, const CentView& cv, long long seg, i
       // autotune on a sample of this bin: threads per block x screening items per SM
       SolveCfg t = cfg;
       t.pair64 = nullptr;
-      // a sample of about 2^17 pairs, at least 256 objects
-      t.nobj = std::min<long long>(cnt, std::max<long long>(256, (1LL << 17) / std::max(K, 1)));
+      // a sample of about 2^20 pairs, at least 256 objects: several waves of
+      // warps, so the timing ranks throughput (a one-wave sample ranks the
+      // per-pair latency and favoured Vogel's start where the staircase is
+      // faster at scale)
+      t.nobj = std::min<long long>(cnt, std::max<long long>(256, (1LL << 20) / std::max(K, 1)));
       int rc = D2_OK;
       int* tl = static_cast<int*>(grow(c, kTuneLab, (size_t)v.count * 4, &rc));
       double* td = static_cast<double*>(grow(c, kTuneD2, (size_t)v.count * 8, &rc));
